@@ -1,0 +1,172 @@
+"""FP64 CPU oracle of the MacLABSWE step (Zhou, arXiv:1902.02999).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only users.  The CUDA library never
+imports, links or calls anything here, and nothing here touches the CUDA
+library.
+
+The arithmetic lives in ``maclab_oracle.c`` (plain C, double precision,
+compiled with -O2 -ffp-contract=off); this module compiles it with gcc on
+first use and marshals numpy arrays through ctypes.
+
+Pins (tests/test_oracle_pins.py, tests/test_oracle_tidal.py) tie it to the
+paper: the moment identities of Eq. feq-full, a 3x3 step worked by hand
+from Eqs. feq-full and Mac.lb.6/7, lake at rest over an arbitrary bed,
+exact mass conservation in closed basins, the uniform-flow fixed point, the
+uniform-force closed form, the viscosity of Eq. mlb-viscosity, mirror
+symmetry, the push form of Eq. lb.1 at tau = 1, and the asymptotic tidal
+solution of Section 4.1 within the paper's level bound.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "maclab_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.c_double),
+        ("e", ctypes.c_double), ("g", ctypes.c_double),
+        ("rho_w", ctypes.c_double), ("rho_a", ctypes.c_double), ("Cw", ctypes.c_double),
+        ("wind_u", ctypes.c_double), ("wind_v", ctypes.c_double),
+        ("Cb", ctypes.c_double), ("Omega", ctypes.c_double),
+        ("edge", ctypes.c_int * 4),
+        ("bc", ctypes.c_double * 48),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build/liboracle.so (gcc, -O2,
+    -ffp-contract=off, no architecture-specific flags)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-std=c99", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            # ORACLE_LIB lets the mutation tests load a deliberately broken
+            # build of this same source; it is never set otherwise.
+            lib = ctypes.CDLL(os.environ.get("ORACLE_LIB") or build())
+            P = ctypes.POINTER
+            d, u8 = P(ctypes.c_double), P(ctypes.c_uint8)
+            pp = P(_Problem)
+            lib.oracle_feq.argtypes = [ctypes.c_double] * 5 + [d]
+            lib.oracle_force.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double, d]
+            lib.oracle_step.argtypes = [pp, d, u8, d, d, d, d, d, d, ctypes.c_double]
+            lib.oracle_run.argtypes = [pp, d, u8, d, d, d, ctypes.c_int64, ctypes.c_int64]
+            lib.oracle_residual.argtypes = [pp, u8, d, d, d, d, d, d, d]
+            lib.oracle_step_push.argtypes = [pp, d, d, d, d, d, d, d]
+            _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _problem(case) -> _Problem:
+    p = _Problem()
+    p.nx, p.ny, p.dx = case.nx, case.ny, case.dx
+    p.e, p.g = case.e, case.g
+    p.rho_w, p.rho_a, p.Cw = case.rho_w, case.rho_a, case.cw
+    p.wind_u, p.wind_v = case.wind_u, case.wind_v
+    p.Cb, p.Omega = case.cb, case.omega
+    for k in range(4):
+        p.edge[k] = int(case.edges[k])
+    bc = np.ascontiguousarray(case.bc, dtype=np.float64).reshape(-1)
+    for k in range(48):
+        p.bc[k] = bc[k]
+    return p
+
+
+def _arr(a, case):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(case.ny, case.nx)).copy()
+
+
+def feq(h: float, u: float, v: float, e: float, g: float) -> np.ndarray:
+    """f^eq_0..8 of Eq. feq-full."""
+    out = np.zeros(9)
+    _load().oracle_feq(h, u, v, e, g, _dp(out))
+    return out
+
+
+def force(case, h: float, u: float, v: float) -> np.ndarray:
+    """F of Eq. SWE-force at one node."""
+    out = np.zeros(2)
+    _load().oracle_force(ctypes.byref(_problem(case)), h, u, v, _dp(out))
+    return out
+
+
+def step(case, h, u, v, t_next: float):
+    """One step from (h,u,v) at t_n; t_next = t_{n+1}.  Returns new arrays."""
+    lib = _load()
+    h, u, v = _arr(h, case), _arr(u, case), _arr(v, case)
+    h1, u1, v1 = np.empty_like(h), np.empty_like(h), np.empty_like(h)
+    zb = np.ascontiguousarray(case.zb, dtype=np.float64)
+    mask = np.ascontiguousarray(case.mask, dtype=np.uint8)
+    rc = lib.oracle_step(ctypes.byref(_problem(case)), _dp(zb),
+                         mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                         _dp(h), _dp(u), _dp(v), _dp(h1), _dp(u1), _dp(v1), float(t_next))
+    if rc != 0:
+        raise ValueError("oracle_step: Dirichlet node off the grid edge")
+    return h1, u1, v1
+
+
+def run(case, nsteps: int, state=None, n0: int = 0):
+    """Advance ``nsteps`` steps from ``state`` (default: the case's initial
+    state) starting at step index n0.  Returns (h, u, v)."""
+    lib = _load()
+    if state is None:
+        state = (case.h0, case.u0, case.v0)
+    h, u, v = (_arr(a, case) for a in state)
+    zb = np.ascontiguousarray(case.zb, dtype=np.float64)
+    mask = np.ascontiguousarray(case.mask, dtype=np.uint8)
+    rc = lib.oracle_run(ctypes.byref(_problem(case)), _dp(zb),
+                        mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                        _dp(h), _dp(u), _dp(v), int(n0), int(nsteps))
+    if rc != 0:
+        raise ValueError("oracle_run failed (%d)" % rc)
+    return h, u, v
+
+
+def residual(case, s0, s1):
+    """(r, mass, max|u|) of state s1 against the previous state s0."""
+    lib = _load()
+    a = [_arr(x, case) for x in (*s0, *s1)]
+    out = np.zeros(3)
+    mask = np.ascontiguousarray(case.mask, dtype=np.uint8)
+    lib.oracle_residual(ctypes.byref(_problem(case)),
+                        mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                        *[_dp(x) for x in a], _dp(out))
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def step_push(case, h, u, v):
+    """Distribution (push) form of Eq. lb.1 at tau = 1, all-fluid periodic grids."""
+    lib = _load()
+    h, u, v = _arr(h, case), _arr(u, case), _arr(v, case)
+    h1, u1, v1 = np.empty_like(h), np.empty_like(h), np.empty_like(h)
+    zb = np.ascontiguousarray(case.zb, dtype=np.float64)
+    rc = lib.oracle_step_push(ctypes.byref(_problem(case)), _dp(zb), _dp(h), _dp(u), _dp(v),
+                              _dp(h1), _dp(u1), _dp(v1))
+    if rc != 0:
+        raise MemoryError("oracle_step_push")
+    return h1, u1, v1
