@@ -1,0 +1,308 @@
+#!/usr/bin/env python
+"""Throughput of the MacLABSWE FP32 step (Zhou, arXiv:1902.02999, Section 3)
+on one GB300, printed as one JSON line.
+
+Workload: channel flow over a seeded Gaussian bump, 8192 x 2048 nodes, FP32
+perturbation storage, inflow discharge and outflow depth as Dirichlet
+columns, free-slip side walls, Chezy friction (inputs.bump_channel, seed 0).
+A step is one MacLABSWE time step over the whole grid (fused step kernel +
+Dirichlet kernel).  The state (2 x 3 x 67 MB + 67 MB depth + 17 MB types)
+is far larger than the 129 MB L2, so no flush is needed between steps.
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+With --gpus N > 1 (launched by torch.distributed.run) every rank advances
+its own replica of the workload (the path is run as independent replicas);
+value = nodes x steps summed over ranks / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("MLUPS & % of HBM roofline (FP32 step); wall time to residual 1e-8, "
+          "warm-start vs plain")
+BYTES_PER_NODE = {"f32": 29, "f64": 57}   # read eta,u,v,D + type, write eta,u,v
+FALLBACK_HBM_GBS = 6800.0
+PROFILE_JSON = os.path.join(ROOT, "profiles", "step_fast_kernel_traffic.json")
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("maclab_kernels.cuh", "maclab.cu"):
+        with open(os.path.join(ROOT, "paper_1902_02999_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs"):
+            if k in d:
+                return float(d[k]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def traffic_per_launch(precision, workload):
+    try:
+        with open(PROFILE_JSON) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_sha256") != kernel_source_hash() or d.get("workload") != workload or \
+            d.get("precision") != precision:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.lines = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self):
+        return time.time()
+
+    def stop(self, t0, t1):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r for (t, r) in self.lines if t0 - 0.25 <= t <= t1 + 0.25] or \
+            [r for (_, r) in self.lines]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(case, max_seconds=30.0):
+    """The oracle as it stands, single-threaded, on one full-grid step (or
+    more while under 10 s)."""
+    import oracle
+    oracle.build()
+    state = (case.h0, case.u0, case.v0)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        state = oracle.run(case, 1, state, n0=steps)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= 10.0 or el * (steps + 1) / steps > max_seconds:
+            break
+    return {"value": case.nodes * steps / el / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%d full-grid step(s) of the %dx%d workload, %.1f s" % (steps, case.nx,
+                                                                               case.ny, el)}
+
+
+def run_reference(args, workload):
+    """The oracle on the host cores, on bounded samples of the workload."""
+    import inputs
+    import oracle
+    oracle.build()
+    rate_guess = 2.0e6                       # oracle node updates per second (one core)
+    nodes = int(150.0 * rate_guess / max(1, args.steps + args.warmup))
+    ny = max(8, min(256, nodes // 512))
+    case = inputs.bump_channel(512, ny, seed=0)
+    state = (case.h0, case.u0, case.v0)
+    for k in range(args.warmup):
+        state = oracle.run(case, 1, state, n0=k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        state = oracle.run(case, 1, state, n0=args.warmup + k)
+    el = time.perf_counter() - t0
+    value = case.nodes * args.steps / el / 1e6
+    sample = "each step: one oracle step of a 512x%d slice of the workload generator" % ny
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el * 1e3 / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload, "sample_nodes": case.nodes},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--nx", type=int, default=8192)
+    ap.add_argument("--ny", type=int, default=2048)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tile-rows", type=int, default=0)
+    args = ap.parse_args()
+    workload = "bump_channel_%dx%d_%s" % (args.nx, args.ny, args.precision)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, workload)
+        return
+
+    import torch
+    import inputs
+    from paper_1902_02999_gb300 import Simulation
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    case = inputs.bump_channel(args.nx, args.ny, seed=0)
+    sim = Simulation.from_case(case, precision=args.precision)
+    if args.tile_rows:
+        sim.set_tile_rows(args.tile_rows)
+    stream = torch.cuda.current_stream()
+    info = sim.info
+    n_general = info["n_fluid"] - info["n_fast"] - info["n_dirichlet"]
+    launches_per_step = 1 + (n_general > 0) + (info["n_dirichlet"] > 0)
+
+    sampler = ClockSampler(local)
+    sim.step(max(args.warmup, 3))
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    t_wall0 = sampler.mark()
+    sim.set_profiling(True)
+    ev0.record(stream)
+    sim.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall1 = sampler.mark()
+    kernel_ms, kernel_launches = sim.get_profile()
+    sim.set_profiling(False)
+    ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop(t_wall0, t_wall1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    nodes = case.nodes
+    value = world * nodes * args.steps / (ms / 1e3) / 1e6
+
+    # roofline of the dominant kernel (the fused step kernel)
+    avg_kernel_s = kernel_ms / 1e3 / max(1, kernel_launches)
+    achieved = BYTES_PER_NODE[args.precision] * nodes / avg_kernel_s / 1e9
+    peak, peak_src = hbm_peak()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src,
+                "kernel": "step_fast_kernel<%s>" % ("float" if args.precision == "f32" else "double"),
+                "bytes_per_node": BYTES_PER_NODE[args.precision],
+                "kernel_ms_per_launch": avg_kernel_s * 1e3,
+                "traffic": traffic_per_launch(args.precision, workload)}
+
+    # end to end through the public API: pinned host state in, one step, state out
+    N = nodes
+    hp = [torch.empty(N, dtype=torch.float64, pin_memory=True).numpy() for _ in range(3)]
+    hin = [torch.empty(N, dtype=torch.float64, pin_memory=True).numpy() for _ in range(3)]
+    st = sim.get_state()
+    for k in range(3):
+        hin[k][:] = st[k].reshape(-1)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        sim.set_state(*hin)
+        sim.step(1)
+        sim.get_state(out=hp)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * N * args.e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 3 * 8 * N,
+           "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(case)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": args.precision, "data": "synthetic",
+                "config": {"workload": workload, "nodes": nodes,
+                           "l2": "inputs larger than L2 (state %.0f MB), no flush" %
+                                 (nodes * BYTES_PER_NODE[args.precision] / 1e6),
+                           "parallelism": "replicas" if world > 1 else "single-gpu",
+                           "tile_rows": sim.info["tile_rows"]},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * maclab.h -- C ABI of the GB300 MacLABSWE streaming-step library.
+ *
+ * MacLABSWE (Zhou, arXiv:1902.02999, Section 3) advances the shallow water
+ * equations (Eqs. swe-con, swe-mom) with a streaming-only lattice Boltzmann
+ * update on a D2Q9 lattice: at every node and step,
+ *
+ *   h(x,t)     = sum_a f^eq_a(x - e_a dt, t - dt)
+ *                - (g/e^2) sum_a C_a hbar [z_b(x) - z_b(x - e_a dt)]
+ *                + (dt/e^2) sum_a C_a e_aj F_j                    (Eq. Mac.lb.6)
+ *   h u_i(x,t) = the same sums weighted by e_ai                    (Eq. Mac.lb.7)
+ *
+ * with f^eq from Eq. feq-full, F from Eqs. SWE-force / wind_u-stress /
+ * bed-stress evaluated at the link midpoint (Eq. force-CS), hbar from
+ * Eq. h-bar, e = 6 nu / dx (Eq. mlb-viscosity) and dt = dx / e.  Only the
+ * macroscopic state (h, u, v) is stored; boundary rules follow Section 3:
+ * bounce-back at walls and depth / discharge prescribed directly.
+ *
+ * Conventions
+ *   - Grids are row-major [ny][nx], x fastest, node (i, j) at (i dx, j dx).
+ *   - Every host array passed in is read during the call and copied; the
+ *     caller keeps ownership of all buffers.  Host state arrays are always
+ *     double precision, whatever the handle's storage precision.
+ *   - Every function returns a maclab_status; nothing throws across the ABI.
+ *     On failure maclab_last_error() describes the cause.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ *   - maclab_step() only enqueues work on the handle's stream and never
+ *     synchronises; the query calls (get_state, residual, run_to_steady,
+ *     time) synchronise the stream.
+ *   - All device work of a handle runs in the library's own CUDA kernels
+ *     (sm_103a); there is no CPU fallback.
+ */
+#ifndef MACLAB_H
+#define MACLAB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MACLAB_ABI_VERSION 1
+
+typedef struct maclab_s* maclab_t; /* opaque; owns device buffers */
+
+typedef enum {
+    MACLAB_OK = 0,
+    MACLAB_E_ARG = -1,      /* invalid argument (sizes, codes, geometry)       */
+    MACLAB_E_CUDA = -2,     /* a CUDA runtime call or kernel launch failed     */
+    MACLAB_E_NOMEM = -3,    /* device allocation failed                        */
+    MACLAB_E_UNSTABLE = -4, /* non-finite value in the state                   */
+    MACLAB_E_STATE = -5     /* call not valid in the handle's current state    */
+} maclab_status;
+
+/* Storage and arithmetic precision of a handle. */
+typedef enum {
+    MACLAB_F32 = 0, /* h stored as eta = h - D in float, D = h_ref - z_b     */
+    MACLAB_F64 = 1  /* same perturbation storage in double                   */
+} maclab_precision;
+
+/* Node types of the uint8 mask. */
+typedef enum {
+    MACLAB_SOLID = 0,  /* not part of the fluid; links into it bounce back    */
+    MACLAB_FLUID = 1,  /* interior node: Eqs. Mac.lb.6 / Mac.lb.7             */
+    MACLAB_NOSLIP = 2, /* wall node: h from Eq. Mac.lb.6, u = v = 0 (Sec. 3)  */
+    MACLAB_DIR_H = 3,  /* depth prescribed, velocity extrapolated             */
+    MACLAB_DIR_Q = 4,  /* discharge (h u, h v) prescribed, depth extrapolated */
+    MACLAB_DIR_HU = 5  /* depth and discharge prescribed                      */
+} maclab_node;
+
+/* What lies beyond each grid edge. */
+typedef enum {
+    MACLAB_BOUNCEBACK = 0, /* a wall: links from outside bounce back          */
+    MACLAB_SPECULAR = 1,   /* free-slip mirror half a node outside the edge   */
+    MACLAB_PERIODIC = 2    /* wraps to the opposite edge (must be paired)     */
+} maclab_edge_kind;
+
+enum { MACLAB_W = 0, MACLAB_E = 1, MACLAB_S = 2, MACLAB_N = 3 };
+
+typedef struct {
+    int nx, ny; /* nodes per row / rows, each >= 1                           */
+    double dx;  /* lattice size delta x in metres, > 0                       */
+} maclab_grid;
+
+typedef struct {
+    int precision;   /* maclab_precision                                      */
+    double nu;       /* eddy viscosity (m^2/s); used when e <= 0              */
+    double e;        /* particle speed (m/s); if > 0 it overrides nu           */
+    double g;        /* gravity (m/s^2), Section 2: 9.81                       */
+    double rho_w;    /* water density (kg/m^3)                                 */
+    double rho_a;    /* air density (kg/m^3), Eq. wind_u-stress: 1.293         */
+    double Cw;       /* wind drag coefficient, Eq. wind_u-stress: 0.0026       */
+    double wind_u;   /* uniform wind velocity (m/s)                            */
+    double wind_v;
+    double Cb;       /* bed friction C_b = g / C_z^2, Eq. bed-stress           */
+    double Omega;    /* Coriolis parameter (1/s), Eq. SWE-force                */
+    double h_ref;    /* still-water level (m): storage uses eta = h - (h_ref - z_b) */
+} maclab_params;
+
+/* A boundary value v(t) = mean + amp * sin(omega * t + phase). */
+typedef struct {
+    double mean, amp, omega, phase;
+} maclab_wave;
+
+/* Edge kinds and Dirichlet data of the four edges (index MACLAB_W..N).
+ * A Dirichlet node must lie on a grid edge; its edge is the first of
+ * W, E, S, N that it touches, and the two nodes inward along that edge's
+ * normal must be non-solid and not Dirichlet.  Prescribed values take their
+ * value at the new time t_{n+1}; the other quantity is extrapolated linearly
+ * from the new values of the two inward nodes. */
+typedef struct {
+    int edge[4];
+    maclab_wave h[4];  /* depth for DIR_H / DIR_HU nodes                   */
+    maclab_wave qx[4]; /* discharge h u for DIR_Q / DIR_HU nodes           */
+    maclab_wave qy[4]; /* discharge h v for DIR_Q / DIR_HU nodes           */
+} maclab_bc;
+
+/* Optional device allocator (for example a framework's caching allocator).
+ * alloc returns device memory of at least `bytes` bytes aligned to 256
+ * bytes, or NULL; release frees it.  With a NULL allocator the library uses
+ * cudaMalloc / cudaFree. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*release)(void* ptr, void* ctx);
+    void* ctx;
+} maclab_allocator;
+
+/* Read-only facts about a handle. */
+typedef struct {
+    int nx, ny, pitch;       /* pitch = padded row length of device arrays   */
+    int precision;
+    double dx, e, dt, nu;    /* nu = e dx / 6                                  */
+    int64_t n_dirichlet;     /* Dirichlet nodes                                */
+    int64_t n_fluid;         /* non-solid nodes                                */
+    int64_t n_fast;          /* nodes updated on the interior fast path        */
+    size_t device_bytes;     /* device memory held by the handle               */
+    int tile_rows;           /* rows per warp strip of the step kernel         */
+} maclab_info;
+
+/* Create a simulation (procedure steps (a)-(b) of Section 3).
+ *   grid, params, bc : problem description (see above); bc may be NULL for
+ *                      four bounce-back edges and no Dirichlet data.
+ *   zb     : host double [ny*nx], bed elevation z_b (m).
+ *   mask   : host uint8 [ny*nx], maclab_node codes.
+ *   h0,u0,v0 : host double [ny*nx] initial state, or all three NULL for
+ *              still water: h = h_ref - z_b, u = v = 0.
+ *   alloc  : optional allocator, NULL for cudaMalloc.
+ *   stream : cudaStream_t the handle launches on (NULL = legacy stream).
+ * Errors: MACLAB_E_ARG for bad sizes, codes, unpaired periodic edges or
+ * misplaced Dirichlet nodes; MACLAB_E_NOMEM; MACLAB_E_CUDA.
+ * Uses the current CUDA device. */
+int maclab_create(const maclab_grid* grid, const maclab_params* params, const maclab_bc* bc,
+                  const double* zb, const uint8_t* mask, const double* h0, const double* u0,
+                  const double* v0, const maclab_allocator* alloc, void* stream,
+                  maclab_t* out);
+
+/* Change the stream later calls launch on (cudaStream_t). */
+int maclab_set_stream(maclab_t sim, void* stream);
+
+/* Advance n >= 0 steps (procedure steps (c)-(e) of Section 3): one launch
+ * of the fused step kernel per step, plus the Dirichlet kernel when the grid
+ * has Dirichlet nodes.  Asynchronous on the handle's stream. */
+int maclab_step(maclab_t sim, int64_t n);
+
+/* Copy the current state to caller-owned host double arrays [ny*nx]
+ * (any may be NULL).  h is reconstructed as (h_ref - z_b) + eta in double.
+ * Synchronises the stream. */
+int maclab_get_state(maclab_t sim, double* h, double* u, double* v);
+
+/* Replace the current state from host double arrays [ny*nx] (all three
+ * required).  Does not change the time.  Asynchronous: the call returns
+ * once the host arrays have been read. */
+int maclab_set_state(maclab_t sim, const double* h, const double* u, const double* v);
+
+/* Residual and mass of the last step, reduced in double precision over
+ * non-solid nodes:
+ *   out[0] = ||(dh, d(hu), d(hv))||_2 / ||(h, hu, hv)||_2 between the two
+ *            most recent states (the stopping test "until a solution is
+ *            reached" of procedure step (e));
+ *   out[1] = sum of h (mass per dx^2);
+ *   out[2] = max |u|;
+ *   out[3] = number of non-finite values.
+ * MACLAB_E_STATE if no step was taken since create / set_state;
+ * MACLAB_E_UNSTABLE (with out filled) if out[3] > 0.  Synchronises. */
+int maclab_residual(maclab_t sim, double out[4]);
+
+/* Step until the residual of a step is <= tol, checking every check_every
+ * steps, for at most max_steps steps.  Reports the steps taken and the last
+ * residual.  Returns MACLAB_OK when converged, MACLAB_E_STATE when
+ * max_steps ran out, MACLAB_E_UNSTABLE on a non-finite state. */
+int maclab_run_to_steady(maclab_t sim, double tol, int64_t max_steps, int check_every,
+                         int64_t* steps_done, double* r_final);
+
+/* Time t = n dt and step count n of the current state. */
+int maclab_time(maclab_t sim, double* t, int64_t* n);
+
+/* Rows per warp strip of the step kernel (rows >= 1); a tuning knob.
+ * Results are bitwise identical for every value. */
+int maclab_set_tile_rows(maclab_t sim, int rows);
+
+/* Kernel timing for benchmarks.  While enabled (on != 0), every step
+ * records a CUDA event pair around the launch of the fused step kernel on
+ * the handle's stream.  maclab_get_profile synchronises, adds up the
+ * recorded durations (milliseconds) and the number of step-kernel launches
+ * since profiling was enabled, and clears the record.  Enabling resets it. */
+int maclab_set_profiling(maclab_t sim, int on);
+int maclab_get_profile(maclab_t sim, double* step_kernel_ms, int64_t* launches);
+
+/* Facts about the handle. */
+int maclab_get_info(maclab_t sim, maclab_info* info);
+
+/* Device pointers of the current state arrays (eta, u, v), each
+ * [ny][pitch] of the handle's precision; valid until the next step or
+ * destroy.  For zero-copy views by the caller. */
+int maclab_device_state(maclab_t sim, void** eta, void** u, void** v);
+
+/* Message of the last failure on this handle, or of the last failed
+ * create / NULL-handle call in this thread when sim is NULL. */
+const char* maclab_last_error(maclab_t sim);
+
+/* Free the handle and its device buffers (waits for its stream). */
+void maclab_destroy(maclab_t sim);
+
+/* MACLAB_ABI_VERSION of the loaded library. */
+int maclab_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MACLAB_H */

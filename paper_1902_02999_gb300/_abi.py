@@ -1,0 +1,93 @@
+"""ctypes declarations of include/maclab.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+c_int, c_double, c_int64, c_size_t, c_void_p = (ctypes.c_int, ctypes.c_double, ctypes.c_int64,
+                                                ctypes.c_size_t, ctypes.c_void_p)
+P = ctypes.POINTER
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("dx", c_double)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("precision", c_int), ("nu", c_double), ("e", c_double), ("g", c_double),
+                ("rho_w", c_double), ("rho_a", c_double), ("Cw", c_double),
+                ("wind_u", c_double), ("wind_v", c_double), ("Cb", c_double),
+                ("Omega", c_double), ("h_ref", c_double)]
+
+
+class Wave(ctypes.Structure):
+    _fields_ = [("mean", c_double), ("amp", c_double), ("omega", c_double), ("phase", c_double)]
+
+
+class BC(ctypes.Structure):
+    _fields_ = [("edge", c_int * 4), ("h", Wave * 4), ("qx", Wave * 4), ("qy", Wave * 4)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p)
+RELEASE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("release", RELEASE_FN), ("ctx", c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("pitch", c_int), ("precision", c_int),
+                ("dx", c_double), ("e", c_double), ("dt", c_double), ("nu", c_double),
+                ("n_dirichlet", c_int64), ("n_fluid", c_int64), ("n_fast", c_int64),
+                ("device_bytes", c_size_t), ("tile_rows", c_int)]
+
+
+# (name, restype, argtypes) of every exported entry point of include/maclab.h
+PROTOTYPES = [
+    ("maclab_abi_version", c_int, []),
+    ("maclab_create", c_int, [P(Grid), P(Params), P(BC), P(c_double), P(ctypes.c_uint8),
+                              P(c_double), P(c_double), P(c_double), P(Allocator), c_void_p,
+                              P(c_void_p)]),
+    ("maclab_set_stream", c_int, [c_void_p, c_void_p]),
+    ("maclab_step", c_int, [c_void_p, c_int64]),
+    ("maclab_get_state", c_int, [c_void_p, P(c_double), P(c_double), P(c_double)]),
+    ("maclab_set_state", c_int, [c_void_p, P(c_double), P(c_double), P(c_double)]),
+    ("maclab_residual", c_int, [c_void_p, P(c_double)]),
+    ("maclab_run_to_steady", c_int, [c_void_p, c_double, c_int64, c_int, P(c_int64),
+                                     P(c_double)]),
+    ("maclab_time", c_int, [c_void_p, P(c_double), P(c_int64)]),
+    ("maclab_set_tile_rows", c_int, [c_void_p, c_int]),
+    ("maclab_set_profiling", c_int, [c_void_p, c_int]),
+    ("maclab_get_profile", c_int, [c_void_p, P(c_double), P(c_int64)]),
+    ("maclab_get_info", c_int, [c_void_p, P(Info)]),
+    ("maclab_device_state", c_int, [c_void_p, P(c_void_p), P(c_void_p), P(c_void_p)]),
+    ("maclab_last_error", ctypes.c_char_p, [c_void_p]),
+    ("maclab_destroy", None, [c_void_p]),
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load the in-tree CUDA library.  Raises if it is missing and cannot be
+    built: there is no fallback implementation."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing:
+                path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError("maclab CUDA library not built: %s (run build())" % path)
+            lib = ctypes.CDLL(path)
+            for name, res, args in PROTOTYPES:
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib

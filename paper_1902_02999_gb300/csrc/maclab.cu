@@ -1,0 +1,634 @@
+// maclab.cu -- host side of the C ABI declared in include/maclab.h.
+//
+// Procedure of Section 3 of Zhou, arXiv:1902.02999: (a) initialise depth and
+// velocity, (b) e = 6 nu / dx (Eq. mlb-viscosity), dt = dx / e, (c)-(d)
+// update depth and velocity by Eqs. Mac.lb.6 / Mac.lb.7, (e) apply the
+// boundary conditions and repeat.  Steps (c)-(e) run in the kernels of
+// maclab_kernels.cuh; this file validates the problem, lays out device
+// memory, classifies nodes, and sequences the launches.
+#include "maclab.h"
+#include "maclab_kernels.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace maclab;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct maclab_s {
+    maclab_grid grid{};
+    maclab_params params{};
+    maclab_bc bc{};
+    maclab_allocator alloc{};
+    bool has_alloc = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int pitch = 0;
+    int prec = MACLAB_F32;
+    size_t esize = 4;
+    double e = 0, dt = 0;
+    int64_t n = 0;             // step count of the current state
+    bool have_prev = false;    // the other buffer holds the previous state
+    int cur = 0;               // which of the two state buffers is current
+    std::vector<Buf> bufs;     // everything allocated, for release
+    void* eta[2] = {nullptr, nullptr};
+    void* u[2] = {nullptr, nullptr};
+    void* v[2] = {nullptr, nullptr};
+    void* D = nullptr;         // still-water depth in the state precision
+    double* D64 = nullptr;     // still-water depth in double
+    uint8_t* type = nullptr;
+    int* general = nullptr;    // node indices (j * nx + i) of general-link nodes
+    int n_general = 0;
+    DirNode* dir = nullptr;
+    int n_dir = 0;
+    double* stage = nullptr;   // 3 * nx * ny doubles for state transfer
+    double* partial = nullptr; // residual block partials
+    double* red_out = nullptr; // RED_NVAL doubles
+    int red_blocks = 0;
+    int ncb = 0, nrb = 0, ty = 0;
+    int64_t n_fluid = 0, n_fast = 0;
+    double sumD = 0;           // sum of D64 over non-solid nodes
+    size_t device_bytes = 0;
+    bool profiling = false;
+    std::vector<cudaEvent_t> events;  // pairs around step-kernel launches
+    size_t events_used = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(maclab_t s, int code, const std::string& msg)
+{
+    if (s) s->err = msg;
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(maclab_t s, cudaError_t e, const char* what)
+{
+    return fail(s, MACLAB_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void* dev_alloc(maclab_t s, size_t bytes)
+{
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (s->has_alloc) {
+        p = s->alloc.alloc(bytes, s->alloc.ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        s->bufs.push_back(Buf{p, bytes});
+        s->device_bytes += bytes;
+    }
+    return p;
+}
+
+void release_all(maclab_t s)
+{
+    for (auto& b : s->bufs) {
+        if (s->has_alloc)
+            s->alloc.release(b.p, s->alloc.ctx);
+        else
+            cudaFree(b.p);
+    }
+    s->bufs.clear();
+}
+
+template <typename T>
+Coef<T> make_coef(const maclab_s* s)
+{
+    const maclab_params& p = s->params;
+    const double e = s->e, dt = s->dt;
+    const double wmag = std::sqrt(p.wind_u * p.wind_u + p.wind_v * p.wind_v);
+    Coef<T> c;
+    c.e = (T)e;
+    c.G6 = (T)(p.g / (6.0 * e * e));
+    c.K6 = (T)(1.0 / (6.0 * e * e));
+    c.k3 = (T)(1.0 / (3.0 * e));
+    c.k2 = (T)(1.0 / (2.0 * e * e));
+    c.k1 = (T)(1.0 / (e * e));
+    c.KF = (T)(dt / (6.0 * e));
+    c.hdt = (T)(0.5 * dt);
+    c.wfx = (T)(p.rho_a * p.Cw * p.wind_u * wmag / p.rho_w);
+    c.wfy = (T)(p.rho_a * p.Cw * p.wind_v * wmag / p.rho_w);
+    c.Cb = (T)p.Cb;
+    c.Om = (T)p.Omega;
+    return c;
+}
+
+template <typename T>
+Fields<T> make_fields(const maclab_s* s)
+{
+    Fields<T> f;
+    const int a = s->cur, b = 1 - s->cur;
+    f.eta = (const T*)s->eta[a];
+    f.u = (const T*)s->u[a];
+    f.v = (const T*)s->v[a];
+    f.D = (const T*)s->D;
+    f.type = s->type;
+    f.eta1 = (T*)s->eta[b];
+    f.u1 = (T*)s->u[b];
+    f.v1 = (T*)s->v[b];
+    f.nx = s->grid.nx;
+    f.ny = s->grid.ny;
+    f.pitch = s->pitch;
+    for (int k = 0; k < 4; ++k) f.edge[k] = s->bc.edge[k];
+    f.c = make_coef<T>(s);
+    return f;
+}
+
+double wave(const maclab_wave& w, double t) { return w.mean + w.amp * std::sin(w.omega * t + w.phase); }
+
+template <typename T>
+int launch_step(maclab_t s)
+{
+    const Fields<T> f = make_fields<T>(s);
+    const int warps = s->ncb * s->nrb;
+    const int blocks = (warps + 3) / 4;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (s->profiling) {
+        while (s->events.size() < s->events_used + 2) {
+            cudaEvent_t ev;
+            if (cudaEventCreate(&ev) != cudaSuccess) return cuda_fail(s, cudaGetLastError(), "event");
+            s->events.push_back(ev);
+        }
+        ev0 = s->events[s->events_used];
+        ev1 = s->events[s->events_used + 1];
+        s->events_used += 2;
+        cudaEventRecord(ev0, s->stream);
+    }
+    step_fast_kernel<T><<<blocks, 128, 0, s->stream>>>(f, s->ncb, s->nrb, s->ty);
+    if (s->profiling) cudaEventRecord(ev1, s->stream);
+    if (s->n_general > 0)
+        step_general_kernel<T><<<(s->n_general + 127) / 128, 128, 0, s->stream>>>(f, s->general,
+                                                                                  s->n_general);
+    if (s->n_dir > 0) {
+        DirValues bv;
+        const double t1 = (double)(s->n + 1) * s->dt;
+        for (int k = 0; k < 4; ++k) {
+            bv.h[k] = wave(s->bc.h[k], t1);
+            bv.qx[k] = wave(s->bc.qx[k], t1);
+            bv.qy[k] = wave(s->bc.qy[k], t1);
+        }
+        const int b = 1 - s->cur;
+        dirichlet_kernel<T><<<(s->n_dir + 127) / 128, 128, 0, s->stream>>>(
+            (T*)s->eta[b], (T*)s->u[b], (T*)s->v[b], (const T*)s->D, s->D64, s->dir, s->n_dir, bv);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
+    s->cur = 1 - s->cur;
+    s->n += 1;
+    s->have_prev = true;
+    return MACLAB_OK;
+}
+
+template <typename T>
+int launch_residual(maclab_t s)
+{
+    const int a = s->cur, b = 1 - s->cur;
+    residual_partial_kernel<T><<<s->red_blocks, RED_THREADS, 0, s->stream>>>(
+        (const T*)s->eta[b], (const T*)s->u[b], (const T*)s->v[b], (const T*)s->eta[a],
+        (const T*)s->u[a], (const T*)s->v[a], (const T*)s->D, s->type, s->grid.nx, s->grid.ny,
+        s->pitch, s->partial);
+    residual_final_kernel<<<1, 32 * RED_NVAL, 0, s->stream>>>(s->partial, s->red_blocks, s->red_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(s, e, "residual launch");
+    return MACLAB_OK;
+}
+
+int grid_blocks(size_t total, int threads, int cap)
+{
+    size_t b = (total + threads - 1) / threads;
+    return (int)std::max<size_t>(1, std::min<size_t>(b, (size_t)cap));
+}
+
+template <typename T>
+int upload_state(maclab_t s, const double* h, const double* u, const double* v)
+{
+    const size_t N = (size_t)s->grid.nx * s->grid.ny;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(s->stage, h, N * 8, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(s->stage + N, u, N * 8, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(s->stage + 2 * N, v, N * 8, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess)
+        return cuda_fail(s, e, "state upload");
+    const int a = s->cur, b = 1 - s->cur;
+    state_in_kernel<T><<<grid_blocks(N, 256, 4096), 256, 0, s->stream>>>(
+        s->stage, s->stage + N, s->stage + 2 * N, s->D64, s->type, (T*)s->eta[a], (T*)s->u[a],
+        (T*)s->v[a], (T*)s->eta[b], (T*)s->u[b], (T*)s->v[b], s->grid.nx, s->grid.ny, s->pitch);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(s, e, "state conversion");
+    // the host arrays must stay valid until the copies have read them
+    if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return cuda_fail(s, e, "state upload");
+    s->have_prev = false;
+    return MACLAB_OK;
+}
+
+template <typename T>
+int download_state(maclab_t s, double* h, double* u, double* v)
+{
+    const size_t N = (size_t)s->grid.nx * s->grid.ny;
+    const int a = s->cur;
+    state_out_kernel<T><<<grid_blocks(N, 256, 4096), 256, 0, s->stream>>>(
+        (const T*)s->eta[a], (const T*)s->u[a], (const T*)s->v[a], s->D64, s->stage, s->stage + N,
+        s->stage + 2 * N, s->grid.nx, s->grid.ny, s->pitch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(s, e, "state conversion");
+    double* dst[3] = {h, u, v};
+    for (int k = 0; k < 3; ++k)
+        if (dst[k] && (e = cudaMemcpyAsync(dst[k], s->stage + k * N, N * 8, cudaMemcpyDeviceToHost,
+                                           s->stream)) != cudaSuccess)
+            return cuda_fail(s, e, "state download");
+    if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return cuda_fail(s, e, "state download");
+    return MACLAB_OK;
+}
+
+// Rows per warp strip: enough strips to fill every SM a few times over
+// while keeping strips tall (each strip re-reads two halo rows).
+int choose_tile_rows(int ny, int ncb, int sms)
+{
+    const int target = sms * 32;  // warps: 32 per SM
+    int strips = std::max(1, target / std::max(1, ncb));
+    int ty = (ny + strips - 1) / strips;
+    ty = std::max(ty, 8);
+    ty = std::min(ty, std::max(ny, 1));
+    return ty;
+}
+
+}  // namespace
+
+extern "C" {
+
+int maclab_abi_version(void) { return MACLAB_ABI_VERSION; }
+
+const char* maclab_last_error(maclab_t sim)
+{
+    if (sim) return sim->err.c_str();
+    return g_last_error.c_str();
+}
+
+int maclab_create(const maclab_grid* grid, const maclab_params* params, const maclab_bc* bc,
+                  const double* zb, const uint8_t* mask, const double* h0, const double* u0,
+                  const double* v0, const maclab_allocator* alloc, void* stream, maclab_t* out)
+{
+    if (!out) return fail(nullptr, MACLAB_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!grid || !params || !zb || !mask) return fail(nullptr, MACLAB_E_ARG, "grid, params, zb and mask are required");
+    const int nx = grid->nx, ny = grid->ny;
+    if (nx < 1 || ny < 1) return fail(nullptr, MACLAB_E_ARG, "nx and ny must be >= 1");
+    if ((int64_t)nx * ny > (int64_t)1 << 31 || nx > (1 << 30) - 64)
+        return fail(nullptr, MACLAB_E_ARG, "grid too large (nx*ny must fit in 31 bits)");
+    if (!(grid->dx > 0) || !std::isfinite(grid->dx)) return fail(nullptr, MACLAB_E_ARG, "dx must be > 0");
+    if (params->precision != MACLAB_F32 && params->precision != MACLAB_F64)
+        return fail(nullptr, MACLAB_E_ARG, "unknown precision");
+    double e = params->e > 0 ? params->e : 6.0 * params->nu / grid->dx;
+    if (!(e > 0) || !std::isfinite(e)) return fail(nullptr, MACLAB_E_ARG, "need e > 0 or nu > 0");
+    if (!(params->g > 0) || !(params->rho_w > 0)) return fail(nullptr, MACLAB_E_ARG, "need g > 0 and rho_w > 0");
+    if ((h0 == nullptr) != (u0 == nullptr) || (h0 == nullptr) != (v0 == nullptr))
+        return fail(nullptr, MACLAB_E_ARG, "h0, u0, v0 must be all given or all NULL");
+    if (alloc && (!alloc->alloc || !alloc->release))
+        return fail(nullptr, MACLAB_E_ARG, "allocator needs alloc and release");
+
+    maclab_bc b{};
+    if (bc) b = *bc;
+    for (int k = 0; k < 4; ++k)
+        if (b.edge[k] < MACLAB_BOUNCEBACK || b.edge[k] > MACLAB_PERIODIC)
+            return fail(nullptr, MACLAB_E_ARG, "unknown edge kind");
+    if ((b.edge[0] == MACLAB_PERIODIC) != (b.edge[1] == MACLAB_PERIODIC) ||
+        (b.edge[2] == MACLAB_PERIODIC) != (b.edge[3] == MACLAB_PERIODIC))
+        return fail(nullptr, MACLAB_E_ARG, "periodic edges must come in W/E or S/N pairs");
+
+    const size_t N = (size_t)nx * ny;
+    for (size_t k = 0; k < N; ++k)
+        if (mask[k] > MACLAB_DIR_HU) return fail(nullptr, MACLAB_E_ARG, "unknown node type in mask");
+
+    maclab_s* s = new maclab_s();
+    s->grid = *grid;
+    s->params = *params;
+    s->bc = b;
+    s->prec = params->precision;
+    s->esize = s->prec == MACLAB_F32 ? 4 : 8;
+    s->e = e;
+    s->dt = grid->dx / e;
+    s->stream = (cudaStream_t)stream;
+    if (alloc) {
+        s->alloc = *alloc;
+        s->has_alloc = true;
+    }
+    s->pitch = (nx + 63) / 64 * 64;
+    cudaGetDevice(&s->device);
+    const int pitch = s->pitch;
+
+    // ---- classify nodes (host) ----
+    auto kind_at = [&](int i, int j) { return mask[(size_t)j * nx + i]; };
+    auto resolve = [&](int i, int n, int lo, int hi) -> int {
+        if (i >= 0 && i < n) return i;
+        int kd = i < 0 ? lo : hi;
+        if (kd == MACLAB_PERIODIC) return ((i % n) + n) % n;
+        if (kd == MACLAB_SPECULAR) {
+            i = i < 0 ? -1 - i : 2 * n - 1 - i;
+            return (i >= 0 && i < n) ? i : -1;
+        }
+        return -1;
+    };
+    static const int CX[9] = {0, 1, 1, 0, -1, -1, -1, 0, 1};
+    static const int CY[9] = {0, 0, 1, 1, 1, 0, -1, -1, -1};
+    std::vector<uint8_t> type((size_t)pitch * ny, (uint8_t)K_SOLID);
+    std::vector<int> general;
+    std::vector<DirNode> dirs;
+    double sumD = 0;
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            const uint8_t kd = kind_at(i, j);
+            uint8_t t = kd;
+            if (kd != MACLAB_SOLID) {
+                s->n_fluid++;
+                sumD += params->h_ref - zb[(size_t)j * nx + i];
+                if (kd >= MACLAB_DIR_H) {
+                    int di = 0, dj = 0, ed;
+                    if (i == 0) { di = 1; ed = 0; }
+                    else if (i == nx - 1) { di = -1; ed = 1; }
+                    else if (j == 0) { dj = 1; ed = 2; }
+                    else if (j == ny - 1) { dj = -1; ed = 3; }
+                    else {
+                        delete s;
+                        return fail(nullptr, MACLAB_E_ARG, "Dirichlet node not on a grid edge");
+                    }
+                    const int i1 = i + di, j1 = j + dj, i2 = i + 2 * di, j2 = j + 2 * dj;
+                    if (i2 < 0 || i2 >= nx || j2 < 0 || j2 >= ny || kind_at(i1, j1) == MACLAB_SOLID ||
+                        kind_at(i2, j2) == MACLAB_SOLID || kind_at(i1, j1) >= MACLAB_DIR_H ||
+                        kind_at(i2, j2) >= MACLAB_DIR_H) {
+                        delete s;
+                        return fail(nullptr, MACLAB_E_ARG,
+                                    "the two inward nodes of a Dirichlet node must be non-solid and not Dirichlet");
+                    }
+                    dirs.push_back(DirNode{j * pitch + i, j1 * pitch + i1, j2 * pitch + i2, (int)kd | (ed << 4)});
+                } else {
+                    bool gen = false;
+                    for (int a = 1; a < 9 && !gen; ++a) {
+                        const int si = resolve(i - CX[a], nx, b.edge[0], b.edge[1]);
+                        const int sj = resolve(j - CY[a], ny, b.edge[2], b.edge[3]);
+                        gen = si < 0 || sj < 0 || kind_at(si, sj) == MACLAB_SOLID;
+                    }
+                    if (gen) {
+                        t |= GENERAL_BIT;
+                        general.push_back(j * nx + i);
+                    } else {
+                        s->n_fast++;
+                    }
+                }
+            }
+            type[(size_t)j * pitch + i] = t;
+        }
+    }
+    s->sumD = sumD;
+
+    // ---- device buffers ----
+    const size_t NP = (size_t)pitch * ny;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (sms <= 0) sms = 152;
+    s->red_blocks = std::max(1, std::min(sms * 4, (int)((N + RED_THREADS - 1) / RED_THREADS)));
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; ++k) {
+        ok = (s->eta[k] = dev_alloc(s, NP * s->esize)) && (s->u[k] = dev_alloc(s, NP * s->esize)) &&
+             (s->v[k] = dev_alloc(s, NP * s->esize));
+    }
+    ok = ok && (s->D = dev_alloc(s, NP * s->esize)) && (s->D64 = (double*)dev_alloc(s, NP * 8)) &&
+         (s->type = (uint8_t*)dev_alloc(s, NP + 64)) && (s->stage = (double*)dev_alloc(s, 3 * N * 8)) &&
+         (s->partial = (double*)dev_alloc(s, (size_t)s->red_blocks * RED_NVAL * 8)) &&
+         (s->red_out = (double*)dev_alloc(s, RED_NVAL * 8));
+    if (ok && !general.empty()) ok = (s->general = (int*)dev_alloc(s, general.size() * sizeof(int))) != nullptr;
+    if (ok && !dirs.empty()) ok = (s->dir = (DirNode*)dev_alloc(s, dirs.size() * sizeof(DirNode))) != nullptr;
+    if (!ok) {
+        release_all(s);
+        delete s;
+        return fail(nullptr, MACLAB_E_NOMEM, "device allocation failed");
+    }
+    s->n_general = (int)general.size();
+    s->n_dir = (int)dirs.size();
+
+    // ---- upload static data ----
+    std::vector<double> D64(NP, 0.0);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) D64[(size_t)j * pitch + i] = params->h_ref - zb[(size_t)j * nx + i];
+    cudaError_t ce = cudaSuccess;
+    auto put = [&](void* dst, const void* src, size_t bytes) {
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream);
+    };
+    put(s->D64, D64.data(), NP * 8);
+    if (s->prec == MACLAB_F32) {
+        std::vector<float> Df(NP);
+        for (size_t k = 0; k < NP; ++k) Df[k] = (float)D64[k];
+        put(s->D, Df.data(), NP * 4);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+    } else {
+        put(s->D, D64.data(), NP * 8);
+    }
+    std::vector<uint8_t> tpad(type);
+    tpad.resize(NP + 64, 0);
+    put(s->type, tpad.data(), NP + 64);
+    if (!general.empty()) put(s->general, general.data(), general.size() * sizeof(int));
+    if (!dirs.empty()) put(s->dir, dirs.data(), dirs.size() * sizeof(DirNode));
+    for (int k = 0; k < 2 && ce == cudaSuccess; ++k) {
+        ce = cudaMemsetAsync(s->eta[k], 0, NP * s->esize, s->stream);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(s->u[k], 0, NP * s->esize, s->stream);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(s->v[k], 0, NP * s->esize, s->stream);
+    }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+    if (ce != cudaSuccess) {
+        cuda_fail(nullptr, ce, "upload");
+        release_all(s);
+        delete s;
+        return MACLAB_E_CUDA;
+    }
+    if (h0) {
+        int rc = s->prec == MACLAB_F32 ? upload_state<float>(s, h0, u0, v0)
+                                        : upload_state<double>(s, h0, u0, v0);
+        if (rc != MACLAB_OK) {
+            g_last_error = s->err;
+            release_all(s);
+            delete s;
+            return rc;
+        }
+    }
+    // ---- launch geometry of the step kernel ----
+    s->ncb = (nx + 1 + WCOLS - 1) / WCOLS;
+    s->ty = choose_tile_rows(ny, s->ncb, sms);
+    s->nrb = (ny + s->ty - 1) / s->ty;
+    *out = s;
+    return MACLAB_OK;
+}
+
+int maclab_set_stream(maclab_t s, void* stream)
+{
+    if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    s->stream = (cudaStream_t)stream;
+    return MACLAB_OK;
+}
+
+int maclab_step(maclab_t s, int64_t n)
+{
+    if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    if (n < 0) return fail(s, MACLAB_E_ARG, "n must be >= 0");
+    for (int64_t k = 0; k < n; ++k) {
+        int rc = s->prec == MACLAB_F32 ? launch_step<float>(s) : launch_step<double>(s);
+        if (rc != MACLAB_OK) return rc;
+    }
+    return MACLAB_OK;
+}
+
+int maclab_get_state(maclab_t s, double* h, double* u, double* v)
+{
+    if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    return s->prec == MACLAB_F32 ? download_state<float>(s, h, u, v) : download_state<double>(s, h, u, v);
+}
+
+int maclab_set_state(maclab_t s, const double* h, const double* u, const double* v)
+{
+    if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    if (!h || !u || !v) return fail(s, MACLAB_E_ARG, "h, u and v are required");
+    return s->prec == MACLAB_F32 ? upload_state<float>(s, h, u, v) : upload_state<double>(s, h, u, v);
+}
+
+int maclab_residual(maclab_t s, double out[4])
+{
+    if (!s || !out) return fail(s, MACLAB_E_ARG, "NULL argument");
+    if (!s->have_prev) return fail(s, MACLAB_E_STATE, "no step taken since create / set_state");
+    int rc = s->prec == MACLAB_F32 ? launch_residual<float>(s) : launch_residual<double>(s);
+    if (rc != MACLAB_OK) return rc;
+    double r[RED_NVAL];
+    cudaError_t e = cudaMemcpyAsync(r, s->red_out, sizeof(r), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "residual");
+    out[0] = r[1] > 0 ? std::sqrt(r[0]) / std::sqrt(r[1]) : 0.0;
+    out[1] = s->sumD + r[2];
+    out[2] = std::sqrt(r[3]);
+    out[3] = r[4];
+    if (r[4] > 0 || !std::isfinite(out[0])) return fail(s, MACLAB_E_UNSTABLE, "non-finite values in the state");
+    return MACLAB_OK;
+}
+
+int maclab_run_to_steady(maclab_t s, double tol, int64_t max_steps, int check_every,
+                         int64_t* steps_done, double* r_final)
+{
+    if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    if (check_every < 1 || max_steps < 0 || !(tol >= 0)) return fail(s, MACLAB_E_ARG, "bad tol / max_steps / check_every");
+    int64_t done = 0;
+    double r = INFINITY;
+    int rc = MACLAB_E_STATE;
+    while (done < max_steps) {
+        const int64_t k = std::min<int64_t>(check_every, max_steps - done);
+        if ((rc = maclab_step(s, k)) != MACLAB_OK) break;
+        done += k;
+        double out[4];
+        rc = maclab_residual(s, out);
+        r = out[0];
+        if (rc != MACLAB_OK) break;
+        if (r <= tol) break;
+        rc = MACLAB_E_STATE;
+    }
+    if (steps_done) *steps_done = done;
+    if (r_final) *r_final = r;
+    if (rc == MACLAB_E_STATE) fail(s, rc, "max_steps reached before the residual fell to tol");
+    return rc;
+}
+
+int maclab_time(maclab_t s, double* t, int64_t* n)
+{
+    if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    if (t) *t = (double)s->n * s->dt;
+    if (n) *n = s->n;
+    return MACLAB_OK;
+}
+
+int maclab_set_tile_rows(maclab_t s, int rows)
+{
+    if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    if (rows < 1) return fail(s, MACLAB_E_ARG, "rows must be >= 1");
+    s->ty = std::min(rows, s->grid.ny);
+    s->nrb = (s->grid.ny + s->ty - 1) / s->ty;
+    return MACLAB_OK;
+}
+
+int maclab_set_profiling(maclab_t s, int on)
+{
+    if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    s->profiling = on != 0;
+    s->events_used = 0;
+    return MACLAB_OK;
+}
+
+int maclab_get_profile(maclab_t s, double* ms, int64_t* launches)
+{
+    if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "profile");
+    double total = 0;
+    for (size_t k = 0; k + 1 < s->events_used; k += 2) {
+        float t = 0;
+        if ((e = cudaEventElapsedTime(&t, s->events[k], s->events[k + 1])) != cudaSuccess)
+            return cuda_fail(s, e, "profile");
+        total += t;
+    }
+    if (ms) *ms = total;
+    if (launches) *launches = (int64_t)(s->events_used / 2);
+    s->events_used = 0;
+    return MACLAB_OK;
+}
+
+int maclab_get_info(maclab_t s, maclab_info* info)
+{
+    if (!s || !info) return fail(s, MACLAB_E_ARG, "NULL argument");
+    info->nx = s->grid.nx;
+    info->ny = s->grid.ny;
+    info->pitch = s->pitch;
+    info->precision = s->prec;
+    info->dx = s->grid.dx;
+    info->e = s->e;
+    info->dt = s->dt;
+    info->nu = s->e * s->grid.dx / 6.0;
+    info->n_dirichlet = s->n_dir;
+    info->n_fluid = s->n_fluid;
+    info->n_fast = s->n_fast;
+    info->device_bytes = s->device_bytes;
+    info->tile_rows = s->ty;
+    return MACLAB_OK;
+}
+
+int maclab_device_state(maclab_t s, void** eta, void** u, void** v)
+{
+    if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    if (eta) *eta = s->eta[s->cur];
+    if (u) *u = s->u[s->cur];
+    if (v) *v = s->v[s->cur];
+    return MACLAB_OK;
+}
+
+void maclab_destroy(maclab_t s)
+{
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    for (cudaEvent_t ev : s->events) cudaEventDestroy(ev);
+    release_all(s);
+    delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,566 @@
+// maclab_kernels.cuh -- device code of the MacLABSWE step (Zhou,
+// arXiv:1902.02999, Section 3) for sm_103a.
+//
+// Storage: structure of arrays, row pitch `pitch` (a multiple of 64 nodes):
+//   eta = h - D (perturbation about still water), u, v   [two copies, ping-pong]
+//   D   = h_ref - z_b (still-water depth), in the state precision
+//   type: uint8, bits 0-2 node kind, bit 3 = "general links" (some link of
+//         the node bounces back, so the interior fast path does not apply)
+//
+// Perturbation form of Eqs. Mac.lb.6 / Mac.lb.7.  With G6 = g/(6e^2),
+// K6 = 1/(6e^2), KF = dt/(6e), lambda_a = 1 (axis) or 1/4 (diagonal),
+// C_a = lambda_a / 3, and for a source node y
+//     a'(y)  = h (G6 eta - K6 |u|^2)            (f^eq difference, minus G6 eta D)
+//     q'(y)  = h u / (3e) + KF F                (first moment plus source force)
+//     s(y)   = (h u^2/(2e^2), h v^2/(2e^2), h u v / e^2)
+//     o_a(y) = lambda_a [a' + c_a.q' + c_ax^2 s_xx + c_ay^2 s_yy + c_ax c_ay s_xy]
+// the still-water part of f^eq_a(y) plus the still-water bed term of each
+// link is lambda_a g D(x)^2/(6e^2), independent of y, so it cancels against
+// the still-water part of h(x) exactly (lake at rest is exact in any
+// precision).  What remains for an interior node x with eight usable links:
+//     eta'  = eta - h (5 G6 eta + 4 K6 |u|^2)                 (a = 0 term)
+//             + sum_a o_a(x - c_a)
+//             + sum_a lambda_a [G6 eta_x D_x + G6 D_x eta_y - G6 eta_x D_y]   (bed)
+//     h u'  = e sum_a c_a [o_a(y) + lambda_a (G6 D_x eta_y - G6 eta_x D_y)] + dt F(x) / 2
+// where the bed term of each link is -(g/e^2) C_a hbar [z_b(x) - z_b(y)]
+// with hbar = (h(x) + h(y))/2 (Eq. h-bar at the old level) and z_b = h_ref - D,
+// and the centred force of Eq. force-CS is split into its source half (in
+// q') and its receiver half (sum_a lambda_a KF c_a.F(x) = 0 and
+// e sum_a lambda_a KF c_a (c_a.F(x)) = dt F(x) / 2).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace maclab {
+
+enum : uint8_t {
+    K_SOLID = 0, K_FLUID = 1, K_NOSLIP = 2, K_DIR_H = 3, K_DIR_Q = 4, K_DIR_HU = 5,
+    KIND_MASK = 7, GENERAL_BIT = 8
+};
+enum : int { EDGE_BB = 0, EDGE_SPEC = 1, EDGE_PER = 2 };
+
+// Constants of one handle, in the state precision T.
+template <typename T>
+struct Coef {
+    T e;     // particle speed (Eq. mlb-viscosity)
+    T G6;    // g / (6 e^2)
+    T K6;    // 1 / (6 e^2)
+    T k3;    // 1 / (3 e)
+    T k2;    // 1 / (2 e^2)
+    T k1;    // 1 / e^2
+    T KF;    // dt / (6 e)
+    T hdt;   // dt / 2
+    T wfx;   // tau_w,x / rho_w  (Eq. wind_u-stress)
+    T wfy;
+    T Cb;    // C_b (Eq. bed-stress)
+    T Om;    // Omega (Eq. SWE-force)
+};
+
+template <typename T>
+struct Fields {
+    const T* eta;
+    const T* u;
+    const T* v;
+    const T* D;
+    const uint8_t* type;
+    T* eta1;
+    T* u1;
+    T* v1;
+    int nx, ny, pitch;
+    int edge[4];  // W, E, S, N
+    Coef<T> c;
+};
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+// ---------------------------------------------------------------------------
+// Raw node values and the per-source quantities of the fast path.
+template <typename T>
+struct Raw {
+    T eta, u, v, D;
+    uint8_t type;
+    uint8_t flip;  // bit 0: mirrored in x, bit 1: mirrored in y (specular ghost)
+};
+
+template <typename T>
+struct Src {
+    T eta, D;
+    T o1, o2, o3, o4, o5, o6, o7, o8;
+    T ownh;        // eta - h (5 G6 eta + 4 K6 |u|^2)
+    T hFx, hFy;    // dt F / 2
+    uint8_t type;
+};
+
+template <typename T>
+__device__ __forceinline__ T my_sqrt(T x) { return sqrt(x); }
+template <>
+__device__ __forceinline__ float my_sqrt<float>(float x) { return sqrtf(x); }
+
+// Source-side quantities of one node (see the header comment).
+template <typename T>
+__device__ __forceinline__ void derive(const Coef<T>& c, const Raw<T>& r, Src<T>& s)
+{
+    T u = r.u, v = r.v, wfx = c.wfx, wfy = c.wfy, Om = c.Om;
+    if (r.flip) {  // specular ghost: normal components reversed, rotation sense too
+        if (r.flip & 1) { u = -u; wfx = -wfx; }
+        if (r.flip & 2) { v = -v; wfy = -wfy; }
+        if ((r.flip & 3) != 3) Om = -Om;
+    }
+    const T eta = r.eta, D = r.D;
+    const T h = D + eta;
+    const T uu = u * u + v * v;
+    const T ge = c.G6 * eta;
+    const T ku = c.K6 * uu;
+    const T ap = h * (ge - ku);
+    s.ownh = eta - h * (T(5) * ge + T(4) * ku);
+    const T sp = my_sqrt(uu);
+    const T Fx = wfx - c.Cb * u * sp + Om * h * v;
+    const T Fy = wfy - c.Cb * v * sp - Om * h * u;
+    s.hFx = c.hdt * Fx;
+    s.hFy = c.hdt * Fy;
+    const T hu = h * u, hv = h * v;
+    const T qx = hu * c.k3 + c.KF * Fx;
+    const T qy = hv * c.k3 + c.KF * Fy;
+    const T sxx = hu * u * c.k2;
+    const T syy = hv * v * c.k2;
+    const T sxy = hu * v * c.k1;
+    const T ax = ap + sxx, ay = ap + syy;
+    s.o1 = ax + qx;
+    s.o5 = ax - qx;
+    s.o3 = ay + qy;
+    s.o7 = ay - qy;
+    const T d = ax + syy;
+    const T dp = T(0.25) * (d + sxy), dm = T(0.25) * (d - sxy);
+    const T s4 = T(0.25) * (qx + qy), t4 = T(0.25) * (qx - qy);
+    s.o2 = dp + s4;
+    s.o6 = dp - s4;
+    s.o8 = dm + t4;
+    s.o4 = dm - t4;
+    s.eta = eta;
+    s.D = D;
+    s.type = r.type;
+}
+
+// Map a column / row index outside the grid through the edge kinds.
+// Returns the in-grid index, or -1 if it lies behind a bounce-back edge or
+// maps outside the grid; sets the mirror flag for specular edges.
+__device__ __forceinline__ int resolve_index(int i, int n, int lo_kind, int hi_kind, uint8_t bit,
+                                             uint8_t& flip)
+{
+    if (i >= 0 && i < n) return i;
+    int kind = i < 0 ? lo_kind : hi_kind;
+    if (kind == EDGE_PER) {
+        i %= n;
+        return i < 0 ? i + n : i;
+    }
+    if (kind == EDGE_SPEC) {
+        i = i < 0 ? -1 - i : 2 * n - 1 - i;
+        flip |= bit;
+        return (i >= 0 && i < n) ? i : -1;
+    }
+    return -1;
+}
+
+// ---------------------------------------------------------------------------
+// Fast-path step kernel.  A warp owns a strip of 64 columns (2 per lane) and
+// `ty` rows; it walks the rows, keeping the source quantities of three
+// consecutive rows in registers (y neighbours) and exchanging the edge
+// columns of each lane with warp shuffles (x neighbours).  Output columns
+// are the 62 inner ones: [62 cb - 1, 62 cb + 60].
+constexpr int CPL = 2;                 // columns per lane
+constexpr int WCOLS = 32 * CPL - 2;    // output columns per warp
+
+template <typename T>
+struct Row {
+    Src<T> col[CPL + 2];  // [0] = left neighbour, [1..CPL] own, [CPL+1] = right neighbour
+};
+
+template <typename T>
+__device__ __forceinline__ void load_row(const Fields<T>& f, int r, int xl, Raw<T> (&raw)[CPL])
+{
+    uint8_t fy = 0;
+    int rr = resolve_index(r, f.ny, f.edge[2], f.edge[3], 2, fy);
+    const bool inside = xl >= 0 && xl + CPL <= f.nx;
+    if (rr >= 0 && inside) {
+        const size_t base = (size_t)rr * f.pitch + xl;
+        using V2 = typename Vec2<T>::type;
+        V2 e2 = *reinterpret_cast<const V2*>(f.eta + base);
+        V2 u2 = *reinterpret_cast<const V2*>(f.u + base);
+        V2 v2 = *reinterpret_cast<const V2*>(f.v + base);
+        V2 d2 = *reinterpret_cast<const V2*>(f.D + base);
+        uint16_t t2 = *reinterpret_cast<const uint16_t*>(f.type + base);
+        raw[0] = Raw<T>{e2.x, u2.x, v2.x, d2.x, (uint8_t)(t2 & 0xff), fy};
+        raw[1] = Raw<T>{e2.y, u2.y, v2.y, d2.y, (uint8_t)(t2 >> 8), fy};
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        uint8_t fl = fy;
+        int cc = resolve_index(xl + k, f.nx, f.edge[0], f.edge[1], 1, fl);
+        if (rr >= 0 && cc >= 0) {
+            const size_t idx = (size_t)rr * f.pitch + cc;
+            raw[k] = Raw<T>{f.eta[idx], f.u[idx], f.v[idx], f.D[idx], f.type[idx], fl};
+        } else {
+            raw[k] = Raw<T>{T(0), T(0), T(0), T(0), (uint8_t)K_SOLID, 0};
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void derive_row(const Coef<T>& c, const Raw<T> (&raw)[CPL], Row<T>& row)
+{
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) derive(c, raw[k], row.col[k + 1]);
+    const unsigned full = 0xffffffffu;
+    // left neighbour of column 1 = last column of lane-1 (it sends o1, o2, o8)
+    Src<T>& L = row.col[0];
+    const Src<T>& sl = row.col[CPL];
+    L.o1 = __shfl_up_sync(full, sl.o1, 1);
+    L.o2 = __shfl_up_sync(full, sl.o2, 1);
+    L.o8 = __shfl_up_sync(full, sl.o8, 1);
+    L.eta = __shfl_up_sync(full, sl.eta, 1);
+    L.D = __shfl_up_sync(full, sl.D, 1);
+    // right neighbour of column CPL = first column of lane+1 (it sends o5, o4, o6)
+    Src<T>& R = row.col[CPL + 1];
+    const Src<T>& sr = row.col[1];
+    R.o5 = __shfl_down_sync(full, sr.o5, 1);
+    R.o4 = __shfl_down_sync(full, sr.o4, 1);
+    R.o6 = __shfl_down_sync(full, sr.o6, 1);
+    R.eta = __shfl_down_sync(full, sr.eta, 1);
+    R.D = __shfl_down_sync(full, sr.D, 1);
+}
+
+// Interior update of output row j from source rows m = j-1, c = j, p = j+1.
+template <typename T>
+__device__ __forceinline__ void emit_row(const Fields<T>& f, int j, int xl, int lane,
+                                         const Row<T>& m, const Row<T>& c, const Row<T>& p)
+{
+    const Coef<T>& K = f.c;
+#pragma unroll
+    for (int k = 1; k <= CPL; ++k) {
+        const int x = xl + k - 1;
+        const bool edge_col = (lane == 0 && k == 1) || (lane == 31 && k == CPL);
+        const uint8_t ty = c.col[k].type;
+        if (edge_col || x < 0 || x >= f.nx || j >= f.ny) continue;
+        if ((ty & KIND_MASK) == K_SOLID || (ty & GENERAL_BIT)) continue;
+        const Src<T>& mL = m.col[k - 1]; const Src<T>& mC = m.col[k]; const Src<T>& mR = m.col[k + 1];
+        const Src<T>& cL = c.col[k - 1]; const Src<T>& cC = c.col[k]; const Src<T>& cR = c.col[k + 1];
+        const Src<T>& pL = p.col[k - 1]; const Src<T>& pC = p.col[k]; const Src<T>& pR = p.col[k + 1];
+        // streamed equilibria
+        const T OL = cL.o1 + mL.o2 + pL.o8;
+        const T OR = cR.o5 + mR.o4 + pR.o6;
+        const T Sh = (OL + OR) + (mC.o3 + pC.o7);
+        const T Sx = OL - OR;
+        const T Sy = (mL.o2 + mR.o4 + mC.o3) - (pL.o8 + pR.o6 + pC.o7);
+        // lambda-weighted stencils of eta and D: sum, x-moment, y-moment
+        const T q = T(0.25);
+        const T MLe = cL.eta + q * (mL.eta + pL.eta), MRe = cR.eta + q * (mR.eta + pR.eta);
+        const T MLd = cL.D + q * (mL.D + pL.D), MRd = cR.D + q * (mR.D + pR.D);
+        const T Se = (MLe + MRe) + (mC.eta + pC.eta);
+        const T Sd = (MLd + MRd) + (mC.D + pC.D);
+        const T Xe = MLe - MRe, Xd = MLd - MRd;
+        const T Ye = (mC.eta - pC.eta) + q * ((mL.eta + mR.eta) - (pL.eta + pR.eta));
+        const T Yd = (mC.D - pC.D) + q * ((mL.D + mR.D) - (pL.D + pR.D));
+        const T etax = cC.eta, Dx = cC.D;
+        const T A = K.G6 * Dx, B = K.G6 * etax;
+        const T eta1 = cC.ownh + Sh + T(5) * A * etax + (A * Se - B * Sd);
+        const T hu1 = K.e * (Sx + (A * Xe - B * Xd)) + cC.hFx;
+        const T hv1 = K.e * (Sy + (A * Ye - B * Yd)) + cC.hFy;
+        const T inv = T(1) / (Dx + eta1);
+        T u1 = hu1 * inv, v1 = hv1 * inv;
+        if ((ty & KIND_MASK) == K_NOSLIP) { u1 = T(0); v1 = T(0); }
+        const size_t idx = (size_t)j * f.pitch + x;
+        f.eta1[idx] = eta1;
+        f.u1[idx] = u1;
+        f.v1[idx] = v1;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) step_fast_kernel(const Fields<T> f, int ncb, int nrb, int ty)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int cb = warp % ncb, rb = warp / ncb;
+    if (rb >= nrb) return;  // whole warp
+    const int xl = WCOLS * cb - 2 + CPL * lane;  // first column of this lane
+    const int j0 = rb * ty;
+    const int j1 = min(f.ny, j0 + ty);
+    Raw<T> nxt[CPL], cur[CPL];
+    Row<T> A, B, C;
+    load_row(f, j0 - 1, xl, nxt);
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) cur[k] = nxt[k];
+    load_row(f, j0, xl, nxt);
+    derive_row(f.c, cur, A);
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) cur[k] = nxt[k];
+    load_row(f, j0 + 1, xl, nxt);
+    derive_row(f.c, cur, B);
+    // rows rotate A -> B -> C so that no register copies of Row are needed
+    for (int j = j0;; j += 3) {
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) cur[k] = nxt[k];
+        if (j + 2 <= j1) load_row(f, j + 2, xl, nxt);
+        derive_row(f.c, cur, C);
+        emit_row(f, j, xl, lane, A, B, C);
+        if (j + 1 >= j1) break;
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) cur[k] = nxt[k];
+        if (j + 3 <= j1) load_row(f, j + 3, xl, nxt);
+        derive_row(f.c, cur, A);
+        emit_row(f, j + 1, xl, lane, B, C, A);
+        if (j + 2 >= j1) break;
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) cur[k] = nxt[k];
+        if (j + 4 <= j1) load_row(f, j + 4, xl, nxt);
+        derive_row(f.c, cur, B);
+        emit_row(f, j + 2, xl, lane, C, A, B);
+        if (j + 3 >= j1) break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// General-link kernel: nodes with at least one bounce-back link (next to a
+// solid node or a bounce-back edge).  Each link is resolved as in the
+// paper's boundary rules: a solid or walled-off source bounces back
+// (f^eq of the opposite direction at the node itself, no bed or force
+// term); a specular source is the mirror image; a periodic source wraps.
+__constant__ int c_cx[9] = {0, 1, 1, 0, -1, -1, -1, 0, 1};
+__constant__ int c_cy[9] = {0, 0, 1, 1, 1, 0, -1, -1, -1};
+
+template <typename T>
+struct NodeQ {  // per-node quantities for the general path
+    T eta, D, h, u, v, uu, Fx, Fy;
+};
+
+template <typename T>
+__device__ __forceinline__ NodeQ<T> node_q(const Fields<T>& f, size_t idx, uint8_t flip)
+{
+    const Coef<T>& c = f.c;
+    NodeQ<T> n;
+    n.eta = f.eta[idx];
+    n.D = f.D[idx];
+    n.u = f.u[idx];
+    n.v = f.v[idx];
+    T wfx = c.wfx, wfy = c.wfy, Om = c.Om;
+    if (flip & 1) { n.u = -n.u; wfx = -wfx; }
+    if (flip & 2) { n.v = -n.v; wfy = -wfy; }
+    if ((flip & 3) == 1 || (flip & 3) == 2) Om = -Om;
+    n.h = n.D + n.eta;
+    n.uu = n.u * n.u + n.v * n.v;
+    const T sp = my_sqrt(n.uu);
+    n.Fx = wfx - c.Cb * n.u * sp + Om * n.h * n.v;
+    n.Fy = wfy - c.Cb * n.v * sp - Om * n.h * n.u;
+    return n;
+}
+
+// f^eq_a(h,u) - f^eq_a(D,0) for direction a != 0 with lattice vector (cx, cy)
+template <typename T>
+__device__ __forceinline__ T feq_diff(const Coef<T>& c, const NodeQ<T>& n, int cx, int cy)
+{
+    const T lam = (cx != 0 && cy != 0) ? T(0.25) : T(1);
+    const T cu = T(cx) * n.u + T(cy) * n.v;
+    return lam * (c.G6 * n.eta * (T(2) * n.D + n.eta) + n.h * cu * c.k3 +
+                  n.h * cu * cu * c.k2 - c.K6 * n.h * n.uu);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) step_general_kernel(const Fields<T> f, const int* __restrict__ list,
+                                                           int count)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int node = list[t];
+    const int i = node % f.nx, j = node / f.nx;
+    const size_t xi = (size_t)j * f.pitch + i;
+    const Coef<T>& c = f.c;
+    const NodeQ<T> X = node_q(f, xi, 0);
+    T Sh = X.eta - T(5) * c.G6 * X.eta * (T(2) * X.D + X.eta) - T(4) * c.K6 * X.h * X.uu;
+    T Sx = T(0), Sy = T(0);
+#pragma unroll 1
+    for (int a = 1; a < 9; ++a) {
+        const int cx = c_cx[a], cy = c_cy[a];
+        const T lam = (a & 1) ? T(1) : T(0.25);
+        uint8_t flip = 0;
+        const int si = resolve_index(i - cx, f.nx, f.edge[0], f.edge[1], 1, flip);
+        const int sj = resolve_index(j - cy, f.ny, f.edge[2], f.edge[3], 2, flip);
+        bool bounce = si < 0 || sj < 0;
+        size_t s = 0;
+        if (!bounce) {
+            s = (size_t)sj * f.pitch + si;
+            bounce = (f.type[s] & KIND_MASK) == K_SOLID;
+        }
+        T w;
+        if (bounce) {
+            w = feq_diff(c, X, -cx, -cy);
+        } else {
+            const NodeQ<T> Y = node_q(f, s, flip);  // the mirrored node when flip != 0
+            w = feq_diff(c, Y, cx, cy) +
+                lam * c.G6 * (X.eta + Y.eta) * (X.D - Y.D) +
+                lam * c.KF * (T(cx) * (X.Fx + Y.Fx) + T(cy) * (X.Fy + Y.Fy));
+        }
+        Sh += w;
+        Sx += T(cx) * w;
+        Sy += T(cy) * w;
+    }
+    const T hu1 = c.e * Sx, hv1 = c.e * Sy;
+    const T inv = T(1) / (X.D + Sh);
+    T u1 = hu1 * inv, v1 = hv1 * inv;
+    if ((f.type[xi] & KIND_MASK) == K_NOSLIP) { u1 = T(0); v1 = T(0); }
+    f.eta1[xi] = Sh;
+    f.u1[xi] = u1;
+    f.v1[xi] = v1;
+}
+
+// ---------------------------------------------------------------------------
+// Dirichlet nodes, after every other node holds its new value.
+struct DirNode {
+    int x, n1, n2;  // storage indices (row * pitch + col) of the node and its two inward nodes
+    int meta;       // kind | (edge << 4)
+};
+struct DirValues {
+    double h[4], qx[4], qy[4];  // prescribed values at t_{n+1} per edge
+};
+
+template <typename T>
+__global__ void dirichlet_kernel(T* __restrict__ eta, T* __restrict__ u, T* __restrict__ v,
+                                 const T* __restrict__ D, const double* __restrict__ D64,
+                                 const DirNode* __restrict__ list, int count, const DirValues bv)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const DirNode d = list[t];
+    const int kind = d.meta & 15, ed = d.meta >> 4;
+    if (kind == K_DIR_H) {
+        eta[d.x] = (T)(bv.h[ed] - D64[d.x]);
+        u[d.x] = T(2) * u[d.n1] - u[d.n2];
+        v[d.x] = T(2) * v[d.n1] - v[d.n2];
+        return;
+    }
+    double h;
+    if (kind == K_DIR_Q) {
+        const double h1 = (double)D[d.n1] + (double)eta[d.n1];
+        const double h2 = (double)D[d.n2] + (double)eta[d.n2];
+        h = 2.0 * h1 - h2;
+    } else {
+        h = bv.h[ed];
+    }
+    eta[d.x] = (T)(h - D64[d.x]);
+    u[d.x] = (T)(bv.qx[ed] / h);
+    v[d.x] = (T)(bv.qy[ed] / h);
+}
+
+// ---------------------------------------------------------------------------
+// Residual / mass / stability reduction in double precision.
+constexpr int RED_THREADS = 256;
+constexpr int RED_NVAL = 5;  // sum dq^2, sum q^2, sum eta, max |u|^2, non-finite count
+
+__device__ __forceinline__ double warp_sum(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+__device__ __forceinline__ double warp_max(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS)
+residual_partial_kernel(const T* __restrict__ e0, const T* __restrict__ u0, const T* __restrict__ v0,
+                        const T* __restrict__ e1, const T* __restrict__ u1, const T* __restrict__ v1,
+                        const T* __restrict__ D, const uint8_t* __restrict__ type, int nx, int ny,
+                        int pitch, double* __restrict__ partial)
+{
+    double s[RED_NVAL] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const size_t total = (size_t)nx * ny;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const size_t j = k / nx, i = k - j * nx;
+        const size_t x = j * pitch + i;
+        if ((type[x] & KIND_MASK) == K_SOLID) continue;
+        const double d = (double)D[x];
+        const double a0 = (double)e0[x], a1 = (double)e1[x];
+        const double h0 = d + a0, h1 = d + a1;
+        const double qx0 = h0 * (double)u0[x], qy0 = h0 * (double)v0[x];
+        const double qx1 = h1 * (double)u1[x], qy1 = h1 * (double)v1[x];
+        const double dh = a1 - a0, dqx = qx1 - qx0, dqy = qy1 - qy0;
+        s[0] += dh * dh + dqx * dqx + dqy * dqy;
+        s[1] += h1 * h1 + qx1 * qx1 + qy1 * qy1;
+        s[2] += a1;
+        const double uu = (double)u1[x] * (double)u1[x] + (double)v1[x] * (double)v1[x];
+        s[3] = fmax(s[3], uu);
+        if (!isfinite(a1) || !isfinite(uu)) s[4] += 1.0;
+    }
+    __shared__ double sh[RED_NVAL][RED_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < RED_NVAL; ++q) {
+        const double r = (q == 3) ? warp_max(s[q]) : warp_sum(s[q]);
+        if (lane == 0) sh[q][w] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x < RED_NVAL) {
+        const int q = threadIdx.x;
+        double r = sh[q][0];
+        for (int k = 1; k < RED_THREADS / 32; ++k) r = (q == 3) ? fmax(r, sh[q][k]) : r + sh[q][k];
+        partial[(size_t)blockIdx.x * RED_NVAL + q] = r;
+    }
+}
+
+__global__ void residual_final_kernel(const double* __restrict__ partial, int nblocks,
+                                      double* __restrict__ out)
+{
+    // one warp per value, fixed order -> deterministic
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (q >= RED_NVAL) return;
+    double r = (q == 3) ? 0.0 : 0.0;
+    for (int b = lane; b < nblocks; b += 32) {
+        const double x = partial[(size_t)b * RED_NVAL + q];
+        r = (q == 3) ? fmax(r, x) : r + x;
+    }
+    r = (q == 3) ? warp_max(r) : warp_sum(r);
+    if (lane == 0) out[q] = r;
+}
+
+// ---------------------------------------------------------------------------
+// State conversion between host-facing double (h, u, v) [ny][nx] and the
+// device storage (eta, u, v) [ny][pitch].
+template <typename T>
+__global__ void state_in_kernel(const double* __restrict__ h, const double* __restrict__ u,
+                                const double* __restrict__ v, const double* __restrict__ D64,
+                                const uint8_t* __restrict__ type, T* e0, T* u0, T* v0, T* e1,
+                                T* u1, T* v1, int nx, int ny, int pitch)
+{
+    const size_t total = (size_t)nx * ny;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const size_t j = k / nx, i = k - j * nx, x = j * pitch + i;
+        const T a = (T)(h[k] - D64[x]), b = (T)u[k], c = (T)v[k];
+        e0[x] = a; u0[x] = b; v0[x] = c;
+        if ((type[x] & KIND_MASK) == K_SOLID) { e1[x] = a; u1[x] = b; v1[x] = c; }
+    }
+}
+
+template <typename T>
+__global__ void state_out_kernel(const T* __restrict__ e, const T* __restrict__ u,
+                                 const T* __restrict__ v, const double* __restrict__ D64,
+                                 double* h, double* uo, double* vo, int nx, int ny, int pitch)
+{
+    const size_t total = (size_t)nx * ny;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const size_t j = k / nx, i = k - j * nx, x = j * pitch + i;
+        h[k] = D64[x] + (double)e[x];
+        uo[k] = (double)u[x];
+        vo[k] = (double)v[x];
+    }
+}
+
+}  // namespace maclab

@@ -1,0 +1,279 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle,
+element by element on the same seeded inputs.
+
+Tolerances (relative max-norm over non-solid nodes, normalised by the
+largest reference magnitude of that field):
+  FP64 storage: <= 1e-12 on h, u, v after 1000 steps.
+  FP32 storage: <= 2e-5 on h and <= 1e-4 on u, v after 1000 steps.
+Lake at rest is checked bitwise in FP32 (the perturbation form makes it
+exact).  The full-size channel (8192 x 2048) runs in the same launch
+configuration as the benchmark and is compared on every node after one
+step and after two.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+from inputs import BOUNCEBACK, DIR_H, FLUID, NOSLIP, PERIODIC, SOLID, SPECULAR
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": (1e-12, 1e-12), "f32": (2e-5, 1e-4)}
+
+
+def sim_of(case, precision, **kw):
+    from paper_1902_02999_gb300 import Simulation
+    return Simulation.from_case(case, precision=precision, **kw)
+
+
+def relerr(a, b, live):
+    if not live.any():
+        return 0.0
+    scale = max(np.abs(b[live]).max(), 1e-300)
+    return float(np.abs(a[live] - b[live]).max() / scale)
+
+
+def compare(case, got, want, precision, label=""):
+    live = case.mask != SOLID
+    th, tu = TOL[precision]
+    eh = relerr(got[0], want[0], live)
+    eu = relerr(got[1], want[1], live)
+    ev = relerr(got[2], want[2], live)
+    assert np.isfinite(got[0][live]).all()
+    assert eh <= th, (label, "h", eh)
+    # velocity: normalised by the largest speed of the reference
+    live_u = live & (case.mask != NOSLIP)
+    scale = max(np.hypot(want[1], want[2])[live].max(), 1e-30)
+    eu = float(np.abs(got[1] - want[1])[live].max() / scale)
+    ev = float(np.abs(got[2] - want[2])[live].max() / scale)
+    assert eu <= tu and ev <= tu, (label, "u,v", eu, ev)
+    if live_u.any():
+        assert (got[1][case.mask == NOSLIP] == 0).all()
+    return eh, eu, ev
+
+
+CASES = [
+    # (nx, ny, seed, edges)  -- sizes span several 62-column warp strips and ragged tails
+    (131, 97, 1, (BOUNCEBACK, BOUNCEBACK, SPECULAR, SPECULAR)),
+    (67, 45, 2, (PERIODIC, PERIODIC, SPECULAR, SPECULAR)),
+    (125, 66, 3, (SPECULAR, SPECULAR, SPECULAR, SPECULAR)),
+    (64, 63, 4, (PERIODIC, PERIODIC, PERIODIC, PERIODIC)),
+    (63, 40, 5, (BOUNCEBACK, BOUNCEBACK, BOUNCEBACK, BOUNCEBACK)),
+    (190, 33, 6, (BOUNCEBACK, SPECULAR, PERIODIC, PERIODIC)),
+]
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("nx,ny,seed,edges", CASES)
+def test_parity_random(nx, ny, seed, edges, precision):
+    case = inputs.random_case(nx, ny, seed, edges=edges)
+    nsteps = 1000 if nx * ny < 9000 else 400
+    want = oracle.run(case, nsteps)
+    sim = sim_of(case, precision)
+    sim.step(nsteps)
+    got = sim.get_state()
+    compare(case, got, want, precision, (nx, ny, seed, edges))
+    assert sim.time()[1] == nsteps
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_hand_step_3x3(precision):
+    rows = np.loadtxt(__file__.replace("test_parity_gpu.py", "golden/hand_step_3x3.txt"))
+    z = np.zeros((3, 3))
+    c = inputs.Case("hand", 3, 3, 1.0, 2.0, z, np.full((3, 3), FLUID, np.uint8), np.ones((3, 3)),
+                    z.copy(), z.copy(), edges=(PERIODIC,) * 4, h_ref=1.0)
+    c.h0[1, 1] = 1.1
+    sim = sim_of(c, precision)
+    sim.step(1)
+    h, u, v = sim.get_state()
+    tol = 1e-14 if precision == "f64" else 2e-7
+    for i, j, hn, hun, hvn in rows:
+        i, j = int(i), int(j)
+        assert abs(h[j, i] - hn) < tol
+        assert abs(h[j, i] * u[j, i] - hun) < tol
+        assert abs(h[j, i] * v[j, i] - hvn) < tol
+
+
+@pytest.mark.parametrize("rows", [1, 3, 8, 1000])
+def test_tile_rows_do_not_change_results(rows):
+    case = inputs.random_case(131, 50, 9, edges=(BOUNCEBACK, BOUNCEBACK, SPECULAR, SPECULAR))
+    ref = sim_of(case, "f32")
+    ref.step(50)
+    a = ref.get_state()
+    sim = sim_of(case, "f32")
+    sim.set_tile_rows(rows)
+    sim.step(50)
+    b = sim.get_state()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("n", [64, 101])
+def test_lake_at_rest_bitwise_f32(n):
+    case = inputs.dish_lake(n, seed=3)
+    case.wind_u = case.wind_v = 0.0
+    sim = sim_of(case, "f32", initial=False)   # still water: eta = 0, u = v = 0
+    sim.step(1000)
+    eta, u, v = (t.cpu().numpy() for t in sim.device_state())
+    assert (eta == 0).all() and (u == 0).all() and (v == 0).all()
+    h, _, _ = sim.get_state()
+    live = case.mask != SOLID
+    assert (h[live] == (case.h_ref - case.zb)[live]).all()
+
+
+def test_lake_at_rest_f64_arbitrary_bed():
+    case = inputs.random_case(90, 70, 12, edges=(SPECULAR,) * 4, dirichlet=False)
+    live = case.mask != SOLID
+    case.h0 = np.where(live, case.h_ref - case.zb, 0.0)
+    case.u0[:] = 0
+    case.v0[:] = 0
+    case.wind_u = case.wind_v = 0.0
+    sim = sim_of(case, "f64")
+    sim.step(1000)
+    h, u, v = sim.get_state()
+    assert np.abs(h - case.h0)[live].max() < 1e-13
+    assert np.abs(u).max() < 1e-13 and np.abs(v).max() < 1e-13
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-13), ("f32", 2e-6)])
+def test_mass_conservation_closed_basin(precision, tol):
+    case = inputs.random_case(140, 90, 13, edges=(BOUNCEBACK,) * 4, dirichlet=False)
+    live = case.mask != SOLID
+    m0 = case.h0[live].sum()
+    sim = sim_of(case, precision)
+    sim.step(1000)
+    r, mass, umax = sim.residual()
+    assert abs(mass - m0) / m0 < tol
+    h, _, _ = sim.get_state()
+    assert abs(h[live].sum() - m0) / m0 < tol
+
+
+def test_residual_matches_oracle():
+    case = inputs.random_case(77, 51, 14)
+    s1 = oracle.run(case, 30)
+    s2 = oracle.run(case, 1, s1, n0=30)
+    r_o, m_o, u_o = oracle.residual(case, s1, s2)
+    sim = sim_of(case, "f64")
+    sim.step(31)
+    r, m, umax = sim.residual()
+    assert abs(r - r_o) <= 1e-9 * r_o
+    assert abs(m - m_o) <= 1e-12 * m_o
+    assert abs(umax - u_o) <= 1e-11 * u_o
+
+
+def test_paper_tidal_case_on_gpu():
+    """Section 4.1 at the paper's resolution, FP64 on the GPU: matches the
+    oracle and keeps the level error under the paper's 0.005 %."""
+    case = inputs.tidal_strip(201, 1)
+    n = int(round(10800.0 / case.dt))
+    sim = sim_of(case, "f64")
+    sim.step(n)
+    h, u, v = sim.get_state()
+    want = oracle.run(case, n)
+    compare(case, (h, u, v), want, "f64", "tidal")
+    om = 4 * math.pi / 86400
+    eta = 20 - 4 * math.sin(om * n * case.dt + math.pi / 2)
+    assert np.abs(h[0] + case.zb[0] - eta).max() / eta < 5e-5
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_tidal_strip_400x3(precision):
+    """The 400 x 3 strip with free-slip side walls, 2000 steps."""
+    case = inputs.tidal_strip(400, 3)
+    sim = sim_of(case, precision)
+    sim.step(2000)
+    compare(case, sim.get_state(), oracle.run(case, 2000), precision, "strip")
+
+
+@pytest.mark.parametrize("nx,ny,edges", [
+    (1, 1, (PERIODIC,) * 4), (2, 3, (PERIODIC,) * 4), (1, 7, (SPECULAR,) * 4),
+    (9, 1, (SPECULAR,) * 4), (65, 2, (PERIODIC, PERIODIC, SPECULAR, SPECULAR)),
+    (127, 5, (SPECULAR, BOUNCEBACK, PERIODIC, PERIODIC)), (3, 3, (BOUNCEBACK,) * 4)])
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_small_and_degenerate_grids(nx, ny, edges, precision):
+    case = inputs.random_case(nx, ny, 40 + nx, edges=edges, solids=False, dirichlet=False, amp=0.1)
+    want = oracle.run(case, 20)
+    sim = sim_of(case, precision)
+    sim.step(20)
+    compare(case, sim.get_state(), want, precision, (nx, ny))
+
+
+def test_all_solid_grid_is_inert():
+    case = inputs.random_case(20, 10, 50, dirichlet=False)
+    case.mask[:] = SOLID
+    sim = sim_of(case, "f32")
+    h0, u0, v0 = sim.get_state()
+    sim.step(5)
+    h1, u1, v1 = sim.get_state()
+    assert np.array_equal(h0, h1) and np.array_equal(u0, u1)
+    r, mass, umax = sim.residual()
+    assert r == 0.0 and mass == 0.0
+
+
+def test_state_roundtrip_and_time():
+    case = inputs.random_case(70, 30, 60)
+    sim = sim_of(case, "f64")
+    h, u, v = sim.get_state()
+    live = case.mask != SOLID
+    assert np.abs(h - case.h0)[live].max() < 1e-15
+    assert np.array_equal(u[live], case.u0[live])
+    sim.step(7)
+    t, n = sim.time()
+    assert n == 7 and abs(t - 7 * case.dt) < 1e-12
+    s7 = sim.get_state()
+    sim.set_state(*s7)
+    sim.step(3)
+    a = sim.get_state()
+    want = oracle.run(case, 3, s7, n0=7)
+    compare(case, a, want, "f64", "resume")
+
+
+def test_errors_are_reported():
+    from paper_1902_02999_gb300 import MaclabError
+    case = inputs.random_case(30, 20, 70)
+    bad = case.copy()
+    bad.mask[10, 10] = DIR_H                       # Dirichlet node off the edge
+    with pytest.raises(MaclabError) as ei:
+        sim_of(bad, "f32")
+    assert ei.value.code == -1
+    sim = sim_of(case, "f32")
+    with pytest.raises(MaclabError) as ei:
+        sim.residual()                             # no step yet
+    assert ei.value.code == -5
+    h = case.h0.copy()
+    j, i = np.argwhere(case.mask == FLUID)[len(np.argwhere(case.mask == FLUID)) // 2]
+    h[j, i] = np.nan
+    sim.set_state(h, case.u0, case.v0)
+    sim.step(2)
+    with pytest.raises(MaclabError) as ei:
+        sim.residual()
+    assert ei.value.code == -4
+
+
+def test_run_to_steady_converges():
+    case = inputs.paper_hump(41)
+    case.nu = 40.0   # dx = 25 m here: keeps R_le = U dx / nu < 1
+    sim = sim_of(case, "f64")
+    ok, steps, r = sim.run_to_steady(tol=1e-9, max_steps=200000, check_every=500)
+    assert ok and r <= 1e-9
+    _, _, umax = sim.residual()
+    assert umax * case.dx / case.nu < 1.0          # R_le < 1 (Section 3)
+
+
+@pytest.mark.parametrize("precision", ["f32"])
+def test_full_size_bump_channel(precision):
+    """8192 x 2048 channel in the benchmark's launch configuration, every
+    node compared with the oracle after one step and after two."""
+    case = inputs.bump_channel(8192, 2048, seed=0)
+    sim = sim_of(case, precision)
+    sim.step(1)
+    s1 = sim.get_state()
+    w1 = oracle.step(case, case.h0, case.u0, case.v0, case.dt)
+    compare(case, s1, w1, precision, "full-1")
+    sim.step(1)
+    w2 = oracle.step(case, *w1, 2 * case.dt)
+    compare(case, sim.get_state(), w2, precision, "full-2")
