@@ -14,8 +14,10 @@ missing.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
-from typing import Optional, Sequence
+import weakref
+from typing import Sequence
 
 import numpy as np
 
@@ -81,6 +83,19 @@ class _TorchAllocator:
         self.struct = _abi.Allocator(self._alloc, self._release, None)
 
 
+_live = weakref.WeakSet()
+
+
+@atexit.register
+def _close_all():
+    # release device buffers while torch's allocator is still alive
+    for sim in list(_live):
+        try:
+            sim.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
 class Simulation:
     """One MacLABSWE problem resident on the current CUDA device.
 
@@ -139,6 +154,7 @@ class Simulation:
         if rc != 0:
             raise MaclabError(rc, self._lib.maclab_last_error(None).decode())
         self._h = handle
+        _live.add(self)
         info = _abi.Info()
         self._check(self._lib.maclab_get_info(self._h, ctypes.byref(info)))
         self.info = {f: getattr(info, f) for f, _ in _abi.Info._fields_}
