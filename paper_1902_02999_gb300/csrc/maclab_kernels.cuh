@@ -18,9 +18,10 @@
 // link is lambda_a g D(x)^2/(6e^2), independent of y, so it cancels against
 // the still-water part of h(x) exactly (lake at rest is exact in any
 // precision).  What remains for an interior node x with eight usable links:
-//     eta'  = eta - h (5 G6 eta + 4 K6 |u|^2)                 (a = 0 term)
+//     eta'  = eta - h (5 G6 eta + 4 K6 |u|^2)   (a = 0 term plus the receiver-only
+//                                                bed part sum_a lambda_a G6 eta_x D_x)
 //             + sum_a o_a(x - c_a)
-//             + sum_a lambda_a [G6 eta_x D_x + G6 D_x eta_y - G6 eta_x D_y]   (bed)
+//             + sum_a lambda_a [G6 D_x eta_y - G6 eta_x D_y]              (bed, cross part)
 //     h u'  = e sum_a c_a [o_a(y) + lambda_a (G6 D_x eta_y - G6 eta_x D_y)] + dt F(x) / 2
 // where the bed term of each link is -(g/e^2) C_a hbar [z_b(x) - z_b(y)]
 // with hbar = (h(x) + h(y))/2 (Eq. h-bar at the old level) and z_b = h_ref - D,
@@ -265,7 +266,8 @@ __device__ __forceinline__ void emit_row(const Fields<T>& f, int j, int xl, int 
         const T Yd = (mC.D - pC.D) + q * ((mL.D + mR.D) - (pL.D + pR.D));
         const T etax = cC.eta, Dx = cC.D;
         const T A = K.G6 * Dx, B = K.G6 * etax;
-        const T eta1 = cC.ownh + Sh + T(5) * A * etax + (A * Se - B * Sd);
+        // ownh already holds the receiver-only bed part 5 G6 eta_x D_x
+        const T eta1 = cC.ownh + Sh + (A * Se - B * Sd);
         const T hu1 = K.e * (Sx + (A * Xe - B * Xd)) + cC.hFx;
         const T hv1 = K.e * (Sy + (A * Ye - B * Yd)) + cC.hFy;
         const T inv = T(1) / (Dx + eta1);
