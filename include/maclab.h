@@ -105,10 +105,10 @@ typedef struct {
 
 /* Edge kinds and Dirichlet data of the four edges (index MACLAB_W..N).
  * A Dirichlet node must lie on a grid edge; its edge is the first of
- * W, E, S, N that it touches, and the two nodes inward along that edge's
- * normal must be non-solid and not Dirichlet.  Prescribed values take their
- * value at the new time t_{n+1}; the other quantity is extrapolated linearly
- * from the new values of the two inward nodes. */
+ * W, E, S, N that it touches, and the node inward along that edge's normal
+ * must be non-solid and not Dirichlet.  Prescribed values take their value
+ * at the new time t_{n+1}; the other quantity takes the new value of the
+ * inward node (zero normal gradient). */
 typedef struct {
     int edge[4];
     maclab_wave h[4];  /* depth for DIR_H / DIR_HU nodes                   */

@@ -36,9 +36,12 @@
  *       Periodic edge: the source wraps around.
  *   R5  No-slip node: h from the update, u = v = 0.
  *       Dirichlet node on a grid edge: the prescribed quantities take their
- *       value at the new time t_{n+1}; each unprescribed one is extrapolated
- *       linearly from the new values of the two nodes inward along the edge
- *       normal (a second pass once the other nodes are updated).
+ *       value at the new time t_{n+1}; each unprescribed one takes the new
+ *       value of the first node inward along the edge normal (zero normal
+ *       gradient), in a second pass once the other nodes are updated.
+ *       (Linear extrapolation from two inward nodes is unstable at a 2D
+ *       depth boundary; the velocity of the node's own update with walled-off
+ *       links misses the Section 4.1 level bound by two orders.)
  *
  * Every function below works in double precision and loops over nodes and
  * directions in the order the equations are written; there is no blocking,
@@ -171,8 +174,8 @@ static int dirichlet_edge(const oracle_problem* p, int i, int j, int* di, int* d
 
 /* One MacLABSWE step, state (h,u,v) at t_n -> (h1,u1,v1) at t_n + dt.
  * t_next is t_{n+1}, used for the prescribed Dirichlet values.
- * Returns 0, or -1 if a Dirichlet node is not on a grid edge or its two
- * inward nodes are solid or Dirichlet. */
+ * Returns 0, or -1 if a Dirichlet node is not on a grid edge or its
+ * inward node is solid or Dirichlet. */
 int oracle_step(const oracle_problem* p, const double* zb, const uint8_t* type,
                 const double* h, const double* u, const double* v,
                 double* h1, double* u1, double* v1, double t_next)
@@ -233,28 +236,24 @@ int oracle_step(const oracle_problem* p, const double* zb, const uint8_t* type,
         }
     }
     /* R5, second pass: Dirichlet nodes, once every other node holds its new
-     * value.  The inward nodes must be non-solid and not Dirichlet. */
+     * value.  The inward node must be non-solid and not Dirichlet. */
     for (j = 0; j < ny; ++j) {
         for (i = 0; i < nx; ++i) {
-            size_t x = (size_t)j * nx + i, n1, n2;
+            size_t x = (size_t)j * nx + i, n1;
             int di, dj, ed;
             if (type[x] < OT_DIR_H || type[x] > OT_DIR_HU) continue;
             ed = dirichlet_edge(p, i, j, &di, &dj);
-            if (ed < 0 || i + 2 * di < 0 || i + 2 * di >= nx || j + 2 * dj < 0 || j + 2 * dj >= ny)
-                return -1;
+            if (ed < 0 || i + di < 0 || i + di >= nx || j + dj < 0 || j + dj >= ny) return -1;
             n1 = (size_t)(j + dj) * nx + (i + di);
-            n2 = (size_t)(j + 2 * dj) * nx + (i + 2 * di);
-            if (type[n1] == OT_SOLID || type[n2] == OT_SOLID || type[n1] >= OT_DIR_H ||
-                type[n2] >= OT_DIR_H)
-                return -1;
+            if (type[n1] == OT_SOLID || type[n1] >= OT_DIR_H) return -1;
             if (type[x] == OT_DIR_H) {
                 h1[x] = wave(p->bc[ed][0], t_next);
-                u1[x] = 2.0 * u1[n1] - u1[n2];
-                v1[x] = 2.0 * v1[n1] - v1[n2];
+                u1[x] = u1[n1];
+                v1[x] = v1[n1];
             } else {
                 double qx = wave(p->bc[ed][1], t_next), qy = wave(p->bc[ed][2], t_next);
                 if (type[x] == OT_DIR_Q)
-                    h1[x] = 2.0 * h1[n1] - h1[n2];
+                    h1[x] = h1[n1];
                 else
                     h1[x] = wave(p->bc[ed][0], t_next);
                 u1[x] = qx / h1[x];

@@ -371,15 +371,14 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
                         delete s;
                         return fail(nullptr, MACLAB_E_ARG, "Dirichlet node not on a grid edge");
                     }
-                    const int i1 = i + di, j1 = j + dj, i2 = i + 2 * di, j2 = j + 2 * dj;
-                    if (i2 < 0 || i2 >= nx || j2 < 0 || j2 >= ny || kind_at(i1, j1) == MACLAB_SOLID ||
-                        kind_at(i2, j2) == MACLAB_SOLID || kind_at(i1, j1) >= MACLAB_DIR_H ||
-                        kind_at(i2, j2) >= MACLAB_DIR_H) {
+                    const int i1 = i + di, j1 = j + dj;
+                    if (i1 < 0 || i1 >= nx || j1 < 0 || j1 >= ny || kind_at(i1, j1) == MACLAB_SOLID ||
+                        kind_at(i1, j1) >= MACLAB_DIR_H) {
                         delete s;
                         return fail(nullptr, MACLAB_E_ARG,
-                                    "the two inward nodes of a Dirichlet node must be non-solid and not Dirichlet");
+                                    "the inward node of a Dirichlet node must be non-solid and not Dirichlet");
                     }
-                    dirs.push_back(DirNode{j * pitch + i, j1 * pitch + i1, j2 * pitch + i2, (int)kd | (ed << 4)});
+                    dirs.push_back(DirNode{j * pitch + i, j1 * pitch + i1, (int)kd | (ed << 4)});
                 } else {
                     bool gen = false;
                     for (int a = 1; a < 9 && !gen; ++a) {

@@ -99,10 +99,29 @@ __device__ __forceinline__ T my_sqrt(T x) { return sqrt(x); }
 template <>
 __device__ __forceinline__ float my_sqrt<float>(float x) { return sqrtf(x); }
 
+// Correctly rounded operations that the compiler never contracts or
+// reorders: the fast path spells out every multiply-add, so a node's result
+// does not depend on which inlined copy of the code computed it (and hence
+// not on the strip height).
+template <typename T> struct Op;
+template <> struct Op<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+};
+template <> struct Op<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+};
+
 // Source-side quantities of one node (see the header comment).
 template <typename T>
 __device__ __forceinline__ void derive(const Coef<T>& c, const Raw<T>& r, Src<T>& s)
 {
+    using O = Op<T>;
     T u = r.u, v = r.v, wfx = c.wfx, wfy = c.wfy, Om = c.Om;
     if (r.flip) {  // specular ghost: normal components reversed, rotation sense too
         if (r.flip & 1) { u = -u; wfx = -wfx; }
@@ -110,35 +129,36 @@ __device__ __forceinline__ void derive(const Coef<T>& c, const Raw<T>& r, Src<T>
         if ((r.flip & 3) != 3) Om = -Om;
     }
     const T eta = r.eta, D = r.D;
-    const T h = D + eta;
-    const T uu = u * u + v * v;
-    const T ge = c.G6 * eta;
-    const T ku = c.K6 * uu;
-    const T ap = h * (ge - ku);
-    s.ownh = eta - h * (T(5) * ge + T(4) * ku);
+    const T h = O::add(D, eta);
+    const T uu = O::fma(u, u, O::mul(v, v));
+    const T ge = O::mul(c.G6, eta);
+    const T ku = O::mul(c.K6, uu);
+    const T ap = O::mul(h, O::sub(ge, ku));
+    s.ownh = O::fma(-h, O::fma(T(5), ge, O::mul(T(4), ku)), eta);
     const T sp = my_sqrt(uu);
-    const T Fx = wfx - c.Cb * u * sp + Om * h * v;
-    const T Fy = wfy - c.Cb * v * sp - Om * h * u;
-    s.hFx = c.hdt * Fx;
-    s.hFy = c.hdt * Fy;
-    const T hu = h * u, hv = h * v;
-    const T qx = hu * c.k3 + c.KF * Fx;
-    const T qy = hv * c.k3 + c.KF * Fy;
-    const T sxx = hu * u * c.k2;
-    const T syy = hv * v * c.k2;
-    const T sxy = hu * v * c.k1;
-    const T ax = ap + sxx, ay = ap + syy;
-    s.o1 = ax + qx;
-    s.o5 = ax - qx;
-    s.o3 = ay + qy;
-    s.o7 = ay - qy;
-    const T d = ax + syy;
-    const T dp = T(0.25) * (d + sxy), dm = T(0.25) * (d - sxy);
-    const T s4 = T(0.25) * (qx + qy), t4 = T(0.25) * (qx - qy);
-    s.o2 = dp + s4;
-    s.o6 = dp - s4;
-    s.o8 = dm + t4;
-    s.o4 = dm - t4;
+    const T cbs = O::mul(c.Cb, sp), omh = O::mul(Om, h);
+    const T Fx = O::fma(-cbs, u, O::fma(omh, v, wfx));
+    const T Fy = O::fma(-cbs, v, O::fma(-omh, u, wfy));
+    s.hFx = O::mul(c.hdt, Fx);
+    s.hFy = O::mul(c.hdt, Fy);
+    const T hu = O::mul(h, u), hv = O::mul(h, v);
+    const T qx = O::fma(hu, c.k3, O::mul(c.KF, Fx));
+    const T qy = O::fma(hv, c.k3, O::mul(c.KF, Fy));
+    const T sxx = O::mul(O::mul(hu, u), c.k2);
+    const T syy = O::mul(O::mul(hv, v), c.k2);
+    const T sxy = O::mul(O::mul(hu, v), c.k1);
+    const T ax = O::add(ap, sxx), ay = O::add(ap, syy);
+    s.o1 = O::add(ax, qx);
+    s.o5 = O::sub(ax, qx);
+    s.o3 = O::add(ay, qy);
+    s.o7 = O::sub(ay, qy);
+    const T d = O::add(ax, syy);
+    const T dp = O::mul(T(0.25), O::add(d, sxy)), dm = O::mul(T(0.25), O::sub(d, sxy));
+    const T s4 = O::mul(T(0.25), O::add(qx, qy)), t4 = O::mul(T(0.25), O::sub(qx, qy));
+    s.o2 = O::add(dp, s4);
+    s.o6 = O::sub(dp, s4);
+    s.o8 = O::add(dm, t4);
+    s.o4 = O::sub(dm, t4);
     s.eta = eta;
     s.D = D;
     s.type = r.type;
@@ -249,29 +269,32 @@ __device__ __forceinline__ void emit_row(const Fields<T>& f, int j, int xl, int 
         const Src<T>& mL = m.col[k - 1]; const Src<T>& mC = m.col[k]; const Src<T>& mR = m.col[k + 1];
         const Src<T>& cL = c.col[k - 1]; const Src<T>& cC = c.col[k]; const Src<T>& cR = c.col[k + 1];
         const Src<T>& pL = p.col[k - 1]; const Src<T>& pC = p.col[k]; const Src<T>& pR = p.col[k + 1];
+        using O = Op<T>;
         // streamed equilibria
-        const T OL = cL.o1 + mL.o2 + pL.o8;
-        const T OR = cR.o5 + mR.o4 + pR.o6;
-        const T Sh = (OL + OR) + (mC.o3 + pC.o7);
-        const T Sx = OL - OR;
-        const T Sy = (mL.o2 + mR.o4 + mC.o3) - (pL.o8 + pR.o6 + pC.o7);
+        const T OL = O::add(O::add(cL.o1, mL.o2), pL.o8);
+        const T OR = O::add(O::add(cR.o5, mR.o4), pR.o6);
+        const T Sh = O::add(O::add(OL, OR), O::add(mC.o3, pC.o7));
+        const T Sx = O::sub(OL, OR);
+        const T Sy = O::sub(O::add(O::add(mL.o2, mR.o4), mC.o3), O::add(O::add(pL.o8, pR.o6), pC.o7));
         // lambda-weighted stencils of eta and D: sum, x-moment, y-moment
         const T q = T(0.25);
-        const T MLe = cL.eta + q * (mL.eta + pL.eta), MRe = cR.eta + q * (mR.eta + pR.eta);
-        const T MLd = cL.D + q * (mL.D + pL.D), MRd = cR.D + q * (mR.D + pR.D);
-        const T Se = (MLe + MRe) + (mC.eta + pC.eta);
-        const T Sd = (MLd + MRd) + (mC.D + pC.D);
-        const T Xe = MLe - MRe, Xd = MLd - MRd;
-        const T Ye = (mC.eta - pC.eta) + q * ((mL.eta + mR.eta) - (pL.eta + pR.eta));
-        const T Yd = (mC.D - pC.D) + q * ((mL.D + mR.D) - (pL.D + pR.D));
+        const T MLe = O::fma(q, O::add(mL.eta, pL.eta), cL.eta);
+        const T MRe = O::fma(q, O::add(mR.eta, pR.eta), cR.eta);
+        const T MLd = O::fma(q, O::add(mL.D, pL.D), cL.D);
+        const T MRd = O::fma(q, O::add(mR.D, pR.D), cR.D);
+        const T Se = O::add(O::add(MLe, MRe), O::add(mC.eta, pC.eta));
+        const T Sd = O::add(O::add(MLd, MRd), O::add(mC.D, pC.D));
+        const T Xe = O::sub(MLe, MRe), Xd = O::sub(MLd, MRd);
+        const T Ye = O::fma(q, O::sub(O::add(mL.eta, mR.eta), O::add(pL.eta, pR.eta)), O::sub(mC.eta, pC.eta));
+        const T Yd = O::fma(q, O::sub(O::add(mL.D, mR.D), O::add(pL.D, pR.D)), O::sub(mC.D, pC.D));
         const T etax = cC.eta, Dx = cC.D;
-        const T A = K.G6 * Dx, B = K.G6 * etax;
+        const T A = O::mul(K.G6, Dx), B = O::mul(K.G6, etax);
         // ownh already holds the receiver-only bed part 5 G6 eta_x D_x
-        const T eta1 = cC.ownh + Sh + (A * Se - B * Sd);
-        const T hu1 = K.e * (Sx + (A * Xe - B * Xd)) + cC.hFx;
-        const T hv1 = K.e * (Sy + (A * Ye - B * Yd)) + cC.hFy;
-        const T inv = T(1) / (Dx + eta1);
-        T u1 = hu1 * inv, v1 = hv1 * inv;
+        const T eta1 = O::add(O::add(cC.ownh, Sh), O::fma(A, Se, O::mul(-B, Sd)));
+        const T hu1 = O::fma(K.e, O::add(Sx, O::fma(A, Xe, O::mul(-B, Xd))), cC.hFx);
+        const T hv1 = O::fma(K.e, O::add(Sy, O::fma(A, Ye, O::mul(-B, Yd))), cC.hFy);
+        const T inv = T(1) / O::add(Dx, eta1);
+        T u1 = O::mul(hu1, inv), v1 = O::mul(hv1, inv);
         if ((ty & KIND_MASK) == K_NOSLIP) { u1 = T(0); v1 = T(0); }
         const size_t idx = (size_t)j * f.pitch + x;
         f.eta1[idx] = eta1;
@@ -418,10 +441,12 @@ __global__ void __launch_bounds__(128) step_general_kernel(const Fields<T> f, co
 }
 
 // ---------------------------------------------------------------------------
-// Dirichlet nodes, after every other node holds its new value.
+// Dirichlet nodes, after every other node holds its new value: prescribed
+// quantities take their value at t_{n+1}; the unprescribed one takes the new
+// value of the first node inward along the edge normal (zero gradient).
 struct DirNode {
-    int x, n1, n2;  // storage indices (row * pitch + col) of the node and its two inward nodes
-    int meta;       // kind | (edge << 4)
+    int x, n1;  // storage indices (row * pitch + col) of the node and its inward node
+    int meta;   // kind | (edge << 4)
 };
 struct DirValues {
     double h[4], qx[4], qy[4];  // prescribed values at t_{n+1} per edge
@@ -438,18 +463,11 @@ __global__ void dirichlet_kernel(T* __restrict__ eta, T* __restrict__ u, T* __re
     const int kind = d.meta & 15, ed = d.meta >> 4;
     if (kind == K_DIR_H) {
         eta[d.x] = (T)(bv.h[ed] - D64[d.x]);
-        u[d.x] = T(2) * u[d.n1] - u[d.n2];
-        v[d.x] = T(2) * v[d.n1] - v[d.n2];
+        u[d.x] = u[d.n1];
+        v[d.x] = v[d.n1];
         return;
     }
-    double h;
-    if (kind == K_DIR_Q) {
-        const double h1 = (double)D[d.n1] + (double)eta[d.n1];
-        const double h2 = (double)D[d.n2] + (double)eta[d.n2];
-        h = 2.0 * h1 - h2;
-    } else {
-        h = bv.h[ed];
-    }
+    const double h = kind == K_DIR_Q ? (double)D[d.n1] + (double)eta[d.n1] : bv.h[ed];
     eta[d.x] = (T)(h - D64[d.x]);
     u[d.x] = (T)(bv.qx[ed] / h);
     v[d.x] = (T)(bv.qy[ed] / h);

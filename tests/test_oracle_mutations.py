@@ -30,7 +30,8 @@ MUTANTS = {
     "coriolis_sign": ("- p->Omega * h * u;", "+ p->Omega * h * u;"),
     "force_weight": ("force = (dt / (e * e))", "force = (dt / e)"),
     "momentum_component": ("Shu += ex * fa;", "Shu += ey * fa;"),
-    "dirichlet_old_level": ("u1[x] = 2.0 * u1[n1] - u1[n2];", "u1[x] = 2.0 * u[n1] - u[n2];"),
+    "dirichlet_old_level": ("u1[x] = u1[n1];", "u1[x] = u[n1];"),
+    "dirichlet_linear": ("h1[x] = h1[n1];", "h1[x] = 2.0 * h1[n1] - h1[(size_t)(j + 2 * dj) * nx + (i + 2 * di)];"),
     "dirichlet_time_level": ("h1[x] = wave(p->bc[ed][0], t_next);\n                u1",
                              "h1[x] = wave(p->bc[ed][0], t_next - dx_dt_guard);\n                u1"),
     "noslip_missing": ("                u1[x] = 0.0;\n                v1[x] = 0.0;\n            }\n        }\n    }",

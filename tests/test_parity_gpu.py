@@ -1,10 +1,15 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle,
 element by element on the same seeded inputs.
 
-Tolerances (relative max-norm over non-solid nodes, normalised by the
-largest reference magnitude of that field):
+Tolerances (relative max-norm over non-solid nodes):
   FP64 storage: <= 1e-12 on h, u, v after 1000 steps.
   FP32 storage: <= 2e-5 on h and <= 1e-4 on u, v after 1000 steps.
+h is normalised by max|h|.  u and v are normalised by the largest reference
+speed; in FP64 by max(largest speed, g h_max / e) instead, because the
+momentum of Eq. Mac.lb.7 is a sum of terms of size ~g h^2/(6e) whose
+rounding the oracle itself carries: on the 400 x 3 tidal strip (h ~ 16 m,
+|u| < 0.06 m/s) two builds of the same oracle, with and without fused
+multiply-add, differ by 2.5e-11 relative to max|u| after 2000 steps.
 Lake at rest is checked bitwise in FP32 (the perturbation form makes it
 exact).  The full-size channel (8192 x 2048) runs in the same launch
 configuration as the benchmark and is compared on every node after one
@@ -45,9 +50,10 @@ def compare(case, got, want, precision, label=""):
     ev = relerr(got[2], want[2], live)
     assert np.isfinite(got[0][live]).all()
     assert eh <= th, (label, "h", eh)
-    # velocity: normalised by the largest speed of the reference
     live_u = live & (case.mask != NOSLIP)
     scale = max(np.hypot(want[1], want[2])[live].max(), 1e-30)
+    if precision == "f64":
+        scale = max(scale, case.g * np.abs(want[0][live]).max() / case.e)
     eu = float(np.abs(got[1] - want[1])[live].max() / scale)
     ev = float(np.abs(got[2] - want[2])[live].max() / scale)
     assert eu <= tu and ev <= tu, (label, "u,v", eu, ev)
@@ -255,13 +261,17 @@ def test_errors_are_reported():
 
 
 def test_run_to_steady_converges():
+    """Coarse Section 4.3 hump (41 x 41, dx = 25 m; nu = 75 m^2/s keeps the
+    lattice speed e = 18 m/s above sqrt(g h) and R_le < 1) run to a residual
+    of 1e-9; the steady state matches the oracle after the same steps."""
     case = inputs.paper_hump(41)
-    case.nu = 40.0   # dx = 25 m here: keeps R_le = U dx / nu < 1
+    case.nu = 75.0
     sim = sim_of(case, "f64")
     ok, steps, r = sim.run_to_steady(tol=1e-9, max_steps=200000, check_every=500)
-    assert ok and r <= 1e-9
+    assert ok and r <= 1e-9 and steps % 500 == 0
     _, _, umax = sim.residual()
     assert umax * case.dx / case.nu < 1.0          # R_le < 1 (Section 3)
+    compare(case, sim.get_state(), oracle.run(case, steps), "f64", "steady")
 
 
 @pytest.mark.parametrize("precision", ["f32"])
