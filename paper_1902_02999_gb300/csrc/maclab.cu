@@ -62,6 +62,7 @@ struct maclab_s {
     double* red_out = nullptr; // RED_NVAL doubles
     int red_blocks = 0;
     int ncb = 0, nrb = 0, ty = 0;
+    int fmode = 0;             // force terms present: F_WIND | F_FRICTION | F_CORIOLIS
     int64_t n_fluid = 0, n_fast = 0;
     double sumD = 0;           // sum of D64 over non-solid nodes
     size_t device_bytes = 0;
@@ -163,7 +164,7 @@ int launch_step(maclab_t s)
 {
     const Fields<T> f = make_fields<T>(s);
     const int warps = s->ncb * s->nrb;
-    const int blocks = (warps + 3) / 4;
+    const int blocks = (warps + WARPS - 1) / WARPS;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (s->profiling) {
         while (s->events.size() < s->events_used + 2) {
@@ -176,7 +177,12 @@ int launch_step(maclab_t s)
         s->events_used += 2;
         cudaEventRecord(ev0, s->stream);
     }
-    step_fast_kernel<T><<<blocks, 128, 0, s->stream>>>(f, s->ncb, s->nrb, s->ty);
+    switch (s->fmode) {  // compile-time variants for the force terms present
+#define MACLAB_FM(m) \
+    case m: step_fast_kernel<T, m><<<blocks, 32 * WARPS, 0, s->stream>>>(f, s->ncb, s->nrb, s->ty); break;
+        MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
+#undef MACLAB_FM
+    }
     if (s->profiling) cudaEventRecord(ev1, s->stream);
     if (s->n_general > 0)
         step_general_kernel<T><<<(s->n_general + 127) / 128, 128, 0, s->stream>>>(f, s->general,
@@ -333,6 +339,8 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
         s->has_alloc = true;
     }
     s->pitch = (nx + 63) / 64 * 64;
+    s->fmode = ((params->wind_u != 0 || params->wind_v != 0) ? F_WIND : 0) |
+               (params->Cb != 0 ? F_FRICTION : 0) | (params->Omega != 0 ? F_CORIOLIS : 0);
     cudaGetDevice(&s->device);
     const int pitch = s->pitch;
 

@@ -81,7 +81,6 @@ template <> struct Vec2<double> { using type = double2; };
 template <typename T>
 struct Raw {
     T eta, u, v, D;
-    uint8_t type;
     uint8_t flip;  // bit 0: mirrored in x, bit 1: mirrored in y (specular ghost)
 };
 
@@ -109,16 +108,34 @@ template <> struct Op<float> {
     static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
     static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
     static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    // hardware approximations (about 1 ulp), ample for the FP32 path
+    static __device__ __forceinline__ float rcp(float a)
+    {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+        return r;
+    }
+    static __device__ __forceinline__ float sqrt(float a)
+    {
+        float r;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+        return r;
+    }
 };
 template <> struct Op<double> {
     static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
     static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
     static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
     static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double rcp(double a) { return 1.0 / a; }
+    static __device__ __forceinline__ double sqrt(double a) { return ::sqrt(a); }
 };
 
+// Which force terms of Eq. SWE-force are present (compile-time variants).
+enum : int { F_WIND = 1, F_FRICTION = 2, F_CORIOLIS = 4 };
+
 // Source-side quantities of one node (see the header comment).
-template <typename T>
+template <typename T, int FM>
 __device__ __forceinline__ void derive(const Coef<T>& c, const Raw<T>& r, Src<T>& s)
 {
     using O = Op<T>;
@@ -135,15 +152,29 @@ __device__ __forceinline__ void derive(const Coef<T>& c, const Raw<T>& r, Src<T>
     const T ku = O::mul(c.K6, uu);
     const T ap = O::mul(h, O::sub(ge, ku));
     s.ownh = O::fma(-h, O::fma(T(5), ge, O::mul(T(4), ku)), eta);
-    const T sp = my_sqrt(uu);
-    const T cbs = O::mul(c.Cb, sp), omh = O::mul(Om, h);
-    const T Fx = O::fma(-cbs, u, O::fma(omh, v, wfx));
-    const T Fy = O::fma(-cbs, v, O::fma(-omh, u, wfy));
-    s.hFx = O::mul(c.hdt, Fx);
-    s.hFy = O::mul(c.hdt, Fy);
+    // F = tau_w / rho - C_b u |u| + Omega h (v, -u)
+    T Fx = (FM & F_WIND) ? wfx : T(0), Fy = (FM & F_WIND) ? wfy : T(0);
+    if (FM & F_CORIOLIS) {
+        const T omh = O::mul(Om, h);
+        Fx = O::fma(omh, v, Fx);
+        Fy = O::fma(-omh, u, Fy);
+    }
+    if (FM & F_FRICTION) {
+        const T cbs = O::mul(c.Cb, O::sqrt(uu));
+        Fx = O::fma(-cbs, u, Fx);
+        Fy = O::fma(-cbs, v, Fy);
+    }
     const T hu = O::mul(h, u), hv = O::mul(h, v);
-    const T qx = O::fma(hu, c.k3, O::mul(c.KF, Fx));
-    const T qy = O::fma(hv, c.k3, O::mul(c.KF, Fy));
+    T qx = O::mul(hu, c.k3), qy = O::mul(hv, c.k3);
+    if (FM) {
+        s.hFx = O::mul(c.hdt, Fx);
+        s.hFy = O::mul(c.hdt, Fy);
+        qx = O::fma(c.KF, Fx, qx);
+        qy = O::fma(c.KF, Fy, qy);
+    } else {
+        s.hFx = T(0);
+        s.hFy = T(0);
+    }
     const T sxx = O::mul(O::mul(hu, u), c.k2);
     const T syy = O::mul(O::mul(hv, v), c.k2);
     const T sxy = O::mul(O::mul(hu, v), c.k1);
@@ -161,7 +192,6 @@ __device__ __forceinline__ void derive(const Coef<T>& c, const Raw<T>& r, Src<T>
     s.o4 = O::sub(dm, t4);
     s.eta = eta;
     s.D = D;
-    s.type = r.type;
 }
 
 // Map a column / row index outside the grid through the edge kinds.
@@ -190,50 +220,102 @@ __device__ __forceinline__ int resolve_index(int i, int n, int lo_kind, int hi_k
 // consecutive rows in registers (y neighbours) and exchanging the edge
 // columns of each lane with warp shuffles (x neighbours).  Output columns
 // are the 62 inner ones: [62 cb - 1, 62 cb + 60].
+//
+// Input rows are staged through a per-warp ring of STAGES rows in shared
+// memory with cp.async: each lane copies its own two columns of eta, u, v, D
+// and reads back only those, so the ring needs no synchronisation beyond
+// cp.async.wait_group, and STAGES - 1 rows per warp are in flight while the
+// current row is computed.  The type byte of a row is loaded when the row
+// is consumed (it is first needed one row later).
 constexpr int CPL = 2;                 // columns per lane
 constexpr int WCOLS = 32 * CPL - 2;    // output columns per warp
+constexpr int WARPS = 4;               // warps per block
+template <typename T> struct Stages { static constexpr int value = 6; };
+template <> struct Stages<double> { static constexpr int value = 4; };
 
 template <typename T>
 struct Row {
     Src<T> col[CPL + 2];  // [0] = left neighbour, [1..CPL] own, [CPL+1] = right neighbour
 };
 
+__device__ __forceinline__ void cp_async(uint32_t dst, const void* src, int bytes_valid, int size)
+{
+    if (size == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(bytes_valid));
+    else if (size == 16)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes_valid));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(bytes_valid));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Per-lane column geometry (fixed for the whole strip).
+struct LaneCols {
+    int xl;             // first column of the lane
+    bool inside;        // both columns inside the grid
+    int src[CPL];       // resolved column (or -1)
+    uint8_t flip[CPL];  // x-mirror flag per column
+};
+
+// Issue the copies of source row r into ring slot `slot` (one commit group).
 template <typename T>
-__device__ __forceinline__ void load_row(const Fields<T>& f, int r, int xl, Raw<T> (&raw)[CPL])
+__device__ __forceinline__ void fetch_row(const Fields<T>& f, const LaneCols& lc, int r, uint32_t slot_addr)
 {
     uint8_t fy = 0;
-    int rr = resolve_index(r, f.ny, f.edge[2], f.edge[3], 2, fy);
-    const bool inside = xl >= 0 && xl + CPL <= f.nx;
-    if (rr >= 0 && inside) {
-        const size_t base = (size_t)rr * f.pitch + xl;
-        using V2 = typename Vec2<T>::type;
-        V2 e2 = *reinterpret_cast<const V2*>(f.eta + base);
-        V2 u2 = *reinterpret_cast<const V2*>(f.u + base);
-        V2 v2 = *reinterpret_cast<const V2*>(f.v + base);
-        V2 d2 = *reinterpret_cast<const V2*>(f.D + base);
-        uint16_t t2 = *reinterpret_cast<const uint16_t*>(f.type + base);
-        raw[0] = Raw<T>{e2.x, u2.x, v2.x, d2.x, (uint8_t)(t2 & 0xff), fy};
-        raw[1] = Raw<T>{e2.y, u2.y, v2.y, d2.y, (uint8_t)(t2 >> 8), fy};
-        return;
+    const int rr = resolve_index(r, f.ny, f.edge[2], f.edge[3], 2, fy);
+    const T* fld[4] = {f.eta, f.u, f.v, f.D};
+    constexpr uint32_t FSTRIDE = 32 * CPL * sizeof(T);  // bytes per field in a slot
+    if (rr >= 0 && lc.inside) {
+        const size_t base = (size_t)rr * f.pitch + lc.xl;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cp_async(slot_addr + q * FSTRIDE, fld[q] + base, CPL * sizeof(T), CPL * sizeof(T));
+    } else {
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) {
+            const bool ok = rr >= 0 && lc.src[k] >= 0;
+            const size_t idx = ok ? (size_t)rr * f.pitch + lc.src[k] : 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                cp_async(slot_addr + q * FSTRIDE + k * sizeof(T), fld[q] + idx, ok ? (int)sizeof(T) : 0,
+                         sizeof(T));
+        }
+    }
+    cp_async_commit();
+}
+
+// Read the staged row r back and derive its source quantities; exchange the
+// edge columns with the neighbouring lanes.
+template <typename T, int FM>
+__device__ __forceinline__ void consume_row(const Fields<T>& f, const LaneCols& lc, int r, const T* slot,
+                                            int lane, Row<T>& row)
+{
+    uint8_t fy = 0;
+    const int rr = resolve_index(r, f.ny, f.edge[2], f.edge[3], 2, fy);
+    constexpr int FE = 32 * CPL;  // elements per field in a slot
+    using V2 = typename Vec2<T>::type;
+    const V2 e2 = *reinterpret_cast<const V2*>(slot + 0 * FE + CPL * lane);
+    const V2 u2 = *reinterpret_cast<const V2*>(slot + 1 * FE + CPL * lane);
+    const V2 v2 = *reinterpret_cast<const V2*>(slot + 2 * FE + CPL * lane);
+    const V2 d2 = *reinterpret_cast<const V2*>(slot + 3 * FE + CPL * lane);
+    Raw<T> raw[CPL] = {{e2.x, u2.x, v2.x, d2.x, (uint8_t)(fy | lc.flip[0])},
+                       {e2.y, u2.y, v2.y, d2.y, (uint8_t)(fy | lc.flip[1])}};
+    uint8_t t[CPL];
+    if (rr >= 0 && lc.inside) {
+        const uint16_t t2 = *reinterpret_cast<const uint16_t*>(f.type + (size_t)rr * f.pitch + lc.xl);
+        t[0] = (uint8_t)(t2 & 0xff);
+        t[1] = (uint8_t)(t2 >> 8);
+    } else {
+#pragma unroll
+        for (int k = 0; k < CPL; ++k)
+            t[k] = (rr >= 0 && lc.src[k] >= 0) ? f.type[(size_t)rr * f.pitch + lc.src[k]] : (uint8_t)K_SOLID;
     }
 #pragma unroll
     for (int k = 0; k < CPL; ++k) {
-        uint8_t fl = fy;
-        int cc = resolve_index(xl + k, f.nx, f.edge[0], f.edge[1], 1, fl);
-        if (rr >= 0 && cc >= 0) {
-            const size_t idx = (size_t)rr * f.pitch + cc;
-            raw[k] = Raw<T>{f.eta[idx], f.u[idx], f.v[idx], f.D[idx], f.type[idx], fl};
-        } else {
-            raw[k] = Raw<T>{T(0), T(0), T(0), T(0), (uint8_t)K_SOLID, 0};
-        }
+        derive<T, FM>(f.c, raw[k], row.col[k + 1]);
+        row.col[k + 1].type = t[k];
     }
-}
-
-template <typename T>
-__device__ __forceinline__ void derive_row(const Coef<T>& c, const Raw<T> (&raw)[CPL], Row<T>& row)
-{
-#pragma unroll
-    for (int k = 0; k < CPL; ++k) derive(c, raw[k], row.col[k + 1]);
     const unsigned full = 0xffffffffu;
     // left neighbour of column 1 = last column of lane-1 (it sends o1, o2, o8)
     Src<T>& L = row.col[0];
@@ -293,7 +375,7 @@ __device__ __forceinline__ void emit_row(const Fields<T>& f, int j, int xl, int 
         const T eta1 = O::add(O::add(cC.ownh, Sh), O::fma(A, Se, O::mul(-B, Sd)));
         const T hu1 = O::fma(K.e, O::add(Sx, O::fma(A, Xe, O::mul(-B, Xd))), cC.hFx);
         const T hv1 = O::fma(K.e, O::add(Sy, O::fma(A, Ye, O::mul(-B, Yd))), cC.hFy);
-        const T inv = T(1) / O::add(Dx, eta1);
+        const T inv = O::rcp(O::add(Dx, eta1));
         T u1 = O::mul(hu1, inv), v1 = O::mul(hv1, inv);
         if ((ty & KIND_MASK) == K_NOSLIP) { u1 = T(0); v1 = T(0); }
         const size_t idx = (size_t)j * f.pitch + x;
@@ -303,48 +385,60 @@ __device__ __forceinline__ void emit_row(const Fields<T>& f, int j, int xl, int 
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128) step_fast_kernel(const Fields<T> f, int ncb, int nrb, int ty)
+template <typename T, int FM>
+__global__ void __launch_bounds__(32 * WARPS) step_fast_kernel(const Fields<T> f, int ncb, int nrb, int ty)
 {
-    const int lane = threadIdx.x & 31;
+    constexpr int S = Stages<T>::value;
+    constexpr int SLOT = 4 * 32 * CPL;  // elements of T per ring slot
+    __shared__ __align__(16) T ring[WARPS][S][SLOT];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int cb = warp % ncb, rb = warp / ncb;
     if (rb >= nrb) return;  // whole warp
-    const int xl = WCOLS * cb - 2 + CPL * lane;  // first column of this lane
+    LaneCols lc;
+    lc.xl = WCOLS * cb - 2 + CPL * lane;
+    lc.inside = lc.xl >= 0 && lc.xl + CPL <= f.nx;
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        lc.flip[k] = 0;
+        lc.src[k] = resolve_index(lc.xl + k, f.nx, f.edge[0], f.edge[1], 1, lc.flip[k]);
+    }
     const int j0 = rb * ty;
     const int j1 = min(f.ny, j0 + ty);
-    Raw<T> nxt[CPL], cur[CPL];
+    const int nrows = j1 - j0 + 2;  // source rows j0-1 .. j1
+    T(*my)[SLOT] = ring[wib];
+    const uint32_t ring_addr = (uint32_t)__cvta_generic_to_shared(&my[0][0]) + lane * CPL * sizeof(T);
+    auto slot_addr = [&](int q) { return ring_addr + (uint32_t)((q % S) * SLOT * sizeof(T)); };
+    auto slot_ptr = [&](int q) { return &my[q % S][0]; };
+    // prologue: S-1 rows in flight
+#pragma unroll
+    for (int q = 0; q < S - 1; ++q) {
+        if (q < nrows) fetch_row(f, lc, j0 - 1 + q, slot_addr(q));
+        else cp_async_commit();
+    }
+    // consume row q after issuing row q + S - 1
+    auto advance = [&](int q, Row<T>& dst) {
+        if (q + S - 1 < nrows) fetch_row(f, lc, j0 - 1 + q + S - 1, slot_addr(q + S - 1));
+        else cp_async_commit();
+        cp_async_wait<S - 1>();
+        consume_row<T, FM>(f, lc, j0 - 1 + q, slot_ptr(q), lane, dst);
+    };
     Row<T> A, B, C;
-    load_row(f, j0 - 1, xl, nxt);
-#pragma unroll
-    for (int k = 0; k < CPL; ++k) cur[k] = nxt[k];
-    load_row(f, j0, xl, nxt);
-    derive_row(f.c, cur, A);
-#pragma unroll
-    for (int k = 0; k < CPL; ++k) cur[k] = nxt[k];
-    load_row(f, j0 + 1, xl, nxt);
-    derive_row(f.c, cur, B);
+    advance(0, A);
+    advance(1, B);
     // rows rotate A -> B -> C so that no register copies of Row are needed
     for (int j = j0;; j += 3) {
-#pragma unroll
-        for (int k = 0; k < CPL; ++k) cur[k] = nxt[k];
-        if (j + 2 <= j1) load_row(f, j + 2, xl, nxt);
-        derive_row(f.c, cur, C);
-        emit_row(f, j, xl, lane, A, B, C);
+        advance(j - j0 + 2, C);
+        emit_row(f, j, lc.xl, lane, A, B, C);
         if (j + 1 >= j1) break;
-#pragma unroll
-        for (int k = 0; k < CPL; ++k) cur[k] = nxt[k];
-        if (j + 3 <= j1) load_row(f, j + 3, xl, nxt);
-        derive_row(f.c, cur, A);
-        emit_row(f, j + 1, xl, lane, B, C, A);
+        advance(j - j0 + 3, A);
+        emit_row(f, j + 1, lc.xl, lane, B, C, A);
         if (j + 2 >= j1) break;
-#pragma unroll
-        for (int k = 0; k < CPL; ++k) cur[k] = nxt[k];
-        if (j + 4 <= j1) load_row(f, j + 4, xl, nxt);
-        derive_row(f.c, cur, B);
-        emit_row(f, j + 2, xl, lane, C, A, B);
+        advance(j - j0 + 4, B);
+        emit_row(f, j + 2, lc.xl, lane, C, A, B);
         if (j + 3 >= j1) break;
     }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
