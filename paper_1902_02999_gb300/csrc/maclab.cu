@@ -477,7 +477,11 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
         }
     }
     // ---- launch geometry of the step kernel ----
-    s->ncb = (nx + 1 + WCOLS - 1) / WCOLS;
+    {
+        const int cpl = s->prec == MACLAB_F32 ? Cfg<float>::CPL : Cfg<double>::CPL;
+        const int w = s->prec == MACLAB_F32 ? strip_width<float>() : strip_width<double>();
+        s->ncb = (nx - 1 + cpl + w - 1) / w;
+    }
     s->ty = choose_tile_rows(ny, s->ncb, sms);
     s->nrb = (ny + s->ty - 1) / s->ty;
     *out = s;

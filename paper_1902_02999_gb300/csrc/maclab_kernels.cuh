@@ -90,7 +90,6 @@ struct Src {
     T o1, o2, o3, o4, o5, o6, o7, o8;
     T ownh;        // eta - h (5 G6 eta + 4 K6 |u|^2)
     T hFx, hFy;    // dt F / 2
-    uint8_t type;
 };
 
 template <typename T>
@@ -215,54 +214,70 @@ __device__ __forceinline__ int resolve_index(int i, int n, int lo_kind, int hi_k
 }
 
 // ---------------------------------------------------------------------------
-// Fast-path step kernel.  A warp owns a strip of 64 columns (2 per lane) and
-// `ty` rows; it walks the rows, keeping the source quantities of three
-// consecutive rows in registers (y neighbours) and exchanging the edge
-// columns of each lane with warp shuffles (x neighbours).  Output columns
-// are the 62 inner ones: [62 cb - 1, 62 cb + 60].
+// Fast-path step kernel.  A warp owns a strip of 32*CPL columns (CPL per
+// lane) and `ty` rows; it walks the rows, keeping the source quantities of
+// three consecutive rows in registers (y neighbours) and exchanging the edge
+// columns of each lane with warp shuffles (x neighbours).  Of the strip's
+// local columns 0 .. 32 CPL - 1, the W = 31 CPL columns 1 .. W are written:
+// strip cb covers global columns [W cb - CPL, W cb - CPL + 32 CPL) and writes
+// [W cb - CPL + 1, W cb - CPL + W].
 //
 // Input rows are staged through a per-warp ring of STAGES rows in shared
-// memory with cp.async: each lane copies its own two columns of eta, u, v, D
+// memory with cp.async: each lane copies its own CPL columns of eta, u, v, D
 // and reads back only those, so the ring needs no synchronisation beyond
 // cp.async.wait_group, and STAGES - 1 rows per warp are in flight while the
-// current row is computed.  The type byte of a row is loaded when the row
-// is consumed (it is first needed one row later).
-constexpr int CPL = 2;                 // columns per lane
-constexpr int WCOLS = 32 * CPL - 2;    // output columns per warp
-constexpr int WARPS = 4;               // warps per block
-template <typename T> struct Stages { static constexpr int value = 6; };
-template <> struct Stages<double> { static constexpr int value = 4; };
+// current row is computed.  The type bytes of a row are loaded when the row
+// is consumed and unpacked one row later, when it is the output row.
+constexpr int WARPS = 4;  // warps per block
+template <typename T> struct Cfg;
+template <> struct Cfg<float> { static constexpr int CPL = 4, STAGES = 5; };
+template <> struct Cfg<double> { static constexpr int CPL = 2, STAGES = 4; };
+template <typename T> __host__ __device__ constexpr int strip_width() { return 31 * Cfg<T>::CPL; }
+
+template <typename T, int CPL> struct VecT;
+template <> struct VecT<float, 4> { using type = float4; };
+template <> struct VecT<double, 2> { using type = double2; };
+template <int CPL> struct TypeWord;
+template <> struct TypeWord<4> { using type = uint32_t; };
+template <> struct TypeWord<2> { using type = uint16_t; };
 
 template <typename T>
 struct Row {
-    Src<T> col[CPL + 2];  // [0] = left neighbour, [1..CPL] own, [CPL+1] = right neighbour
+    Src<T> col[Cfg<T>::CPL + 2];  // [0] left neighbour, [1..CPL] own, [CPL+1] right neighbour
+    uint32_t types;               // type bytes of the lane's columns (byte k = column k)
 };
 
-__device__ __forceinline__ void cp_async(uint32_t dst, const void* src, int bytes_valid, int size)
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int bytes_valid)
 {
-    if (size == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(bytes_valid));
-    else if (size == 16)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes_valid));
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(bytes_valid));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes_valid));
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, int bytes_valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(bytes_valid));
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, int bytes_valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(bytes_valid));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 // Per-lane column geometry (fixed for the whole strip).
+template <int CPL>
 struct LaneCols {
     int xl;             // first column of the lane
-    bool inside;        // both columns inside the grid
+    bool inside;        // all CPL columns inside the grid
     int src[CPL];       // resolved column (or -1)
     uint8_t flip[CPL];  // x-mirror flag per column
 };
 
-// Issue the copies of source row r into ring slot `slot` (one commit group).
+// Issue the copies of source row r into a ring slot (one commit group).
 template <typename T>
-__device__ __forceinline__ void fetch_row(const Fields<T>& f, const LaneCols& lc, int r, uint32_t slot_addr)
+__device__ __forceinline__ void fetch_row(const Fields<T>& f, const LaneCols<Cfg<T>::CPL>& lc, int r,
+                                          uint32_t slot_addr)
 {
+    constexpr int CPL = Cfg<T>::CPL;
     uint8_t fy = 0;
     const int rr = resolve_index(r, f.ny, f.edge[2], f.edge[3], 2, fy);
     const T* fld[4] = {f.eta, f.u, f.v, f.D};
@@ -270,51 +285,54 @@ __device__ __forceinline__ void fetch_row(const Fields<T>& f, const LaneCols& lc
     if (rr >= 0 && lc.inside) {
         const size_t base = (size_t)rr * f.pitch + lc.xl;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) cp_async(slot_addr + q * FSTRIDE, fld[q] + base, CPL * sizeof(T), CPL * sizeof(T));
+        for (int q = 0; q < 4; ++q) cp_async16(slot_addr + q * FSTRIDE, fld[q] + base, 16);
     } else {
 #pragma unroll
         for (int k = 0; k < CPL; ++k) {
             const bool ok = rr >= 0 && lc.src[k] >= 0;
             const size_t idx = ok ? (size_t)rr * f.pitch + lc.src[k] : 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                cp_async(slot_addr + q * FSTRIDE + k * sizeof(T), fld[q] + idx, ok ? (int)sizeof(T) : 0,
-                         sizeof(T));
+            for (int q = 0; q < 4; ++q) {
+                if (sizeof(T) == 4)
+                    cp_async4(slot_addr + q * FSTRIDE + k * sizeof(T), fld[q] + idx, ok ? 4 : 0);
+                else
+                    cp_async8(slot_addr + q * FSTRIDE + k * sizeof(T), fld[q] + idx, ok ? 8 : 0);
+            }
         }
     }
     cp_async_commit();
 }
 
-// Read the staged row r back and derive its source quantities; exchange the
+// Read the staged row r back, derive its source quantities and exchange the
 // edge columns with the neighbouring lanes.
 template <typename T, int FM>
-__device__ __forceinline__ void consume_row(const Fields<T>& f, const LaneCols& lc, int r, const T* slot,
-                                            int lane, Row<T>& row)
+__device__ __forceinline__ void consume_row(const Fields<T>& f, const LaneCols<Cfg<T>::CPL>& lc, int r,
+                                            const T* slot, int lane, Row<T>& row)
 {
+    constexpr int CPL = Cfg<T>::CPL;
+    constexpr int FE = 32 * CPL;  // elements per field in a slot
     uint8_t fy = 0;
     const int rr = resolve_index(r, f.ny, f.edge[2], f.edge[3], 2, fy);
-    constexpr int FE = 32 * CPL;  // elements per field in a slot
-    using V2 = typename Vec2<T>::type;
-    const V2 e2 = *reinterpret_cast<const V2*>(slot + 0 * FE + CPL * lane);
-    const V2 u2 = *reinterpret_cast<const V2*>(slot + 1 * FE + CPL * lane);
-    const V2 v2 = *reinterpret_cast<const V2*>(slot + 2 * FE + CPL * lane);
-    const V2 d2 = *reinterpret_cast<const V2*>(slot + 3 * FE + CPL * lane);
-    Raw<T> raw[CPL] = {{e2.x, u2.x, v2.x, d2.x, (uint8_t)(fy | lc.flip[0])},
-                       {e2.y, u2.y, v2.y, d2.y, (uint8_t)(fy | lc.flip[1])}};
-    uint8_t t[CPL];
+    using V = typename VecT<T, CPL>::type;
+    const V* sp = reinterpret_cast<const V*>(slot + CPL * lane);
+    const V e4 = sp[0], u4 = sp[FE / CPL], v4 = sp[2 * FE / CPL], d4 = sp[3 * FE / CPL];
+    const T* e = reinterpret_cast<const T*>(&e4);
+    const T* u = reinterpret_cast<const T*>(&u4);
+    const T* v = reinterpret_cast<const T*>(&v4);
+    const T* d = reinterpret_cast<const T*>(&d4);
     if (rr >= 0 && lc.inside) {
-        const uint16_t t2 = *reinterpret_cast<const uint16_t*>(f.type + (size_t)rr * f.pitch + lc.xl);
-        t[0] = (uint8_t)(t2 & 0xff);
-        t[1] = (uint8_t)(t2 >> 8);
+        row.types = *reinterpret_cast<const typename TypeWord<CPL>::type*>(f.type + (size_t)rr * f.pitch + lc.xl);
     } else {
+        uint32_t t = 0;
 #pragma unroll
         for (int k = 0; k < CPL; ++k)
-            t[k] = (rr >= 0 && lc.src[k] >= 0) ? f.type[(size_t)rr * f.pitch + lc.src[k]] : (uint8_t)K_SOLID;
+            if (rr >= 0 && lc.src[k] >= 0) t |= (uint32_t)f.type[(size_t)rr * f.pitch + lc.src[k]] << (8 * k);
+        row.types = t;
     }
 #pragma unroll
     for (int k = 0; k < CPL; ++k) {
-        derive<T, FM>(f.c, raw[k], row.col[k + 1]);
-        row.col[k + 1].type = t[k];
+        const Raw<T> raw = {e[k], u[k], v[k], d[k], (uint8_t)(fy | lc.flip[k])};
+        derive<T, FM>(f.c, raw, row.col[k + 1]);
     }
     const unsigned full = 0xffffffffu;
     // left neighbour of column 1 = last column of lane-1 (it sends o1, o2, o8)
@@ -340,18 +358,23 @@ template <typename T>
 __device__ __forceinline__ void emit_row(const Fields<T>& f, int j, int xl, int lane,
                                          const Row<T>& m, const Row<T>& c, const Row<T>& p)
 {
+    constexpr int CPL = Cfg<T>::CPL;
+    constexpr int W = strip_width<T>();
     const Coef<T>& K = f.c;
+    using O = Op<T>;
+    T oe[CPL], ou[CPL], ov[CPL];
+    unsigned okmask = 0;
 #pragma unroll
     for (int k = 1; k <= CPL; ++k) {
+        const int loc = CPL * lane + k - 1;  // local column in the strip
         const int x = xl + k - 1;
-        const bool edge_col = (lane == 0 && k == 1) || (lane == 31 && k == CPL);
-        const uint8_t ty = c.col[k].type;
-        if (edge_col || x < 0 || x >= f.nx || j >= f.ny) continue;
-        if ((ty & KIND_MASK) == K_SOLID || (ty & GENERAL_BIT)) continue;
+        const uint8_t ty = (uint8_t)(c.types >> (8 * (k - 1)));
+        const bool ok = loc >= 1 && loc <= W && x >= 0 && x < f.nx && (ty & KIND_MASK) != K_SOLID &&
+                        !(ty & GENERAL_BIT);
+        okmask |= (ok ? 1u : 0u) << (k - 1);
         const Src<T>& mL = m.col[k - 1]; const Src<T>& mC = m.col[k]; const Src<T>& mR = m.col[k + 1];
         const Src<T>& cL = c.col[k - 1]; const Src<T>& cC = c.col[k]; const Src<T>& cR = c.col[k + 1];
         const Src<T>& pL = p.col[k - 1]; const Src<T>& pC = p.col[k]; const Src<T>& pR = p.col[k + 1];
-        using O = Op<T>;
         // streamed equilibria
         const T OL = O::add(O::add(cL.o1, mL.o2), pL.o8);
         const T OR = O::add(O::add(cR.o5, mR.o4), pR.o6);
@@ -376,27 +399,42 @@ __device__ __forceinline__ void emit_row(const Fields<T>& f, int j, int xl, int 
         const T hu1 = O::fma(K.e, O::add(Sx, O::fma(A, Xe, O::mul(-B, Xd))), cC.hFx);
         const T hv1 = O::fma(K.e, O::add(Sy, O::fma(A, Ye, O::mul(-B, Yd))), cC.hFy);
         const T inv = O::rcp(O::add(Dx, eta1));
-        T u1 = O::mul(hu1, inv), v1 = O::mul(hv1, inv);
-        if ((ty & KIND_MASK) == K_NOSLIP) { u1 = T(0); v1 = T(0); }
-        const size_t idx = (size_t)j * f.pitch + x;
-        f.eta1[idx] = eta1;
-        f.u1[idx] = u1;
-        f.v1[idx] = v1;
+        const bool noslip = (ty & KIND_MASK) == K_NOSLIP;
+        oe[k - 1] = eta1;
+        ou[k - 1] = noslip ? T(0) : O::mul(hu1, inv);
+        ov[k - 1] = noslip ? T(0) : O::mul(hv1, inv);
+    }
+    if (j >= f.ny || okmask == 0) return;
+    const size_t row0 = (size_t)j * f.pitch;
+    using V = typename VecT<T, CPL>::type;
+    if (okmask == (1u << CPL) - 1) {
+        *reinterpret_cast<V*>(f.eta1 + row0 + xl) = *reinterpret_cast<const V*>(oe);
+        *reinterpret_cast<V*>(f.u1 + row0 + xl) = *reinterpret_cast<const V*>(ou);
+        *reinterpret_cast<V*>(f.v1 + row0 + xl) = *reinterpret_cast<const V*>(ov);
+    } else {
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) {
+            if (okmask & (1u << k)) {
+                f.eta1[row0 + xl + k] = oe[k];
+                f.u1[row0 + xl + k] = ou[k];
+                f.v1[row0 + xl + k] = ov[k];
+            }
+        }
     }
 }
 
 template <typename T, int FM>
 __global__ void __launch_bounds__(32 * WARPS) step_fast_kernel(const Fields<T> f, int ncb, int nrb, int ty)
 {
-    constexpr int S = Stages<T>::value;
+    constexpr int CPL = Cfg<T>::CPL, S = Cfg<T>::STAGES;
     constexpr int SLOT = 4 * 32 * CPL;  // elements of T per ring slot
     __shared__ __align__(16) T ring[WARPS][S][SLOT];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int cb = warp % ncb, rb = warp / ncb;
     if (rb >= nrb) return;  // whole warp
-    LaneCols lc;
-    lc.xl = WCOLS * cb - 2 + CPL * lane;
+    LaneCols<CPL> lc;
+    lc.xl = strip_width<T>() * cb - CPL + CPL * lane;
     lc.inside = lc.xl >= 0 && lc.xl + CPL <= f.nx;
 #pragma unroll
     for (int k = 0; k < CPL; ++k) {
@@ -408,33 +446,38 @@ __global__ void __launch_bounds__(32 * WARPS) step_fast_kernel(const Fields<T> f
     const int nrows = j1 - j0 + 2;  // source rows j0-1 .. j1
     T(*my)[SLOT] = ring[wib];
     const uint32_t ring_addr = (uint32_t)__cvta_generic_to_shared(&my[0][0]) + lane * CPL * sizeof(T);
-    auto slot_addr = [&](int q) { return ring_addr + (uint32_t)((q % S) * SLOT * sizeof(T)); };
-    auto slot_ptr = [&](int q) { return &my[q % S][0]; };
+    constexpr uint32_t SLOT_BYTES = SLOT * sizeof(T);
     // prologue: S-1 rows in flight
 #pragma unroll
     for (int q = 0; q < S - 1; ++q) {
-        if (q < nrows) fetch_row(f, lc, j0 - 1 + q, slot_addr(q));
+        if (q < nrows) fetch_row(f, lc, j0 - 1 + q, ring_addr + q * SLOT_BYTES);
         else cp_async_commit();
     }
+    int slot_c = 0;          // ring slot of the next row to consume
+    int slot_f = S - 1;      // ring slot of the next row to fetch
+    int q = 0;               // index of the next row to consume
     // consume row q after issuing row q + S - 1
-    auto advance = [&](int q, Row<T>& dst) {
-        if (q + S - 1 < nrows) fetch_row(f, lc, j0 - 1 + q + S - 1, slot_addr(q + S - 1));
+    auto advance = [&](Row<T>& dst) {
+        if (q + S - 1 < nrows) fetch_row(f, lc, j0 - 1 + q + S - 1, ring_addr + slot_f * SLOT_BYTES);
         else cp_async_commit();
         cp_async_wait<S - 1>();
-        consume_row<T, FM>(f, lc, j0 - 1 + q, slot_ptr(q), lane, dst);
+        consume_row<T, FM>(f, lc, j0 - 1 + q, &my[slot_c][0], lane, dst);
+        slot_c = slot_c == S - 1 ? 0 : slot_c + 1;
+        slot_f = slot_f == S - 1 ? 0 : slot_f + 1;
+        ++q;
     };
     Row<T> A, B, C;
-    advance(0, A);
-    advance(1, B);
+    advance(A);
+    advance(B);
     // rows rotate A -> B -> C so that no register copies of Row are needed
     for (int j = j0;; j += 3) {
-        advance(j - j0 + 2, C);
+        advance(C);
         emit_row(f, j, lc.xl, lane, A, B, C);
         if (j + 1 >= j1) break;
-        advance(j - j0 + 3, A);
+        advance(A);
         emit_row(f, j + 1, lc.xl, lane, B, C, A);
         if (j + 2 >= j1) break;
-        advance(j - j0 + 4, B);
+        advance(B);
         emit_row(f, j + 2, lc.xl, lane, C, A, B);
         if (j + 3 >= j1) break;
     }
