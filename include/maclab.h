@@ -199,6 +199,11 @@ int maclab_time(maclab_t sim, double* t, int64_t* n);
  * Results are bitwise identical for every value. */
 int maclab_set_tile_rows(maclab_t sim, int rows);
 
+/* Launch shape of the step kernel: rows per warp strip (>= 1) and a cap on
+ * the number of 128-thread blocks (0 = one warp per strip; otherwise warps
+ * walk the strips in turn).  Tuning only: results are bitwise identical. */
+int maclab_set_launch(maclab_t sim, int rows, int blocks);
+
 /* Kernel timing for benchmarks.  While enabled (on != 0), every step
  * records a CUDA event pair around the launch of the fused step kernel on
  * the handle's stream.  maclab_get_profile synchronises, adds up the

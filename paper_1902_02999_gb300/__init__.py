@@ -219,6 +219,12 @@ class Simulation:
         self._check(self._lib.maclab_set_tile_rows(self._h, int(rows)))
         self.info["tile_rows"] = min(int(rows), self.ny)
 
+    def set_launch(self, rows: int, blocks: int = 0) -> None:
+        """Rows per warp strip and a cap on step-kernel blocks (0 = none)."""
+        self._check(self._lib.maclab_set_launch(self._h, int(rows), int(blocks)))
+        self.info["tile_rows"] = min(int(rows), self.ny)
+        self.info["grid_blocks"] = int(blocks)
+
     def set_profiling(self, on: bool) -> None:
         self._check(self._lib.maclab_set_profiling(self._h, 1 if on else 0))
 

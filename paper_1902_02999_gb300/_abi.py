@@ -61,6 +61,7 @@ PROTOTYPES = [
                                      P(c_double)]),
     ("maclab_time", c_int, [c_void_p, P(c_double), P(c_int64)]),
     ("maclab_set_tile_rows", c_int, [c_void_p, c_int]),
+    ("maclab_set_launch", c_int, [c_void_p, c_int, c_int]),
     ("maclab_set_profiling", c_int, [c_void_p, c_int]),
     ("maclab_get_profile", c_int, [c_void_p, P(c_double), P(c_int64)]),
     ("maclab_get_info", c_int, [c_void_p, P(Info)]),
@@ -80,7 +81,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     with _lock:
         if _lib is None:
             path = _build.LIB
-            if build_if_missing:
+            if os.environ.get("MACLAB_LIB"):
+                # an alternative build of the same sources (tuning experiments)
+                path = os.environ["MACLAB_LIB"]
+            elif build_if_missing:
                 path = _build.build()
             if not os.path.exists(path):
                 raise RuntimeError("maclab CUDA library not built: %s (run build())" % path)

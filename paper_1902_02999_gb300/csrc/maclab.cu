@@ -63,6 +63,7 @@ struct maclab_s {
     int red_blocks = 0;
     int ncb = 0, nrb = 0, ty = 0;
     int fmode = 0;             // force terms present: F_WIND | F_FRICTION | F_CORIOLIS
+    int grid_blocks = 0;       // cap on step-kernel blocks (0 = one warp per strip)
     int64_t n_fluid = 0, n_fast = 0;
     double sumD = 0;           // sum of D64 over non-solid nodes
     size_t device_bytes = 0;
@@ -164,7 +165,8 @@ int launch_step(maclab_t s)
 {
     const Fields<T> f = make_fields<T>(s);
     const int warps = s->ncb * s->nrb;
-    const int blocks = (warps + WARPS - 1) / WARPS;
+    int blocks = (warps + WARPS - 1) / WARPS;
+    if (s->grid_blocks > 0) blocks = std::min(blocks, s->grid_blocks);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (s->profiling) {
         while (s->events.size() < s->events_used + 2) {
@@ -572,10 +574,16 @@ int maclab_time(maclab_t s, double* t, int64_t* n)
 
 int maclab_set_tile_rows(maclab_t s, int rows)
 {
+    return maclab_set_launch(s, rows, s ? s->grid_blocks : 0);
+}
+
+int maclab_set_launch(maclab_t s, int rows, int blocks)
+{
     if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
-    if (rows < 1) return fail(s, MACLAB_E_ARG, "rows must be >= 1");
+    if (rows < 1 || blocks < 0) return fail(s, MACLAB_E_ARG, "rows must be >= 1 and blocks >= 0");
     s->ty = std::min(rows, s->grid.ny);
     s->nrb = (s->grid.ny + s->ty - 1) / s->ty;
+    s->grid_blocks = blocks;
     return MACLAB_OK;
 }
 

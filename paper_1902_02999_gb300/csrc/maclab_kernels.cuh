@@ -228,14 +228,25 @@ __device__ __forceinline__ int resolve_index(int i, int n, int lo_kind, int hi_k
 // cp.async.wait_group, and STAGES - 1 rows per warp are in flight while the
 // current row is computed.  The type bytes of a row are loaded when the row
 // is consumed and unpacked one row later, when it is the output row.
+// Build-time tuning knobs (defaults are the measured best on GB300).
+#ifndef MACLAB_F32_CPL
+#define MACLAB_F32_CPL 4
+#endif
+#ifndef MACLAB_F32_STAGES
+#define MACLAB_F32_STAGES 5
+#endif
+#ifndef MACLAB_MIN_BLOCKS
+#define MACLAB_MIN_BLOCKS 1
+#endif
 constexpr int WARPS = 4;  // warps per block
 template <typename T> struct Cfg;
-template <> struct Cfg<float> { static constexpr int CPL = 4, STAGES = 5; };
+template <> struct Cfg<float> { static constexpr int CPL = MACLAB_F32_CPL, STAGES = MACLAB_F32_STAGES; };
 template <> struct Cfg<double> { static constexpr int CPL = 2, STAGES = 4; };
 template <typename T> __host__ __device__ constexpr int strip_width() { return 31 * Cfg<T>::CPL; }
 
 template <typename T, int CPL> struct VecT;
 template <> struct VecT<float, 4> { using type = float4; };
+template <> struct VecT<float, 2> { using type = float2; };
 template <> struct VecT<double, 2> { using type = double2; };
 template <int CPL> struct TypeWord;
 template <> struct TypeWord<4> { using type = uint32_t; };
@@ -285,7 +296,10 @@ __device__ __forceinline__ void fetch_row(const Fields<T>& f, const LaneCols<Cfg
     if (rr >= 0 && lc.inside) {
         const size_t base = (size_t)rr * f.pitch + lc.xl;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) cp_async16(slot_addr + q * FSTRIDE, fld[q] + base, 16);
+        for (int q = 0; q < 4; ++q) {
+            if (CPL * sizeof(T) == 16) cp_async16(slot_addr + q * FSTRIDE, fld[q] + base, 16);
+            else cp_async8(slot_addr + q * FSTRIDE, fld[q] + base, 8);
+        }
     } else {
 #pragma unroll
         for (int k = 0; k < CPL; ++k) {
@@ -423,16 +437,13 @@ __device__ __forceinline__ void emit_row(const Fields<T>& f, int j, int xl, int 
     }
 }
 
+// One strip: rows [j0, j1) of column strip cb.
 template <typename T, int FM>
-__global__ void __launch_bounds__(32 * WARPS) step_fast_kernel(const Fields<T> f, int ncb, int nrb, int ty)
+__device__ __forceinline__ void step_strip(const Fields<T>& f, int cb, int j0, int j1, int lane,
+                                           T (*my)[4 * 32 * Cfg<T>::CPL])
 {
     constexpr int CPL = Cfg<T>::CPL, S = Cfg<T>::STAGES;
     constexpr int SLOT = 4 * 32 * CPL;  // elements of T per ring slot
-    __shared__ __align__(16) T ring[WARPS][S][SLOT];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-    const int cb = warp % ncb, rb = warp / ncb;
-    if (rb >= nrb) return;  // whole warp
     LaneCols<CPL> lc;
     lc.xl = strip_width<T>() * cb - CPL + CPL * lane;
     lc.inside = lc.xl >= 0 && lc.xl + CPL <= f.nx;
@@ -441,10 +452,7 @@ __global__ void __launch_bounds__(32 * WARPS) step_fast_kernel(const Fields<T> f
         lc.flip[k] = 0;
         lc.src[k] = resolve_index(lc.xl + k, f.nx, f.edge[0], f.edge[1], 1, lc.flip[k]);
     }
-    const int j0 = rb * ty;
-    const int j1 = min(f.ny, j0 + ty);
     const int nrows = j1 - j0 + 2;  // source rows j0-1 .. j1
-    T(*my)[SLOT] = ring[wib];
     const uint32_t ring_addr = (uint32_t)__cvta_generic_to_shared(&my[0][0]) + lane * CPL * sizeof(T);
     constexpr uint32_t SLOT_BYTES = SLOT * sizeof(T);
     // prologue: S-1 rows in flight
@@ -482,6 +490,25 @@ __global__ void __launch_bounds__(32 * WARPS) step_fast_kernel(const Fields<T> f
         if (j + 3 >= j1) break;
     }
     cp_async_wait<0>();
+}
+
+// Warps take strips (cb, rb) in turn; with a grid smaller than the strip
+// count each warp walks several strips (persistent launch).
+template <typename T, int FM>
+__global__ void __launch_bounds__(32 * WARPS, MACLAB_MIN_BLOCKS)
+step_fast_kernel(const Fields<T> f, int ncb, int nrb, int ty)
+{
+    constexpr int S = Cfg<T>::STAGES;
+    constexpr int SLOT = 4 * 32 * Cfg<T>::CPL;
+    __shared__ __align__(16) T ring[WARPS][S][SLOT];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nwarps = (int)(gridDim.x * (blockDim.x >> 5));
+    const int nstrips = ncb * nrb;
+    for (int strip = (int)(blockIdx.x * (blockDim.x >> 5)) + wib; strip < nstrips; strip += nwarps) {
+        const int cb = strip % ncb, rb = strip / ncb;
+        const int j0 = rb * ty;
+        step_strip<T, FM>(f, cb, j0, min(f.ny, j0 + ty), lane, ring[wib]);
+    }
 }
 
 // ---------------------------------------------------------------------------
