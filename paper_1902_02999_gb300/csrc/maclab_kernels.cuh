@@ -243,6 +243,12 @@ template <typename T> struct Cfg;
 template <> struct Cfg<float> { static constexpr int CPL = MACLAB_F32_CPL, STAGES = MACLAB_F32_STAGES; };
 template <> struct Cfg<double> { static constexpr int CPL = 2, STAGES = 4; };
 template <typename T> __host__ __device__ constexpr int strip_width() { return 31 * Cfg<T>::CPL; }
+// elements of T per ring slot: 4 fields of 32 CPL values, plus 32 CPL type
+// bytes when CPL == 4 (rounded up to whole elements)
+template <typename T> __host__ __device__ constexpr int slot_elems()
+{
+    return 4 * 32 * Cfg<T>::CPL + (Cfg<T>::CPL == 4 ? (32 * Cfg<T>::CPL + (int)sizeof(T) - 1) / (int)sizeof(T) : 0);
+}
 
 template <typename T, int CPL> struct VecT;
 template <> struct VecT<float, 4> { using type = float4; };
@@ -283,35 +289,54 @@ struct LaneCols {
     uint8_t flip[CPL];  // x-mirror flag per column
 };
 
+// Edge lanes (a column outside the grid or a wrapped / mirrored row): one
+// element at a time, resolved through the edge kinds; zero-filled where the
+// source lies behind a wall.  Kept out of line so the interior loop stays small.
+template <typename T>
+__device__ __noinline__ void fetch_row_edge(const Fields<T>& f, const LaneCols<Cfg<T>::CPL>& lc, int rr,
+                                            uint32_t slot_addr)
+{
+    constexpr int CPL = Cfg<T>::CPL;
+    const T* fld[4] = {f.eta, f.u, f.v, f.D};
+    constexpr uint32_t FSTRIDE = 32 * CPL * sizeof(T);  // bytes per field in a slot
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        const bool ok = rr >= 0 && lc.src[k] >= 0;
+        const size_t idx = ok ? (size_t)rr * f.pitch + lc.src[k] : 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (sizeof(T) == 4)
+                cp_async4(slot_addr + q * FSTRIDE + k * sizeof(T), fld[q] + idx, ok ? 4 : 0);
+            else
+                cp_async8(slot_addr + q * FSTRIDE + k * sizeof(T), fld[q] + idx, ok ? 8 : 0);
+        }
+    }
+}
+
 // Issue the copies of source row r into a ring slot (one commit group).
+// Slot layout: eta, u, v, D (32 CPL elements each), then the type bytes
+// (32 CPL bytes) when CPL == 4.
 template <typename T>
 __device__ __forceinline__ void fetch_row(const Fields<T>& f, const LaneCols<Cfg<T>::CPL>& lc, int r,
-                                          uint32_t slot_addr)
+                                          uint32_t slot_addr, uint32_t type_addr)
 {
     constexpr int CPL = Cfg<T>::CPL;
     uint8_t fy = 0;
     const int rr = resolve_index(r, f.ny, f.edge[2], f.edge[3], 2, fy);
-    const T* fld[4] = {f.eta, f.u, f.v, f.D};
     constexpr uint32_t FSTRIDE = 32 * CPL * sizeof(T);  // bytes per field in a slot
     if (rr >= 0 && lc.inside) {
         const size_t base = (size_t)rr * f.pitch + lc.xl;
+        const T* fld[4] = {f.eta, f.u, f.v, f.D};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             if (CPL * sizeof(T) == 16) cp_async16(slot_addr + q * FSTRIDE, fld[q] + base, 16);
             else cp_async8(slot_addr + q * FSTRIDE, fld[q] + base, 8);
         }
+        if (CPL == 4) cp_async4(type_addr, f.type + base, 4);
     } else {
-#pragma unroll
-        for (int k = 0; k < CPL; ++k) {
-            const bool ok = rr >= 0 && lc.src[k] >= 0;
-            const size_t idx = ok ? (size_t)rr * f.pitch + lc.src[k] : 0;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (sizeof(T) == 4)
-                    cp_async4(slot_addr + q * FSTRIDE + k * sizeof(T), fld[q] + idx, ok ? 4 : 0);
-                else
-                    cp_async8(slot_addr + q * FSTRIDE + k * sizeof(T), fld[q] + idx, ok ? 8 : 0);
-            }
+        fetch_row_edge(f, lc, rr, slot_addr);
+        if (CPL == 4) {
+            // the type word of an edge lane is assembled at consume time
         }
     }
     cp_async_commit();
@@ -335,7 +360,10 @@ __device__ __forceinline__ void consume_row(const Fields<T>& f, const LaneCols<C
     const T* v = reinterpret_cast<const T*>(&v4);
     const T* d = reinterpret_cast<const T*>(&d4);
     if (rr >= 0 && lc.inside) {
-        row.types = *reinterpret_cast<const typename TypeWord<CPL>::type*>(f.type + (size_t)rr * f.pitch + lc.xl);
+        if (CPL == 4)
+            row.types = *reinterpret_cast<const uint32_t*>(reinterpret_cast<const uint8_t*>(slot + 4 * FE) + CPL * lane);
+        else
+            row.types = *reinterpret_cast<const typename TypeWord<CPL>::type*>(f.type + (size_t)rr * f.pitch + lc.xl);
     } else {
         uint32_t t = 0;
 #pragma unroll
@@ -440,10 +468,10 @@ __device__ __forceinline__ void emit_row(const Fields<T>& f, int j, int xl, int 
 // One strip: rows [j0, j1) of column strip cb.
 template <typename T, int FM>
 __device__ __forceinline__ void step_strip(const Fields<T>& f, int cb, int j0, int j1, int lane,
-                                           T (*my)[4 * 32 * Cfg<T>::CPL])
+                                           T (*my)[slot_elems<T>()])
 {
     constexpr int CPL = Cfg<T>::CPL, S = Cfg<T>::STAGES;
-    constexpr int SLOT = 4 * 32 * CPL;  // elements of T per ring slot
+    constexpr int SLOT = slot_elems<T>();  // elements of T per ring slot
     LaneCols<CPL> lc;
     lc.xl = strip_width<T>() * cb - CPL + CPL * lane;
     lc.inside = lc.xl >= 0 && lc.xl + CPL <= f.nx;
@@ -454,11 +482,12 @@ __device__ __forceinline__ void step_strip(const Fields<T>& f, int cb, int j0, i
     }
     const int nrows = j1 - j0 + 2;  // source rows j0-1 .. j1
     const uint32_t ring_addr = (uint32_t)__cvta_generic_to_shared(&my[0][0]) + lane * CPL * sizeof(T);
+    const uint32_t type_off = 4 * 32 * CPL * sizeof(T) - lane * CPL * sizeof(T) + lane * CPL;
     constexpr uint32_t SLOT_BYTES = SLOT * sizeof(T);
     // prologue: S-1 rows in flight
 #pragma unroll
     for (int q = 0; q < S - 1; ++q) {
-        if (q < nrows) fetch_row(f, lc, j0 - 1 + q, ring_addr + q * SLOT_BYTES);
+        if (q < nrows) fetch_row(f, lc, j0 - 1 + q, ring_addr + q * SLOT_BYTES, ring_addr + q * SLOT_BYTES + type_off);
         else cp_async_commit();
     }
     int slot_c = 0;          // ring slot of the next row to consume
@@ -466,7 +495,9 @@ __device__ __forceinline__ void step_strip(const Fields<T>& f, int cb, int j0, i
     int q = 0;               // index of the next row to consume
     // consume row q after issuing row q + S - 1
     auto advance = [&](Row<T>& dst) {
-        if (q + S - 1 < nrows) fetch_row(f, lc, j0 - 1 + q + S - 1, ring_addr + slot_f * SLOT_BYTES);
+        if (q + S - 1 < nrows)
+            fetch_row(f, lc, j0 - 1 + q + S - 1, ring_addr + slot_f * SLOT_BYTES,
+                      ring_addr + slot_f * SLOT_BYTES + type_off);
         else cp_async_commit();
         cp_async_wait<S - 1>();
         consume_row<T, FM>(f, lc, j0 - 1 + q, &my[slot_c][0], lane, dst);
@@ -499,7 +530,7 @@ __global__ void __launch_bounds__(32 * WARPS, MACLAB_MIN_BLOCKS)
 step_fast_kernel(const Fields<T> f, int ncb, int nrb, int ty)
 {
     constexpr int S = Cfg<T>::STAGES;
-    constexpr int SLOT = 4 * 32 * Cfg<T>::CPL;
+    constexpr int SLOT = slot_elems<T>();
     __shared__ __align__(16) T ring[WARPS][S][SLOT];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nwarps = (int)(gridDim.x * (blockDim.x >> 5));
