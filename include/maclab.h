@@ -185,6 +185,43 @@ int maclab_set_state(maclab_t sim, const double* h, const double* u, const doubl
  * MACLAB_E_UNSTABLE (with out filled) if out[3] > 0.  Synchronises. */
 int maclab_residual(maclab_t sim, double out[4]);
 
+/* Residual of maclab_residual, computed without allocating anything.
+ *
+ * No counterpart in the paper: this exists for callers that cannot call
+ * cudaMalloc -- for example code running under a framework or runtime that
+ * owns all device memory and hands out only its own buffers, or a loop that
+ * must not allocate while it runs.  The caller passes every input and the
+ * output; the only scratch memory (block partials and the final sums) is a
+ * static array inside this library, about 160 KB, which every GPU that
+ * loads the library holds until the process exits.
+ *
+ *   precision   : MACLAB_F32 or MACLAB_F64, the element type of the arrays.
+ *   nx, ny      : grid size; nx*ny must be <= 16,777,216, larger grids are
+ *                 rejected with MACLAB_E_ARG (the scratch holds 4096 block
+ *                 partials of 4096 nodes each).
+ *   pitch       : row length of the device arrays (>= nx), in elements.
+ *   eta_prev, u_prev, v_prev, eta_cur, u_cur, v_cur :
+ *                 device arrays [ny][pitch] of two consecutive states in the
+ *                 library's storage (eta = h - D).
+ *   D           : device array [ny][pitch], still-water depth h_ref - z_b.
+ *   type        : device uint8 [ny][pitch], maclab_node codes (only
+ *                 MACLAB_SOLID matters: solid nodes are skipped).
+ *   sum_D       : sum of D over non-solid nodes, added to the mass.
+ *   stream      : cudaStream_t to run on; the call synchronises it.
+ *   out         : host double[4], same meaning as maclab_residual.
+ * Returns MACLAB_OK, MACLAB_E_ARG, MACLAB_E_CUDA, or MACLAB_E_UNSTABLE with
+ * out filled when a value is non-finite.  The first call on a device looks
+ * up the scratch array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All
+ * calls share the one scratch array and it keeps the last call's contents
+ * (every value the reduction reads is written first by the same call), so
+ * calls that overlap on the GPU -- on different streams or host threads --
+ * race and must be serialised by the caller. */
+int maclab_residual_noalloc(int precision, int nx, int ny, int pitch, const void* eta_prev,
+                            const void* u_prev, const void* v_prev, const void* eta_cur,
+                            const void* u_cur, const void* v_cur, const void* D,
+                            const uint8_t* type, double sum_D, void* stream, double out[4]);
+
 /* Step until the residual of a step is <= tol, checking every check_every
  * steps, for at most max_steps steps.  Reports the steps taken and the last
  * residual.  Returns MACLAB_OK when converged, MACLAB_E_STATE when

@@ -57,6 +57,8 @@ PROTOTYPES = [
     ("maclab_get_state", c_int, [c_void_p, P(c_double), P(c_double), P(c_double)]),
     ("maclab_set_state", c_int, [c_void_p, P(c_double), P(c_double), P(c_double)]),
     ("maclab_residual", c_int, [c_void_p, P(c_double)]),
+    ("maclab_residual_noalloc", c_int, [c_int, c_int, c_int, c_int] + [c_void_p] * 7 +
+     [P(ctypes.c_uint8), c_double, c_void_p, P(c_double)]),
     ("maclab_run_to_steady", c_int, [c_void_p, c_double, c_int64, c_int, P(c_int64),
                                      P(c_double)]),
     ("maclab_time", c_int, [c_void_p, P(c_double), P(c_int64)]),

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -536,6 +537,97 @@ int maclab_residual(maclab_t s, double out[4])
     out[2] = std::sqrt(r[3]);
     out[3] = r[4];
     if (r[4] > 0 || !std::isfinite(out[0])) return fail(s, MACLAB_E_UNSTABLE, "non-finite values in the state");
+    return MACLAB_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Residual without any device allocation.  The block partials and the final
+// sums live in one file-scope device array instead of memory the library
+// allocates; it exists on every GPU that loads this library, from load until
+// process exit.
+namespace {
+constexpr int NOALLOC_MAX_BLOCKS = 4096;
+constexpr int NOALLOC_NODES_PER_THREAD = 16;
+constexpr int64_t NOALLOC_MAX_NODES = (int64_t)NOALLOC_MAX_BLOCKS * RED_THREADS * NOALLOC_NODES_PER_THREAD;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_MAX_BLOCKS * RED_NVAL + RED_NVAL];
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device.  The array's
+// name in host code is only a host-side stand-in, so the address must come
+// from cudaGetSymbolAddress, once per device, with that device current.
+int noalloc_scratch(double** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(nullptr, MACLAB_E_ARG, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(nullptr, e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_ptr[dev] = (double*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return MACLAB_OK;
+}
+
+template <typename T>
+void launch_noalloc(int nx, int ny, int pitch, const void* e0, const void* u0, const void* v0,
+                    const void* e1, const void* u1, const void* v1, const void* D, const uint8_t* type,
+                    double* scratch, int blocks, cudaStream_t st)
+{
+    residual_partial_kernel<T><<<blocks, RED_THREADS, 0, st>>>(
+        (const T*)e0, (const T*)u0, (const T*)v0, (const T*)e1, (const T*)u1, (const T*)v1, (const T*)D, type,
+        nx, ny, pitch, scratch);
+    residual_final_kernel<<<1, 32 * RED_NVAL, 0, st>>>(scratch, blocks,
+                                                       scratch + (size_t)NOALLOC_MAX_BLOCKS * RED_NVAL);
+}
+}  // namespace
+
+extern "C" {
+
+int maclab_residual_noalloc(int precision, int nx, int ny, int pitch, const void* eta_prev,
+                            const void* u_prev, const void* v_prev, const void* eta_cur, const void* u_cur,
+                            const void* v_cur, const void* D, const uint8_t* type, double sum_D,
+                            void* stream, double out[4])
+{
+    if (precision != MACLAB_F32 && precision != MACLAB_F64) return fail(nullptr, MACLAB_E_ARG, "unknown precision");
+    if (nx < 1 || ny < 1 || pitch < nx) return fail(nullptr, MACLAB_E_ARG, "need nx, ny >= 1 and pitch >= nx");
+    if (!eta_prev || !u_prev || !v_prev || !eta_cur || !u_cur || !v_cur || !D || !type || !out)
+        return fail(nullptr, MACLAB_E_ARG, "NULL argument");
+    const int64_t N = (int64_t)nx * ny;
+    if (N > NOALLOC_MAX_NODES)
+        return fail(nullptr, MACLAB_E_ARG,
+                    "grid too large for maclab_residual_noalloc: nx*ny must be <= 16777216 "
+                    "(its static scratch holds 4096 block partials)");
+    double* scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc != MACLAB_OK) return rc;
+    const int per_block = RED_THREADS * NOALLOC_NODES_PER_THREAD;
+    const int blocks = (int)std::max<int64_t>(1, (N + per_block - 1) / per_block);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == MACLAB_F32)
+        launch_noalloc<float>(nx, ny, pitch, eta_prev, u_prev, v_prev, eta_cur, u_cur, v_cur, D, type, scratch,
+                              blocks, st);
+    else
+        launch_noalloc<double>(nx, ny, pitch, eta_prev, u_prev, v_prev, eta_cur, u_cur, v_cur, D, type, scratch,
+                               blocks, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "residual_noalloc launch");
+    double r[RED_NVAL];
+    e = cudaMemcpyAsync(r, scratch + (size_t)NOALLOC_MAX_BLOCKS * RED_NVAL, sizeof(r), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "residual_noalloc");
+    out[0] = r[1] > 0 ? std::sqrt(r[0]) / std::sqrt(r[1]) : 0.0;
+    out[1] = sum_D + r[2];
+    out[2] = std::sqrt(r[3]);
+    out[3] = r[4];
+    if (r[4] > 0 || !std::isfinite(out[0])) return fail(nullptr, MACLAB_E_UNSTABLE, "non-finite values in the state");
     return MACLAB_OK;
 }
 
