@@ -65,6 +65,7 @@ struct maclab_s {
     int ncb = 0, nrb = 0, ty = 0;
     int fmode = 0;             // force terms present: F_WIND | F_FRICTION | F_CORIOLIS
     int grid_blocks = 0;       // cap on step-kernel blocks (0 = one warp per strip)
+    bool use_tile = true;      // tile kernel (default) or warp-strip kernel
     int64_t n_fluid = 0, n_fast = 0;
     double sumD = 0;           // sum of D64 over non-solid nodes
     size_t device_bytes = 0;
@@ -180,11 +181,22 @@ int launch_step(maclab_t s)
         s->events_used += 2;
         cudaEventRecord(ev0, s->stream);
     }
-    switch (s->fmode) {  // compile-time variants for the force terms present
+    if (s->use_tile) {
+        const int tx = (s->grid.nx + tile::TX - 1) / tile::TX, ty = (s->grid.ny + tile::TY - 1) / tile::TY;
+        const size_t smem = sizeof(tile::Smem<T>);
+        switch (s->fmode) {  // compile-time variants for the force terms present
+#define MACLAB_FM(m) \
+    case m: step_tile_kernel<T, m><<<tx * ty, tile::THREADS, smem, s->stream>>>(f, tx); break;
+            MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
+#undef MACLAB_FM
+        }
+    } else {
+        switch (s->fmode) {
 #define MACLAB_FM(m) \
     case m: step_fast_kernel<T, m><<<blocks, 32 * WARPS, 0, s->stream>>>(f, s->ncb, s->nrb, s->ty); break;
-        MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
+            MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
 #undef MACLAB_FM
+        }
     }
     if (s->profiling) cudaEventRecord(ev1, s->stream);
     if (s->n_general > 0)
@@ -477,6 +489,31 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
             release_all(s);
             delete s;
             return rc;
+        }
+    }
+    // ---- shared memory of the tile kernel (above the 48 KB default for FP64) ----
+    {
+#ifdef MACLAB_STRIP_KERNEL
+        s->use_tile = false;
+#endif
+        cudaError_t ae = cudaSuccess;
+#define MACLAB_ATTR(T, m)                                                                                  \
+    if (ae == cudaSuccess)                                                                                 \
+        ae = cudaFuncSetAttribute(step_tile_kernel<T, m>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  (int)sizeof(tile::Smem<T>));
+        if (s->prec == MACLAB_F32) {
+            MACLAB_ATTR(float, 0) MACLAB_ATTR(float, 1) MACLAB_ATTR(float, 2) MACLAB_ATTR(float, 3)
+            MACLAB_ATTR(float, 4) MACLAB_ATTR(float, 5) MACLAB_ATTR(float, 6) MACLAB_ATTR(float, 7)
+        } else {
+            MACLAB_ATTR(double, 0) MACLAB_ATTR(double, 1) MACLAB_ATTR(double, 2) MACLAB_ATTR(double, 3)
+            MACLAB_ATTR(double, 4) MACLAB_ATTR(double, 5) MACLAB_ATTR(double, 6) MACLAB_ATTR(double, 7)
+        }
+#undef MACLAB_ATTR
+        if (ae != cudaSuccess) {
+            cuda_fail(nullptr, ae, "cudaFuncSetAttribute");
+            release_all(s);
+            delete s;
+            return MACLAB_E_CUDA;
         }
     }
     // ---- launch geometry of the step kernel ----

@@ -543,6 +543,190 @@ step_fast_kernel(const Fields<T> f, int ncb, int nrb, int ty)
 }
 
 // ---------------------------------------------------------------------------
+// Tile step kernel (the default fast path).  A 256-thread block updates a
+// tile of TX x TY = 64 x 16 nodes in two phases:
+//   A. every thread loads node pairs of the tile plus its one-node halo
+//      (68 x 18 nodes), derives their source quantities and writes the eight
+//      outgoing values and (eta, D) to shared memory; the pairs a thread will
+//      update stay in its registers (own term, dt F / 2, node type);
+//   B. after one barrier every thread gathers, for each of its 2 x 2 nodes,
+//      the eight incoming values and the eta / D stencils from shared memory
+//      and writes eta, u, v.
+// Shared memory per block: 8 x 18 x 68 outgoing values + 18 x 68 (eta, D).
+namespace tile {
+constexpr int TX = 64, TY = 16;            // nodes updated per block
+constexpr int THREADS = 256;               // 32 x 8
+constexpr int PC = TX / 2 + 2;             // 34 node pairs per tile row (with halo)
+constexpr int IR = TY + 2;                 // 18 tile rows (with halo)
+constexpr int IW = 2 * PC;                 // 68 tile columns
+constexpr int HALO_PAIRS = 2 * IR + 2 * (PC - 2);  // 100
+template <typename T>
+struct Smem {
+    T o[8][IR][IW];                        // outgoing values o_1 .. o_8
+    typename Vec2<T>::type ed[IR][IW];     // (eta, D)
+};
+// blocks per SM the register budget is sized for (shared memory allows
+// 4 FP32 blocks and 2 FP64 blocks)
+template <typename T> struct MinBlocks { static constexpr int value = 3; };
+template <> struct MinBlocks<double> { static constexpr int value = 2; };
+}  // namespace tile
+
+template <typename T>
+__device__ __forceinline__ void load_pair(const Fields<T>& f, int y, int x, Raw<T> (&raw)[2], uint32_t& types)
+{
+    uint8_t fy = 0;
+    const int rr = resolve_index(y, f.ny, f.edge[2], f.edge[3], 2, fy);
+    if (rr >= 0 && x >= 0 && x + 2 <= f.nx) {
+        const size_t base = (size_t)rr * f.pitch + x;
+        using V2 = typename Vec2<T>::type;
+        const V2 e2 = *reinterpret_cast<const V2*>(f.eta + base);
+        const V2 u2 = *reinterpret_cast<const V2*>(f.u + base);
+        const V2 v2 = *reinterpret_cast<const V2*>(f.v + base);
+        const V2 d2 = *reinterpret_cast<const V2*>(f.D + base);
+        types = *reinterpret_cast<const uint16_t*>(f.type + base);
+        raw[0] = Raw<T>{e2.x, u2.x, v2.x, d2.x, fy};
+        raw[1] = Raw<T>{e2.y, u2.y, v2.y, d2.y, fy};
+        return;
+    }
+    types = 0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        uint8_t fl = fy;
+        const int cc = resolve_index(x + k, f.nx, f.edge[0], f.edge[1], 1, fl);
+        if (rr >= 0 && cc >= 0) {
+            const size_t idx = (size_t)rr * f.pitch + cc;
+            raw[k] = Raw<T>{f.eta[idx], f.u[idx], f.v[idx], f.D[idx], fl};
+            types |= (uint32_t)f.type[idx] << (8 * k);
+        } else {
+            raw[k] = Raw<T>{T(0), T(0), T(0), T(0), 0};
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_pair(tile::Smem<T>& sm, int pr, int lc, const Src<T>& a, const Src<T>& b)
+{
+    using V2 = typename Vec2<T>::type;
+    const T oa[8] = {a.o1, a.o2, a.o3, a.o4, a.o5, a.o6, a.o7, a.o8};
+    const T ob[8] = {b.o1, b.o2, b.o3, b.o4, b.o5, b.o6, b.o7, b.o8};
+#pragma unroll
+    for (int d = 0; d < 8; ++d) *reinterpret_cast<V2*>(&sm.o[d][pr][lc]) = V2{oa[d], ob[d]};
+    sm.ed[pr][lc] = V2{a.eta, a.D};
+    sm.ed[pr][lc + 1] = V2{b.eta, b.D};
+}
+
+template <typename T, int FM>
+__global__ void __launch_bounds__(tile::THREADS, tile::MinBlocks<T>::value)
+step_tile_kernel(const Fields<T> f, int tiles_x)
+{
+    using namespace tile;
+    using O = Op<T>;
+    using V2 = typename Vec2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<T>& sm = *reinterpret_cast<Smem<T>*>(smem_raw);
+    const int tx = threadIdx.x & 31, tyy = threadIdx.x >> 5;
+    const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY;
+    // ---- phase A: own pairs (tile pair column 1 + tx, tile rows 1 + 2 tyy + r)
+    Src<T> own[2][2];
+    uint32_t own_types[2];
+    {
+        Raw<T> raw[2][2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) load_pair(f, y0 + 2 * tyy + r, x0 + 2 * tx, raw[r], own_types[r]);
+        Raw<T> hraw[2];
+        uint32_t htypes;
+        int hpr = 0, hpc = 0;
+        const bool has_halo = threadIdx.x < HALO_PAIRS;
+        if (has_halo) {
+            const int t = threadIdx.x;
+            if (t < 2 * IR) { hpc = t < IR ? 0 : PC - 1; hpr = t % IR; }
+            else { const int u = t - 2 * IR; hpr = u < PC - 2 ? 0 : IR - 1; hpc = 1 + u % (PC - 2); }
+            load_pair(f, y0 - 1 + hpr, x0 - 2 + 2 * hpc, hraw, htypes);
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            derive<T, FM>(f.c, raw[r][0], own[r][0]);
+            derive<T, FM>(f.c, raw[r][1], own[r][1]);
+            store_pair(sm, 1 + 2 * tyy + r, 2 + 2 * tx, own[r][0], own[r][1]);
+        }
+        if (has_halo) {
+            Src<T> h0, h1;
+            derive<T, FM>(f.c, hraw[0], h0);
+            derive<T, FM>(f.c, hraw[1], h1);
+            store_pair(sm, hpr, 2 * hpc, h0, h1);
+        }
+    }
+    __syncthreads();
+    // ---- phase B: nodes (x0 + 2 tx + k, y0 + 2 tyy + r)
+    const Coef<T>& K = f.c;
+    const T q = T(0.25);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int lr = 1 + 2 * tyy + r;    // tile row of the node
+        const int y = y0 + 2 * tyy + r;
+        T oe[2], ou[2], ov[2];
+        unsigned okmask = 0;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int lc = 2 + 2 * tx + k;  // tile column of the node
+            const int x = x0 + 2 * tx + k;
+            const uint8_t ty = (uint8_t)(own_types[r] >> (8 * k));
+            const bool ok = x < f.nx && y < f.ny && (ty & KIND_MASK) != K_SOLID && !(ty & GENERAL_BIT);
+            okmask |= (ok ? 1u : 0u) << k;
+            // streamed equilibria: sources x - c_a
+            const T cL_o1 = sm.o[0][lr][lc - 1], mL_o2 = sm.o[1][lr - 1][lc - 1], pL_o8 = sm.o[7][lr + 1][lc - 1];
+            const T cR_o5 = sm.o[4][lr][lc + 1], mR_o4 = sm.o[3][lr - 1][lc + 1], pR_o6 = sm.o[5][lr + 1][lc + 1];
+            const T mC_o3 = sm.o[2][lr - 1][lc], pC_o7 = sm.o[6][lr + 1][lc];
+            const V2 mL = sm.ed[lr - 1][lc - 1], mC = sm.ed[lr - 1][lc], mR = sm.ed[lr - 1][lc + 1];
+            const V2 cL = sm.ed[lr][lc - 1], cR = sm.ed[lr][lc + 1];
+            const V2 pL = sm.ed[lr + 1][lc - 1], pC = sm.ed[lr + 1][lc], pR = sm.ed[lr + 1][lc + 1];
+            const T OL = O::add(O::add(cL_o1, mL_o2), pL_o8);
+            const T OR = O::add(O::add(cR_o5, mR_o4), pR_o6);
+            const T Sh = O::add(O::add(OL, OR), O::add(mC_o3, pC_o7));
+            const T Sx = O::sub(OL, OR);
+            const T Sy = O::sub(O::add(O::add(mL_o2, mR_o4), mC_o3), O::add(O::add(pL_o8, pR_o6), pC_o7));
+            // lambda-weighted stencils of eta (.x) and D (.y): sum, x-moment, y-moment
+            const T MLe = O::fma(q, O::add(mL.x, pL.x), cL.x);
+            const T MRe = O::fma(q, O::add(mR.x, pR.x), cR.x);
+            const T MLd = O::fma(q, O::add(mL.y, pL.y), cL.y);
+            const T MRd = O::fma(q, O::add(mR.y, pR.y), cR.y);
+            const T Se = O::add(O::add(MLe, MRe), O::add(mC.x, pC.x));
+            const T Sd = O::add(O::add(MLd, MRd), O::add(mC.y, pC.y));
+            const T Xe = O::sub(MLe, MRe), Xd = O::sub(MLd, MRd);
+            const T Ye = O::fma(q, O::sub(O::add(mL.x, mR.x), O::add(pL.x, pR.x)), O::sub(mC.x, pC.x));
+            const T Yd = O::fma(q, O::sub(O::add(mL.y, mR.y), O::add(pL.y, pR.y)), O::sub(mC.y, pC.y));
+            const Src<T>& me = own[r][k];
+            const T A = O::mul(K.G6, me.D), B = O::mul(K.G6, me.eta);
+            // ownh already holds the receiver-only bed part 5 G6 eta_x D_x
+            const T eta1 = O::add(O::add(me.ownh, Sh), O::fma(A, Se, O::mul(-B, Sd)));
+            const T hu1 = O::fma(K.e, O::add(Sx, O::fma(A, Xe, O::mul(-B, Xd))), me.hFx);
+            const T hv1 = O::fma(K.e, O::add(Sy, O::fma(A, Ye, O::mul(-B, Yd))), me.hFy);
+            const T inv = O::rcp(O::add(me.D, eta1));
+            const bool noslip = (ty & KIND_MASK) == K_NOSLIP;
+            oe[k] = eta1;
+            ou[k] = noslip ? T(0) : O::mul(hu1, inv);
+            ov[k] = noslip ? T(0) : O::mul(hv1, inv);
+        }
+        if (okmask == 0) continue;
+        const size_t idx = (size_t)y * f.pitch + x0 + 2 * tx;
+        if (okmask == 3u) {
+            *reinterpret_cast<V2*>(f.eta1 + idx) = V2{oe[0], oe[1]};
+            *reinterpret_cast<V2*>(f.u1 + idx) = V2{ou[0], ou[1]};
+            *reinterpret_cast<V2*>(f.v1 + idx) = V2{ov[0], ov[1]};
+        } else {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (okmask & (1u << k)) {
+                    f.eta1[idx + k] = oe[k];
+                    f.u1[idx + k] = ou[k];
+                    f.v1[idx + k] = ov[k];
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // General-link kernel: nodes with at least one bounce-back link (next to a
 // solid node or a bounce-back edge).  Each link is resolved as in the
 // paper's boundary rules: a solid or walled-off source bounces back
