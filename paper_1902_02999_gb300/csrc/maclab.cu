@@ -66,6 +66,7 @@ struct maclab_s {
     int fmode = 0;             // force terms present: F_WIND | F_FRICTION | F_CORIOLIS
     int grid_blocks = 0;       // cap on step-kernel blocks (0 = one warp per strip)
     bool use_tile = true;      // tile kernel (default) or warp-strip kernel
+    int tile_blocks = 0;       // persistent blocks of the tile kernel
     int64_t n_fluid = 0, n_fast = 0;
     double sumD = 0;           // sum of D64 over non-solid nodes
     size_t device_bytes = 0;
@@ -183,10 +184,12 @@ int launch_step(maclab_t s)
     }
     if (s->use_tile) {
         const int tx = (s->grid.nx + tile::TX - 1) / tile::TX, ty = (s->grid.ny + tile::TY - 1) / tile::TY;
-        const size_t smem = sizeof(tile::Smem<T>);
+        const int ntiles = tx * ty;
+        const size_t smem = tile::smem_bytes<T>();
+        const int tb = std::min(ntiles, s->tile_blocks);
         switch (s->fmode) {  // compile-time variants for the force terms present
 #define MACLAB_FM(m) \
-    case m: step_tile_kernel<T, m><<<tx * ty, tile::THREADS, smem, s->stream>>>(f, tx); break;
+    case m: step_tile_kernel<T, m><<<tb, tile::THREADS, smem, s->stream>>>(f, tx, ntiles); break;
             MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
 #undef MACLAB_FM
         }
@@ -500,7 +503,7 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
 #define MACLAB_ATTR(T, m)                                                                                  \
     if (ae == cudaSuccess)                                                                                 \
         ae = cudaFuncSetAttribute(step_tile_kernel<T, m>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                  (int)sizeof(tile::Smem<T>));
+                                  (int)tile::smem_bytes<T>());
         if (s->prec == MACLAB_F32) {
             MACLAB_ATTR(float, 0) MACLAB_ATTR(float, 1) MACLAB_ATTR(float, 2) MACLAB_ATTR(float, 3)
             MACLAB_ATTR(float, 4) MACLAB_ATTR(float, 5) MACLAB_ATTR(float, 6) MACLAB_ATTR(float, 7)
@@ -516,7 +519,17 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
             return MACLAB_E_CUDA;
         }
     }
-    // ---- launch geometry of the step kernel ----
+    // ---- launch geometry of the step kernels ----
+    {
+        int per_sm = 0;
+        cudaError_t oe = s->prec == MACLAB_F32
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_tile_kernel<float, 0>, tile::THREADS,
+                                                            tile::smem_bytes<float>())
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_tile_kernel<double, 0>, tile::THREADS,
+                                                            tile::smem_bytes<double>());
+        if (oe != cudaSuccess || per_sm < 1) per_sm = 1;
+        s->tile_blocks = sms * per_sm;
+    }
     {
         const int cpl = s->prec == MACLAB_F32 ? Cfg<float>::CPL : Cfg<double>::CPL;
         const int w = s->prec == MACLAB_F32 ? strip_width<float>() : strip_width<double>();

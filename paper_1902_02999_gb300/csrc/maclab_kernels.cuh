@@ -543,187 +543,237 @@ step_fast_kernel(const Fields<T> f, int ncb, int nrb, int ty)
 }
 
 // ---------------------------------------------------------------------------
-// Tile step kernel (the default fast path).  A 256-thread block updates a
-// tile of TX x TY = 64 x 16 nodes in two phases:
-//   A. every thread loads node pairs of the tile plus its one-node halo
-//      (68 x 18 nodes), derives their source quantities and writes the eight
-//      outgoing values and (eta, D) to shared memory; the pairs a thread will
-//      update stay in its registers (own term, dt F / 2, node type);
-//   B. after one barrier every thread gathers, for each of its 2 x 2 nodes,
-//      the eight incoming values and the eta / D stencils from shared memory
-//      and writes eta, u, v.
-// Shared memory per block: 8 x 18 x 68 outgoing values + 18 x 68 (eta, D).
+// Tile step kernel (the default fast path).  A 256-thread block updates
+// tiles of TX x TY = 64 x 16 nodes; blocks are persistent and walk the tiles
+// in turn.  Per tile:
+//   0. (FP32, interior tiles) the raw rows of eta, u, v, D and the node types
+//      of the tile and its one-node halo were staged in shared memory with
+//      cp.async while the previous tile was computed (double buffer);
+//   A. every thread derives the source quantities of its nodes of the tile
+//      plus halo (68 x 18 nodes) and writes the eight outgoing values and
+//      (eta, D) to shared memory; the nodes a thread updates keep their own
+//      term, dt F / 2 and type in registers;
+//   B. after a barrier every thread gathers, for each of its four nodes, the
+//      eight incoming values and the eta / D stencils and writes eta, u, v.
+// Thread (tx, ty) of 32 x 8 owns tile columns 2 + tx and 34 + tx at tile
+// rows 1 + 2 ty and 2 + 2 ty, so every shared-memory access of a warp is
+// stride-1 (no bank conflicts) and every global access is coalesced.
+// Edge tiles (whose halo leaves the grid) load straight from global memory
+// through the edge rules.
 namespace tile {
-constexpr int TX = 64, TY = 16;            // nodes updated per block
+constexpr int TX = 64, TY = 16;            // nodes updated per tile
 constexpr int THREADS = 256;               // 32 x 8
-constexpr int PC = TX / 2 + 2;             // 34 node pairs per tile row (with halo)
 constexpr int IR = TY + 2;                 // 18 tile rows (with halo)
-constexpr int IW = 2 * PC;                 // 68 tile columns
-constexpr int HALO_PAIRS = 2 * IR + 2 * (PC - 2);  // 100
+constexpr int IW = TX + 4;                 // 68 tile columns (with halo; cols 1 and 66 are used)
+constexpr int RW = TX + 8;                 // 72 staged columns: global x0 - 4 .. x0 + 67
+constexpr int HALO = 4 * IR + 2 * TX;      // 200 halo nodes: columns 0, 1, 66, 67 and rows 0, 17
 template <typename T>
-struct Smem {
+struct Derived {
     T o[8][IR][IW];                        // outgoing values o_1 .. o_8
     typename Vec2<T>::type ed[IR][IW];     // (eta, D)
 };
-// blocks per SM the register budget is sized for (shared memory allows
-// 4 FP32 blocks and 2 FP64 blocks)
-template <typename T> struct MinBlocks { static constexpr int value = 3; };
-template <> struct MinBlocks<double> { static constexpr int value = 2; };
+template <typename T>
+struct Staged {
+    T f[4][IR][RW];                        // eta, u, v, D
+    uint8_t type[IR][RW];
+};
+template <typename T> struct Cfg;
+template <> struct Cfg<float> { static constexpr bool STAGE = true; static constexpr int MINB = 2; };
+template <> struct Cfg<double> { static constexpr bool STAGE = false; static constexpr int MINB = 2; };
+template <typename T>
+__host__ __device__ constexpr size_t smem_bytes()
+{
+    return sizeof(Derived<T>) + (Cfg<T>::STAGE ? 2 * sizeof(Staged<T>) : 0);
+}
 }  // namespace tile
 
+// One node straight from global memory through the edge rules.
 template <typename T>
-__device__ __forceinline__ void load_pair(const Fields<T>& f, int y, int x, Raw<T> (&raw)[2], uint32_t& types)
+__device__ __forceinline__ Raw<T> load_node(const Fields<T>& f, int y, int x, uint8_t& type)
 {
-    uint8_t fy = 0;
-    const int rr = resolve_index(y, f.ny, f.edge[2], f.edge[3], 2, fy);
-    if (rr >= 0 && x >= 0 && x + 2 <= f.nx) {
-        const size_t base = (size_t)rr * f.pitch + x;
-        using V2 = typename Vec2<T>::type;
-        const V2 e2 = *reinterpret_cast<const V2*>(f.eta + base);
-        const V2 u2 = *reinterpret_cast<const V2*>(f.u + base);
-        const V2 v2 = *reinterpret_cast<const V2*>(f.v + base);
-        const V2 d2 = *reinterpret_cast<const V2*>(f.D + base);
-        types = *reinterpret_cast<const uint16_t*>(f.type + base);
-        raw[0] = Raw<T>{e2.x, u2.x, v2.x, d2.x, fy};
-        raw[1] = Raw<T>{e2.y, u2.y, v2.y, d2.y, fy};
-        return;
+    uint8_t fl = 0;
+    const int rr = resolve_index(y, f.ny, f.edge[2], f.edge[3], 2, fl);
+    const int cc = resolve_index(x, f.nx, f.edge[0], f.edge[1], 1, fl);
+    if (rr >= 0 && cc >= 0) {
+        const size_t idx = (size_t)rr * f.pitch + cc;
+        type = f.type[idx];
+        return Raw<T>{f.eta[idx], f.u[idx], f.v[idx], f.D[idx], fl};
     }
-    types = 0;
+    type = K_SOLID;
+    return Raw<T>{T(0), T(0), T(0), T(0), 0};
+}
+
+template <typename T>
+__device__ __forceinline__ void store_derived(tile::Derived<T>& sm, int lr, int lc, const Src<T>& a)
+{
+    sm.o[0][lr][lc] = a.o1;
+    sm.o[1][lr][lc] = a.o2;
+    sm.o[2][lr][lc] = a.o3;
+    sm.o[3][lr][lc] = a.o4;
+    sm.o[4][lr][lc] = a.o5;
+    sm.o[5][lr][lc] = a.o6;
+    sm.o[6][lr][lc] = a.o7;
+    sm.o[7][lr][lc] = a.o8;
+    sm.ed[lr][lc] = typename Vec2<T>::type{a.eta, a.D};
+}
+
+// Issue the cp.async copies of the raw window of tile (x0, y0) into `st`.
+__device__ __forceinline__ void stage_tile(const Fields<float>& f, tile::Staged<float>& st, int x0, int y0)
+{
+    using namespace tile;
+    constexpr int CH = RW / 4;                 // 16-byte chunks per staged row: 18
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        uint8_t fl = fy;
-        const int cc = resolve_index(x + k, f.nx, f.edge[0], f.edge[1], 1, fl);
-        if (rr >= 0 && cc >= 0) {
-            const size_t idx = (size_t)rr * f.pitch + cc;
-            raw[k] = Raw<T>{f.eta[idx], f.u[idx], f.v[idx], f.D[idx], fl};
-            types |= (uint32_t)f.type[idx] << (8 * k);
-        } else {
-            raw[k] = Raw<T>{T(0), T(0), T(0), T(0), 0};
+    for (int q = 0; q < 4; ++q) {
+        const float* src = q == 0 ? f.eta : q == 1 ? f.u : q == 2 ? f.v : f.D;
+        for (int c = threadIdx.x; c < IR * CH; c += THREADS) {
+            const int r = c / CH, k = c - r * CH;
+            const size_t g = (size_t)(y0 - 1 + r) * f.pitch + (x0 - 4 + 4 * k);
+            cp_async16((uint32_t)__cvta_generic_to_shared(&st.f[q][r][4 * k]), src + g, 16);
         }
+    }
+    for (int c = threadIdx.x; c < IR * CH; c += THREADS) {
+        const int r = c / CH, k = c - r * CH;
+        const size_t g = (size_t)(y0 - 1 + r) * f.pitch + (x0 - 4 + 4 * k);
+        cp_async4((uint32_t)__cvta_generic_to_shared(&st.type[r][4 * k]), f.type + g, 4);
     }
 }
 
 template <typename T>
-__device__ __forceinline__ void store_pair(tile::Smem<T>& sm, int pr, int lc, const Src<T>& a, const Src<T>& b)
+__device__ __forceinline__ bool interior_tile(const Fields<T>& f, int x0, int y0)
 {
-    using V2 = typename Vec2<T>::type;
-    const T oa[8] = {a.o1, a.o2, a.o3, a.o4, a.o5, a.o6, a.o7, a.o8};
-    const T ob[8] = {b.o1, b.o2, b.o3, b.o4, b.o5, b.o6, b.o7, b.o8};
-#pragma unroll
-    for (int d = 0; d < 8; ++d) *reinterpret_cast<V2*>(&sm.o[d][pr][lc]) = V2{oa[d], ob[d]};
-    sm.ed[pr][lc] = V2{a.eta, a.D};
-    sm.ed[pr][lc + 1] = V2{b.eta, b.D};
+    using namespace tile;
+    return x0 - 4 >= 0 && x0 + TX + 4 <= f.nx && y0 - 1 >= 0 && y0 + TY + 1 <= f.ny;
 }
 
 template <typename T, int FM>
-__global__ void __launch_bounds__(tile::THREADS, tile::MinBlocks<T>::value)
-step_tile_kernel(const Fields<T> f, int tiles_x)
+__global__ void __launch_bounds__(tile::THREADS, tile::Cfg<T>::MINB)
+step_tile_kernel(const Fields<T> f, int tiles_x, int ntiles)
 {
     using namespace tile;
     using O = Op<T>;
-    using V2 = typename Vec2<T>::type;
+    constexpr bool STAGE = tile::Cfg<T>::STAGE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem<T>& sm = *reinterpret_cast<Smem<T>*>(smem_raw);
+    Derived<T>& sm = *reinterpret_cast<Derived<T>*>(smem_raw);
+    Staged<float>* stg = reinterpret_cast<Staged<float>*>(smem_raw + sizeof(Derived<T>));
     const int tx = threadIdx.x & 31, tyy = threadIdx.x >> 5;
-    const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY;
-    // ---- phase A: own pairs (tile pair column 1 + tx, tile rows 1 + 2 tyy + r)
-    Src<T> own[2][2];
-    uint32_t own_types[2];
-    {
-        Raw<T> raw[2][2];
-#pragma unroll
-        for (int r = 0; r < 2; ++r) load_pair(f, y0 + 2 * tyy + r, x0 + 2 * tx, raw[r], own_types[r]);
-        Raw<T> hraw[2];
-        uint32_t htypes;
-        int hpr = 0, hpc = 0;
-        const bool has_halo = threadIdx.x < HALO_PAIRS;
-        if (has_halo) {
-            const int t = threadIdx.x;
-            if (t < 2 * IR) { hpc = t < IR ? 0 : PC - 1; hpr = t % IR; }
-            else { const int u = t - 2 * IR; hpr = u < PC - 2 ? 0 : IR - 1; hpc = 1 + u % (PC - 2); }
-            load_pair(f, y0 - 1 + hpr, x0 - 2 + 2 * hpc, hraw, htypes);
+    const Coef<T>& K = f.c;
+    int t = blockIdx.x;
+    int buf = 0;
+    if (STAGE && t < ntiles) {
+        const int x0 = (t % tiles_x) * TX, y0 = (t / tiles_x) * TY;
+        if (interior_tile(f, x0, y0)) stage_tile(*reinterpret_cast<const Fields<float>*>(&f), stg[0], x0, y0);
+    }
+    if (STAGE) cp_async_commit();
+    for (; t < ntiles; t += gridDim.x, buf ^= 1) {
+        const int x0 = (t % tiles_x) * TX, y0 = (t / tiles_x) * TY;
+        const bool staged = STAGE && interior_tile(f, x0, y0);
+        if (STAGE) {
+            // prefetch the next tile of this block into the other buffer
+            const int tn = t + gridDim.x;
+            if (tn < ntiles) {
+                const int xn = (tn % tiles_x) * TX, yn = (tn / tiles_x) * TY;
+                if (interior_tile(f, xn, yn))
+                    stage_tile(*reinterpret_cast<const Fields<float>*>(&f), stg[buf ^ 1], xn, yn);
+            }
+            cp_async_commit();
+            cp_async_wait<1>();
         }
+        __syncthreads();  // staged data visible; previous tile's phase B done
+        // ---- phase A ----
+        Src<T> own[2][2];
+        uint8_t own_type[2][2];
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
-            derive<T, FM>(f.c, raw[r][0], own[r][0]);
-            derive<T, FM>(f.c, raw[r][1], own[r][1]);
-            store_pair(sm, 1 + 2 * tyy + r, 2 + 2 * tx, own[r][0], own[r][1]);
-        }
-        if (has_halo) {
-            Src<T> h0, h1;
-            derive<T, FM>(f.c, hraw[0], h0);
-            derive<T, FM>(f.c, hraw[1], h1);
-            store_pair(sm, hpr, 2 * hpc, h0, h1);
-        }
-    }
-    __syncthreads();
-    // ---- phase B: nodes (x0 + 2 tx + k, y0 + 2 tyy + r)
-    const Coef<T>& K = f.c;
-    const T q = T(0.25);
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int lr = 1 + 2 * tyy + r;    // tile row of the node
-        const int y = y0 + 2 * tyy + r;
-        T oe[2], ou[2], ov[2];
-        unsigned okmask = 0;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int lc = 2 + 2 * tx + k;  // tile column of the node
-            const int x = x0 + 2 * tx + k;
-            const uint8_t ty = (uint8_t)(own_types[r] >> (8 * k));
-            const bool ok = x < f.nx && y < f.ny && (ty & KIND_MASK) != K_SOLID && !(ty & GENERAL_BIT);
-            okmask |= (ok ? 1u : 0u) << k;
-            // streamed equilibria: sources x - c_a
-            const T cL_o1 = sm.o[0][lr][lc - 1], mL_o2 = sm.o[1][lr - 1][lc - 1], pL_o8 = sm.o[7][lr + 1][lc - 1];
-            const T cR_o5 = sm.o[4][lr][lc + 1], mR_o4 = sm.o[3][lr - 1][lc + 1], pR_o6 = sm.o[5][lr + 1][lc + 1];
-            const T mC_o3 = sm.o[2][lr - 1][lc], pC_o7 = sm.o[6][lr + 1][lc];
-            const V2 mL = sm.ed[lr - 1][lc - 1], mC = sm.ed[lr - 1][lc], mR = sm.ed[lr - 1][lc + 1];
-            const V2 cL = sm.ed[lr][lc - 1], cR = sm.ed[lr][lc + 1];
-            const V2 pL = sm.ed[lr + 1][lc - 1], pC = sm.ed[lr + 1][lc], pR = sm.ed[lr + 1][lc + 1];
-            const T OL = O::add(O::add(cL_o1, mL_o2), pL_o8);
-            const T OR = O::add(O::add(cR_o5, mR_o4), pR_o6);
-            const T Sh = O::add(O::add(OL, OR), O::add(mC_o3, pC_o7));
-            const T Sx = O::sub(OL, OR);
-            const T Sy = O::sub(O::add(O::add(mL_o2, mR_o4), mC_o3), O::add(O::add(pL_o8, pR_o6), pC_o7));
-            // lambda-weighted stencils of eta (.x) and D (.y): sum, x-moment, y-moment
-            const T MLe = O::fma(q, O::add(mL.x, pL.x), cL.x);
-            const T MRe = O::fma(q, O::add(mR.x, pR.x), cR.x);
-            const T MLd = O::fma(q, O::add(mL.y, pL.y), cL.y);
-            const T MRd = O::fma(q, O::add(mR.y, pR.y), cR.y);
-            const T Se = O::add(O::add(MLe, MRe), O::add(mC.x, pC.x));
-            const T Sd = O::add(O::add(MLd, MRd), O::add(mC.y, pC.y));
-            const T Xe = O::sub(MLe, MRe), Xd = O::sub(MLd, MRd);
-            const T Ye = O::fma(q, O::sub(O::add(mL.x, mR.x), O::add(pL.x, pR.x)), O::sub(mC.x, pC.x));
-            const T Yd = O::fma(q, O::sub(O::add(mL.y, mR.y), O::add(pL.y, pR.y)), O::sub(mC.y, pC.y));
-            const Src<T>& me = own[r][k];
-            const T A = O::mul(K.G6, me.D), B = O::mul(K.G6, me.eta);
-            // ownh already holds the receiver-only bed part 5 G6 eta_x D_x
-            const T eta1 = O::add(O::add(me.ownh, Sh), O::fma(A, Se, O::mul(-B, Sd)));
-            const T hu1 = O::fma(K.e, O::add(Sx, O::fma(A, Xe, O::mul(-B, Xd))), me.hFx);
-            const T hv1 = O::fma(K.e, O::add(Sy, O::fma(A, Ye, O::mul(-B, Yd))), me.hFy);
-            const T inv = O::rcp(O::add(me.D, eta1));
-            const bool noslip = (ty & KIND_MASK) == K_NOSLIP;
-            oe[k] = eta1;
-            ou[k] = noslip ? T(0) : O::mul(hu1, inv);
-            ov[k] = noslip ? T(0) : O::mul(hv1, inv);
-        }
-        if (okmask == 0) continue;
-        const size_t idx = (size_t)y * f.pitch + x0 + 2 * tx;
-        if (okmask == 3u) {
-            *reinterpret_cast<V2*>(f.eta1 + idx) = V2{oe[0], oe[1]};
-            *reinterpret_cast<V2*>(f.u1 + idx) = V2{ou[0], ou[1]};
-            *reinterpret_cast<V2*>(f.v1 + idx) = V2{ov[0], ov[1]};
-        } else {
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                if (okmask & (1u << k)) {
-                    f.eta1[idx + k] = oe[k];
-                    f.u1[idx + k] = ou[k];
-                    f.v1[idx + k] = ov[k];
+                const int lr = 1 + 2 * tyy + r, lc = 2 + tx + 32 * k;
+                Raw<T> raw;
+                if (staged) {
+                    const Staged<float>& st = stg[buf];
+                    raw = Raw<T>{(T)st.f[0][lr][lc + 2], (T)st.f[1][lr][lc + 2], (T)st.f[2][lr][lc + 2],
+                                 (T)st.f[3][lr][lc + 2], 0};
+                    own_type[r][k] = st.type[lr][lc + 2];
+                } else {
+                    raw = load_node(f, y0 - 1 + lr, x0 - 2 + lc, own_type[r][k]);
                 }
+                derive<T, FM>(f.c, raw, own[r][k]);
+                store_derived(sm, lr, lc, own[r][k]);
+            }
+        }
+        if (threadIdx.x < HALO) {
+            const int h = threadIdx.x;
+            int lr, lc;
+            if (h < 4 * IR) {
+                const int cs = h / IR;                    // 0..3 -> tile columns 0, 1, 66, 67
+                lc = cs < 2 ? cs : IW - 4 + cs;
+                lr = h - cs * IR;
+            } else {
+                const int u = h - 4 * IR;                 // rows 0 and 17, columns 2 .. 65
+                lr = u < TX ? 0 : IR - 1;
+                lc = 2 + (u < TX ? u : u - TX);
+            }
+            Raw<T> raw;
+            if (staged) {
+                const Staged<float>& st = stg[buf];
+                raw = Raw<T>{(T)st.f[0][lr][lc + 2], (T)st.f[1][lr][lc + 2], (T)st.f[2][lr][lc + 2],
+                             (T)st.f[3][lr][lc + 2], 0};
+            } else {
+                uint8_t dummy;
+                raw = load_node(f, y0 - 1 + lr, x0 - 2 + lc, dummy);
+            }
+            Src<T> hs;
+            derive<T, FM>(f.c, raw, hs);
+            store_derived(sm, lr, lc, hs);
+        }
+        __syncthreads();
+        // ---- phase B ----
+        const T q = T(0.25);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int lr = 1 + 2 * tyy + r, lc = 2 + tx + 32 * k;
+                const int x = x0 + tx + 32 * k, y = y0 + 2 * tyy + r;
+                const uint8_t ty = own_type[r][k];
+                if (x >= f.nx || y >= f.ny || (ty & KIND_MASK) == K_SOLID || (ty & GENERAL_BIT)) continue;
+                using V2 = typename Vec2<T>::type;
+                const T cL_o1 = sm.o[0][lr][lc - 1], mL_o2 = sm.o[1][lr - 1][lc - 1], pL_o8 = sm.o[7][lr + 1][lc - 1];
+                const T cR_o5 = sm.o[4][lr][lc + 1], mR_o4 = sm.o[3][lr - 1][lc + 1], pR_o6 = sm.o[5][lr + 1][lc + 1];
+                const T mC_o3 = sm.o[2][lr - 1][lc], pC_o7 = sm.o[6][lr + 1][lc];
+                const V2 mL = sm.ed[lr - 1][lc - 1], mC = sm.ed[lr - 1][lc], mR = sm.ed[lr - 1][lc + 1];
+                const V2 cL = sm.ed[lr][lc - 1], cR = sm.ed[lr][lc + 1];
+                const V2 pL = sm.ed[lr + 1][lc - 1], pC = sm.ed[lr + 1][lc], pR = sm.ed[lr + 1][lc + 1];
+                const T OL = O::add(O::add(cL_o1, mL_o2), pL_o8);
+                const T OR = O::add(O::add(cR_o5, mR_o4), pR_o6);
+                const T Sh = O::add(O::add(OL, OR), O::add(mC_o3, pC_o7));
+                const T Sx = O::sub(OL, OR);
+                const T Sy = O::sub(O::add(O::add(mL_o2, mR_o4), mC_o3), O::add(O::add(pL_o8, pR_o6), pC_o7));
+                // lambda-weighted stencils of eta (.x) and D (.y): sum, x-moment, y-moment
+                const T MLe = O::fma(q, O::add(mL.x, pL.x), cL.x);
+                const T MRe = O::fma(q, O::add(mR.x, pR.x), cR.x);
+                const T MLd = O::fma(q, O::add(mL.y, pL.y), cL.y);
+                const T MRd = O::fma(q, O::add(mR.y, pR.y), cR.y);
+                const T Se = O::add(O::add(MLe, MRe), O::add(mC.x, pC.x));
+                const T Sd = O::add(O::add(MLd, MRd), O::add(mC.y, pC.y));
+                const T Xe = O::sub(MLe, MRe), Xd = O::sub(MLd, MRd);
+                const T Ye = O::fma(q, O::sub(O::add(mL.x, mR.x), O::add(pL.x, pR.x)), O::sub(mC.x, pC.x));
+                const T Yd = O::fma(q, O::sub(O::add(mL.y, mR.y), O::add(pL.y, pR.y)), O::sub(mC.y, pC.y));
+                const Src<T>& me = own[r][k];
+                const T A = O::mul(K.G6, me.D), B = O::mul(K.G6, me.eta);
+                // ownh already holds the receiver-only bed part 5 G6 eta_x D_x
+                const T eta1 = O::add(O::add(me.ownh, Sh), O::fma(A, Se, O::mul(-B, Sd)));
+                const T hu1 = O::fma(K.e, O::add(Sx, O::fma(A, Xe, O::mul(-B, Xd))), me.hFx);
+                const T hv1 = O::fma(K.e, O::add(Sy, O::fma(A, Ye, O::mul(-B, Yd))), me.hFy);
+                const T inv = O::rcp(O::add(me.D, eta1));
+                const bool noslip = (ty & KIND_MASK) == K_NOSLIP;
+                const size_t idx = (size_t)y * f.pitch + x;
+                f.eta1[idx] = eta1;
+                f.u1[idx] = noslip ? T(0) : O::mul(hu1, inv);
+                f.v1[idx] = noslip ? T(0) : O::mul(hv1, inv);
             }
         }
     }
+    if (STAGE) cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
