@@ -496,7 +496,7 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
     }
     // ---- shared memory of the tile kernel (above the 48 KB default for FP64) ----
     {
-#ifndef MACLAB_TILE_KERNEL
+#ifdef MACLAB_STRIP_KERNEL
         s->use_tile = false;
 #endif
         cudaError_t ae = cudaSuccess;

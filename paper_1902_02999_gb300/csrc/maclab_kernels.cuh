@@ -243,12 +243,7 @@ template <typename T> struct Cfg;
 template <> struct Cfg<float> { static constexpr int CPL = MACLAB_F32_CPL, STAGES = MACLAB_F32_STAGES; };
 template <> struct Cfg<double> { static constexpr int CPL = 2, STAGES = 4; };
 template <typename T> __host__ __device__ constexpr int strip_width() { return 31 * Cfg<T>::CPL; }
-#ifndef MACLAB_PACKED_F32
-#define MACLAB_PACKED_F32 1
-#endif
-// FP32 with 4 columns per lane uses the paired FP32 instructions
-template <typename T> struct PACKED { static constexpr bool value = false; };
-template <> struct PACKED<float> { static constexpr bool value = MACLAB_PACKED_F32 && Cfg<float>::CPL == 4; };
+
 // elements of T per ring slot: 4 fields of 32 CPL values, plus 32 CPL type
 // bytes when CPL == 4 (rounded up to whole elements)
 template <typename T> __host__ __device__ constexpr int slot_elems()
@@ -471,241 +466,6 @@ __device__ __forceinline__ void emit_row(const Fields<T>& f, int j, int xl, int 
     }
 }
 
-// ---------------------------------------------------------------------------
-// Packed FP32 path of the strip kernel (4 columns per lane): Blackwell's
-// paired FP32 instructions (__fadd2_rn, __fmul2_rn, __ffma2_rn) update two
-// nodes per instruction.  A lane's columns 0..3 form the pairs A = (0, 2)
-// and B = (1, 3), so A's right neighbours are B and B's left neighbours
-// are A; only A's left pair (-1, 1) and B's right pair (2, 4) are assembled
-// from a shuffled column.  Every operation rounds exactly as the scalar
-// path, so results are bitwise identical to it.
-struct P2 {
-    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-    static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
-    static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-    static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-    static __device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
-    static __device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
-};
-
-struct Src2 {
-    float2 eta, D;
-    float2 o1, o2, o3, o4, o5, o6, o7, o8;
-    float2 ownh, hFx, hFy;
-};
-
-struct Row2 {
-    Src2 A, B;                      // pairs (0, 2) and (1, 3) of the lane's columns
-    float Lo1, Lo2, Lo8, Leta, LD;  // column -1 (last column of lane - 1)
-    float Ro5, Ro4, Ro6, Reta, RD;  // column 4 (first column of lane + 1)
-    uint32_t types;
-};
-
-__device__ __forceinline__ float2 flipsel(float2 v, uint8_t f0, uint8_t f1, uint8_t bit)
-{
-    return make_float2((f0 & bit) ? -v.x : v.x, (f1 & bit) ? -v.y : v.y);
-}
-
-template <int FM>
-__device__ __forceinline__ void derive2(const Coef<float>& c, float2 eta, float2 u, float2 v, float2 D,
-                                        uint8_t f0, uint8_t f1, Src2& s)
-{
-    using O = P2;
-    float2 wfx = O::bc(c.wfx), wfy = O::bc(c.wfy), Om = O::bc(c.Om);
-    if (f0 | f1) {  // specular ghosts: normal components reversed, rotation sense too
-        u = flipsel(u, f0, f1, 1);
-        v = flipsel(v, f0, f1, 2);
-        wfx = flipsel(wfx, f0, f1, 1);
-        wfy = flipsel(wfy, f0, f1, 2);
-        Om = make_float2(((f0 & 3) == 1 || (f0 & 3) == 2) ? -c.Om : c.Om,
-                         ((f1 & 3) == 1 || (f1 & 3) == 2) ? -c.Om : c.Om);
-    }
-    const float2 h = O::add(D, eta);
-    const float2 uu = O::fma(u, u, O::mul(v, v));
-    const float2 ge = O::mul(O::bc(c.G6), eta);
-    const float2 ku = O::mul(O::bc(c.K6), uu);
-    const float2 ap = O::mul(h, O::sub(ge, ku));
-    s.ownh = O::fma(O::neg(h), O::fma(O::bc(5.f), ge, O::mul(O::bc(4.f), ku)), eta);
-    float2 Fx = (FM & F_WIND) ? wfx : O::bc(0.f), Fy = (FM & F_WIND) ? wfy : O::bc(0.f);
-    if (FM & F_CORIOLIS) {
-        const float2 omh = O::mul(Om, h);
-        Fx = O::fma(omh, v, Fx);
-        Fy = O::fma(O::neg(omh), u, Fy);
-    }
-    if (FM & F_FRICTION) {
-        const float2 cbs = O::mul(O::bc(c.Cb), make_float2(Op<float>::sqrt(uu.x), Op<float>::sqrt(uu.y)));
-        Fx = O::fma(O::neg(cbs), u, Fx);
-        Fy = O::fma(O::neg(cbs), v, Fy);
-    }
-    const float2 hu = O::mul(h, u), hv = O::mul(h, v);
-    float2 qx = O::mul(hu, O::bc(c.k3)), qy = O::mul(hv, O::bc(c.k3));
-    if (FM) {
-        s.hFx = O::mul(O::bc(c.hdt), Fx);
-        s.hFy = O::mul(O::bc(c.hdt), Fy);
-        qx = O::fma(O::bc(c.KF), Fx, qx);
-        qy = O::fma(O::bc(c.KF), Fy, qy);
-    } else {
-        s.hFx = O::bc(0.f);
-        s.hFy = O::bc(0.f);
-    }
-    const float2 sxx = O::mul(O::mul(hu, u), O::bc(c.k2));
-    const float2 syy = O::mul(O::mul(hv, v), O::bc(c.k2));
-    const float2 sxy = O::mul(O::mul(hu, v), O::bc(c.k1));
-    const float2 ax = O::add(ap, sxx), ay = O::add(ap, syy);
-    s.o1 = O::add(ax, qx);
-    s.o5 = O::sub(ax, qx);
-    s.o3 = O::add(ay, qy);
-    s.o7 = O::sub(ay, qy);
-    const float2 d = O::add(ax, syy);
-    const float2 q = O::bc(0.25f);
-    const float2 dp = O::mul(q, O::add(d, sxy)), dm = O::mul(q, O::sub(d, sxy));
-    const float2 s4 = O::mul(q, O::add(qx, qy)), t4 = O::mul(q, O::sub(qx, qy));
-    s.o2 = O::add(dp, s4);
-    s.o6 = O::sub(dp, s4);
-    s.o8 = O::add(dm, t4);
-    s.o4 = O::sub(dm, t4);
-    s.eta = eta;
-    s.D = D;
-}
-
-template <int FM>
-__device__ __forceinline__ void consume_row_p(const Fields<float>& f, const LaneCols<4>& lc, int r,
-                                              const float* slot, int lane, Row2& row)
-{
-    constexpr int FE = 32 * 4;
-    uint8_t fy = 0;
-    const int rr = resolve_index(r, f.ny, f.edge[2], f.edge[3], 2, fy);
-    const float4* sp = reinterpret_cast<const float4*>(slot + 4 * lane);
-    const float4 e4 = sp[0], u4 = sp[FE / 4], v4 = sp[2 * FE / 4], d4 = sp[3 * FE / 4];
-    if (rr >= 0 && lc.inside) {
-        row.types = *reinterpret_cast<const uint32_t*>(reinterpret_cast<const uint8_t*>(slot + 4 * FE) + 4 * lane);
-    } else {
-        uint32_t t = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (rr >= 0 && lc.src[k] >= 0) t |= (uint32_t)f.type[(size_t)rr * f.pitch + lc.src[k]] << (8 * k);
-        row.types = t;
-    }
-    derive2<FM>(f.c, make_float2(e4.x, e4.z), make_float2(u4.x, u4.z), make_float2(v4.x, v4.z),
-                make_float2(d4.x, d4.z), (uint8_t)(fy | lc.flip[0]), (uint8_t)(fy | lc.flip[2]), row.A);
-    derive2<FM>(f.c, make_float2(e4.y, e4.w), make_float2(u4.y, u4.w), make_float2(v4.y, v4.w),
-                make_float2(d4.y, d4.w), (uint8_t)(fy | lc.flip[1]), (uint8_t)(fy | lc.flip[3]), row.B);
-    const unsigned full = 0xffffffffu;
-    // column -1 = column 3 of lane - 1 = B.y there; column 4 = column 0 of lane + 1 = A.x there
-    row.Lo1 = __shfl_up_sync(full, row.B.o1.y, 1);
-    row.Lo2 = __shfl_up_sync(full, row.B.o2.y, 1);
-    row.Lo8 = __shfl_up_sync(full, row.B.o8.y, 1);
-    row.Leta = __shfl_up_sync(full, row.B.eta.y, 1);
-    row.LD = __shfl_up_sync(full, row.B.D.y, 1);
-    row.Ro5 = __shfl_down_sync(full, row.A.o5.x, 1);
-    row.Ro4 = __shfl_down_sync(full, row.A.o4.x, 1);
-    row.Ro6 = __shfl_down_sync(full, row.A.o6.x, 1);
-    row.Reta = __shfl_down_sync(full, row.A.eta.x, 1);
-    row.RD = __shfl_down_sync(full, row.A.D.x, 1);
-}
-
-// The update of one pair from its sources (same operations as emit_row).
-struct Nb2 {  // sources of a pair: left / centre / right columns at rows m, c, p
-    float2 cL_o1, mL_o2, pL_o8, cR_o5, mR_o4, pR_o6, mC_o3, pC_o7;
-    float2 mLe, pLe, cLe, mRe, pRe, cRe, mCe, pCe;
-    float2 mLd, pLd, cLd, mRd, pRd, cRd, mCd, pCd;
-};
-
-__device__ __forceinline__ void update2(const Coef<float>& K, const Nb2& n, const Src2& me, float2& eta1,
-                                        float2& hu1, float2& hv1)
-{
-    using O = P2;
-    const float2 OL = O::add(O::add(n.cL_o1, n.mL_o2), n.pL_o8);
-    const float2 OR = O::add(O::add(n.cR_o5, n.mR_o4), n.pR_o6);
-    const float2 Sh = O::add(O::add(OL, OR), O::add(n.mC_o3, n.pC_o7));
-    const float2 Sx = O::sub(OL, OR);
-    const float2 Sy = O::sub(O::add(O::add(n.mL_o2, n.mR_o4), n.mC_o3), O::add(O::add(n.pL_o8, n.pR_o6), n.pC_o7));
-    const float2 q = O::bc(0.25f);
-    const float2 MLe = O::fma(q, O::add(n.mLe, n.pLe), n.cLe);
-    const float2 MRe = O::fma(q, O::add(n.mRe, n.pRe), n.cRe);
-    const float2 MLd = O::fma(q, O::add(n.mLd, n.pLd), n.cLd);
-    const float2 MRd = O::fma(q, O::add(n.mRd, n.pRd), n.cRd);
-    const float2 Se = O::add(O::add(MLe, MRe), O::add(n.mCe, n.pCe));
-    const float2 Sd = O::add(O::add(MLd, MRd), O::add(n.mCd, n.pCd));
-    const float2 Xe = O::sub(MLe, MRe), Xd = O::sub(MLd, MRd);
-    const float2 Ye = O::fma(q, O::sub(O::add(n.mLe, n.mRe), O::add(n.pLe, n.pRe)), O::sub(n.mCe, n.pCe));
-    const float2 Yd = O::fma(q, O::sub(O::add(n.mLd, n.mRd), O::add(n.pLd, n.pRd)), O::sub(n.mCd, n.pCd));
-    const float2 A = O::mul(O::bc(K.G6), me.D), B = O::mul(O::bc(K.G6), me.eta);
-    const float2 nB = O::neg(B);
-    // ownh already holds the receiver-only bed part 5 G6 eta_x D_x
-    eta1 = O::add(O::add(me.ownh, Sh), O::fma(A, Se, O::mul(nB, Sd)));
-    hu1 = O::fma(O::bc(K.e), O::add(Sx, O::fma(A, Xe, O::mul(nB, Xd))), me.hFx);
-    hv1 = O::fma(O::bc(K.e), O::add(Sy, O::fma(A, Ye, O::mul(nB, Yd))), me.hFy);
-}
-
-__device__ __forceinline__ void emit_row_p(const Fields<float>& f, int j, int xl, int lane, const Row2& m,
-                                           const Row2& c, const Row2& p)
-{
-    constexpr int W = 31 * 4;
-    Nb2 n;
-    // pair A = columns (0, 2): left (-1, 1), centre A, right B
-    n.cL_o1 = make_float2(c.Lo1, c.B.o1.x);
-    n.mL_o2 = make_float2(m.Lo2, m.B.o2.x);
-    n.pL_o8 = make_float2(p.Lo8, p.B.o8.x);
-    n.cR_o5 = c.B.o5; n.mR_o4 = m.B.o4; n.pR_o6 = p.B.o6;
-    n.mC_o3 = m.A.o3; n.pC_o7 = p.A.o7;
-    n.mLe = make_float2(m.Leta, m.B.eta.x); n.cLe = make_float2(c.Leta, c.B.eta.x); n.pLe = make_float2(p.Leta, p.B.eta.x);
-    n.mLd = make_float2(m.LD, m.B.D.x); n.cLd = make_float2(c.LD, c.B.D.x); n.pLd = make_float2(p.LD, p.B.D.x);
-    n.mRe = m.B.eta; n.cRe = c.B.eta; n.pRe = p.B.eta;
-    n.mRd = m.B.D; n.cRd = c.B.D; n.pRd = p.B.D;
-    n.mCe = m.A.eta; n.pCe = p.A.eta; n.mCd = m.A.D; n.pCd = p.A.D;
-    float2 eA, huA, hvA;
-    update2(f.c, n, c.A, eA, huA, hvA);
-    // pair B = columns (1, 3): left A, centre B, right (2, 4)
-    n.cL_o1 = c.A.o1; n.mL_o2 = m.A.o2; n.pL_o8 = p.A.o8;
-    n.cR_o5 = make_float2(c.A.o5.y, c.Ro5);
-    n.mR_o4 = make_float2(m.A.o4.y, m.Ro4);
-    n.pR_o6 = make_float2(p.A.o6.y, p.Ro6);
-    n.mC_o3 = m.B.o3; n.pC_o7 = p.B.o7;
-    n.mLe = m.A.eta; n.cLe = c.A.eta; n.pLe = p.A.eta;
-    n.mLd = m.A.D; n.cLd = c.A.D; n.pLd = p.A.D;
-    n.mRe = make_float2(m.A.eta.y, m.Reta); n.cRe = make_float2(c.A.eta.y, c.Reta); n.pRe = make_float2(p.A.eta.y, p.Reta);
-    n.mRd = make_float2(m.A.D.y, m.RD); n.cRd = make_float2(c.A.D.y, c.RD); n.pRd = make_float2(p.A.D.y, p.RD);
-    n.mCe = m.B.eta; n.pCe = p.B.eta; n.mCd = m.B.D; n.pCd = p.B.D;
-    float2 eB, huB, hvB;
-    update2(f.c, n, c.B, eB, huB, hvB);
-    // columns 0..3 = A.x, B.x, A.y, B.y
-    const float e[4] = {eA.x, eB.x, eA.y, eB.y};
-    const float hu[4] = {huA.x, huB.x, huA.y, huB.y};
-    const float hv[4] = {hvA.x, hvB.x, hvA.y, hvB.y};
-    const float Dn[4] = {c.A.D.x, c.B.D.x, c.A.D.y, c.B.D.y};
-    float ou[4], ov[4];
-    unsigned okmask = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int loc = 4 * lane + k, x = xl + k;
-        const uint8_t ty = (uint8_t)(c.types >> (8 * k));
-        const bool ok = loc >= 1 && loc <= W && x >= 0 && x < f.nx && (ty & KIND_MASK) != K_SOLID &&
-                        !(ty & GENERAL_BIT);
-        okmask |= (ok ? 1u : 0u) << k;
-        const float inv = Op<float>::rcp(Op<float>::add(Dn[k], e[k]));
-        const bool noslip = (ty & KIND_MASK) == K_NOSLIP;
-        ou[k] = noslip ? 0.f : Op<float>::mul(hu[k], inv);
-        ov[k] = noslip ? 0.f : Op<float>::mul(hv[k], inv);
-    }
-    if (j >= f.ny || okmask == 0) return;
-    const size_t row0 = (size_t)j * f.pitch;
-    if (okmask == 15u) {
-        *reinterpret_cast<float4*>(f.eta1 + row0 + xl) = make_float4(e[0], e[1], e[2], e[3]);
-        *reinterpret_cast<float4*>(f.u1 + row0 + xl) = make_float4(ou[0], ou[1], ou[2], ou[3]);
-        *reinterpret_cast<float4*>(f.v1 + row0 + xl) = make_float4(ov[0], ov[1], ov[2], ov[3]);
-    } else {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (okmask & (1u << k)) {
-                f.eta1[row0 + xl + k] = e[k];
-                f.u1[row0 + xl + k] = ou[k];
-                f.v1[row0 + xl + k] = ov[k];
-            }
-        }
-    }
-}
-
 // One strip: rows [j0, j1) of column strip cb.
 template <typename T, int FM>
 __device__ __forceinline__ void step_strip(const Fields<T>& f, int cb, int j0, int j1, int lane,
@@ -746,49 +506,20 @@ __device__ __forceinline__ void step_strip(const Fields<T>& f, int cb, int j0, i
         slot_f = slot_f == S - 1 ? 0 : slot_f + 1;
         ++q;
     };
-    if constexpr (PACKED<T>::value) {
-        // consume row q after issuing row q + S - 1 (packed FP32x2 path)
-        auto advance2 = [&](Row2& dst) {
-            if (q + S - 1 < nrows)
-                fetch_row(f, lc, j0 - 1 + q + S - 1, ring_addr + slot_f * SLOT_BYTES,
-                          ring_addr + slot_f * SLOT_BYTES + type_off);
-            else cp_async_commit();
-            cp_async_wait<S - 1>();
-            consume_row_p<FM>(f, lc, j0 - 1 + q, &my[slot_c][0], lane, dst);
-            slot_c = slot_c == S - 1 ? 0 : slot_c + 1;
-            slot_f = slot_f == S - 1 ? 0 : slot_f + 1;
-            ++q;
-        };
-        Row2 A, B, C;
-        advance2(A);
-        advance2(B);
-        for (int j = j0;; j += 3) {
-            advance2(C);
-            emit_row_p(f, j, lc.xl, lane, A, B, C);
-            if (j + 1 >= j1) break;
-            advance2(A);
-            emit_row_p(f, j + 1, lc.xl, lane, B, C, A);
-            if (j + 2 >= j1) break;
-            advance2(B);
-            emit_row_p(f, j + 2, lc.xl, lane, C, A, B);
-            if (j + 3 >= j1) break;
-        }
-    } else {
-        Row<T> A, B, C;
+    Row<T> A, B, C;
+    advance(A);
+    advance(B);
+    // rows rotate A -> B -> C so that no register copies of Row are needed
+    for (int j = j0;; j += 3) {
+        advance(C);
+        emit_row(f, j, lc.xl, lane, A, B, C);
+        if (j + 1 >= j1) break;
         advance(A);
+        emit_row(f, j + 1, lc.xl, lane, B, C, A);
+        if (j + 2 >= j1) break;
         advance(B);
-        // rows rotate A -> B -> C so that no register copies of Row are needed
-        for (int j = j0;; j += 3) {
-            advance(C);
-            emit_row(f, j, lc.xl, lane, A, B, C);
-            if (j + 1 >= j1) break;
-            advance(A);
-            emit_row(f, j + 1, lc.xl, lane, B, C, A);
-            if (j + 2 >= j1) break;
-            advance(B);
-            emit_row(f, j + 2, lc.xl, lane, C, A, B);
-            if (j + 3 >= j1) break;
-        }
+        emit_row(f, j + 2, lc.xl, lane, C, A, B);
+        if (j + 3 >= j1) break;
     }
     cp_async_wait<0>();
 }
@@ -813,30 +544,28 @@ step_fast_kernel(const Fields<T> f, int ncb, int nrb, int ty)
 }
 
 // ---------------------------------------------------------------------------
-// Tile step kernel (the default fast path).  A 256-thread block updates
-// tiles of TX x TY = 64 x 16 nodes; blocks are persistent and walk the tiles
-// in turn.  Per tile:
-//   0. (FP32, interior tiles) the raw rows of eta, u, v, D and the node types
-//      of the tile and its one-node halo were staged in shared memory with
-//      cp.async while the previous tile was computed (double buffer);
-//   A. every thread derives the source quantities of its nodes of the tile
-//      plus halo (68 x 18 nodes) and writes the eight outgoing values and
-//      (eta, D) to shared memory; the nodes a thread updates keep their own
-//      term, dt F / 2 and type in registers;
-//   B. after a barrier every thread gathers, for each of its four nodes, the
-//      eight incoming values and the eta / D stencils and writes eta, u, v.
-// Thread (tx, ty) of 32 x 8 owns tile columns 2 + tx and 34 + tx at tile
-// rows 1 + 2 ty and 2 + 2 ty, so every shared-memory access of a warp is
-// stride-1 (no bank conflicts) and every global access is coalesced.
-// Edge tiles (whose halo leaves the grid) load straight from global memory
-// through the edge rules.
+// Tile step kernel.  A 256-thread block updates tiles of TX x TY = 64 x 16
+// nodes; blocks are persistent and walk the tiles in turn.  Per tile:
+//   A. every thread derives the source quantities of its node pairs of the
+//      tile plus its one-node halo (68 x 18 nodes) and writes the eight
+//      outgoing values and (eta, D) to shared memory; the pairs it updates
+//      keep their own term, dt F / 2 and types in registers;
+//   B. after a barrier every thread gathers, for each of its 2 x 2 nodes,
+//      the eight incoming values and the eta / D stencils and writes
+//      eta, u, v.
+// The raw eta, u, v, D and types of an interior tile (halo inside the grid)
+// are staged in shared memory with cp.async, issued during phase B of the
+// previous tile; edge tiles load straight from global memory through the
+// edge rules.  Thread (tx, ty) of 32 x 8 owns the node pairs at tile
+// columns 2 + 2 tx, 3 + 2 tx of tile rows 1 + 2 ty and 2 + 2 ty.
 namespace tile {
 constexpr int TX = 64, TY = 16;            // nodes updated per tile
 constexpr int THREADS = 256;               // 32 x 8
+constexpr int PC = TX / 2 + 2;             // 34 node pairs per tile row (with halo)
 constexpr int IR = TY + 2;                 // 18 tile rows (with halo)
-constexpr int IW = TX + 4;                 // 68 tile columns (with halo; cols 1 and 66 are used)
+constexpr int IW = 2 * PC;                 // 68 tile columns: global x0 - 2 .. x0 + 65
 constexpr int RW = TX + 8;                 // 72 staged columns: global x0 - 4 .. x0 + 67
-constexpr int HALO = 4 * IR + 2 * TX;      // 200 halo nodes: columns 0, 1, 66, 67 and rows 0, 17
+constexpr int HALO_PAIRS = 2 * IR + 2 * (PC - 2);  // 100
 template <typename T>
 struct Derived {
     T o[8][IR][IW];                        // outgoing values o_1 .. o_8
@@ -848,43 +577,72 @@ struct Staged {
     uint8_t type[IR][RW];
 };
 template <typename T> struct Cfg;
-template <> struct Cfg<float> { static constexpr bool STAGE = true; static constexpr int MINB = 2; };
+template <> struct Cfg<float> { static constexpr bool STAGE = true; static constexpr int MINB = 3; };
 template <> struct Cfg<double> { static constexpr bool STAGE = false; static constexpr int MINB = 2; };
 template <typename T>
 __host__ __device__ constexpr size_t smem_bytes()
 {
-    return sizeof(Derived<T>) + (Cfg<T>::STAGE ? 2 * sizeof(Staged<T>) : 0);
+    return sizeof(Derived<T>) + (Cfg<T>::STAGE ? sizeof(Staged<T>) : 0);
 }
 }  // namespace tile
 
-// One node straight from global memory through the edge rules.
 template <typename T>
-__device__ __forceinline__ Raw<T> load_node(const Fields<T>& f, int y, int x, uint8_t& type)
+__device__ __forceinline__ void load_pair(const Fields<T>& f, int y, int x, Raw<T> (&raw)[2], uint32_t& types)
 {
-    uint8_t fl = 0;
-    const int rr = resolve_index(y, f.ny, f.edge[2], f.edge[3], 2, fl);
-    const int cc = resolve_index(x, f.nx, f.edge[0], f.edge[1], 1, fl);
-    if (rr >= 0 && cc >= 0) {
-        const size_t idx = (size_t)rr * f.pitch + cc;
-        type = f.type[idx];
-        return Raw<T>{f.eta[idx], f.u[idx], f.v[idx], f.D[idx], fl};
+    uint8_t fy = 0;
+    const int rr = resolve_index(y, f.ny, f.edge[2], f.edge[3], 2, fy);
+    if (rr >= 0 && x >= 0 && x + 2 <= f.nx) {
+        const size_t base = (size_t)rr * f.pitch + x;
+        using V2 = typename Vec2<T>::type;
+        const V2 e2 = *reinterpret_cast<const V2*>(f.eta + base);
+        const V2 u2 = *reinterpret_cast<const V2*>(f.u + base);
+        const V2 v2 = *reinterpret_cast<const V2*>(f.v + base);
+        const V2 d2 = *reinterpret_cast<const V2*>(f.D + base);
+        types = *reinterpret_cast<const uint16_t*>(f.type + base);
+        raw[0] = Raw<T>{e2.x, u2.x, v2.x, d2.x, fy};
+        raw[1] = Raw<T>{e2.y, u2.y, v2.y, d2.y, fy};
+        return;
     }
-    type = K_SOLID;
-    return Raw<T>{T(0), T(0), T(0), T(0), 0};
+    types = 0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        uint8_t fl = fy;
+        const int cc = resolve_index(x + k, f.nx, f.edge[0], f.edge[1], 1, fl);
+        if (rr >= 0 && cc >= 0) {
+            const size_t idx = (size_t)rr * f.pitch + cc;
+            raw[k] = Raw<T>{f.eta[idx], f.u[idx], f.v[idx], f.D[idx], fl};
+            types |= (uint32_t)f.type[idx] << (8 * k);
+        } else {
+            raw[k] = Raw<T>{T(0), T(0), T(0), T(0), 0};
+        }
+    }
+}
+
+// Pair at staged row r, staged column s (even) of an interior tile.
+template <typename T>
+__device__ __forceinline__ void staged_pair(const tile::Staged<T>& st, int r, int s, Raw<T> (&raw)[2],
+                                            uint32_t& types)
+{
+    using V2 = typename Vec2<T>::type;
+    const V2 e2 = *reinterpret_cast<const V2*>(&st.f[0][r][s]);
+    const V2 u2 = *reinterpret_cast<const V2*>(&st.f[1][r][s]);
+    const V2 v2 = *reinterpret_cast<const V2*>(&st.f[2][r][s]);
+    const V2 d2 = *reinterpret_cast<const V2*>(&st.f[3][r][s]);
+    types = *reinterpret_cast<const uint16_t*>(&st.type[r][s]);
+    raw[0] = Raw<T>{e2.x, u2.x, v2.x, d2.x, 0};
+    raw[1] = Raw<T>{e2.y, u2.y, v2.y, d2.y, 0};
 }
 
 template <typename T>
-__device__ __forceinline__ void store_derived(tile::Derived<T>& sm, int lr, int lc, const Src<T>& a)
+__device__ __forceinline__ void store_pair(tile::Derived<T>& sm, int pr, int lc, const Src<T>& a, const Src<T>& b)
 {
-    sm.o[0][lr][lc] = a.o1;
-    sm.o[1][lr][lc] = a.o2;
-    sm.o[2][lr][lc] = a.o3;
-    sm.o[3][lr][lc] = a.o4;
-    sm.o[4][lr][lc] = a.o5;
-    sm.o[5][lr][lc] = a.o6;
-    sm.o[6][lr][lc] = a.o7;
-    sm.o[7][lr][lc] = a.o8;
-    sm.ed[lr][lc] = typename Vec2<T>::type{a.eta, a.D};
+    using V2 = typename Vec2<T>::type;
+    const T oa[8] = {a.o1, a.o2, a.o3, a.o4, a.o5, a.o6, a.o7, a.o8};
+    const T ob[8] = {b.o1, b.o2, b.o3, b.o4, b.o5, b.o6, b.o7, b.o8};
+#pragma unroll
+    for (int d = 0; d < 8; ++d) *reinterpret_cast<V2*>(&sm.o[d][pr][lc]) = V2{oa[d], ob[d]};
+    sm.ed[pr][lc] = V2{a.eta, a.D};
+    sm.ed[pr][lc + 1] = V2{b.eta, b.D};
 }
 
 // Issue the cp.async copies of the raw window of tile (x0, y0) into `st`.
@@ -921,92 +679,88 @@ step_tile_kernel(const Fields<T> f, int tiles_x, int ntiles)
 {
     using namespace tile;
     using O = Op<T>;
+    using V2 = typename Vec2<T>::type;
     constexpr bool STAGE = tile::Cfg<T>::STAGE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Derived<T>& sm = *reinterpret_cast<Derived<T>*>(smem_raw);
-    Staged<float>* stg = reinterpret_cast<Staged<float>*>(smem_raw + sizeof(Derived<T>));
+    Staged<float>& st = *reinterpret_cast<Staged<float>*>(smem_raw + sizeof(Derived<T>));
+    const Fields<float>& ff = *reinterpret_cast<const Fields<float>*>(&f);
     const int tx = threadIdx.x & 31, tyy = threadIdx.x >> 5;
     const Coef<T>& K = f.c;
     int t = blockIdx.x;
-    int buf = 0;
     if (STAGE && t < ntiles) {
         const int x0 = (t % tiles_x) * TX, y0 = (t / tiles_x) * TY;
-        if (interior_tile(f, x0, y0)) stage_tile(*reinterpret_cast<const Fields<float>*>(&f), stg[0], x0, y0);
+        if (interior_tile(f, x0, y0)) stage_tile(ff, st, x0, y0);
+        cp_async_commit();
+        cp_async_wait<0>();
     }
-    if (STAGE) cp_async_commit();
-    for (; t < ntiles; t += gridDim.x, buf ^= 1) {
+    __syncthreads();
+    for (; t < ntiles; t += gridDim.x) {
         const int x0 = (t % tiles_x) * TX, y0 = (t / tiles_x) * TY;
         const bool staged = STAGE && interior_tile(f, x0, y0);
+        // ---- phase A: own pairs (tile pair column 1 + tx, tile rows 1 + 2 tyy + r)
+        Src<T> own[2][2];
+        uint32_t own_types[2];
+        {
+            Raw<T> raw[2][2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (staged)
+                    staged_pair(*reinterpret_cast<const Staged<T>*>(&st), 1 + 2 * tyy + r, 4 + 2 * tx, raw[r],
+                                own_types[r]);
+                else
+                    load_pair(f, y0 + 2 * tyy + r, x0 + 2 * tx, raw[r], own_types[r]);
+            }
+            Raw<T> hraw[2];
+            uint32_t htypes;
+            int hpr = 0, hpc = 0;
+            const bool has_halo = threadIdx.x < HALO_PAIRS;
+            if (has_halo) {
+                const int h = threadIdx.x;
+                if (h < 2 * IR) { hpc = h < IR ? 0 : PC - 1; hpr = h % IR; }
+                else { const int u = h - 2 * IR; hpr = u < PC - 2 ? 0 : IR - 1; hpc = 1 + u % (PC - 2); }
+                if (staged)
+                    staged_pair(*reinterpret_cast<const Staged<T>*>(&st), hpr, 2 * hpc + 2, hraw, htypes);
+                else
+                    load_pair(f, y0 - 1 + hpr, x0 - 2 + 2 * hpc, hraw, htypes);
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                derive<T, FM>(f.c, raw[r][0], own[r][0]);
+                derive<T, FM>(f.c, raw[r][1], own[r][1]);
+                store_pair(sm, 1 + 2 * tyy + r, 2 + 2 * tx, own[r][0], own[r][1]);
+            }
+            if (has_halo) {
+                Src<T> h0, h1;
+                derive<T, FM>(f.c, hraw[0], h0);
+                derive<T, FM>(f.c, hraw[1], h1);
+                store_pair(sm, hpr, 2 * hpc, h0, h1);
+            }
+        }
+        __syncthreads();  // derived values visible; the staging buffer is free
         if (STAGE) {
-            // prefetch the next tile of this block into the other buffer
             const int tn = t + gridDim.x;
             if (tn < ntiles) {
                 const int xn = (tn % tiles_x) * TX, yn = (tn / tiles_x) * TY;
-                if (interior_tile(f, xn, yn))
-                    stage_tile(*reinterpret_cast<const Fields<float>*>(&f), stg[buf ^ 1], xn, yn);
+                if (interior_tile(f, xn, yn)) stage_tile(ff, st, xn, yn);
             }
             cp_async_commit();
-            cp_async_wait<1>();
         }
-        __syncthreads();  // staged data visible; previous tile's phase B done
-        // ---- phase A ----
-        Src<T> own[2][2];
-        uint8_t own_type[2][2];
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int lr = 1 + 2 * tyy + r, lc = 2 + tx + 32 * k;
-                Raw<T> raw;
-                if (staged) {
-                    const Staged<float>& st = stg[buf];
-                    raw = Raw<T>{(T)st.f[0][lr][lc + 2], (T)st.f[1][lr][lc + 2], (T)st.f[2][lr][lc + 2],
-                                 (T)st.f[3][lr][lc + 2], 0};
-                    own_type[r][k] = st.type[lr][lc + 2];
-                } else {
-                    raw = load_node(f, y0 - 1 + lr, x0 - 2 + lc, own_type[r][k]);
-                }
-                derive<T, FM>(f.c, raw, own[r][k]);
-                store_derived(sm, lr, lc, own[r][k]);
-            }
-        }
-        if (threadIdx.x < HALO) {
-            const int h = threadIdx.x;
-            int lr, lc;
-            if (h < 4 * IR) {
-                const int cs = h / IR;                    // 0..3 -> tile columns 0, 1, 66, 67
-                lc = cs < 2 ? cs : IW - 4 + cs;
-                lr = h - cs * IR;
-            } else {
-                const int u = h - 4 * IR;                 // rows 0 and 17, columns 2 .. 65
-                lr = u < TX ? 0 : IR - 1;
-                lc = 2 + (u < TX ? u : u - TX);
-            }
-            Raw<T> raw;
-            if (staged) {
-                const Staged<float>& st = stg[buf];
-                raw = Raw<T>{(T)st.f[0][lr][lc + 2], (T)st.f[1][lr][lc + 2], (T)st.f[2][lr][lc + 2],
-                             (T)st.f[3][lr][lc + 2], 0};
-            } else {
-                uint8_t dummy;
-                raw = load_node(f, y0 - 1 + lr, x0 - 2 + lc, dummy);
-            }
-            Src<T> hs;
-            derive<T, FM>(f.c, raw, hs);
-            store_derived(sm, lr, lc, hs);
-        }
-        __syncthreads();
-        // ---- phase B ----
+        // ---- phase B: nodes (x0 + 2 tx + k, y0 + 2 tyy + r)
         const T q = T(0.25);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
+            const int lr = 1 + 2 * tyy + r;    // tile row of the node
+            const int y = y0 + 2 * tyy + r;
+            T oe[2], ou[2], ov[2];
+            unsigned okmask = 0;
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                const int lr = 1 + 2 * tyy + r, lc = 2 + tx + 32 * k;
-                const int x = x0 + tx + 32 * k, y = y0 + 2 * tyy + r;
-                const uint8_t ty = own_type[r][k];
-                if (x >= f.nx || y >= f.ny || (ty & KIND_MASK) == K_SOLID || (ty & GENERAL_BIT)) continue;
-                using V2 = typename Vec2<T>::type;
+                const int lc = 2 + 2 * tx + k;  // tile column of the node
+                const int x = x0 + 2 * tx + k;
+                const uint8_t ty = (uint8_t)(own_types[r] >> (8 * k));
+                const bool ok = x < f.nx && y < f.ny && (ty & KIND_MASK) != K_SOLID && !(ty & GENERAL_BIT);
+                okmask |= (ok ? 1u : 0u) << k;
                 const T cL_o1 = sm.o[0][lr][lc - 1], mL_o2 = sm.o[1][lr - 1][lc - 1], pL_o8 = sm.o[7][lr + 1][lc - 1];
                 const T cR_o5 = sm.o[4][lr][lc + 1], mR_o4 = sm.o[3][lr - 1][lc + 1], pR_o6 = sm.o[5][lr + 1][lc + 1];
                 const T mC_o3 = sm.o[2][lr - 1][lc], pC_o7 = sm.o[6][lr + 1][lc];
@@ -1036,14 +790,30 @@ step_tile_kernel(const Fields<T> f, int tiles_x, int ntiles)
                 const T hv1 = O::fma(K.e, O::add(Sy, O::fma(A, Ye, O::mul(-B, Yd))), me.hFy);
                 const T inv = O::rcp(O::add(me.D, eta1));
                 const bool noslip = (ty & KIND_MASK) == K_NOSLIP;
-                const size_t idx = (size_t)y * f.pitch + x;
-                f.eta1[idx] = eta1;
-                f.u1[idx] = noslip ? T(0) : O::mul(hu1, inv);
-                f.v1[idx] = noslip ? T(0) : O::mul(hv1, inv);
+                oe[k] = eta1;
+                ou[k] = noslip ? T(0) : O::mul(hu1, inv);
+                ov[k] = noslip ? T(0) : O::mul(hv1, inv);
+            }
+            if (okmask == 0) continue;
+            const size_t idx = (size_t)y * f.pitch + x0 + 2 * tx;
+            if (okmask == 3u) {
+                *reinterpret_cast<V2*>(f.eta1 + idx) = V2{oe[0], oe[1]};
+                *reinterpret_cast<V2*>(f.u1 + idx) = V2{ou[0], ou[1]};
+                *reinterpret_cast<V2*>(f.v1 + idx) = V2{ov[0], ov[1]};
+            } else {
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (okmask & (1u << k)) {
+                        f.eta1[idx + k] = oe[k];
+                        f.u1[idx + k] = ou[k];
+                        f.v1[idx + k] = ov[k];
+                    }
+                }
             }
         }
+        if (STAGE) cp_async_wait<0>();
+        __syncthreads();  // next tile staged; phase B done before phase A rewrites shared memory
     }
-    if (STAGE) cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
