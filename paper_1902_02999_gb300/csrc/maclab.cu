@@ -66,7 +66,8 @@ struct maclab_s {
     int fmode = 0;             // force terms present: F_WIND | F_FRICTION | F_CORIOLIS
     int grid_blocks = 0;       // cap on step-kernel blocks (0 = one warp per strip)
     bool use_tile = true;      // tile kernel (default) or warp-strip kernel
-    int tile_blocks = 0;       // persistent blocks of the tile kernel
+    bool dir_fused = false;    // Dirichlet nodes handled inside the tile kernel
+    int* dir_tile_start = nullptr;  // per-tile ranges of the Dirichlet list
     int64_t n_fluid = 0, n_fast = 0;
     double sumD = 0;           // sum of D64 over non-solid nodes
     size_t device_bytes = 0;
@@ -167,9 +168,6 @@ template <typename T>
 int launch_step(maclab_t s)
 {
     const Fields<T> f = make_fields<T>(s);
-    const int warps = s->ncb * s->nrb;
-    int blocks = (warps + WARPS - 1) / WARPS;
-    if (s->grid_blocks > 0) blocks = std::min(blocks, s->grid_blocks);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (s->profiling) {
         while (s->events.size() < s->events_used + 2) {
@@ -182,41 +180,45 @@ int launch_step(maclab_t s)
         s->events_used += 2;
         cudaEventRecord(ev0, s->stream);
     }
-    if (s->use_tile) {
-        const int tx = (s->grid.nx + tile::TX - 1) / tile::TX, ty = (s->grid.ny + tile::TY - 1) / tile::TY;
-        const int ntiles = tx * ty;
-        const size_t smem = tile::smem_bytes<T>();
-        const int tb = std::min(ntiles, s->tile_blocks);
-        switch (s->fmode) {  // compile-time variants for the force terms present
-#define MACLAB_FM(m) \
-    case m: step_tile_kernel<T, m><<<tb, tile::THREADS, smem, s->stream>>>(f, tx, ntiles); break;
-            MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
-#undef MACLAB_FM
-        }
-    } else {
-        switch (s->fmode) {
-#define MACLAB_FM(m) \
-    case m: step_fast_kernel<T, m><<<blocks, 32 * WARPS, 0, s->stream>>>(f, s->ncb, s->nrb, s->ty); break;
-            MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
-#undef MACLAB_FM
-        }
-    }
-    if (s->profiling) cudaEventRecord(ev1, s->stream);
-    if (s->n_general > 0)
-        step_general_kernel<T><<<(s->n_general + 127) / 128, 128, 0, s->stream>>>(f, s->general,
-                                                                                  s->n_general);
+    DirValues bv{};
     if (s->n_dir > 0) {
-        DirValues bv;
         const double t1 = (double)(s->n + 1) * s->dt;
         for (int k = 0; k < 4; ++k) {
             bv.h[k] = wave(s->bc.h[k], t1);
             bv.qx[k] = wave(s->bc.qx[k], t1);
             bv.qy[k] = wave(s->bc.qy[k], t1);
         }
-        const int b = 1 - s->cur;
+    }
+    const int b = 1 - s->cur;
+    if (s->use_tile) {
+        // one launch: fast nodes, bounce-back-link nodes and (when fused) Dirichlet nodes
+        const int tx = (s->grid.nx + tile::TX - 1) / tile::TX, ty = (s->grid.ny + tile::TY - 1) / tile::TY;
+        const size_t smem = tile::smem_bytes<T>();
+        const TileDirichlet td{s->dir_fused ? s->dir_tile_start : nullptr, s->dir, s->D64, bv};
+        switch (s->fmode) {  // compile-time variants for the force terms present
+#define MACLAB_FM(m) \
+    case m: step_tile_kernel<T, m><<<tx * ty, tile::THREADS, smem, s->stream>>>(f, tx, td); break;
+            MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
+#undef MACLAB_FM
+        }
+    } else {
+        const int warps = s->ncb * s->nrb;
+        int blocks = (warps + WARPS - 1) / WARPS;
+        if (s->grid_blocks > 0) blocks = std::min(blocks, s->grid_blocks);
+        switch (s->fmode) {
+#define MACLAB_FM(m) \
+    case m: step_fast_kernel<T, m><<<blocks, 32 * WARPS, 0, s->stream>>>(f, s->ncb, s->nrb, s->ty); break;
+            MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
+#undef MACLAB_FM
+        }
+        if (s->n_general > 0)
+            step_general_kernel<T><<<(s->n_general + 127) / 128, 128, 0, s->stream>>>(f, s->general,
+                                                                                      s->n_general);
+    }
+    if (s->profiling) cudaEventRecord(ev1, s->stream);
+    if (s->n_dir > 0 && !(s->use_tile && s->dir_fused))
         dirichlet_kernel<T><<<(s->n_dir + 127) / 128, 128, 0, s->stream>>>(
             (T*)s->eta[b], (T*)s->u[b], (T*)s->v[b], (const T*)s->D, s->D64, s->dir, s->n_dir, bv);
-    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
     s->cur = 1 - s->cur;
@@ -425,6 +427,24 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
     }
     s->sumD = sumD;
 
+    // Dirichlet nodes in tile order; the tile kernel applies them itself
+    // when every inward node is updated in the same tile.
+    const int tiles_x = (nx + tile::TX - 1) / tile::TX, tiles_y = (ny + tile::TY - 1) / tile::TY;
+    auto tile_of = [&](int idx) {
+        const int j = idx / pitch, i = idx - j * pitch;
+        return (j / tile::TY) * tiles_x + i / tile::TX;
+    };
+    std::stable_sort(dirs.begin(), dirs.end(),
+                     [&](const DirNode& a, const DirNode& b) { return tile_of(a.x) < tile_of(b.x); });
+    std::vector<int> dir_start((size_t)tiles_x * tiles_y + 1, 0);
+    bool fused = true;
+    for (const DirNode& d : dirs) {
+        fused = fused && tile_of(d.x) == tile_of(d.n1);
+        dir_start[tile_of(d.x) + 1]++;
+    }
+    for (size_t k = 1; k < dir_start.size(); ++k) dir_start[k] += dir_start[k - 1];
+    s->dir_fused = fused && !dirs.empty();
+
     // ---- device buffers ----
     const size_t NP = (size_t)pitch * ny;
     int sms = 0;
@@ -442,6 +462,8 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
          (s->red_out = (double*)dev_alloc(s, RED_NVAL * 8));
     if (ok && !general.empty()) ok = (s->general = (int*)dev_alloc(s, general.size() * sizeof(int))) != nullptr;
     if (ok && !dirs.empty()) ok = (s->dir = (DirNode*)dev_alloc(s, dirs.size() * sizeof(DirNode))) != nullptr;
+    if (ok && s->dir_fused)
+        ok = (s->dir_tile_start = (int*)dev_alloc(s, dir_start.size() * sizeof(int))) != nullptr;
     if (!ok) {
         release_all(s);
         delete s;
@@ -472,6 +494,7 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
     put(s->type, tpad.data(), NP + 64);
     if (!general.empty()) put(s->general, general.data(), general.size() * sizeof(int));
     if (!dirs.empty()) put(s->dir, dirs.data(), dirs.size() * sizeof(DirNode));
+    if (s->dir_fused) put(s->dir_tile_start, dir_start.data(), dir_start.size() * sizeof(int));
     for (int k = 0; k < 2 && ce == cudaSuccess; ++k) {
         ce = cudaMemsetAsync(s->eta[k], 0, NP * s->esize, s->stream);
         if (ce == cudaSuccess) ce = cudaMemsetAsync(s->u[k], 0, NP * s->esize, s->stream);
@@ -519,17 +542,7 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
             return MACLAB_E_CUDA;
         }
     }
-    // ---- launch geometry of the step kernels ----
-    {
-        int per_sm = 0;
-        cudaError_t oe = s->prec == MACLAB_F32
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_tile_kernel<float, 0>, tile::THREADS,
-                                                            tile::smem_bytes<float>())
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_tile_kernel<double, 0>, tile::THREADS,
-                                                            tile::smem_bytes<double>());
-        if (oe != cudaSuccess || per_sm < 1) per_sm = 1;
-        s->tile_blocks = sms * per_sm;
-    }
+    // ---- launch geometry of the strip kernel ----
     {
         const int cpl = s->prec == MACLAB_F32 ? Cfg<float>::CPL : Cfg<double>::CPL;
         const int w = s->prec == MACLAB_F32 ? strip_width<float>() : strip_width<double>();

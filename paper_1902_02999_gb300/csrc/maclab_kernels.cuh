@@ -544,279 +544,6 @@ step_fast_kernel(const Fields<T> f, int ncb, int nrb, int ty)
 }
 
 // ---------------------------------------------------------------------------
-// Tile step kernel.  A 256-thread block updates tiles of TX x TY = 64 x 16
-// nodes; blocks are persistent and walk the tiles in turn.  Per tile:
-//   A. every thread derives the source quantities of its node pairs of the
-//      tile plus its one-node halo (68 x 18 nodes) and writes the eight
-//      outgoing values and (eta, D) to shared memory; the pairs it updates
-//      keep their own term, dt F / 2 and types in registers;
-//   B. after a barrier every thread gathers, for each of its 2 x 2 nodes,
-//      the eight incoming values and the eta / D stencils and writes
-//      eta, u, v.
-// The raw eta, u, v, D and types of an interior tile (halo inside the grid)
-// are staged in shared memory with cp.async, issued during phase B of the
-// previous tile; edge tiles load straight from global memory through the
-// edge rules.  Thread (tx, ty) of 32 x 8 owns the node pairs at tile
-// columns 2 + 2 tx, 3 + 2 tx of tile rows 1 + 2 ty and 2 + 2 ty.
-namespace tile {
-constexpr int TX = 64, TY = 16;            // nodes updated per tile
-constexpr int THREADS = 256;               // 32 x 8
-constexpr int PC = TX / 2 + 2;             // 34 node pairs per tile row (with halo)
-constexpr int IR = TY + 2;                 // 18 tile rows (with halo)
-constexpr int IW = 2 * PC;                 // 68 tile columns: global x0 - 2 .. x0 + 65
-constexpr int RW = TX + 8;                 // 72 staged columns: global x0 - 4 .. x0 + 67
-constexpr int HALO_PAIRS = 2 * IR + 2 * (PC - 2);  // 100
-template <typename T>
-struct Derived {
-    T o[8][IR][IW];                        // outgoing values o_1 .. o_8
-    typename Vec2<T>::type ed[IR][IW];     // (eta, D)
-};
-template <typename T>
-struct Staged {
-    T f[4][IR][RW];                        // eta, u, v, D
-    uint8_t type[IR][RW];
-};
-template <typename T> struct Cfg;
-template <> struct Cfg<float> { static constexpr bool STAGE = true; static constexpr int MINB = 3; };
-template <> struct Cfg<double> { static constexpr bool STAGE = false; static constexpr int MINB = 2; };
-template <typename T>
-__host__ __device__ constexpr size_t smem_bytes()
-{
-    return sizeof(Derived<T>) + (Cfg<T>::STAGE ? sizeof(Staged<T>) : 0);
-}
-}  // namespace tile
-
-template <typename T>
-__device__ __forceinline__ void load_pair(const Fields<T>& f, int y, int x, Raw<T> (&raw)[2], uint32_t& types)
-{
-    uint8_t fy = 0;
-    const int rr = resolve_index(y, f.ny, f.edge[2], f.edge[3], 2, fy);
-    if (rr >= 0 && x >= 0 && x + 2 <= f.nx) {
-        const size_t base = (size_t)rr * f.pitch + x;
-        using V2 = typename Vec2<T>::type;
-        const V2 e2 = *reinterpret_cast<const V2*>(f.eta + base);
-        const V2 u2 = *reinterpret_cast<const V2*>(f.u + base);
-        const V2 v2 = *reinterpret_cast<const V2*>(f.v + base);
-        const V2 d2 = *reinterpret_cast<const V2*>(f.D + base);
-        types = *reinterpret_cast<const uint16_t*>(f.type + base);
-        raw[0] = Raw<T>{e2.x, u2.x, v2.x, d2.x, fy};
-        raw[1] = Raw<T>{e2.y, u2.y, v2.y, d2.y, fy};
-        return;
-    }
-    types = 0;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        uint8_t fl = fy;
-        const int cc = resolve_index(x + k, f.nx, f.edge[0], f.edge[1], 1, fl);
-        if (rr >= 0 && cc >= 0) {
-            const size_t idx = (size_t)rr * f.pitch + cc;
-            raw[k] = Raw<T>{f.eta[idx], f.u[idx], f.v[idx], f.D[idx], fl};
-            types |= (uint32_t)f.type[idx] << (8 * k);
-        } else {
-            raw[k] = Raw<T>{T(0), T(0), T(0), T(0), 0};
-        }
-    }
-}
-
-// Pair at staged row r, staged column s (even) of an interior tile.
-template <typename T>
-__device__ __forceinline__ void staged_pair(const tile::Staged<T>& st, int r, int s, Raw<T> (&raw)[2],
-                                            uint32_t& types)
-{
-    using V2 = typename Vec2<T>::type;
-    const V2 e2 = *reinterpret_cast<const V2*>(&st.f[0][r][s]);
-    const V2 u2 = *reinterpret_cast<const V2*>(&st.f[1][r][s]);
-    const V2 v2 = *reinterpret_cast<const V2*>(&st.f[2][r][s]);
-    const V2 d2 = *reinterpret_cast<const V2*>(&st.f[3][r][s]);
-    types = *reinterpret_cast<const uint16_t*>(&st.type[r][s]);
-    raw[0] = Raw<T>{e2.x, u2.x, v2.x, d2.x, 0};
-    raw[1] = Raw<T>{e2.y, u2.y, v2.y, d2.y, 0};
-}
-
-template <typename T>
-__device__ __forceinline__ void store_pair(tile::Derived<T>& sm, int pr, int lc, const Src<T>& a, const Src<T>& b)
-{
-    using V2 = typename Vec2<T>::type;
-    const T oa[8] = {a.o1, a.o2, a.o3, a.o4, a.o5, a.o6, a.o7, a.o8};
-    const T ob[8] = {b.o1, b.o2, b.o3, b.o4, b.o5, b.o6, b.o7, b.o8};
-#pragma unroll
-    for (int d = 0; d < 8; ++d) *reinterpret_cast<V2*>(&sm.o[d][pr][lc]) = V2{oa[d], ob[d]};
-    sm.ed[pr][lc] = V2{a.eta, a.D};
-    sm.ed[pr][lc + 1] = V2{b.eta, b.D};
-}
-
-// Issue the cp.async copies of the raw window of tile (x0, y0) into `st`.
-__device__ __forceinline__ void stage_tile(const Fields<float>& f, tile::Staged<float>& st, int x0, int y0)
-{
-    using namespace tile;
-    constexpr int CH = RW / 4;                 // 16-byte chunks per staged row: 18
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float* src = q == 0 ? f.eta : q == 1 ? f.u : q == 2 ? f.v : f.D;
-        for (int c = threadIdx.x; c < IR * CH; c += THREADS) {
-            const int r = c / CH, k = c - r * CH;
-            const size_t g = (size_t)(y0 - 1 + r) * f.pitch + (x0 - 4 + 4 * k);
-            cp_async16((uint32_t)__cvta_generic_to_shared(&st.f[q][r][4 * k]), src + g, 16);
-        }
-    }
-    for (int c = threadIdx.x; c < IR * CH; c += THREADS) {
-        const int r = c / CH, k = c - r * CH;
-        const size_t g = (size_t)(y0 - 1 + r) * f.pitch + (x0 - 4 + 4 * k);
-        cp_async4((uint32_t)__cvta_generic_to_shared(&st.type[r][4 * k]), f.type + g, 4);
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ bool interior_tile(const Fields<T>& f, int x0, int y0)
-{
-    using namespace tile;
-    return x0 - 4 >= 0 && x0 + TX + 4 <= f.nx && y0 - 1 >= 0 && y0 + TY + 1 <= f.ny;
-}
-
-template <typename T, int FM>
-__global__ void __launch_bounds__(tile::THREADS, tile::Cfg<T>::MINB)
-step_tile_kernel(const Fields<T> f, int tiles_x, int ntiles)
-{
-    using namespace tile;
-    using O = Op<T>;
-    using V2 = typename Vec2<T>::type;
-    constexpr bool STAGE = tile::Cfg<T>::STAGE;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Derived<T>& sm = *reinterpret_cast<Derived<T>*>(smem_raw);
-    Staged<float>& st = *reinterpret_cast<Staged<float>*>(smem_raw + sizeof(Derived<T>));
-    const Fields<float>& ff = *reinterpret_cast<const Fields<float>*>(&f);
-    const int tx = threadIdx.x & 31, tyy = threadIdx.x >> 5;
-    const Coef<T>& K = f.c;
-    int t = blockIdx.x;
-    if (STAGE && t < ntiles) {
-        const int x0 = (t % tiles_x) * TX, y0 = (t / tiles_x) * TY;
-        if (interior_tile(f, x0, y0)) stage_tile(ff, st, x0, y0);
-        cp_async_commit();
-        cp_async_wait<0>();
-    }
-    __syncthreads();
-    for (; t < ntiles; t += gridDim.x) {
-        const int x0 = (t % tiles_x) * TX, y0 = (t / tiles_x) * TY;
-        const bool staged = STAGE && interior_tile(f, x0, y0);
-        // ---- phase A: own pairs (tile pair column 1 + tx, tile rows 1 + 2 tyy + r)
-        Src<T> own[2][2];
-        uint32_t own_types[2];
-        {
-            Raw<T> raw[2][2];
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                if (staged)
-                    staged_pair(*reinterpret_cast<const Staged<T>*>(&st), 1 + 2 * tyy + r, 4 + 2 * tx, raw[r],
-                                own_types[r]);
-                else
-                    load_pair(f, y0 + 2 * tyy + r, x0 + 2 * tx, raw[r], own_types[r]);
-            }
-            Raw<T> hraw[2];
-            uint32_t htypes;
-            int hpr = 0, hpc = 0;
-            const bool has_halo = threadIdx.x < HALO_PAIRS;
-            if (has_halo) {
-                const int h = threadIdx.x;
-                if (h < 2 * IR) { hpc = h < IR ? 0 : PC - 1; hpr = h % IR; }
-                else { const int u = h - 2 * IR; hpr = u < PC - 2 ? 0 : IR - 1; hpc = 1 + u % (PC - 2); }
-                if (staged)
-                    staged_pair(*reinterpret_cast<const Staged<T>*>(&st), hpr, 2 * hpc + 2, hraw, htypes);
-                else
-                    load_pair(f, y0 - 1 + hpr, x0 - 2 + 2 * hpc, hraw, htypes);
-            }
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                derive<T, FM>(f.c, raw[r][0], own[r][0]);
-                derive<T, FM>(f.c, raw[r][1], own[r][1]);
-                store_pair(sm, 1 + 2 * tyy + r, 2 + 2 * tx, own[r][0], own[r][1]);
-            }
-            if (has_halo) {
-                Src<T> h0, h1;
-                derive<T, FM>(f.c, hraw[0], h0);
-                derive<T, FM>(f.c, hraw[1], h1);
-                store_pair(sm, hpr, 2 * hpc, h0, h1);
-            }
-        }
-        __syncthreads();  // derived values visible; the staging buffer is free
-        if (STAGE) {
-            const int tn = t + gridDim.x;
-            if (tn < ntiles) {
-                const int xn = (tn % tiles_x) * TX, yn = (tn / tiles_x) * TY;
-                if (interior_tile(f, xn, yn)) stage_tile(ff, st, xn, yn);
-            }
-            cp_async_commit();
-        }
-        // ---- phase B: nodes (x0 + 2 tx + k, y0 + 2 tyy + r)
-        const T q = T(0.25);
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int lr = 1 + 2 * tyy + r;    // tile row of the node
-            const int y = y0 + 2 * tyy + r;
-            T oe[2], ou[2], ov[2];
-            unsigned okmask = 0;
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int lc = 2 + 2 * tx + k;  // tile column of the node
-                const int x = x0 + 2 * tx + k;
-                const uint8_t ty = (uint8_t)(own_types[r] >> (8 * k));
-                const bool ok = x < f.nx && y < f.ny && (ty & KIND_MASK) != K_SOLID && !(ty & GENERAL_BIT);
-                okmask |= (ok ? 1u : 0u) << k;
-                const T cL_o1 = sm.o[0][lr][lc - 1], mL_o2 = sm.o[1][lr - 1][lc - 1], pL_o8 = sm.o[7][lr + 1][lc - 1];
-                const T cR_o5 = sm.o[4][lr][lc + 1], mR_o4 = sm.o[3][lr - 1][lc + 1], pR_o6 = sm.o[5][lr + 1][lc + 1];
-                const T mC_o3 = sm.o[2][lr - 1][lc], pC_o7 = sm.o[6][lr + 1][lc];
-                const V2 mL = sm.ed[lr - 1][lc - 1], mC = sm.ed[lr - 1][lc], mR = sm.ed[lr - 1][lc + 1];
-                const V2 cL = sm.ed[lr][lc - 1], cR = sm.ed[lr][lc + 1];
-                const V2 pL = sm.ed[lr + 1][lc - 1], pC = sm.ed[lr + 1][lc], pR = sm.ed[lr + 1][lc + 1];
-                const T OL = O::add(O::add(cL_o1, mL_o2), pL_o8);
-                const T OR = O::add(O::add(cR_o5, mR_o4), pR_o6);
-                const T Sh = O::add(O::add(OL, OR), O::add(mC_o3, pC_o7));
-                const T Sx = O::sub(OL, OR);
-                const T Sy = O::sub(O::add(O::add(mL_o2, mR_o4), mC_o3), O::add(O::add(pL_o8, pR_o6), pC_o7));
-                // lambda-weighted stencils of eta (.x) and D (.y): sum, x-moment, y-moment
-                const T MLe = O::fma(q, O::add(mL.x, pL.x), cL.x);
-                const T MRe = O::fma(q, O::add(mR.x, pR.x), cR.x);
-                const T MLd = O::fma(q, O::add(mL.y, pL.y), cL.y);
-                const T MRd = O::fma(q, O::add(mR.y, pR.y), cR.y);
-                const T Se = O::add(O::add(MLe, MRe), O::add(mC.x, pC.x));
-                const T Sd = O::add(O::add(MLd, MRd), O::add(mC.y, pC.y));
-                const T Xe = O::sub(MLe, MRe), Xd = O::sub(MLd, MRd);
-                const T Ye = O::fma(q, O::sub(O::add(mL.x, mR.x), O::add(pL.x, pR.x)), O::sub(mC.x, pC.x));
-                const T Yd = O::fma(q, O::sub(O::add(mL.y, mR.y), O::add(pL.y, pR.y)), O::sub(mC.y, pC.y));
-                const Src<T>& me = own[r][k];
-                const T A = O::mul(K.G6, me.D), B = O::mul(K.G6, me.eta);
-                // ownh already holds the receiver-only bed part 5 G6 eta_x D_x
-                const T eta1 = O::add(O::add(me.ownh, Sh), O::fma(A, Se, O::mul(-B, Sd)));
-                const T hu1 = O::fma(K.e, O::add(Sx, O::fma(A, Xe, O::mul(-B, Xd))), me.hFx);
-                const T hv1 = O::fma(K.e, O::add(Sy, O::fma(A, Ye, O::mul(-B, Yd))), me.hFy);
-                const T inv = O::rcp(O::add(me.D, eta1));
-                const bool noslip = (ty & KIND_MASK) == K_NOSLIP;
-                oe[k] = eta1;
-                ou[k] = noslip ? T(0) : O::mul(hu1, inv);
-                ov[k] = noslip ? T(0) : O::mul(hv1, inv);
-            }
-            if (okmask == 0) continue;
-            const size_t idx = (size_t)y * f.pitch + x0 + 2 * tx;
-            if (okmask == 3u) {
-                *reinterpret_cast<V2*>(f.eta1 + idx) = V2{oe[0], oe[1]};
-                *reinterpret_cast<V2*>(f.u1 + idx) = V2{ou[0], ou[1]};
-                *reinterpret_cast<V2*>(f.v1 + idx) = V2{ov[0], ov[1]};
-            } else {
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    if (okmask & (1u << k)) {
-                        f.eta1[idx + k] = oe[k];
-                        f.u1[idx + k] = ou[k];
-                        f.v1[idx + k] = ov[k];
-                    }
-                }
-            }
-        }
-        if (STAGE) cp_async_wait<0>();
-        __syncthreads();  // next tile staged; phase B done before phase A rewrites shared memory
-    }
-}
-
-// ---------------------------------------------------------------------------
 // General-link kernel: nodes with at least one bounce-back link (next to a
 // solid node or a bounce-back edge).  Each link is resolved as in the
 // paper's boundary rules: a solid or walled-off source bounces back
@@ -861,14 +588,10 @@ __device__ __forceinline__ T feq_diff(const Coef<T>& c, const NodeQ<T>& n, int c
                   n.h * cu * cu * c.k2 - c.K6 * n.h * n.uu);
 }
 
+// Update of one node (i, j) with the links resolved one by one.
 template <typename T>
-__global__ void __launch_bounds__(128) step_general_kernel(const Fields<T> f, const int* __restrict__ list,
-                                                           int count)
+__device__ __noinline__ void general_node(const Fields<T>& f, int i, int j)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= count) return;
-    const int node = list[t];
-    const int i = node % f.nx, j = node / f.nx;
     const size_t xi = (size_t)j * f.pitch + i;
     const Coef<T>& c = f.c;
     const NodeQ<T> X = node_q(f, xi, 0);
@@ -909,6 +632,16 @@ __global__ void __launch_bounds__(128) step_general_kernel(const Fields<T> f, co
     f.v1[xi] = v1;
 }
 
+template <typename T>
+__global__ void __launch_bounds__(128) step_general_kernel(const Fields<T> f, const int* __restrict__ list,
+                                                           int count)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int node = list[t];
+    general_node(f, node % f.nx, node / f.nx);
+}
+
 // ---------------------------------------------------------------------------
 // Dirichlet nodes, after every other node holds its new value: prescribed
 // quantities take their value at t_{n+1}; the unprescribed one takes the new
@@ -922,13 +655,9 @@ struct DirValues {
 };
 
 template <typename T>
-__global__ void dirichlet_kernel(T* __restrict__ eta, T* __restrict__ u, T* __restrict__ v,
-                                 const T* __restrict__ D, const double* __restrict__ D64,
-                                 const DirNode* __restrict__ list, int count, const DirValues bv)
+__device__ __forceinline__ void dirichlet_node(T* eta, T* u, T* v, const T* D, const double* D64, const DirNode d,
+                                               const DirValues& bv)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= count) return;
-    const DirNode d = list[t];
     const int kind = d.meta & 15, ed = d.meta >> 4;
     if (kind == K_DIR_H) {
         eta[d.x] = (T)(bv.h[ed] - D64[d.x]);
@@ -940,6 +669,227 @@ __global__ void dirichlet_kernel(T* __restrict__ eta, T* __restrict__ u, T* __re
     eta[d.x] = (T)(h - D64[d.x]);
     u[d.x] = (T)(bv.qx[ed] / h);
     v[d.x] = (T)(bv.qy[ed] / h);
+}
+
+template <typename T>
+__global__ void dirichlet_kernel(T* __restrict__ eta, T* __restrict__ u, T* __restrict__ v,
+                                 const T* __restrict__ D, const double* __restrict__ D64,
+                                 const DirNode* __restrict__ list, int count, const DirValues bv)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    dirichlet_node(eta, u, v, D, D64, list[t], bv);
+}
+
+// ---------------------------------------------------------------------------
+// Tile step kernel (the default).  A 256-thread block updates a tile of
+// TX x TY = 64 x 16 nodes:
+//   A. every thread loads node pairs of the tile plus its one-node halo
+//      (68 x 18 nodes), derives their source quantities and writes the eight
+//      outgoing values and (eta, D) to shared memory; the pairs it updates
+//      keep their own term, dt F / 2 and types in registers;
+//   B. after a barrier every thread gathers, for each of its 2 x 2 nodes,
+//      the eight incoming values and the eta / D stencils and writes
+//      eta, u, v; nodes with a bounce-back link take the per-link path
+//      (general_node) instead;
+//   C. when the tile holds Dirichlet nodes whose inward node lies in the
+//      same tile, after a second barrier they are set from the new values.
+// Thread (tx, ty) of 32 x 8 owns the node pairs at tile columns 2 + 2 tx,
+// 3 + 2 tx of tile rows 1 + 2 ty and 2 + 2 ty.
+namespace tile {
+constexpr int TX = 64, TY = 16;            // nodes updated per tile
+constexpr int THREADS = 256;               // 32 x 8
+constexpr int PC = TX / 2 + 2;             // 34 node pairs per tile row (with halo)
+constexpr int IR = TY + 2;                 // 18 tile rows (with halo)
+constexpr int IW = 2 * PC;                 // 68 tile columns: global x0 - 2 .. x0 + 65
+constexpr int HALO_PAIRS = 2 * IR + 2 * (PC - 2);  // 100
+template <typename T>
+struct Derived {
+    T o[8][IR][IW];                        // outgoing values o_1 .. o_8
+    typename Vec2<T>::type ed[IR][IW];     // (eta, D)
+};
+template <typename T> struct MinBlocks { static constexpr int value = 3; };
+template <> struct MinBlocks<double> { static constexpr int value = 2; };
+template <typename T>
+__host__ __device__ constexpr size_t smem_bytes() { return sizeof(Derived<T>); }
+}  // namespace tile
+
+// Dirichlet nodes handled inside the tile kernel: those of tile t are
+// list[start[t] .. start[t + 1]).
+struct TileDirichlet {
+    const int* start;      // nullptr when the tile kernel does not handle them
+    const DirNode* list;
+    const double* D64;
+    DirValues bv;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_pair(const Fields<T>& f, int y, int x, Raw<T> (&raw)[2], uint32_t& types)
+{
+    uint8_t fy = 0;
+    const int rr = resolve_index(y, f.ny, f.edge[2], f.edge[3], 2, fy);
+    if (rr >= 0 && x >= 0 && x + 2 <= f.nx) {
+        const size_t base = (size_t)rr * f.pitch + x;
+        using V2 = typename Vec2<T>::type;
+        const V2 e2 = *reinterpret_cast<const V2*>(f.eta + base);
+        const V2 u2 = *reinterpret_cast<const V2*>(f.u + base);
+        const V2 v2 = *reinterpret_cast<const V2*>(f.v + base);
+        const V2 d2 = *reinterpret_cast<const V2*>(f.D + base);
+        types = *reinterpret_cast<const uint16_t*>(f.type + base);
+        raw[0] = Raw<T>{e2.x, u2.x, v2.x, d2.x, fy};
+        raw[1] = Raw<T>{e2.y, u2.y, v2.y, d2.y, fy};
+        return;
+    }
+    types = 0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        uint8_t fl = fy;
+        const int cc = resolve_index(x + k, f.nx, f.edge[0], f.edge[1], 1, fl);
+        if (rr >= 0 && cc >= 0) {
+            const size_t idx = (size_t)rr * f.pitch + cc;
+            raw[k] = Raw<T>{f.eta[idx], f.u[idx], f.v[idx], f.D[idx], fl};
+            types |= (uint32_t)f.type[idx] << (8 * k);
+        } else {
+            raw[k] = Raw<T>{T(0), T(0), T(0), T(0), 0};
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_pair(tile::Derived<T>& sm, int pr, int lc, const Src<T>& a, const Src<T>& b)
+{
+    using V2 = typename Vec2<T>::type;
+    const T oa[8] = {a.o1, a.o2, a.o3, a.o4, a.o5, a.o6, a.o7, a.o8};
+    const T ob[8] = {b.o1, b.o2, b.o3, b.o4, b.o5, b.o6, b.o7, b.o8};
+#pragma unroll
+    for (int d = 0; d < 8; ++d) *reinterpret_cast<V2*>(&sm.o[d][pr][lc]) = V2{oa[d], ob[d]};
+    sm.ed[pr][lc] = V2{a.eta, a.D};
+    sm.ed[pr][lc + 1] = V2{b.eta, b.D};
+}
+
+template <typename T, int FM>
+__global__ void __launch_bounds__(tile::THREADS, tile::MinBlocks<T>::value)
+step_tile_kernel(const __grid_constant__ Fields<T> f, int tiles_x, const __grid_constant__ TileDirichlet td)
+{
+    using namespace tile;
+    using O = Op<T>;
+    using V2 = typename Vec2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Derived<T>& sm = *reinterpret_cast<Derived<T>*>(smem_raw);
+    const int tx = threadIdx.x & 31, tyy = threadIdx.x >> 5;
+    const Coef<T>& K = f.c;
+    const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY;
+    // ---- phase A: own pairs (tile pair column 1 + tx, tile rows 1 + 2 tyy + r)
+    Src<T> own[2][2];
+    uint32_t own_types[2];
+    {
+        Raw<T> raw[2][2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) load_pair(f, y0 + 2 * tyy + r, x0 + 2 * tx, raw[r], own_types[r]);
+        Raw<T> hraw[2];
+        uint32_t htypes;
+        int hpr = 0, hpc = 0;
+        const bool has_halo = threadIdx.x < HALO_PAIRS;
+        if (has_halo) {
+            const int h = threadIdx.x;
+            if (h < 2 * IR) { hpc = h < IR ? 0 : PC - 1; hpr = h % IR; }
+            else { const int u = h - 2 * IR; hpr = u < PC - 2 ? 0 : IR - 1; hpc = 1 + u % (PC - 2); }
+            load_pair(f, y0 - 1 + hpr, x0 - 2 + 2 * hpc, hraw, htypes);
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            derive<T, FM>(f.c, raw[r][0], own[r][0]);
+            derive<T, FM>(f.c, raw[r][1], own[r][1]);
+            store_pair(sm, 1 + 2 * tyy + r, 2 + 2 * tx, own[r][0], own[r][1]);
+        }
+        if (has_halo) {
+            Src<T> h0, h1;
+            derive<T, FM>(f.c, hraw[0], h0);
+            derive<T, FM>(f.c, hraw[1], h1);
+            store_pair(sm, hpr, 2 * hpc, h0, h1);
+        }
+    }
+    __syncthreads();
+    // ---- phase B: nodes (x0 + 2 tx + k, y0 + 2 tyy + r)
+    const T q = T(0.25);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int lr = 1 + 2 * tyy + r;    // tile row of the node
+        const int y = y0 + 2 * tyy + r;
+        T oe[2], ou[2], ov[2];
+        unsigned okmask = 0, genmask = 0;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int lc = 2 + 2 * tx + k;  // tile column of the node
+            const int x = x0 + 2 * tx + k;
+            const uint8_t ty = (uint8_t)(own_types[r] >> (8 * k));
+            const bool live = x < f.nx && y < f.ny && (ty & KIND_MASK) != K_SOLID;
+            okmask |= (live && !(ty & GENERAL_BIT) ? 1u : 0u) << k;
+            genmask |= (live && (ty & GENERAL_BIT) ? 1u : 0u) << k;
+            const T cL_o1 = sm.o[0][lr][lc - 1], mL_o2 = sm.o[1][lr - 1][lc - 1], pL_o8 = sm.o[7][lr + 1][lc - 1];
+            const T cR_o5 = sm.o[4][lr][lc + 1], mR_o4 = sm.o[3][lr - 1][lc + 1], pR_o6 = sm.o[5][lr + 1][lc + 1];
+            const T mC_o3 = sm.o[2][lr - 1][lc], pC_o7 = sm.o[6][lr + 1][lc];
+            const V2 mL = sm.ed[lr - 1][lc - 1], mC = sm.ed[lr - 1][lc], mR = sm.ed[lr - 1][lc + 1];
+            const V2 cL = sm.ed[lr][lc - 1], cR = sm.ed[lr][lc + 1];
+            const V2 pL = sm.ed[lr + 1][lc - 1], pC = sm.ed[lr + 1][lc], pR = sm.ed[lr + 1][lc + 1];
+            const T OL = O::add(O::add(cL_o1, mL_o2), pL_o8);
+            const T OR = O::add(O::add(cR_o5, mR_o4), pR_o6);
+            const T Sh = O::add(O::add(OL, OR), O::add(mC_o3, pC_o7));
+            const T Sx = O::sub(OL, OR);
+            const T Sy = O::sub(O::add(O::add(mL_o2, mR_o4), mC_o3), O::add(O::add(pL_o8, pR_o6), pC_o7));
+            // lambda-weighted stencils of eta (.x) and D (.y): sum, x-moment, y-moment
+            const T MLe = O::fma(q, O::add(mL.x, pL.x), cL.x);
+            const T MRe = O::fma(q, O::add(mR.x, pR.x), cR.x);
+            const T MLd = O::fma(q, O::add(mL.y, pL.y), cL.y);
+            const T MRd = O::fma(q, O::add(mR.y, pR.y), cR.y);
+            const T Se = O::add(O::add(MLe, MRe), O::add(mC.x, pC.x));
+            const T Sd = O::add(O::add(MLd, MRd), O::add(mC.y, pC.y));
+            const T Xe = O::sub(MLe, MRe), Xd = O::sub(MLd, MRd);
+            const T Ye = O::fma(q, O::sub(O::add(mL.x, mR.x), O::add(pL.x, pR.x)), O::sub(mC.x, pC.x));
+            const T Yd = O::fma(q, O::sub(O::add(mL.y, mR.y), O::add(pL.y, pR.y)), O::sub(mC.y, pC.y));
+            const Src<T>& me = own[r][k];
+            const T A = O::mul(K.G6, me.D), B = O::mul(K.G6, me.eta);
+            // ownh already holds the receiver-only bed part 5 G6 eta_x D_x
+            const T eta1 = O::add(O::add(me.ownh, Sh), O::fma(A, Se, O::mul(-B, Sd)));
+            const T hu1 = O::fma(K.e, O::add(Sx, O::fma(A, Xe, O::mul(-B, Xd))), me.hFx);
+            const T hv1 = O::fma(K.e, O::add(Sy, O::fma(A, Ye, O::mul(-B, Yd))), me.hFy);
+            const T inv = O::rcp(O::add(me.D, eta1));
+            const bool noslip = (ty & KIND_MASK) == K_NOSLIP;
+            oe[k] = eta1;
+            ou[k] = noslip ? T(0) : O::mul(hu1, inv);
+            ov[k] = noslip ? T(0) : O::mul(hv1, inv);
+        }
+        if (genmask) {
+#pragma unroll 1
+            for (int k = 0; k < 2; ++k)
+                if (genmask & (1u << k)) general_node(f, x0 + 2 * tx + k, y);
+        }
+        if (okmask == 0) continue;
+        const size_t idx = (size_t)y * f.pitch + x0 + 2 * tx;
+        if (okmask == 3u) {
+            *reinterpret_cast<V2*>(f.eta1 + idx) = V2{oe[0], oe[1]};
+            *reinterpret_cast<V2*>(f.u1 + idx) = V2{ou[0], ou[1]};
+            *reinterpret_cast<V2*>(f.v1 + idx) = V2{ov[0], ov[1]};
+        } else {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (okmask & (1u << k)) {
+                    f.eta1[idx + k] = oe[k];
+                    f.u1[idx + k] = ou[k];
+                    f.v1[idx + k] = ov[k];
+                }
+            }
+        }
+    }
+    // ---- phase C: Dirichlet nodes of this tile
+    if (td.start) {
+        const int b = td.start[blockIdx.x], e = td.start[blockIdx.x + 1];
+        if (b < e) {
+            __syncthreads();  // the block's new values are visible to the block
+            for (int k = b + (int)threadIdx.x; k < e; k += THREADS)
+                dirichlet_node(f.eta1, f.u1, f.v1, f.D, td.D64, td.list[k], td.bv);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
