@@ -253,7 +253,9 @@ def main():
     peak, peak_src = hbm_peak()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src,
-                "kernel": "step_fast_kernel<%s>" % ("float" if args.precision == "f32" else "double"),
+                "kernel": "%s<%s>" % ("step_tile_kernel" if info["step_kernel"] == 0 else "step_fast_kernel",
+                                      "float" if args.precision == "f32" else "double"),
+                "dirichlet_fused": bool(info["dirichlet_fused"]),
                 "bytes_per_node": BYTES_PER_NODE[args.precision],
                 "kernel_ms_per_launch": avg_kernel_s * 1e3,
                 "traffic": traffic_per_launch(args.precision, workload)}
@@ -295,7 +297,7 @@ def main():
                            "l2": "inputs larger than L2 (state %.0f MB), no flush" %
                                  (nodes * BYTES_PER_NODE[args.precision] / 1e6),
                            "parallelism": "replicas" if world > 1 else "single-gpu",
-                           "tile_rows": sim.info["tile_rows"]},
+                           "step_kernel": "tile 64x16" if info["step_kernel"] == 0 else "warp strip"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -135,7 +135,9 @@ typedef struct {
     int64_t n_fluid;         /* non-solid nodes                                */
     int64_t n_fast;          /* nodes updated on the interior fast path        */
     size_t device_bytes;     /* device memory held by the handle               */
-    int tile_rows;           /* rows per warp strip of the step kernel         */
+    int tile_rows;           /* rows per warp strip of the strip kernel        */
+    int step_kernel;         /* 0 = 64x16 tile kernel, 1 = warp-strip kernel    */
+    int dirichlet_fused;     /* 1 when Dirichlet nodes are set inside the step kernel */
 } maclab_info;
 
 /* Create a simulation (procedure steps (a)-(b) of Section 3).

@@ -43,7 +43,8 @@ class Info(ctypes.Structure):
     _fields_ = [("nx", c_int), ("ny", c_int), ("pitch", c_int), ("precision", c_int),
                 ("dx", c_double), ("e", c_double), ("dt", c_double), ("nu", c_double),
                 ("n_dirichlet", c_int64), ("n_fluid", c_int64), ("n_fast", c_int64),
-                ("device_bytes", c_size_t), ("tile_rows", c_int)]
+                ("device_bytes", c_size_t), ("tile_rows", c_int), ("step_kernel", c_int),
+                ("dirichlet_fused", c_int)]
 
 
 # (name, restype, argtypes) of every exported entry point of include/maclab.h

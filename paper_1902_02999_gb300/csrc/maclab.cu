@@ -191,7 +191,8 @@ int launch_step(maclab_t s)
     }
     const int b = 1 - s->cur;
     if (s->use_tile) {
-        // one launch: fast nodes, bounce-back-link nodes and (when fused) Dirichlet nodes
+        // fast nodes and (when fused) Dirichlet nodes in one launch; nodes with a
+        // bounce-back link in a second launch when there are any
         const int tx = (s->grid.nx + tile::TX - 1) / tile::TX, ty = (s->grid.ny + tile::TY - 1) / tile::TY;
         const size_t smem = tile::smem_bytes<T>();
         const TileDirichlet td{s->dir_fused ? s->dir_tile_start : nullptr, s->dir, s->D64, bv};
@@ -201,6 +202,9 @@ int launch_step(maclab_t s)
             MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
 #undef MACLAB_FM
         }
+        if (s->n_general > 0)
+            step_general_kernel<T><<<(s->n_general + 127) / 128, 128, 0, s->stream>>>(f, s->general,
+                                                                                      s->n_general);
     } else {
         const int warps = s->ncb * s->nrb;
         int blocks = (warps + WARPS - 1) / WARPS;
@@ -428,7 +432,7 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
     s->sumD = sumD;
 
     // Dirichlet nodes in tile order; the tile kernel applies them itself
-    // when every inward node is updated in the same tile.
+    // when every inward node is updated by the fast path of the same tile.
     const int tiles_x = (nx + tile::TX - 1) / tile::TX, tiles_y = (ny + tile::TY - 1) / tile::TY;
     auto tile_of = [&](int idx) {
         const int j = idx / pitch, i = idx - j * pitch;
@@ -439,7 +443,8 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
     std::vector<int> dir_start((size_t)tiles_x * tiles_y + 1, 0);
     bool fused = true;
     for (const DirNode& d : dirs) {
-        fused = fused && tile_of(d.x) == tile_of(d.n1);
+        const int j1 = d.n1 / pitch, i1 = d.n1 - j1 * pitch;
+        fused = fused && tile_of(d.x) == tile_of(d.n1) && !(type[(size_t)j1 * pitch + i1] & GENERAL_BIT);
         dir_start[tile_of(d.x) + 1]++;
     }
     for (size_t k = 1; k < dir_start.size(); ++k) dir_start[k] += dir_start[k - 1];
@@ -784,6 +789,8 @@ int maclab_get_info(maclab_t s, maclab_info* info)
     info->n_fast = s->n_fast;
     info->device_bytes = s->device_bytes;
     info->tile_rows = s->ty;
+    info->step_kernel = s->use_tile ? 0 : 1;
+    info->dirichlet_fused = (s->use_tile && s->dir_fused) ? 1 : 0;
     return MACLAB_OK;
 }
 

@@ -590,7 +590,7 @@ __device__ __forceinline__ T feq_diff(const Coef<T>& c, const NodeQ<T>& n, int c
 
 // Update of one node (i, j) with the links resolved one by one.
 template <typename T>
-__device__ __noinline__ void general_node(const Fields<T>& f, int i, int j)
+__device__ __forceinline__ void general_node(const Fields<T>& f, int i, int j)
 {
     const size_t xi = (size_t)j * f.pitch + i;
     const Coef<T>& c = f.c;
@@ -690,10 +690,11 @@ __global__ void dirichlet_kernel(T* __restrict__ eta, T* __restrict__ u, T* __re
 //      keep their own term, dt F / 2 and types in registers;
 //   B. after a barrier every thread gathers, for each of its 2 x 2 nodes,
 //      the eight incoming values and the eta / D stencils and writes
-//      eta, u, v; nodes with a bounce-back link take the per-link path
-//      (general_node) instead;
-//   C. when the tile holds Dirichlet nodes whose inward node lies in the
-//      same tile, after a second barrier they are set from the new values.
+//      eta, u, v (nodes with a bounce-back link are left to
+//      step_general_kernel);
+//   C. when every Dirichlet node's inward node lies in the same tile and
+//      has no bounce-back link, the tile's Dirichlet nodes are set from the
+//      new values after a second barrier.
 // Thread (tx, ty) of 32 x 8 owns the node pairs at tile columns 2 + 2 tx,
 // 3 + 2 tx of tile rows 1 + 2 ty and 2 + 2 ty.
 namespace tile {
@@ -817,15 +818,14 @@ step_tile_kernel(const __grid_constant__ Fields<T> f, int tiles_x, const __grid_
         const int lr = 1 + 2 * tyy + r;    // tile row of the node
         const int y = y0 + 2 * tyy + r;
         T oe[2], ou[2], ov[2];
-        unsigned okmask = 0, genmask = 0;
+        unsigned okmask = 0;
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int lc = 2 + 2 * tx + k;  // tile column of the node
             const int x = x0 + 2 * tx + k;
             const uint8_t ty = (uint8_t)(own_types[r] >> (8 * k));
-            const bool live = x < f.nx && y < f.ny && (ty & KIND_MASK) != K_SOLID;
-            okmask |= (live && !(ty & GENERAL_BIT) ? 1u : 0u) << k;
-            genmask |= (live && (ty & GENERAL_BIT) ? 1u : 0u) << k;
+            const bool ok = x < f.nx && y < f.ny && (ty & KIND_MASK) != K_SOLID && !(ty & GENERAL_BIT);
+            okmask |= (ok ? 1u : 0u) << k;
             const T cL_o1 = sm.o[0][lr][lc - 1], mL_o2 = sm.o[1][lr - 1][lc - 1], pL_o8 = sm.o[7][lr + 1][lc - 1];
             const T cR_o5 = sm.o[4][lr][lc + 1], mR_o4 = sm.o[3][lr - 1][lc + 1], pR_o6 = sm.o[5][lr + 1][lc + 1];
             const T mC_o3 = sm.o[2][lr - 1][lc], pC_o7 = sm.o[6][lr + 1][lc];
@@ -858,11 +858,6 @@ step_tile_kernel(const __grid_constant__ Fields<T> f, int tiles_x, const __grid_
             oe[k] = eta1;
             ou[k] = noslip ? T(0) : O::mul(hu1, inv);
             ov[k] = noslip ? T(0) : O::mul(hv1, inv);
-        }
-        if (genmask) {
-#pragma unroll 1
-            for (int k = 0; k < 2; ++k)
-                if (genmask & (1u << k)) general_node(f, x0 + 2 * tx + k, y);
         }
         if (okmask == 0) continue;
         const size_t idx = (size_t)y * f.pitch + x0 + 2 * tx;
