@@ -35,7 +35,7 @@ METRIC = ("MLUPS & % of HBM roofline (FP32 step); wall time to residual 1e-8, "
           "warm-start vs plain")
 BYTES_PER_NODE = {"f32": 29, "f64": 57}   # read eta,u,v,D + type, write eta,u,v
 FALLBACK_HBM_GBS = 6800.0
-PROFILE_JSON = os.path.join(ROOT, "profiles", "step_fast_kernel_traffic.json")
+PROFILE_JSON = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
 
 
 def kernel_source_hash() -> str:
@@ -220,7 +220,7 @@ def main():
     stream = torch.cuda.current_stream()
     info = sim.info
     n_general = info["n_fluid"] - info["n_fast"] - info["n_dirichlet"]
-    launches_per_step = 1 + (n_general > 0) + (info["n_dirichlet"] > 0)
+    launches_per_step = 1 + (n_general > 0) + (info["n_dirichlet"] > 0 and not info["dirichlet_fused"])
 
     sampler = ClockSampler(local)
     sim.step(max(args.warmup, 3))
