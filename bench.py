@@ -188,6 +188,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tile-rows", type=int, default=0)
+    ap.add_argument("--no-extra", action="store_true", help="skip the steady-state and FP64 legs")
+    ap.add_argument("--steady-max-steps", type=int, default=2_000_000)
+    ap.add_argument("--f64-steps", type=int, default=300)
     args = ap.parse_args()
     workload = "bump_channel_%dx%d_%s" % (args.nx, args.ny, args.precision)
 
@@ -288,6 +291,42 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(case)
 
+    # the other half of the metric: wall time to a residual of 1e-8 for the
+    # seeded 256 x 256 dish lake (plain method, FP32 storage)
+    steady = None
+    if not args.no_extra:
+        lake = inputs.dish_lake(256, seed=0)
+        ls = Simulation.from_case(lake, precision="f32")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ok, nsteps, r = ls.run_to_steady(tol=1e-8, max_steps=args.steady_max_steps, check_every=1000)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        steady = {"workload": lake.name, "precision": "f32", "tol": 1e-8, "converged": ok,
+                  "steps": nsteps, "residual": r, "wall_s": wall,
+                  "mlups": lake.nodes * nsteps / wall / 1e6, "simulated_s": nsteps * lake.dt}
+        ls.close()
+
+    # the FP64 variant of the channel step (timed, not the headline)
+    f64 = None
+    if not args.no_extra and args.precision == "f32":
+        s64 = Simulation.from_case(case, precision="f64")
+        s64.step(20)
+        torch.cuda.synchronize()
+        s64.set_profiling(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s64.step(args.f64_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        k64, n64 = s64.get_profile()
+        ms64 = e0.elapsed_time(e1) / args.f64_steps
+        f64 = {"value": nodes / (ms64 / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms64,
+               "kernel_ms_per_launch": k64 / max(1, n64),
+               "achieved_gbs": BYTES_PER_NODE["f64"] * nodes / (k64 / max(1, n64) / 1e3) / 1e9,
+               "bytes_per_node": BYTES_PER_NODE["f64"]}
+        s64.close()
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -299,6 +338,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single-gpu",
                            "step_kernel": "tile 64x16" if info["step_kernel"] == 0 else "warp strip"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "steady_state": steady, "f64": f64,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)
     sim.close()

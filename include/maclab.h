@@ -165,6 +165,13 @@ int maclab_set_stream(maclab_t sim, void* stream);
  * has Dirichlet nodes.  Asynchronous on the handle's stream. */
 int maclab_step(maclab_t sim, int64_t n);
 
+/* Steps per CUDA-graph replay in maclab_step (an even number, 0 = off;
+ * default 64).  When no boundary value depends on time and profiling is
+ * off, maclab_step runs whole blocks of this many steps by replaying a
+ * graph captured once per handle (on a private stream) and launches the
+ * remaining steps one by one.  Results are identical either way. */
+int maclab_set_graph_steps(maclab_t sim, int steps);
+
 /* Copy the current state to caller-owned host double arrays [ny*nx]
  * (any may be NULL).  h is reconstructed as (h_ref - z_b) + eta in double.
  * Synchronises the stream. */

@@ -225,6 +225,10 @@ class Simulation:
         self.info["tile_rows"] = min(int(rows), self.ny)
         self.info["grid_blocks"] = int(blocks)
 
+    def set_graph_steps(self, steps: int) -> None:
+        """Steps per CUDA-graph replay (even, 0 = off)."""
+        self._check(self._lib.maclab_set_graph_steps(self._h, int(steps)))
+
     def set_profiling(self, on: bool) -> None:
         self._check(self._lib.maclab_set_profiling(self._h, 1 if on else 0))
 

@@ -55,6 +55,7 @@ PROTOTYPES = [
                               P(c_void_p)]),
     ("maclab_set_stream", c_int, [c_void_p, c_void_p]),
     ("maclab_step", c_int, [c_void_p, c_int64]),
+    ("maclab_set_graph_steps", c_int, [c_void_p, c_int]),
     ("maclab_get_state", c_int, [c_void_p, P(c_double), P(c_double), P(c_double)]),
     ("maclab_set_state", c_int, [c_void_p, P(c_double), P(c_double), P(c_double)]),
     ("maclab_residual", c_int, [c_void_p, P(c_double)]),

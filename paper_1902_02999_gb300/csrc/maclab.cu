@@ -66,6 +66,10 @@ struct maclab_s {
     int fmode = 0;             // force terms present: F_WIND | F_FRICTION | F_CORIOLIS
     int grid_blocks = 0;       // cap on step-kernel blocks (0 = one warp per strip)
     bool use_tile = true;      // tile kernel (default) or warp-strip kernel
+    int graph_steps = 64;      // steps per CUDA-graph replay (even; 0 = no graphs)
+    bool steady_bc = true;     // no boundary value depends on time
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // per starting buffer parity
     bool dir_fused = false;    // Dirichlet nodes handled inside the tile kernel
     int* dir_tile_start = nullptr;  // per-tile ranges of the Dirichlet list
     int64_t n_fluid = 0, n_fast = 0;
@@ -363,6 +367,8 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
         s->has_alloc = true;
     }
     s->pitch = (nx + 63) / 64 * 64;
+    for (int k = 0; k < 4; ++k)
+        if (b.h[k].amp != 0 || b.qx[k].amp != 0 || b.qy[k].amp != 0) s->steady_bc = false;
     s->fmode = ((params->wind_u != 0 || params->wind_v != 0) ? F_WIND : 0) |
                (params->Cb != 0 ? F_FRICTION : 0) | (params->Omega != 0 ? F_CORIOLIS : 0);
     cudaGetDevice(&s->device);
@@ -566,14 +572,90 @@ int maclab_set_stream(maclab_t s, void* stream)
     return MACLAB_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+void drop_graphs(maclab_t s)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (s->graph[k]) cudaGraphExecDestroy(s->graph[k]);
+        s->graph[k] = nullptr;
+    }
+}
+
+// Capture graph_steps launches of the step starting from buffer parity
+// s->cur on a private stream (nothing runs), then restore the handle.
+int capture_graph(maclab_t s)
+{
+    cudaError_t e = cudaSuccess;
+    if (!s->capture_stream) e = cudaStreamCreateWithFlags(&s->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(s, e, "capture stream");
+    const cudaStream_t user = s->stream;
+    const int cur = s->cur;
+    const int64_t n = s->n;
+    const bool have_prev = s->have_prev;
+    s->stream = s->capture_stream;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(s->capture_stream, cudaStreamCaptureModeThreadLocal);
+    int rc = MACLAB_OK;
+    if (e == cudaSuccess) {
+        for (int k = 0; k < s->graph_steps && rc == MACLAB_OK; ++k)
+            rc = s->prec == MACLAB_F32 ? launch_step<float>(s) : launch_step<double>(s);
+        e = cudaStreamEndCapture(s->capture_stream, &g);
+    }
+    s->stream = user;
+    s->cur = cur;
+    s->n = n;
+    s->have_prev = have_prev;
+    if (rc != MACLAB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&s->graph[cur], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        s->graph[cur] = nullptr;
+        return cuda_fail(s, e, "graph capture");
+    }
+    return MACLAB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int maclab_step(maclab_t s, int64_t n)
 {
     if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
     if (n < 0) return fail(s, MACLAB_E_ARG, "n must be >= 0");
+    // whole blocks of graph_steps steps replay a captured CUDA graph when the
+    // launches do not change from step to step (steady boundary data)
+    const bool graphs = s->graph_steps > 0 && s->steady_bc && !s->profiling;
+    while (graphs && n >= s->graph_steps) {
+        if (!s->graph[s->cur]) {
+            int rc = capture_graph(s);
+            if (rc != MACLAB_OK) return rc;
+        }
+        cudaError_t e = cudaGraphLaunch(s->graph[s->cur], s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "graph launch");
+        s->n += s->graph_steps;  // an even number of steps: the parity is unchanged
+        s->have_prev = true;
+        n -= s->graph_steps;
+    }
     for (int64_t k = 0; k < n; ++k) {
         int rc = s->prec == MACLAB_F32 ? launch_step<float>(s) : launch_step<double>(s);
         if (rc != MACLAB_OK) return rc;
     }
+    return MACLAB_OK;
+}
+
+int maclab_set_graph_steps(maclab_t s, int steps)
+{
+    if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    if (steps < 0 || (steps & 1)) return fail(s, MACLAB_E_ARG, "steps must be an even number >= 0");
+    drop_graphs(s);
+    s->graph_steps = steps;
     return MACLAB_OK;
 }
 
@@ -744,6 +826,7 @@ int maclab_set_launch(maclab_t s, int rows, int blocks)
     s->ty = std::min(rows, s->grid.ny);
     s->nrb = (s->grid.ny + s->ty - 1) / s->ty;
     s->grid_blocks = blocks;
+    drop_graphs(s);
     return MACLAB_OK;
 }
 
@@ -808,6 +891,8 @@ void maclab_destroy(maclab_t s)
     if (!s) return;
     cudaStreamSynchronize(s->stream);
     for (cudaEvent_t ev : s->events) cudaEventDestroy(ev);
+    drop_graphs(s);
+    if (s->capture_stream) cudaStreamDestroy(s->capture_stream);
     release_all(s);
     delete s;
 }
