@@ -276,6 +276,62 @@ void maclab_destroy(maclab_t sim);
 /* MACLAB_ABI_VERSION of the loaded library. */
 int maclab_abi_version(void);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent grids (for example an ensemble of lakes and
+ * channels of different sizes) advanced together by the same update as
+ * maclab_step.  One step is one launch of the step kernel over the packed
+ * tiles of every active instance (plus the small kernels for links into
+ * walls and for Dirichlet nodes when an instance needs them); whole blocks
+ * of steps replay a captured CUDA graph.  Each instance gets exactly the
+ * values a separate handle would give.
+ */
+typedef struct maclab_batch_s* maclab_batch_t;
+
+/* Create a batch of `count` instances.  grids, params: arrays [count];
+ * bcs: array [count] or NULL (bounce-back edges); zb, mask: arrays [count]
+ * of host pointers as in maclab_create; h0, u0, v0: NULL, or arrays [count]
+ * of host pointers each NULL for still water.  All instances must share one
+ * precision, and their boundary data must not depend on time (amp == 0).
+ * Errors as maclab_create; messages via maclab_batch_last_error(NULL). */
+int maclab_batch_create(int count, const maclab_grid* grids, const maclab_params* params,
+                        const maclab_bc* bcs, const double* const* zb, const uint8_t* const* mask,
+                        const double* const* h0, const double* const* u0, const double* const* v0,
+                        const maclab_allocator* alloc, void* stream, maclab_batch_t* out);
+
+/* Advance every active instance n steps (asynchronous). */
+int maclab_batch_step(maclab_batch_t batch, int64_t n);
+
+/* Steps per CUDA-graph replay in maclab_batch_step (even, 0 = off). */
+int maclab_batch_set_graph_steps(maclab_batch_t batch, int steps);
+
+/* Residual of the last step per instance: out[4*i .. 4*i+3] as
+ * maclab_residual for instance i.  Synchronises. */
+int maclab_batch_residual(maclab_batch_t batch, double* out);
+
+/* Instances with flags[i] == 0 stop advancing (their state stays as it is);
+ * flags [count]. */
+int maclab_batch_set_active(maclab_batch_t batch, const uint8_t* flags);
+
+/* Step the batch until every active instance has a step residual <= tol,
+ * checking every check_every steps and switching converged instances off.
+ * steps[i] (may be NULL) receives the batch step count at which instance i
+ * converged (-1 if it did not), r_final[i] its last residual, seconds[i]
+ * the wall-clock time from the call's start to that check.  Returns
+ * MACLAB_E_STATE when max_steps ran out first. */
+int maclab_batch_run_to_steady(maclab_batch_t batch, double tol, int64_t max_steps, int check_every,
+                               int64_t* steps, double* r_final, double* seconds);
+
+/* State of instance i as maclab_get_state / maclab_set_state. */
+int maclab_batch_get_state(maclab_batch_t batch, int i, double* h, double* u, double* v);
+int maclab_batch_set_state(maclab_batch_t batch, int i, const double* h, const double* u,
+                           const double* v);
+
+/* Instance count, total nodes, total tiles and steps taken. */
+int maclab_batch_info(maclab_batch_t batch, int* count, int64_t* nodes, int64_t* tiles, int64_t* steps);
+
+const char* maclab_batch_last_error(maclab_batch_t batch);
+void maclab_batch_destroy(maclab_batch_t batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,7 @@ SOLID, FLUID, NOSLIP, DIR_H, DIR_Q, DIR_HU = 0, 1, 2, 3, 4, 5
 BOUNCEBACK, SPECULAR, PERIODIC = 0, 1, 2
 F32, F64 = 0, 1
 
-__all__ = ["Simulation", "MaclabError", "build_library", "lib"]
+__all__ = ["Simulation", "Batch", "MaclabError", "build_library", "lib"]
 
 
 class MaclabError(RuntimeError):
@@ -278,3 +278,131 @@ class Simulation:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch:
+    """Many independent grids advanced together (maclab_batch_* of the C ABI).
+
+    ``cases`` are objects with the attributes of ``Simulation.from_case``;
+    every instance must have time-independent boundary data.  Each instance
+    gets exactly the values a separate Simulation would give.
+    """
+
+    def __init__(self, cases, precision: str = "f32", initial: bool = True, stream=None,
+                 torch_allocator: bool = True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("maclab needs a CUDA GPU; no CPU fallback exists")
+        self._lib = lib()
+        cases = list(cases)
+        n = len(cases)
+        self.count = n
+        self.shapes = [(c.ny, c.nx) for c in cases]
+        prec = {"f32": F32, "f64": F64}[precision]
+        self.precision = precision
+        grids = (_abi.Grid * n)()
+        params = (_abi.Params * n)()
+        bcs = (_abi.BC * n)()
+        keep = []
+        zbp = (ctypes.POINTER(ctypes.c_double) * n)()
+        mkp = (ctypes.POINTER(ctypes.c_uint8) * n)()
+        hp = (ctypes.POINTER(ctypes.c_double) * n)()
+        up = (ctypes.POINTER(ctypes.c_double) * n)()
+        vp = (ctypes.POINTER(ctypes.c_double) * n)()
+        for i, c in enumerate(cases):
+            N = c.nx * c.ny
+            grids[i] = _abi.Grid(c.nx, c.ny, float(c.dx))
+            params[i] = _abi.Params(prec, float(c.nu), 0.0, float(c.g), float(c.rho_w), float(c.rho_a),
+                                    float(c.cw), float(c.wind_u), float(c.wind_v), float(c.cb),
+                                    float(c.omega), float(c.h_ref))
+            bcv = np.asarray(c.bc, dtype=np.float64).reshape(4, 3, 4)
+            for k in range(4):
+                bcs[i].edge[k] = int(c.edges[k])
+                bcs[i].h[k] = _abi.Wave(*bcv[k, 0])
+                bcs[i].qx[k] = _abi.Wave(*bcv[k, 1])
+                bcs[i].qy[k] = _abi.Wave(*bcv[k, 2])
+            zb = _f64(c.zb, N)
+            mk = np.ascontiguousarray(np.asarray(c.mask, dtype=np.uint8).reshape(-1))
+            keep += [zb, mk]
+            zbp[i] = _dptr(zb)
+            mkp[i] = mk.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+            if initial:
+                h, u, v = _f64(c.h0, N), _f64(c.u0, N), _f64(c.v0, N)
+                keep += [h, u, v]
+                hp[i], up[i], vp[i] = _dptr(h), _dptr(u), _dptr(v)
+        self.device = torch.cuda.current_device()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        sptr = int(getattr(stream, "cuda_stream", stream) or 0)
+        self._alloc = _TorchAllocator(self.device, sptr) if torch_allocator else None
+        handle = ctypes.c_void_p()
+        rc = self._lib.maclab_batch_create(
+            n, grids, params, bcs, zbp, mkp, hp if initial else None, up if initial else None,
+            vp if initial else None, ctypes.byref(self._alloc.struct) if self._alloc else None,
+            ctypes.c_void_p(sptr), ctypes.byref(handle))
+        if rc != 0:
+            raise MaclabError(rc, self._lib.maclab_batch_last_error(None).decode())
+        self._h = handle
+        _live.add(self)
+
+    def _check(self, rc):
+        if rc != 0:
+            raise MaclabError(rc, self._lib.maclab_batch_last_error(self._h).decode())
+
+    def step(self, n: int = 1) -> None:
+        self._check(self._lib.maclab_batch_step(self._h, int(n)))
+
+    def set_graph_steps(self, steps: int) -> None:
+        self._check(self._lib.maclab_batch_set_graph_steps(self._h, int(steps)))
+
+    def residual(self) -> np.ndarray:
+        """[count, 4]: residual, mass, max|u|, non-finite count per instance."""
+        out = np.zeros(4 * self.count)
+        self._check(self._lib.maclab_batch_residual(self._h, _dptr(out)))
+        return out.reshape(self.count, 4)
+
+    def set_active(self, flags) -> None:
+        f = np.ascontiguousarray(np.asarray(flags, dtype=np.uint8))
+        self._check(self._lib.maclab_batch_set_active(self._h, f.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+
+    def run_to_steady(self, tol: float = 1e-8, max_steps: int = 10 ** 7, check_every: int = 1000):
+        """Returns (steps[count], residual[count], seconds[count]) -- steps is -1 for
+        an instance that did not converge within max_steps."""
+        steps = np.zeros(self.count, dtype=np.int64)
+        r = np.zeros(self.count)
+        sec = np.full(self.count, np.nan)
+        rc = self._lib.maclab_batch_run_to_steady(
+            self._h, float(tol), int(max_steps), int(check_every),
+            steps.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dptr(r), _dptr(sec))
+        if rc not in (0, -5):
+            self._check(rc)
+        return steps, r, sec
+
+    def get_state(self, i: int):
+        ny, nx = self.shapes[i]
+        h, u, v = np.empty(nx * ny), np.empty(nx * ny), np.empty(nx * ny)
+        self._check(self._lib.maclab_batch_get_state(self._h, int(i), _dptr(h), _dptr(u), _dptr(v)))
+        return h.reshape(ny, nx), u.reshape(ny, nx), v.reshape(ny, nx)
+
+    def set_state(self, i: int, h, u, v) -> None:
+        ny, nx = self.shapes[i]
+        N = nx * ny
+        h, u, v = _f64(h, N), _f64(u, N), _f64(v, N)
+        self._check(self._lib.maclab_batch_set_state(self._h, int(i), _dptr(h), _dptr(u), _dptr(v)))
+
+    def info(self):
+        c, nodes, tiles, steps = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._lib.maclab_batch_info(self._h, ctypes.byref(c), ctypes.byref(nodes),
+                                                ctypes.byref(tiles), ctypes.byref(steps)))
+        return {"count": c.value, "nodes": nodes.value, "tiles": tiles.value, "steps": steps.value}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.maclab_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

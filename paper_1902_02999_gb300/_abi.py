@@ -71,6 +71,20 @@ PROTOTYPES = [
     ("maclab_get_info", c_int, [c_void_p, P(Info)]),
     ("maclab_device_state", c_int, [c_void_p, P(c_void_p), P(c_void_p), P(c_void_p)]),
     ("maclab_last_error", ctypes.c_char_p, [c_void_p]),
+    ("maclab_batch_create", c_int, [c_int, P(Grid), P(Params), P(BC), P(P(c_double)),
+                                    P(P(ctypes.c_uint8)), P(P(c_double)), P(P(c_double)),
+                                    P(P(c_double)), P(Allocator), c_void_p, P(c_void_p)]),
+    ("maclab_batch_step", c_int, [c_void_p, c_int64]),
+    ("maclab_batch_set_graph_steps", c_int, [c_void_p, c_int]),
+    ("maclab_batch_residual", c_int, [c_void_p, P(c_double)]),
+    ("maclab_batch_set_active", c_int, [c_void_p, P(ctypes.c_uint8)]),
+    ("maclab_batch_run_to_steady", c_int, [c_void_p, c_double, c_int64, c_int, P(c_int64),
+                                           P(c_double), P(c_double)]),
+    ("maclab_batch_get_state", c_int, [c_void_p, c_int, P(c_double), P(c_double), P(c_double)]),
+    ("maclab_batch_set_state", c_int, [c_void_p, c_int, P(c_double), P(c_double), P(c_double)]),
+    ("maclab_batch_info", c_int, [c_void_p, P(c_int), P(c_int64), P(c_int64), P(c_int64)]),
+    ("maclab_batch_last_error", ctypes.c_char_p, [c_void_p]),
+    ("maclab_batch_destroy", None, [c_void_p]),
     ("maclab_destroy", None, [c_void_p]),
 ]
 

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -124,10 +125,8 @@ void release_all(maclab_t s)
 }
 
 template <typename T>
-Coef<T> make_coef(const maclab_s* s)
+Coef<T> make_coef(const maclab_params& p, double e, double dt)
 {
-    const maclab_params& p = s->params;
-    const double e = s->e, dt = s->dt;
     const double wmag = std::sqrt(p.wind_u * p.wind_u + p.wind_v * p.wind_v);
     Coef<T> c;
     c.e = (T)e;
@@ -162,7 +161,7 @@ Fields<T> make_fields(const maclab_s* s)
     f.ny = s->grid.ny;
     f.pitch = s->pitch;
     for (int k = 0; k < 4; ++k) f.edge[k] = s->bc.edge[k];
-    f.c = make_coef<T>(s);
+    f.c = make_coef<T>(s->params, s->e, s->dt);
     return f;
 }
 
@@ -306,6 +305,141 @@ int choose_tile_rows(int ny, int ncb, int sms)
     return ty;
 }
 
+// Host-side preparation of one grid: validation, node classification,
+// Dirichlet list in tile order, still-water depth (procedure steps (a)-(b)
+// of Section 3, done once per grid).
+struct Prepared {
+    int nx = 0, ny = 0, pitch = 0;
+    double e = 0, dt = 0;
+    maclab_params params{};
+    maclab_bc bc{};
+    int fmode = 0;
+    bool steady_bc = true;
+    std::vector<uint8_t> type;      // [ny][pitch], kind | GENERAL_BIT
+    std::vector<int> general;       // j * nx + i of nodes with a bounce-back link
+    std::vector<DirNode> dirs;      // in tile order, storage indices
+    std::vector<int> dir_start;     // per-tile ranges of dirs
+    bool dir_fused = false;
+    std::vector<double> D64;        // [ny][pitch] still-water depth h_ref - z_b
+    double sumD = 0;
+    int64_t n_fluid = 0, n_fast = 0;
+    int tiles_x = 0, tiles_y = 0;
+};
+
+int prepare(const maclab_grid* grid, const maclab_params* params, const maclab_bc* bc, const double* zb,
+            const uint8_t* mask, Prepared& P)
+{
+    if (!grid || !params || !zb || !mask) return fail(nullptr, MACLAB_E_ARG, "grid, params, zb and mask are required");
+    const int nx = grid->nx, ny = grid->ny;
+    if (nx < 1 || ny < 1) return fail(nullptr, MACLAB_E_ARG, "nx and ny must be >= 1");
+    if ((int64_t)nx * ny > (int64_t)1 << 31 || nx > (1 << 30) - 64)
+        return fail(nullptr, MACLAB_E_ARG, "grid too large (nx*ny must fit in 31 bits)");
+    if (!(grid->dx > 0) || !std::isfinite(grid->dx)) return fail(nullptr, MACLAB_E_ARG, "dx must be > 0");
+    if (params->precision != MACLAB_F32 && params->precision != MACLAB_F64)
+        return fail(nullptr, MACLAB_E_ARG, "unknown precision");
+    const double e = params->e > 0 ? params->e : 6.0 * params->nu / grid->dx;
+    if (!(e > 0) || !std::isfinite(e)) return fail(nullptr, MACLAB_E_ARG, "need e > 0 or nu > 0");
+    if (!(params->g > 0) || !(params->rho_w > 0)) return fail(nullptr, MACLAB_E_ARG, "need g > 0 and rho_w > 0");
+    maclab_bc b{};
+    if (bc) b = *bc;
+    for (int k = 0; k < 4; ++k)
+        if (b.edge[k] < MACLAB_BOUNCEBACK || b.edge[k] > MACLAB_PERIODIC)
+            return fail(nullptr, MACLAB_E_ARG, "unknown edge kind");
+    if ((b.edge[0] == MACLAB_PERIODIC) != (b.edge[1] == MACLAB_PERIODIC) ||
+        (b.edge[2] == MACLAB_PERIODIC) != (b.edge[3] == MACLAB_PERIODIC))
+        return fail(nullptr, MACLAB_E_ARG, "periodic edges must come in W/E or S/N pairs");
+    const size_t N = (size_t)nx * ny;
+    for (size_t k = 0; k < N; ++k)
+        if (mask[k] > MACLAB_DIR_HU) return fail(nullptr, MACLAB_E_ARG, "unknown node type in mask");
+
+    P.nx = nx;
+    P.ny = ny;
+    P.pitch = (nx + 63) / 64 * 64;
+    P.e = e;
+    P.dt = grid->dx / e;
+    P.params = *params;
+    P.bc = b;
+    for (int k = 0; k < 4; ++k)
+        if (b.h[k].amp != 0 || b.qx[k].amp != 0 || b.qy[k].amp != 0) P.steady_bc = false;
+    P.fmode = ((params->wind_u != 0 || params->wind_v != 0) ? F_WIND : 0) |
+              (params->Cb != 0 ? F_FRICTION : 0) | (params->Omega != 0 ? F_CORIOLIS : 0);
+    const int pitch = P.pitch;
+    auto kind_at = [&](int i, int j) { return mask[(size_t)j * nx + i]; };
+    auto resolve = [&](int i, int n, int lo, int hi) -> int {
+        if (i >= 0 && i < n) return i;
+        int kd = i < 0 ? lo : hi;
+        if (kd == MACLAB_PERIODIC) return ((i % n) + n) % n;
+        if (kd == MACLAB_SPECULAR) {
+            i = i < 0 ? -1 - i : 2 * n - 1 - i;
+            return (i >= 0 && i < n) ? i : -1;
+        }
+        return -1;
+    };
+    static const int CX[9] = {0, 1, 1, 0, -1, -1, -1, 0, 1};
+    static const int CY[9] = {0, 0, 1, 1, 1, 0, -1, -1, -1};
+    P.type.assign((size_t)pitch * ny, (uint8_t)K_SOLID);
+    P.D64.assign((size_t)pitch * ny, 0.0);
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            const uint8_t kd = kind_at(i, j);
+            uint8_t t = kd;
+            P.D64[(size_t)j * pitch + i] = params->h_ref - zb[(size_t)j * nx + i];
+            if (kd != MACLAB_SOLID) {
+                P.n_fluid++;
+                P.sumD += params->h_ref - zb[(size_t)j * nx + i];
+                if (kd >= MACLAB_DIR_H) {
+                    int di = 0, dj = 0, ed;
+                    if (i == 0) { di = 1; ed = 0; }
+                    else if (i == nx - 1) { di = -1; ed = 1; }
+                    else if (j == 0) { dj = 1; ed = 2; }
+                    else if (j == ny - 1) { dj = -1; ed = 3; }
+                    else return fail(nullptr, MACLAB_E_ARG, "Dirichlet node not on a grid edge");
+                    const int i1 = i + di, j1 = j + dj;
+                    if (i1 < 0 || i1 >= nx || j1 < 0 || j1 >= ny || kind_at(i1, j1) == MACLAB_SOLID ||
+                        kind_at(i1, j1) >= MACLAB_DIR_H)
+                        return fail(nullptr, MACLAB_E_ARG,
+                                    "the inward node of a Dirichlet node must be non-solid and not Dirichlet");
+                    P.dirs.push_back(DirNode{j * pitch + i, j1 * pitch + i1, (int)kd | (ed << 4)});
+                } else {
+                    bool gen = false;
+                    for (int a = 1; a < 9 && !gen; ++a) {
+                        const int si = resolve(i - CX[a], nx, b.edge[0], b.edge[1]);
+                        const int sj = resolve(j - CY[a], ny, b.edge[2], b.edge[3]);
+                        gen = si < 0 || sj < 0 || kind_at(si, sj) == MACLAB_SOLID;
+                    }
+                    if (gen) {
+                        t |= GENERAL_BIT;
+                        P.general.push_back(j * nx + i);
+                    } else {
+                        P.n_fast++;
+                    }
+                }
+            }
+            P.type[(size_t)j * pitch + i] = t;
+        }
+    }
+    // Dirichlet nodes in tile order; the tile kernel applies them itself
+    // when every inward node is updated by the fast path of the same tile.
+    P.tiles_x = (nx + tile::TX - 1) / tile::TX;
+    P.tiles_y = (ny + tile::TY - 1) / tile::TY;
+    auto tile_of = [&](int idx) {
+        const int j = idx / pitch, i = idx - j * pitch;
+        return (j / tile::TY) * P.tiles_x + i / tile::TX;
+    };
+    std::stable_sort(P.dirs.begin(), P.dirs.end(),
+                     [&](const DirNode& a, const DirNode& c) { return tile_of(a.x) < tile_of(c.x); });
+    P.dir_start.assign((size_t)P.tiles_x * P.tiles_y + 1, 0);
+    bool fused = true;
+    for (const DirNode& d : P.dirs) {
+        const int j1 = d.n1 / pitch, i1 = d.n1 - j1 * pitch;
+        fused = fused && tile_of(d.x) == tile_of(d.n1) && !(P.type[(size_t)j1 * pitch + i1] & GENERAL_BIT);
+        P.dir_start[tile_of(d.x) + 1]++;
+    }
+    for (size_t k = 1; k < P.dir_start.size(); ++k) P.dir_start[k] += P.dir_start[k - 1];
+    P.dir_fused = fused && !P.dirs.empty();
+    return MACLAB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -324,137 +458,42 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
 {
     if (!out) return fail(nullptr, MACLAB_E_ARG, "out is NULL");
     *out = nullptr;
-    if (!grid || !params || !zb || !mask) return fail(nullptr, MACLAB_E_ARG, "grid, params, zb and mask are required");
-    const int nx = grid->nx, ny = grid->ny;
-    if (nx < 1 || ny < 1) return fail(nullptr, MACLAB_E_ARG, "nx and ny must be >= 1");
-    if ((int64_t)nx * ny > (int64_t)1 << 31 || nx > (1 << 30) - 64)
-        return fail(nullptr, MACLAB_E_ARG, "grid too large (nx*ny must fit in 31 bits)");
-    if (!(grid->dx > 0) || !std::isfinite(grid->dx)) return fail(nullptr, MACLAB_E_ARG, "dx must be > 0");
-    if (params->precision != MACLAB_F32 && params->precision != MACLAB_F64)
-        return fail(nullptr, MACLAB_E_ARG, "unknown precision");
-    double e = params->e > 0 ? params->e : 6.0 * params->nu / grid->dx;
-    if (!(e > 0) || !std::isfinite(e)) return fail(nullptr, MACLAB_E_ARG, "need e > 0 or nu > 0");
-    if (!(params->g > 0) || !(params->rho_w > 0)) return fail(nullptr, MACLAB_E_ARG, "need g > 0 and rho_w > 0");
     if ((h0 == nullptr) != (u0 == nullptr) || (h0 == nullptr) != (v0 == nullptr))
         return fail(nullptr, MACLAB_E_ARG, "h0, u0, v0 must be all given or all NULL");
     if (alloc && (!alloc->alloc || !alloc->release))
         return fail(nullptr, MACLAB_E_ARG, "allocator needs alloc and release");
-
-    maclab_bc b{};
-    if (bc) b = *bc;
-    for (int k = 0; k < 4; ++k)
-        if (b.edge[k] < MACLAB_BOUNCEBACK || b.edge[k] > MACLAB_PERIODIC)
-            return fail(nullptr, MACLAB_E_ARG, "unknown edge kind");
-    if ((b.edge[0] == MACLAB_PERIODIC) != (b.edge[1] == MACLAB_PERIODIC) ||
-        (b.edge[2] == MACLAB_PERIODIC) != (b.edge[3] == MACLAB_PERIODIC))
-        return fail(nullptr, MACLAB_E_ARG, "periodic edges must come in W/E or S/N pairs");
-
+    Prepared P;
+    int prc = prepare(grid, params, bc, zb, mask, P);
+    if (prc != MACLAB_OK) return prc;
+    const int nx = P.nx, ny = P.ny;
     const size_t N = (size_t)nx * ny;
-    for (size_t k = 0; k < N; ++k)
-        if (mask[k] > MACLAB_DIR_HU) return fail(nullptr, MACLAB_E_ARG, "unknown node type in mask");
 
     maclab_s* s = new maclab_s();
     s->grid = *grid;
     s->params = *params;
-    s->bc = b;
+    s->bc = P.bc;
     s->prec = params->precision;
     s->esize = s->prec == MACLAB_F32 ? 4 : 8;
-    s->e = e;
-    s->dt = grid->dx / e;
+    s->e = P.e;
+    s->dt = P.dt;
     s->stream = (cudaStream_t)stream;
     if (alloc) {
         s->alloc = *alloc;
         s->has_alloc = true;
     }
-    s->pitch = (nx + 63) / 64 * 64;
-    for (int k = 0; k < 4; ++k)
-        if (b.h[k].amp != 0 || b.qx[k].amp != 0 || b.qy[k].amp != 0) s->steady_bc = false;
-    s->fmode = ((params->wind_u != 0 || params->wind_v != 0) ? F_WIND : 0) |
-               (params->Cb != 0 ? F_FRICTION : 0) | (params->Omega != 0 ? F_CORIOLIS : 0);
+    s->pitch = P.pitch;
+    s->steady_bc = P.steady_bc;
+    s->fmode = P.fmode;
     cudaGetDevice(&s->device);
     const int pitch = s->pitch;
-
-    // ---- classify nodes (host) ----
-    auto kind_at = [&](int i, int j) { return mask[(size_t)j * nx + i]; };
-    auto resolve = [&](int i, int n, int lo, int hi) -> int {
-        if (i >= 0 && i < n) return i;
-        int kd = i < 0 ? lo : hi;
-        if (kd == MACLAB_PERIODIC) return ((i % n) + n) % n;
-        if (kd == MACLAB_SPECULAR) {
-            i = i < 0 ? -1 - i : 2 * n - 1 - i;
-            return (i >= 0 && i < n) ? i : -1;
-        }
-        return -1;
-    };
-    static const int CX[9] = {0, 1, 1, 0, -1, -1, -1, 0, 1};
-    static const int CY[9] = {0, 0, 1, 1, 1, 0, -1, -1, -1};
-    std::vector<uint8_t> type((size_t)pitch * ny, (uint8_t)K_SOLID);
-    std::vector<int> general;
-    std::vector<DirNode> dirs;
-    double sumD = 0;
-    for (int j = 0; j < ny; ++j) {
-        for (int i = 0; i < nx; ++i) {
-            const uint8_t kd = kind_at(i, j);
-            uint8_t t = kd;
-            if (kd != MACLAB_SOLID) {
-                s->n_fluid++;
-                sumD += params->h_ref - zb[(size_t)j * nx + i];
-                if (kd >= MACLAB_DIR_H) {
-                    int di = 0, dj = 0, ed;
-                    if (i == 0) { di = 1; ed = 0; }
-                    else if (i == nx - 1) { di = -1; ed = 1; }
-                    else if (j == 0) { dj = 1; ed = 2; }
-                    else if (j == ny - 1) { dj = -1; ed = 3; }
-                    else {
-                        delete s;
-                        return fail(nullptr, MACLAB_E_ARG, "Dirichlet node not on a grid edge");
-                    }
-                    const int i1 = i + di, j1 = j + dj;
-                    if (i1 < 0 || i1 >= nx || j1 < 0 || j1 >= ny || kind_at(i1, j1) == MACLAB_SOLID ||
-                        kind_at(i1, j1) >= MACLAB_DIR_H) {
-                        delete s;
-                        return fail(nullptr, MACLAB_E_ARG,
-                                    "the inward node of a Dirichlet node must be non-solid and not Dirichlet");
-                    }
-                    dirs.push_back(DirNode{j * pitch + i, j1 * pitch + i1, (int)kd | (ed << 4)});
-                } else {
-                    bool gen = false;
-                    for (int a = 1; a < 9 && !gen; ++a) {
-                        const int si = resolve(i - CX[a], nx, b.edge[0], b.edge[1]);
-                        const int sj = resolve(j - CY[a], ny, b.edge[2], b.edge[3]);
-                        gen = si < 0 || sj < 0 || kind_at(si, sj) == MACLAB_SOLID;
-                    }
-                    if (gen) {
-                        t |= GENERAL_BIT;
-                        general.push_back(j * nx + i);
-                    } else {
-                        s->n_fast++;
-                    }
-                }
-            }
-            type[(size_t)j * pitch + i] = t;
-        }
-    }
-    s->sumD = sumD;
-
-    // Dirichlet nodes in tile order; the tile kernel applies them itself
-    // when every inward node is updated by the fast path of the same tile.
-    const int tiles_x = (nx + tile::TX - 1) / tile::TX, tiles_y = (ny + tile::TY - 1) / tile::TY;
-    auto tile_of = [&](int idx) {
-        const int j = idx / pitch, i = idx - j * pitch;
-        return (j / tile::TY) * tiles_x + i / tile::TX;
-    };
-    std::stable_sort(dirs.begin(), dirs.end(),
-                     [&](const DirNode& a, const DirNode& b) { return tile_of(a.x) < tile_of(b.x); });
-    std::vector<int> dir_start((size_t)tiles_x * tiles_y + 1, 0);
-    bool fused = true;
-    for (const DirNode& d : dirs) {
-        const int j1 = d.n1 / pitch, i1 = d.n1 - j1 * pitch;
-        fused = fused && tile_of(d.x) == tile_of(d.n1) && !(type[(size_t)j1 * pitch + i1] & GENERAL_BIT);
-        dir_start[tile_of(d.x) + 1]++;
-    }
-    for (size_t k = 1; k < dir_start.size(); ++k) dir_start[k] += dir_start[k - 1];
-    s->dir_fused = fused && !dirs.empty();
+    s->n_fluid = P.n_fluid;
+    s->n_fast = P.n_fast;
+    s->sumD = P.sumD;
+    s->dir_fused = P.dir_fused;
+    std::vector<uint8_t>& type = P.type;
+    std::vector<int>& general = P.general;
+    std::vector<DirNode>& dirs = P.dirs;
+    std::vector<int>& dir_start = P.dir_start;
 
     // ---- device buffers ----
     const size_t NP = (size_t)pitch * ny;
@@ -484,9 +523,7 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
     s->n_dir = (int)dirs.size();
 
     // ---- upload static data ----
-    std::vector<double> D64(NP, 0.0);
-    for (int j = 0; j < ny; ++j)
-        for (int i = 0; i < nx; ++i) D64[(size_t)j * pitch + i] = params->h_ref - zb[(size_t)j * nx + i];
+    std::vector<double>& D64 = P.D64;
     cudaError_t ce = cudaSuccess;
     auto put = [&](void* dst, const void* src, size_t bytes) {
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream);
@@ -895,6 +932,578 @@ void maclab_destroy(maclab_t s)
     if (s->capture_stream) cudaStreamDestroy(s->capture_stream);
     release_all(s);
     delete s;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batches: many independent grids advanced together (one step-kernel launch
+// for all of them over a packed tile list).
+struct maclab_batch_s {
+    int count = 0;
+    int prec = MACLAB_F32;
+    size_t esize = 4;
+    cudaStream_t stream = nullptr;
+    maclab_allocator alloc{};
+    bool has_alloc = false;
+    std::vector<Buf> bufs;
+    size_t device_bytes = 0;
+    // per-instance host facts
+    std::vector<int> nx, ny, pitch, tiles_x, tile0, ntiles;
+    std::vector<size_t> off;        // element offset of the instance in the packed arrays
+    std::vector<double> dt, sumD;
+    std::vector<int64_t> nodes;
+    int total_tiles = 0;
+    size_t total_np = 0;
+    // device arrays
+    void* eta[2] = {nullptr, nullptr};
+    void* u[2] = {nullptr, nullptr};
+    void* v[2] = {nullptr, nullptr};
+    void* D = nullptr;
+    double* D64 = nullptr;
+    uint8_t* type = nullptr;
+    double* stage = nullptr;
+    void* insts = nullptr;          // BatchInst<T>[count]
+    int* tile_inst = nullptr;
+    uint8_t* active = nullptr;
+    int2* general = nullptr;
+    int n_general = 0;
+    DirNode* dirs = nullptr;
+    int* dir_owner = nullptr;
+    int* dir_start = nullptr;       // per batch tile, when fused
+    int n_dir = 0;
+    bool dir_fused = false;
+    double* partial = nullptr;
+    double* red_out = nullptr;
+    std::vector<uint8_t> active_host;
+    int cur = 0;
+    int64_t n = 0;
+    bool have_prev = false;
+    int graph_steps = 64;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    std::string err;
+};
+
+namespace {
+
+int bfail(maclab_batch_t b, int code, const std::string& msg)
+{
+    if (b) b->err = msg;
+    g_last_error = msg;
+    return code;
+}
+
+void* bdev_alloc(maclab_batch_t b, size_t bytes)
+{
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (b->has_alloc) {
+        p = b->alloc.alloc(bytes, b->alloc.ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        b->bufs.push_back(Buf{p, bytes});
+        b->device_bytes += bytes;
+    }
+    return p;
+}
+
+void brelease(maclab_batch_t b)
+{
+    for (int k = 0; k < 2; ++k)
+        if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    for (auto& x : b->bufs) {
+        if (b->has_alloc)
+            b->alloc.release(x.p, b->alloc.ctx);
+        else
+            cudaFree(x.p);
+    }
+    b->bufs.clear();
+}
+
+template <typename T>
+void fill_insts(maclab_batch_t b, const std::vector<Prepared>& P, std::vector<BatchInst<T>>& out)
+{
+    out.resize(b->count);
+    for (int i = 0; i < b->count; ++i) {
+        BatchInst<T>& in = out[i];
+        const size_t o = b->off[i];
+        for (int par = 0; par < 2; ++par) {
+            Fields<T>& f = in.f[par];
+            f.eta = (const T*)b->eta[par] + o;
+            f.u = (const T*)b->u[par] + o;
+            f.v = (const T*)b->v[par] + o;
+            f.eta1 = (T*)b->eta[1 - par] + o;
+            f.u1 = (T*)b->u[1 - par] + o;
+            f.v1 = (T*)b->v[1 - par] + o;
+            f.D = (const T*)b->D + o;
+            f.type = b->type + o;
+            f.nx = P[i].nx;
+            f.ny = P[i].ny;
+            f.pitch = P[i].pitch;
+            for (int k = 0; k < 4; ++k) f.edge[k] = P[i].bc.edge[k];
+            f.c = make_coef<T>(P[i].params, P[i].e, P[i].dt);
+        }
+        in.tiles_x = P[i].tiles_x;
+        in.tile0 = b->tile0[i];
+        in.ntiles = b->ntiles[i];
+        in.pad = 0;
+        in.D64 = b->D64 + o;
+        for (int k = 0; k < 4; ++k) {  // steady boundary data
+            in.bv.h[k] = P[i].bc.h[k].mean;
+            in.bv.qx[k] = P[i].bc.qx[k].mean;
+            in.bv.qy[k] = P[i].bc.qy[k].mean;
+        }
+    }
+}
+
+template <typename T>
+int batch_launch(maclab_batch_t b, cudaStream_t st)
+{
+    const int par = b->cur;
+    const BatchInst<T>* insts = (const BatchInst<T>*)b->insts;
+    step_batch_kernel<T><<<b->total_tiles, tile::THREADS, tile::smem_bytes<T>(), st>>>(
+        insts, b->tile_inst, b->active, par, b->dir_fused ? b->dir_start : nullptr, b->dirs);
+    if (b->n_general > 0)
+        batch_general_kernel<T><<<(b->n_general + 127) / 128, 128, 0, st>>>(insts, b->general, b->n_general,
+                                                                             b->active, par);
+    if (b->n_dir > 0 && !b->dir_fused)
+        batch_dirichlet_kernel<T><<<(b->n_dir + 127) / 128, 128, 0, st>>>(insts, b->dir_owner, b->dirs,
+                                                                           b->n_dir, b->active, par);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return bfail(b, MACLAB_E_CUDA, std::string("batch step launch: ") + cudaGetErrorString(e));
+    b->cur = 1 - b->cur;
+    b->n += 1;
+    b->have_prev = true;
+    return MACLAB_OK;
+}
+
+int batch_one(maclab_batch_t b, cudaStream_t st)
+{
+    return b->prec == MACLAB_F32 ? batch_launch<float>(b, st) : batch_launch<double>(b, st);
+}
+
+int batch_capture(maclab_batch_t b)
+{
+    cudaError_t e = cudaSuccess;
+    if (!b->capture_stream) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bfail(b, MACLAB_E_CUDA, "capture stream");
+    const int cur = b->cur;
+    const int64_t n = b->n;
+    const bool hp = b->have_prev;
+    cudaGraph_t g = nullptr;
+    int rc = MACLAB_OK;
+    e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int k = 0; k < b->graph_steps && rc == MACLAB_OK; ++k) rc = batch_one(b, b->capture_stream);
+        e = cudaStreamEndCapture(b->capture_stream, &g);
+    }
+    b->cur = cur;
+    b->n = n;
+    b->have_prev = hp;
+    if (rc != MACLAB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph[cur], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph[cur] = nullptr;
+        return bfail(b, MACLAB_E_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+    }
+    return MACLAB_OK;
+}
+
+template <typename T>
+int batch_residual_t(maclab_batch_t b, double* out)
+{
+    // the state before the last step sits in buffer 1 - cur: parity 1 - cur
+    const int par = 1 - b->cur;
+    const BatchInst<T>* insts = (const BatchInst<T>*)b->insts;
+    batch_residual_tile_kernel<T><<<b->total_tiles, RED_THREADS, 0, b->stream>>>(insts, b->tile_inst, par,
+                                                                                 b->partial);
+    batch_residual_final_kernel<T><<<(b->count + 7) / 8, 256, 0, b->stream>>>(insts, b->count, b->partial,
+                                                                             b->red_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return bfail(b, MACLAB_E_CUDA, std::string("batch residual: ") + cudaGetErrorString(e));
+    std::vector<double> r((size_t)b->count * RED_NVAL);
+    e = cudaMemcpyAsync(r.data(), b->red_out, r.size() * 8, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, MACLAB_E_CUDA, std::string("batch residual: ") + cudaGetErrorString(e));
+    int rc = MACLAB_OK;
+    for (int i = 0; i < b->count; ++i) {
+        const double* q = &r[(size_t)i * RED_NVAL];
+        out[4 * i + 0] = q[1] > 0 ? std::sqrt(q[0]) / std::sqrt(q[1]) : 0.0;
+        out[4 * i + 1] = b->sumD[i] + q[2];
+        out[4 * i + 2] = std::sqrt(q[3]);
+        out[4 * i + 3] = q[4];
+        if (q[4] > 0 || !std::isfinite(out[4 * i])) rc = MACLAB_E_UNSTABLE;
+    }
+    if (rc != MACLAB_OK) bfail(b, rc, "non-finite values in a batch instance");
+    return rc;
+}
+
+// Give an instance the same state in both buffers (so that it stays put
+// while inactive, whatever the batch's buffer parity).
+int batch_freeze(maclab_batch_t b, int i)
+{
+    const size_t bytes = (size_t)b->pitch[i] * b->ny[i] * b->esize;
+    const size_t o = b->off[i] * b->esize;
+    const int c = b->cur, d = 1 - b->cur;
+    void* src[3] = {b->eta[c], b->u[c], b->v[c]};
+    void* dst[3] = {b->eta[d], b->u[d], b->v[d]};
+    for (int k = 0; k < 3; ++k) {
+        cudaError_t e = cudaMemcpyAsync((char*)dst[k] + o, (const char*)src[k] + o, bytes, cudaMemcpyDeviceToDevice,
+                                        b->stream);
+        if (e != cudaSuccess) return bfail(b, MACLAB_E_CUDA, "batch freeze");
+    }
+    return MACLAB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int maclab_batch_create(int count, const maclab_grid* grids, const maclab_params* params, const maclab_bc* bcs,
+                        const double* const* zb, const uint8_t* const* mask, const double* const* h0,
+                        const double* const* u0, const double* const* v0, const maclab_allocator* alloc,
+                        void* stream, maclab_batch_t* out)
+{
+    if (!out) return bfail(nullptr, MACLAB_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !grids || !params || !zb || !mask) return bfail(nullptr, MACLAB_E_ARG, "bad batch arguments");
+    if (alloc && (!alloc->alloc || !alloc->release))
+        return bfail(nullptr, MACLAB_E_ARG, "allocator needs alloc and release");
+    std::vector<Prepared> P(count);
+    for (int i = 0; i < count; ++i) {
+        int rc = prepare(&grids[i], &params[i], bcs ? &bcs[i] : nullptr, zb[i], mask[i], P[i]);
+        if (rc != MACLAB_OK) return bfail(nullptr, rc, "instance " + std::to_string(i) + ": " + g_last_error);
+        if (params[i].precision != params[0].precision)
+            return bfail(nullptr, MACLAB_E_ARG, "all instances of a batch need the same precision");
+        if (!P[i].steady_bc)
+            return bfail(nullptr, MACLAB_E_ARG, "batch instances need time-independent boundary data");
+        const bool has0 = h0 && h0[i], has1 = u0 && u0[i], has2 = v0 && v0[i];
+        if (has0 != has1 || has0 != has2)
+            return bfail(nullptr, MACLAB_E_ARG, "h0, u0, v0 of an instance must be all given or all NULL");
+    }
+    maclab_batch_s* b = new maclab_batch_s();
+    b->count = count;
+    b->prec = params[0].precision;
+    b->esize = b->prec == MACLAB_F32 ? 4 : 8;
+    b->stream = (cudaStream_t)stream;
+    if (alloc) {
+        b->alloc = *alloc;
+        b->has_alloc = true;
+    }
+    size_t maxN = 0;
+    std::vector<int> tile_inst;
+    std::vector<int2> general;
+    std::vector<DirNode> dirs;
+    std::vector<int> dir_owner, dir_start(1, 0);
+    bool fused = true;
+    for (int i = 0; i < count; ++i) {
+        const Prepared& p = P[i];
+        b->nx.push_back(p.nx);
+        b->ny.push_back(p.ny);
+        b->pitch.push_back(p.pitch);
+        b->tiles_x.push_back(p.tiles_x);
+        b->tile0.push_back(b->total_tiles);
+        b->ntiles.push_back(p.tiles_x * p.tiles_y);
+        b->off.push_back(b->total_np);
+        b->dt.push_back(p.dt);
+        b->sumD.push_back(p.sumD);
+        b->nodes.push_back((int64_t)p.nx * p.ny);
+        b->total_np += (size_t)p.pitch * p.ny;
+        maxN = std::max(maxN, (size_t)p.nx * p.ny);
+        for (int t = 0; t < p.tiles_x * p.tiles_y; ++t) {
+            tile_inst.push_back(i);
+            for (int k = p.dir_start[t]; k < p.dir_start[t + 1]; ++k) {
+                dirs.push_back(p.dirs[k]);
+                dir_owner.push_back(i);
+            }
+            dir_start.push_back((int)dirs.size());
+        }
+        b->total_tiles += p.tiles_x * p.tiles_y;
+        for (int g : p.general) general.push_back(make_int2(i, g));
+        fused = fused && (p.dirs.empty() || p.dir_fused);
+    }
+    b->n_general = (int)general.size();
+    b->n_dir = (int)dirs.size();
+    b->dir_fused = fused && b->n_dir > 0;
+    const size_t NP = b->total_np;
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; ++k)
+        ok = (b->eta[k] = bdev_alloc(b, NP * b->esize)) && (b->u[k] = bdev_alloc(b, NP * b->esize)) &&
+             (b->v[k] = bdev_alloc(b, NP * b->esize));
+    const size_t inst_bytes = b->prec == MACLAB_F32 ? sizeof(BatchInst<float>) : sizeof(BatchInst<double>);
+    ok = ok && (b->D = bdev_alloc(b, NP * b->esize)) && (b->D64 = (double*)bdev_alloc(b, NP * 8)) &&
+         (b->type = (uint8_t*)bdev_alloc(b, NP + 64)) && (b->stage = (double*)bdev_alloc(b, 3 * maxN * 8)) &&
+         (b->insts = bdev_alloc(b, inst_bytes * count)) &&
+         (b->tile_inst = (int*)bdev_alloc(b, tile_inst.size() * sizeof(int))) &&
+         (b->active = (uint8_t*)bdev_alloc(b, count)) &&
+         (b->partial = (double*)bdev_alloc(b, (size_t)b->total_tiles * RED_NVAL * 8)) &&
+         (b->red_out = (double*)bdev_alloc(b, (size_t)count * RED_NVAL * 8));
+    if (ok && b->n_general) ok = (b->general = (int2*)bdev_alloc(b, general.size() * sizeof(int2))) != nullptr;
+    if (ok && b->n_dir)
+        ok = (b->dirs = (DirNode*)bdev_alloc(b, dirs.size() * sizeof(DirNode))) &&
+             (b->dir_owner = (int*)bdev_alloc(b, dir_owner.size() * sizeof(int)));
+    if (ok && b->dir_fused) ok = (b->dir_start = (int*)bdev_alloc(b, dir_start.size() * sizeof(int))) != nullptr;
+    if (!ok) {
+        brelease(b);
+        delete b;
+        return bfail(nullptr, MACLAB_E_NOMEM, "device allocation failed");
+    }
+    // static data
+    std::vector<double> D64(NP, 0.0);
+    std::vector<uint8_t> type(NP + 64, 0);
+    for (int i = 0; i < count; ++i) {
+        std::copy(P[i].D64.begin(), P[i].D64.end(), D64.begin() + b->off[i]);
+        std::copy(P[i].type.begin(), P[i].type.end(), type.begin() + b->off[i]);
+    }
+    cudaError_t ce = cudaSuccess;
+    auto put = [&](void* dst, const void* src, size_t bytes) {
+        if (ce == cudaSuccess && bytes) ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, b->stream);
+    };
+    put(b->D64, D64.data(), NP * 8);
+    std::vector<float> Df;
+    if (b->prec == MACLAB_F32) {
+        Df.resize(NP);
+        for (size_t k = 0; k < NP; ++k) Df[k] = (float)D64[k];
+        put(b->D, Df.data(), NP * 4);
+    } else {
+        put(b->D, D64.data(), NP * 8);
+    }
+    put(b->type, type.data(), NP + 64);
+    put(b->tile_inst, tile_inst.data(), tile_inst.size() * sizeof(int));
+    if (b->n_general) put(b->general, general.data(), general.size() * sizeof(int2));
+    if (b->n_dir) {
+        put(b->dirs, dirs.data(), dirs.size() * sizeof(DirNode));
+        put(b->dir_owner, dir_owner.data(), dir_owner.size() * sizeof(int));
+    }
+    if (b->dir_fused) put(b->dir_start, dir_start.data(), dir_start.size() * sizeof(int));
+    b->active_host.assign(count, 1);
+    put(b->active, b->active_host.data(), count);
+    std::vector<BatchInst<float>> instf;
+    std::vector<BatchInst<double>> instd;
+    if (b->prec == MACLAB_F32) {
+        fill_insts<float>(b, P, instf);
+        put(b->insts, instf.data(), instf.size() * sizeof(BatchInst<float>));
+    } else {
+        fill_insts<double>(b, P, instd);
+        put(b->insts, instd.data(), instd.size() * sizeof(BatchInst<double>));
+    }
+    for (int k = 0; k < 2 && ce == cudaSuccess; ++k) {
+        ce = cudaMemsetAsync(b->eta[k], 0, NP * b->esize, b->stream);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(b->u[k], 0, NP * b->esize, b->stream);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(b->v[k], 0, NP * b->esize, b->stream);
+    }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);
+    if (ce == cudaSuccess)
+        ce = b->prec == MACLAB_F32
+            ? cudaFuncSetAttribute(step_batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)tile::smem_bytes<float>())
+            : cudaFuncSetAttribute(step_batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)tile::smem_bytes<double>());
+    if (ce != cudaSuccess) {
+        bfail(nullptr, MACLAB_E_CUDA, std::string("batch upload: ") + cudaGetErrorString(ce));
+        brelease(b);
+        delete b;
+        return MACLAB_E_CUDA;
+    }
+    *out = b;
+    for (int i = 0; i < count; ++i) {
+        if (h0 && h0[i]) {
+            int rc = maclab_batch_set_state(b, i, h0[i], u0[i], v0[i]);
+            if (rc != MACLAB_OK) {
+                *out = nullptr;
+                brelease(b);
+                delete b;
+                return rc;
+            }
+        }
+    }
+    b->have_prev = false;
+    return MACLAB_OK;
+}
+
+int maclab_batch_step(maclab_batch_t b, int64_t n)
+{
+    if (!b) return bfail(nullptr, MACLAB_E_ARG, "NULL batch");
+    if (n < 0) return bfail(b, MACLAB_E_ARG, "n must be >= 0");
+    while (b->graph_steps > 0 && n >= b->graph_steps) {
+        if (!b->graph[b->cur]) {
+            int rc = batch_capture(b);
+            if (rc != MACLAB_OK) return rc;
+        }
+        cudaError_t e = cudaGraphLaunch(b->graph[b->cur], b->stream);
+        if (e != cudaSuccess) return bfail(b, MACLAB_E_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
+        b->n += b->graph_steps;
+        b->have_prev = true;
+        n -= b->graph_steps;
+    }
+    for (int64_t k = 0; k < n; ++k) {
+        int rc = batch_one(b, b->stream);
+        if (rc != MACLAB_OK) return rc;
+    }
+    return MACLAB_OK;
+}
+
+int maclab_batch_set_graph_steps(maclab_batch_t b, int steps)
+{
+    if (!b) return bfail(nullptr, MACLAB_E_ARG, "NULL batch");
+    if (steps < 0 || (steps & 1)) return bfail(b, MACLAB_E_ARG, "steps must be an even number >= 0");
+    for (int k = 0; k < 2; ++k) {
+        if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+        b->graph[k] = nullptr;
+    }
+    b->graph_steps = steps;
+    return MACLAB_OK;
+}
+
+int maclab_batch_residual(maclab_batch_t b, double* out)
+{
+    if (!b || !out) return bfail(b, MACLAB_E_ARG, "NULL argument");
+    if (!b->have_prev) return bfail(b, MACLAB_E_STATE, "no step taken since create / set_state");
+    return b->prec == MACLAB_F32 ? batch_residual_t<float>(b, out) : batch_residual_t<double>(b, out);
+}
+
+int maclab_batch_set_active(maclab_batch_t b, const uint8_t* flags)
+{
+    if (!b || !flags) return bfail(b, MACLAB_E_ARG, "NULL argument");
+    for (int i = 0; i < b->count; ++i) {
+        const uint8_t f = flags[i] ? 1 : 0;
+        if (!f && b->active_host[i]) {
+            int rc = batch_freeze(b, i);
+            if (rc != MACLAB_OK) return rc;
+        }
+        b->active_host[i] = f;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->active, b->active_host.data(), b->count, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, MACLAB_E_CUDA, "batch set_active");
+    return MACLAB_OK;
+}
+
+int maclab_batch_run_to_steady(maclab_batch_t b, double tol, int64_t max_steps, int check_every,
+                               int64_t* steps, double* r_final, double* seconds)
+{
+    if (!b) return bfail(nullptr, MACLAB_E_ARG, "NULL batch");
+    if (check_every < 1 || max_steps < 0 || !(tol >= 0)) return bfail(b, MACLAB_E_ARG, "bad tol / max_steps / check_every");
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<double> r(4 * (size_t)b->count, INFINITY);
+    std::vector<uint8_t> act(b->active_host);
+    std::vector<int64_t> done(b->count, -1);
+    int64_t total = 0;
+    int rc = MACLAB_OK;
+    int remaining = 0;
+    for (uint8_t a : act) remaining += a ? 1 : 0;
+    while (remaining > 0 && total < max_steps) {
+        const int64_t k = std::min<int64_t>(check_every, max_steps - total);
+        if ((rc = maclab_batch_step(b, k)) != MACLAB_OK) break;
+        total += k;
+        rc = maclab_batch_residual(b, r.data());
+        if (rc != MACLAB_OK) break;
+        const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        bool changed = false;
+        for (int i = 0; i < b->count; ++i) {
+            if (act[i] && r[4 * i] <= tol) {
+                act[i] = 0;
+                done[i] = total;
+                if (seconds) seconds[i] = secs;
+                changed = true;
+                --remaining;
+            }
+        }
+        if (changed && (rc = maclab_batch_set_active(b, act.data())) != MACLAB_OK) break;
+    }
+    for (int i = 0; i < b->count; ++i) {
+        if (steps) steps[i] = done[i];
+        if (r_final) r_final[i] = r[4 * i];
+    }
+    if (rc == MACLAB_OK && remaining > 0) return bfail(b, MACLAB_E_STATE, "max_steps reached before every instance converged");
+    return rc;
+}
+
+int maclab_batch_get_state(maclab_batch_t b, int i, double* h, double* u, double* v)
+{
+    if (!b || i < 0 || i >= b->count) return bfail(b, MACLAB_E_ARG, "bad instance");
+    const size_t N = (size_t)b->nx[i] * b->ny[i];
+    const int c = b->cur;
+    const size_t o = b->off[i];
+    cudaError_t e;
+    if (b->prec == MACLAB_F32)
+        state_out_kernel<float><<<grid_blocks(N, 256, 4096), 256, 0, b->stream>>>(
+            (const float*)b->eta[c] + o, (const float*)b->u[c] + o, (const float*)b->v[c] + o, b->D64 + o, b->stage,
+            b->stage + N, b->stage + 2 * N, b->nx[i], b->ny[i], b->pitch[i]);
+    else
+        state_out_kernel<double><<<grid_blocks(N, 256, 4096), 256, 0, b->stream>>>(
+            (const double*)b->eta[c] + o, (const double*)b->u[c] + o, (const double*)b->v[c] + o, b->D64 + o,
+            b->stage, b->stage + N, b->stage + 2 * N, b->nx[i], b->ny[i], b->pitch[i]);
+    if ((e = cudaGetLastError()) != cudaSuccess) return bfail(b, MACLAB_E_CUDA, "batch get_state");
+    double* dst[3] = {h, u, v};
+    for (int k = 0; k < 3; ++k)
+        if (dst[k] && (e = cudaMemcpyAsync(dst[k], b->stage + k * N, N * 8, cudaMemcpyDeviceToHost, b->stream)) !=
+                          cudaSuccess)
+            return bfail(b, MACLAB_E_CUDA, "batch get_state");
+    if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return bfail(b, MACLAB_E_CUDA, "batch get_state");
+    return MACLAB_OK;
+}
+
+int maclab_batch_set_state(maclab_batch_t b, int i, const double* h, const double* u, const double* v)
+{
+    if (!b || i < 0 || i >= b->count || !h || !u || !v) return bfail(b, MACLAB_E_ARG, "bad instance or NULL state");
+    const size_t N = (size_t)b->nx[i] * b->ny[i];
+    const size_t o = b->off[i];
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(b->stage, h, N * 8, cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(b->stage + N, u, N * 8, cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(b->stage + 2 * N, v, N * 8, cudaMemcpyHostToDevice, b->stream)) != cudaSuccess)
+        return bfail(b, MACLAB_E_CUDA, "batch set_state");
+    const int c = b->cur, d = 1 - b->cur;
+    // both buffers: the instance is consistent whatever the parity
+    if (b->prec == MACLAB_F32)
+        state_in_kernel<float><<<grid_blocks(N, 256, 4096), 256, 0, b->stream>>>(
+            b->stage, b->stage + N, b->stage + 2 * N, b->D64 + o, b->type + o, (float*)b->eta[c] + o,
+            (float*)b->u[c] + o, (float*)b->v[c] + o, (float*)b->eta[d] + o, (float*)b->u[d] + o,
+            (float*)b->v[d] + o, b->nx[i], b->ny[i], b->pitch[i]);
+    else
+        state_in_kernel<double><<<grid_blocks(N, 256, 4096), 256, 0, b->stream>>>(
+            b->stage, b->stage + N, b->stage + 2 * N, b->D64 + o, b->type + o, (double*)b->eta[c] + o,
+            (double*)b->u[c] + o, (double*)b->v[c] + o, (double*)b->eta[d] + o, (double*)b->u[d] + o,
+            (double*)b->v[d] + o, b->nx[i], b->ny[i], b->pitch[i]);
+    if ((e = cudaGetLastError()) != cudaSuccess) return bfail(b, MACLAB_E_CUDA, "batch set_state");
+    if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return bfail(b, MACLAB_E_CUDA, "batch set_state");
+    int rc = batch_freeze(b, i);
+    if (rc == MACLAB_OK && (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
+        return bfail(b, MACLAB_E_CUDA, "batch set_state");
+    b->have_prev = false;
+    return rc;
+}
+
+int maclab_batch_info(maclab_batch_t b, int* count, int64_t* nodes, int64_t* tiles, int64_t* steps)
+{
+    if (!b) return bfail(nullptr, MACLAB_E_ARG, "NULL batch");
+    int64_t tot = 0;
+    for (int64_t x : b->nodes) tot += x;
+    if (count) *count = b->count;
+    if (nodes) *nodes = tot;
+    if (tiles) *tiles = b->total_tiles;
+    if (steps) *steps = b->n;
+    return MACLAB_OK;
+}
+
+const char* maclab_batch_last_error(maclab_batch_t b) { return b ? b->err.c_str() : g_last_error.c_str(); }
+
+void maclab_batch_destroy(maclab_batch_t b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    brelease(b);
+    delete b;
 }
 
 }  // extern "C"

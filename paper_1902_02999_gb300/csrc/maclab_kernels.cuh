@@ -768,18 +768,18 @@ __device__ __forceinline__ void store_pair(tile::Derived<T>& sm, int pr, int lc,
     sm.ed[pr][lc + 1] = V2{b.eta, b.D};
 }
 
+// Update of one tile whose top-left updated node is (x0, y0); `tile` indexes
+// the per-tile Dirichlet ranges.
 template <typename T, int FM>
-__global__ void __launch_bounds__(tile::THREADS, tile::MinBlocks<T>::value)
-step_tile_kernel(const __grid_constant__ Fields<T> f, int tiles_x, const __grid_constant__ TileDirichlet td)
+__device__ __forceinline__ void tile_update(const Fields<T>& f, int x0, int y0, int tile, const int* dir_start,
+                                            const DirNode* dir_list, const double* D64, const DirValues& bv,
+                                            tile::Derived<T>& sm)
 {
     using namespace tile;
     using O = Op<T>;
     using V2 = typename Vec2<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Derived<T>& sm = *reinterpret_cast<Derived<T>*>(smem_raw);
     const int tx = threadIdx.x & 31, tyy = threadIdx.x >> 5;
     const Coef<T>& K = f.c;
-    const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY;
     // ---- phase A: own pairs (tile pair column 1 + tx, tile rows 1 + 2 tyy + r)
     Src<T> own[2][2];
     uint32_t own_types[2];
@@ -877,14 +877,90 @@ step_tile_kernel(const __grid_constant__ Fields<T> f, int tiles_x, const __grid_
         }
     }
     // ---- phase C: Dirichlet nodes of this tile
-    if (td.start) {
-        const int b = td.start[blockIdx.x], e = td.start[blockIdx.x + 1];
+    if (dir_start) {
+        const int b = dir_start[tile], e = dir_start[tile + 1];
         if (b < e) {
             __syncthreads();  // the block's new values are visible to the block
             for (int k = b + (int)threadIdx.x; k < e; k += THREADS)
-                dirichlet_node(f.eta1, f.u1, f.v1, f.D, td.D64, td.list[k], td.bv);
+                dirichlet_node(f.eta1, f.u1, f.v1, f.D, D64, dir_list[k], bv);
         }
     }
+}
+
+
+template <typename T, int FM>
+__global__ void __launch_bounds__(tile::THREADS, tile::MinBlocks<T>::value)
+step_tile_kernel(const __grid_constant__ Fields<T> f, int tiles_x, const __grid_constant__ TileDirichlet td)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    tile::Derived<T>& sm = *reinterpret_cast<tile::Derived<T>*>(smem_raw);
+    const int x0 = (blockIdx.x % tiles_x) * tile::TX, y0 = (blockIdx.x / tiles_x) * tile::TY;
+    tile_update<T, FM>(f, x0, y0, blockIdx.x, td.start, td.list, td.D64, td.bv, sm);
+}
+
+// ---------------------------------------------------------------------------
+// Batched step: one launch advances every active instance of a batch.  The
+// tiles of all instances form one list; block b updates tile tile_local[b]
+// of instance tile_inst[b] with that instance's fields and coefficients.
+// Instances whose flag in `active` is 0 are skipped (their state stays).
+template <typename T>
+struct BatchInst {
+    Fields<T> f[2];     // fields for the two buffer parities
+    int tiles_x;        // tiles per row of the instance
+    int tile0;          // index of the instance's first tile in the batch list
+    int ntiles;         // tiles of the instance
+    int pad;
+    const double* D64;  // still-water depth in double (Dirichlet depths)
+    DirValues bv;       // steady Dirichlet values
+};
+
+template <typename T>
+__global__ void __launch_bounds__(tile::THREADS, tile::MinBlocks<T>::value)
+step_batch_kernel(const BatchInst<T>* __restrict__ insts, const int* __restrict__ tile_inst,
+                  const uint8_t* __restrict__ active, int parity, const int* __restrict__ dir_start,
+                  const DirNode* __restrict__ dirs)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    tile::Derived<T>& sm = *reinterpret_cast<tile::Derived<T>*>(smem_raw);
+    const int i = tile_inst[blockIdx.x];
+    if (!active[i]) return;  // whole block
+    const BatchInst<T>& in = insts[i];
+    const Fields<T> f = in.f[parity];
+    const int t = blockIdx.x - in.tile0;
+    const int x0 = (t % in.tiles_x) * tile::TX, y0 = (t / in.tiles_x) * tile::TY;
+    // all force terms: absent ones have zero coefficients and contribute
+    // exact zeros, so every instance gets the same values as its own kernel
+    tile_update<T, F_WIND | F_FRICTION | F_CORIOLIS>(f, x0, y0, blockIdx.x, dir_start, dirs, in.D64, in.bv, sm);
+}
+
+// Nodes with a bounce-back link across a batch: (instance, node) pairs.
+template <typename T>
+__global__ void __launch_bounds__(128) batch_general_kernel(const BatchInst<T>* __restrict__ insts,
+                                                            const int2* __restrict__ list, int count,
+                                                            const uint8_t* __restrict__ active, int parity)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int2 e = list[t];
+    if (!active[e.x]) return;
+    const Fields<T>& f = insts[e.x].f[parity];
+    general_node(f, e.y % f.nx, e.y / f.nx);
+}
+
+// Dirichlet nodes across a batch (when they cannot be fused into the tiles):
+// (instance, index into the batch list) pairs.
+template <typename T>
+__global__ void batch_dirichlet_kernel(const BatchInst<T>* __restrict__ insts, const int* __restrict__ owner,
+                                       const DirNode* __restrict__ dirs, int count,
+                                       const uint8_t* __restrict__ active, int parity)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int i = owner[t];
+    if (!active[i]) return;
+    const BatchInst<T>& in = insts[i];
+    const Fields<T>& f = in.f[parity];
+    dirichlet_node(f.eta1, f.u1, f.v1, f.D, in.D64, dirs[t], in.bv);
 }
 
 // ---------------------------------------------------------------------------
@@ -961,6 +1037,73 @@ __global__ void residual_final_kernel(const double* __restrict__ partial, int nb
     }
     r = (q == 3) ? warp_max(r) : warp_sum(r);
     if (lane == 0) out[q] = r;
+}
+
+// Per-instance residual of a batch: block b sums the nodes of tile b of its
+// instance (old state = parity buffers, new = the other ones) into
+// partial[b][RED_NVAL]; then one warp per instance adds its tiles in order.
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS)
+batch_residual_tile_kernel(const BatchInst<T>* __restrict__ insts, const int* __restrict__ tile_inst,
+                           int parity, double* __restrict__ partial)
+{
+    const int i = tile_inst[blockIdx.x];
+    const BatchInst<T>& in = insts[i];
+    const Fields<T>& f = in.f[parity];  // eta = previous state, eta1 = current state
+    const int t = blockIdx.x - in.tile0;
+    const int x0 = (t % in.tiles_x) * tile::TX, y0 = (t / in.tiles_x) * tile::TY;
+    double s[RED_NVAL] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int k = threadIdx.x; k < tile::TX * tile::TY; k += RED_THREADS) {
+        const int x = x0 + (k % tile::TX), y = y0 + k / tile::TX;
+        if (x >= f.nx || y >= f.ny) continue;
+        const size_t p = (size_t)y * f.pitch + x;
+        if ((f.type[p] & KIND_MASK) == K_SOLID) continue;
+        const double d = (double)f.D[p];
+        const double a0 = (double)f.eta[p], a1 = (double)f.eta1[p];
+        const double h0 = d + a0, h1 = d + a1;
+        const double qx0 = h0 * (double)f.u[p], qy0 = h0 * (double)f.v[p];
+        const double qx1 = h1 * (double)f.u1[p], qy1 = h1 * (double)f.v1[p];
+        const double dh = a1 - a0, dqx = qx1 - qx0, dqy = qy1 - qy0;
+        s[0] += dh * dh + dqx * dqx + dqy * dqy;
+        s[1] += h1 * h1 + qx1 * qx1 + qy1 * qy1;
+        s[2] += a1;
+        const double uu = (double)f.u1[p] * (double)f.u1[p] + (double)f.v1[p] * (double)f.v1[p];
+        s[3] = fmax(s[3], uu);
+        if (!isfinite(a1) || !isfinite(uu)) s[4] += 1.0;
+    }
+    __shared__ double sh[RED_NVAL][RED_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < RED_NVAL; ++q) {
+        const double r = (q == 3) ? warp_max(s[q]) : warp_sum(s[q]);
+        if (lane == 0) sh[q][w] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x < RED_NVAL) {
+        const int q = threadIdx.x;
+        double r = sh[q][0];
+        for (int k = 1; k < RED_THREADS / 32; ++k) r = (q == 3) ? fmax(r, sh[q][k]) : r + sh[q][k];
+        partial[(size_t)blockIdx.x * RED_NVAL + q] = r;
+    }
+}
+
+template <typename T>
+__global__ void batch_residual_final_kernel(const BatchInst<T>* __restrict__ insts, int count,
+                                            const double* __restrict__ partial, double* __restrict__ out)
+{
+    const int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= count) return;
+    const int t0 = insts[i].tile0, nt = insts[i].ntiles;
+#pragma unroll 1
+    for (int q = 0; q < RED_NVAL; ++q) {
+        double r = 0.0;
+        for (int b = lane; b < nt; b += 32) {
+            const double x = partial[(size_t)(t0 + b) * RED_NVAL + q];
+            r = (q == 3) ? fmax(r, x) : r + x;
+        }
+        r = (q == 3) ? warp_max(r) : warp_sum(r);
+        if (lane == 0) out[(size_t)i * RED_NVAL + q] = r;
+    }
 }
 
 // ---------------------------------------------------------------------------
