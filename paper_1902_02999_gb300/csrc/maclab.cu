@@ -1434,7 +1434,7 @@ int maclab_batch_get_state(maclab_batch_t b, int i, double* h, double* u, double
     const size_t N = (size_t)b->nx[i] * b->ny[i];
     const int c = b->cur;
     const size_t o = b->off[i];
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
     if (b->prec == MACLAB_F32)
         state_out_kernel<float><<<grid_blocks(N, 256, 4096), 256, 0, b->stream>>>(
             (const float*)b->eta[c] + o, (const float*)b->u[c] + o, (const float*)b->v[c] + o, b->D64 + o, b->stage,

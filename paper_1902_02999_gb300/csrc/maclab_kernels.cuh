@@ -560,6 +560,7 @@ struct NodeQ {  // per-node quantities for the general path
 template <typename T>
 __device__ __forceinline__ NodeQ<T> node_q(const Fields<T>& f, size_t idx, uint8_t flip)
 {
+    using O = Op<T>;
     const Coef<T>& c = f.c;
     NodeQ<T> n;
     n.eta = f.eta[idx];
@@ -570,11 +571,12 @@ __device__ __forceinline__ NodeQ<T> node_q(const Fields<T>& f, size_t idx, uint8
     if (flip & 1) { n.u = -n.u; wfx = -wfx; }
     if (flip & 2) { n.v = -n.v; wfy = -wfy; }
     if ((flip & 3) == 1 || (flip & 3) == 2) Om = -Om;
-    n.h = n.D + n.eta;
-    n.uu = n.u * n.u + n.v * n.v;
-    const T sp = my_sqrt(n.uu);
-    n.Fx = wfx - c.Cb * n.u * sp + Om * n.h * n.v;
-    n.Fy = wfy - c.Cb * n.v * sp - Om * n.h * n.u;
+    n.h = O::add(n.D, n.eta);
+    n.uu = O::fma(n.u, n.u, O::mul(n.v, n.v));
+    const T sp = Op<T>::sqrt(n.uu);
+    const T cbs = O::mul(c.Cb, sp), omh = O::mul(Om, n.h);
+    n.Fx = O::fma(-cbs, n.u, O::fma(omh, n.v, wfx));
+    n.Fy = O::fma(-cbs, n.v, O::fma(-omh, n.u, wfy));
     return n;
 }
 
@@ -582,20 +584,29 @@ __device__ __forceinline__ NodeQ<T> node_q(const Fields<T>& f, size_t idx, uint8
 template <typename T>
 __device__ __forceinline__ T feq_diff(const Coef<T>& c, const NodeQ<T>& n, int cx, int cy)
 {
+    using O = Op<T>;
     const T lam = (cx != 0 && cy != 0) ? T(0.25) : T(1);
-    const T cu = T(cx) * n.u + T(cy) * n.v;
-    return lam * (c.G6 * n.eta * (T(2) * n.D + n.eta) + n.h * cu * c.k3 +
-                  n.h * cu * cu * c.k2 - c.K6 * n.h * n.uu);
+    const T cu = O::fma(T(cx), n.u, O::mul(T(cy), n.v));
+    const T hcu = O::mul(n.h, cu);
+    T acc = O::mul(O::mul(c.G6, n.eta), O::fma(T(2), n.D, n.eta));
+    acc = O::fma(hcu, c.k3, acc);
+    acc = O::fma(O::mul(hcu, cu), c.k2, acc);
+    acc = O::fma(-c.K6, O::mul(n.h, n.uu), acc);
+    return O::mul(lam, acc);
 }
 
-// Update of one node (i, j) with the links resolved one by one.
+// Update of one node (i, j) with the links resolved one by one.  Every
+// rounding is spelled out, so the result does not depend on which kernel
+// the code is inlined into.
 template <typename T>
 __device__ __forceinline__ void general_node(const Fields<T>& f, int i, int j)
 {
+    using O = Op<T>;
     const size_t xi = (size_t)j * f.pitch + i;
     const Coef<T>& c = f.c;
     const NodeQ<T> X = node_q(f, xi, 0);
-    T Sh = X.eta - T(5) * c.G6 * X.eta * (T(2) * X.D + X.eta) - T(4) * c.K6 * X.h * X.uu;
+    T Sh = O::fma(-O::mul(T(5), O::mul(c.G6, X.eta)), O::fma(T(2), X.D, X.eta), X.eta);
+    Sh = O::fma(-O::mul(T(4), c.K6), O::mul(X.h, X.uu), Sh);
     T Sx = T(0), Sy = T(0);
 #pragma unroll 1
     for (int a = 1; a < 9; ++a) {
@@ -615,17 +626,18 @@ __device__ __forceinline__ void general_node(const Fields<T>& f, int i, int j)
             w = feq_diff(c, X, -cx, -cy);
         } else {
             const NodeQ<T> Y = node_q(f, s, flip);  // the mirrored node when flip != 0
-            w = feq_diff(c, Y, cx, cy) +
-                lam * c.G6 * (X.eta + Y.eta) * (X.D - Y.D) +
-                lam * c.KF * (T(cx) * (X.Fx + Y.Fx) + T(cy) * (X.Fy + Y.Fy));
+            const T bed = O::mul(O::mul(lam, c.G6), O::mul(O::add(X.eta, Y.eta), O::sub(X.D, Y.D)));
+            const T frc = O::mul(O::mul(lam, c.KF),
+                                 O::fma(T(cx), O::add(X.Fx, Y.Fx), O::mul(T(cy), O::add(X.Fy, Y.Fy))));
+            w = O::add(O::add(feq_diff(c, Y, cx, cy), bed), frc);
         }
-        Sh += w;
-        Sx += T(cx) * w;
-        Sy += T(cy) * w;
+        Sh = O::add(Sh, w);
+        Sx = O::fma(T(cx), w, Sx);
+        Sy = O::fma(T(cy), w, Sy);
     }
-    const T hu1 = c.e * Sx, hv1 = c.e * Sy;
-    const T inv = T(1) / (X.D + Sh);
-    T u1 = hu1 * inv, v1 = hv1 * inv;
+    const T hu1 = O::mul(c.e, Sx), hv1 = O::mul(c.e, Sy);
+    const T inv = T(1) / O::add(X.D, Sh);
+    T u1 = O::mul(hu1, inv), v1 = O::mul(hv1, inv);
     if ((f.type[xi] & KIND_MASK) == K_NOSLIP) { u1 = T(0); v1 = T(0); }
     f.eta1[xi] = Sh;
     f.u1[xi] = u1;
