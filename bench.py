@@ -189,6 +189,9 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the steady-state and FP64 legs")
     ap.add_argument("--steady-max-steps", type=int, default=2_000_000)
     ap.add_argument("--f64-steps", type=int, default=300)
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--batch-max-steps", type=int, default=100_000)
     args = ap.parse_args()
     workload = "bump_channel_%dx%d_%s" % (args.nx, args.ny, args.precision)
 
@@ -325,6 +328,40 @@ def main():
                "bytes_per_node": BYTES_PER_NODE["f64"]}
         s64.close()
 
+    # the batched ensemble: 512 uneven lakes and channels advanced together
+    batched = None
+    if not args.no_extra and args.batch_count > 0:
+        from paper_1902_02999_gb300 import Batch
+        ens = inputs.ensemble(args.batch_count, seed=0)
+        bt = Batch(ens, precision=args.precision)
+        info_b = bt.info()
+        bt.step(64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bt.step(args.batch_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bms = e0.elapsed_time(e1) / args.batch_steps
+        bt.close()
+        bt = Batch(ens, precision=args.precision)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, rr, secs = bt.run_to_steady(tol=1e-8, max_steps=args.batch_max_steps, check_every=1000)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        conv = st >= 0
+        import numpy as np
+        batched = {"instances": info_b["count"], "nodes": info_b["nodes"], "tiles": info_b["tiles"],
+                   "mlups": info_b["nodes"] / (bms / 1e3) / 1e6, "ms_per_step": bms,
+                   "steady": {"tol": 1e-8, "max_steps": args.batch_max_steps,
+                              "converged": int(conv.sum()), "wall_s": wall,
+                              "p50_s": float(np.percentile(secs[conv], 50)) if conv.any() else None,
+                              "p99_s": float(np.percentile(secs[conv], 99)) if conv.any() else None,
+                              "p50_steps": float(np.percentile(st[conv], 50)) if conv.any() else None,
+                              "p99_steps": float(np.percentile(st[conv], 99)) if conv.any() else None}}
+        bt.close()
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -336,7 +373,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single-gpu",
                            "step_kernel": "tile 64x16" if info["step_kernel"] == 0 else "warp strip"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "steady_state": steady, "f64": f64,
+                "steady_state": steady, "f64": f64, "batched": batched,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)
     sim.close()

@@ -319,3 +319,18 @@ def random_case(nx: int, ny: int, seed: int, edges=(BOUNCEBACK, BOUNCEBACK, SPEC
     return Case("random_%dx%d_s%d" % (nx, ny, seed), nx, ny, dx, nu, zb, mask, h0, u0, v0,
                 edges=tuple(edges), bc=bc, wind_u=float(wind[0]), wind_v=float(wind[1]),
                 cb=cb, omega=om, h_ref=href)
+
+
+def ensemble(count: int = 512, seed: int = 0):
+    """A batch of uneven problems: sizes nx, ny ~ U{64..512} drawn per
+    instance; even instances are seeded dish lakes (n = nx, square), odd
+    ones seeded bump channels (nx x ny), each with its own wind, bump height
+    and Chezy coefficient from the instance seed."""
+    rng = Rng(10_000 + seed)
+    sizes = rng.uniform(2 * count, 64, 513).astype(int)
+    out = []
+    for i in range(count):
+        nx, ny = int(sizes[2 * i]), int(sizes[2 * i + 1])
+        sub = 1_000 * (seed + 1) + i
+        out.append(dish_lake(nx, seed=sub) if i % 2 == 0 else bump_channel(nx, ny, seed=sub))
+    return out
