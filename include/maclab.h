@@ -258,6 +258,14 @@ int maclab_set_launch(maclab_t sim, int rows, int blocks);
 int maclab_set_profiling(maclab_t sim, int on);
 int maclab_get_profile(maclab_t sim, double* step_kernel_ms, int64_t* launches);
 
+/* Time the step-kernel launch shapes on this handle's own grid and keep
+ * the fastest: *choice = 0 for the 64 x 16 tile kernel, k = 1..4 for the
+ * warp-strip kernel with 8, 16, 32 or 64 rows per strip.  Each shape runs
+ * 2 + trial_steps steps; the state, step count and time are restored
+ * afterwards (results are bitwise identical for every shape).  Allocates
+ * and frees a copy of the state.  Synchronises. */
+int maclab_autotune(maclab_t sim, int trial_steps, int* choice);
+
 /* Facts about the handle. */
 int maclab_get_info(maclab_t sim, maclab_info* info);
 

@@ -225,6 +225,16 @@ class Simulation:
         self.info["tile_rows"] = min(int(rows), self.ny)
         self.info["grid_blocks"] = int(blocks)
 
+    def autotune(self, trial_steps: int = 20) -> int:
+        """Pick the fastest step-kernel launch shape for this grid (0 = tile
+        kernel, 1..4 = strip kernel with 8/16/32/64 rows); state unchanged."""
+        c = ctypes.c_int()
+        self._check(self._lib.maclab_autotune(self._h, int(trial_steps), ctypes.byref(c)))
+        info = _abi.Info()
+        self._check(self._lib.maclab_get_info(self._h, ctypes.byref(info)))
+        self.info = {f: getattr(info, f) for f, _ in _abi.Info._fields_}
+        return int(c.value)
+
     def set_graph_steps(self, steps: int) -> None:
         """Steps per CUDA-graph replay (even, 0 = off)."""
         self._check(self._lib.maclab_set_graph_steps(self._h, int(steps)))

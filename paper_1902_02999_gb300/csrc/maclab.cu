@@ -687,6 +687,85 @@ int maclab_step(maclab_t s, int64_t n)
     return MACLAB_OK;
 }
 
+int maclab_autotune(maclab_t s, int trial_steps, int* choice)
+{
+    if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    if (trial_steps < 2) return fail(s, MACLAB_E_ARG, "trial_steps must be >= 2");
+    // keep the state: copies of both buffers, restored at the end
+    const size_t bytes = (size_t)s->pitch * s->grid.ny * s->esize;
+    void* keep[6] = {};
+    void* src[6] = {s->eta[0], s->u[0], s->v[0], s->eta[1], s->u[1], s->v[1]};
+    for (int k = 0; k < 6; ++k) {
+        keep[k] = dev_alloc(s, bytes);
+        if (!keep[k]) return fail(s, MACLAB_E_NOMEM, "autotune scratch");
+        cudaMemcpyAsync(keep[k], src[k], bytes, cudaMemcpyDeviceToDevice, s->stream);
+    }
+    const int cur = s->cur;
+    const int64_t n0 = s->n;
+    const bool hp = s->have_prev;
+    const bool tile0 = s->use_tile;
+    const int ty0 = s->ty;
+    const int prof0 = s->profiling;
+    // candidates: 0 = tile kernel; k >= 1 = strip kernel with 4 << k rows
+    const int rows[5] = {0, 8, 16, 32, 64};
+    double best = 1e300;
+    int best_k = 0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    s->profiling = true;  // one launch per step (no graph replay) while timing
+    int rc = MACLAB_OK;
+    for (int k = 0; k < 5 && rc == MACLAB_OK; ++k) {
+        s->use_tile = k == 0;
+        if (k > 0) {
+            s->ty = std::min(rows[k], s->grid.ny);
+            s->nrb = (s->grid.ny + s->ty - 1) / s->ty;
+        }
+        rc = maclab_step(s, 2);  // warm-up
+        cudaEventRecord(e0, s->stream);
+        if (rc == MACLAB_OK) rc = maclab_step(s, trial_steps);
+        cudaEventRecord(e1, s->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rc == MACLAB_OK && ms < best) {
+            best = ms;
+            best_k = k;
+        }
+    }
+    s->events_used = 0;
+    s->profiling = prof0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s->use_tile = best_k == 0;
+    if (best_k > 0) {
+        s->ty = std::min(rows[best_k], s->grid.ny);
+    } else {
+        s->ty = ty0;
+    }
+    s->nrb = (s->grid.ny + s->ty - 1) / s->ty;
+    (void)tile0;
+    drop_graphs(s);
+    for (int k = 0; k < 6; ++k) cudaMemcpyAsync(src[k], keep[k], bytes, cudaMemcpyDeviceToDevice, s->stream);
+    cudaStreamSynchronize(s->stream);
+    for (int k = 0; k < 6; ++k) {  // give the scratch back
+        for (size_t q = 0; q < s->bufs.size(); ++q) {
+            if (s->bufs[q].p == keep[k]) {
+                if (s->has_alloc) s->alloc.release(keep[k], s->alloc.ctx);
+                else cudaFree(keep[k]);
+                s->device_bytes -= s->bufs[q].bytes;
+                s->bufs.erase(s->bufs.begin() + q);
+                break;
+            }
+        }
+    }
+    s->cur = cur;
+    s->n = n0;
+    s->have_prev = hp;
+    if (choice) *choice = best_k;
+    return rc;
+}
+
 int maclab_set_graph_steps(maclab_t s, int steps)
 {
     if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");

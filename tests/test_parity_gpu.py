@@ -119,6 +119,23 @@ def test_tile_rows_do_not_change_results(rows):
 
 
 @pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_autotune_keeps_state_and_results(precision):
+    case = inputs.random_case(131, 60, 21, edges=(BOUNCEBACK, BOUNCEBACK, SPECULAR, SPECULAR))
+    a = sim_of(case, precision)
+    a.step(7)
+    before = a.get_state()
+    choice = a.autotune(4)
+    assert 0 <= choice <= 4 and a.time()[1] == 7
+    for x, y in zip(a.get_state(), before):
+        assert np.array_equal(x, y)
+    a.step(30)
+    b = sim_of(case, precision)
+    b.step(37)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
 def test_graph_replay_is_bitwise_identical(precision):
     """maclab_step replays captured CUDA graphs for steady boundary data;
     the result equals one launch per step."""
