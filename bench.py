@@ -36,6 +36,9 @@ METRIC = ("MLUPS & % of HBM roofline (FP32 step); wall time to residual 1e-8, "
 BYTES_PER_NODE = {"f32": 29, "f64": 57}   # read eta,u,v,D + type, write eta,u,v
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_JSON = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+# step-kernel codes of the library (maclab_step_kernel)
+KERNEL_SYMBOL = {0: "step_tile_kernel<%s>", 1: "step_fast_kernel<%s>", 2: "step_tile_tma_kernel (%s)"}
+KERNEL_LABEL = {0: "tile 64x16", 1: "warp strip", 2: "TMA-staged tile 64x16, persistent"}
 
 
 def kernel_source_hash() -> str:
@@ -57,14 +60,14 @@ def hbm_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def traffic_per_launch(precision, workload):
+def traffic_per_launch(precision, workload, kernel):
     try:
         with open(PROFILE_JSON) as fh:
             d = json.load(fh)
     except (OSError, ValueError):
         return None
     if d.get("source_sha256") != kernel_source_hash() or d.get("workload") != workload or \
-            d.get("precision") != precision:
+            d.get("precision") != precision or d.get("kernel", "").split("<")[0] != kernel:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -186,6 +189,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tile-rows", type=int, default=0)
+    ap.add_argument("--kernel", default="default", choices=["default", "tile", "strip", "tma"],
+                    help="step kernel of the main leg (default: the library's choice)")
     ap.add_argument("--no-extra", action="store_true", help="skip the steady-state and FP64 legs")
     ap.add_argument("--steady-max-steps", type=int, default=2_000_000)
     ap.add_argument("--f64-steps", type=int, default=300)
@@ -221,6 +226,8 @@ def main():
     sim = Simulation.from_case(case, precision=args.precision)
     if args.tile_rows:
         sim.set_tile_rows(args.tile_rows)
+    if args.kernel != "default":
+        sim.set_step_kernel(args.kernel)
     stream = torch.cuda.current_stream()
     info = sim.info
     n_general = info["n_fluid"] - info["n_fast"] - info["n_dirichlet"]
@@ -257,12 +264,12 @@ def main():
     peak, peak_src = hbm_peak()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src,
-                "kernel": "%s<%s>" % ("step_tile_kernel" if info["step_kernel"] == 0 else "step_fast_kernel",
-                                      "float" if args.precision == "f32" else "double"),
+                "kernel": KERNEL_SYMBOL[info["step_kernel"]] % ("float" if args.precision == "f32" else "double"),
                 "dirichlet_fused": bool(info["dirichlet_fused"]),
                 "bytes_per_node": BYTES_PER_NODE[args.precision],
                 "kernel_ms_per_launch": avg_kernel_s * 1e3,
-                "traffic": traffic_per_launch(args.precision, workload)}
+                "traffic": traffic_per_launch(args.precision, workload,
+                                              KERNEL_SYMBOL[info["step_kernel"]].split("<")[0].split(" ")[0])}
 
     # end to end through the public API: pinned host state in, one step, state out
     N = nodes
@@ -327,7 +334,8 @@ def main():
                "kernel_ms_per_launch": k64 / max(1, n64),
                "achieved_gbs": BYTES_PER_NODE["f64"] * nodes / (k64 / max(1, n64) / 1e3) / 1e9,
                "bytes_per_node": BYTES_PER_NODE["f64"],
-               "step_kernel": "tile 64x16" if choice64 == 0 else "warp strip, %d rows" % (4 << choice64)}
+               "step_kernel": ("tile 64x16" if choice64 == 0 else "TMA-staged tile 64x16" if choice64 == 5
+                               else "warp strip, %d rows" % (4 << choice64))}
         s64.close()
 
     # the batched ensemble: 512 uneven lakes and channels advanced together
@@ -373,7 +381,7 @@ def main():
                            "l2": "inputs larger than L2 (state %.0f MB), no flush" %
                                  (nodes * BYTES_PER_NODE[args.precision] / 1e6),
                            "parallelism": "replicas" if world > 1 else "single-gpu",
-                           "step_kernel": "tile 64x16" if info["step_kernel"] == 0 else "warp strip"},
+                           "step_kernel": KERNEL_LABEL[info["step_kernel"]]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "steady_state": steady, "f64": f64, "batched": batched,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clocks}

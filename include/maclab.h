@@ -78,6 +78,15 @@ typedef enum {
 
 enum { MACLAB_W = 0, MACLAB_E = 1, MACLAB_S = 2, MACLAB_N = 3 };
 
+/* Step kernels.  All three compute the same step and give bitwise
+ * identical results; they differ in how a block reads the old state. */
+typedef enum {
+    MACLAB_KERNEL_TILE = 0,  /* 64 x 16 node tiles, one block per tile         */
+    MACLAB_KERNEL_STRIP = 1, /* one warp per strip of rows                     */
+    MACLAB_KERNEL_TMA = 2    /* FP32 only: persistent blocks; interior tiles
+                                staged in shared memory by tensor copies     */
+} maclab_step_kernel;
+
 typedef struct {
     int nx, ny; /* nodes per row / rows, each >= 1                           */
     double dx;  /* lattice size delta x in metres, > 0                       */
@@ -136,7 +145,7 @@ typedef struct {
     int64_t n_fast;          /* nodes updated on the interior fast path        */
     size_t device_bytes;     /* device memory held by the handle               */
     int tile_rows;           /* rows per warp strip of the strip kernel        */
-    int step_kernel;         /* 0 = 64x16 tile kernel, 1 = warp-strip kernel    */
+    int step_kernel;         /* maclab_step_kernel in use                      */
     int dirichlet_fused;     /* 1 when Dirichlet nodes are set inside the step kernel */
 } maclab_info;
 
@@ -250,6 +259,13 @@ int maclab_set_tile_rows(maclab_t sim, int rows);
  * walk the strips in turn).  Tuning only: results are bitwise identical. */
 int maclab_set_launch(maclab_t sim, int rows, int blocks);
 
+/* Choose the step kernel (maclab_step_kernel).  MACLAB_KERNEL_TMA needs an
+ * FP32 handle; otherwise MACLAB_E_ARG.  Tuning only: results are bitwise
+ * identical.  A TMA-staged step whose copy never arrives (a wait bounded
+ * at about a second) makes the next maclab_residual / maclab_get_state
+ * return MACLAB_E_CUDA. */
+int maclab_set_step_kernel(maclab_t sim, int kernel);
+
 /* Kernel timing for benchmarks.  While enabled (on != 0), every step
  * records a CUDA event pair around the launch of the fused step kernel on
  * the handle's stream.  maclab_get_profile synchronises, adds up the
@@ -260,7 +276,8 @@ int maclab_get_profile(maclab_t sim, double* step_kernel_ms, int64_t* launches);
 
 /* Time the step-kernel launch shapes on this handle's own grid and keep
  * the fastest: *choice = 0 for the 64 x 16 tile kernel, k = 1..4 for the
- * warp-strip kernel with 8, 16, 32 or 64 rows per strip.  Each shape runs
+ * warp-strip kernel with 8, 16, 32 or 64 rows per strip, 5 for the
+ * TMA-staged tile kernel (FP32 handles only).  Each shape runs
  * 2 + trial_steps steps; the state, step count and time are restored
  * afterwards (results are bitwise identical for every shape).  Allocates
  * and frees a copy of the state.  Synchronises. */

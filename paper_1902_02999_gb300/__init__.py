@@ -225,9 +225,18 @@ class Simulation:
         self.info["tile_rows"] = min(int(rows), self.ny)
         self.info["grid_blocks"] = int(blocks)
 
+    KERNELS = {"tile": 0, "strip": 1, "tma": 2}
+
+    def set_step_kernel(self, kernel) -> None:
+        """Step kernel: "tile", "strip" or "tma" (FP32 only), or its code."""
+        code = self.KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+        self._check(self._lib.maclab_set_step_kernel(self._h, code))
+        self.info["step_kernel"] = code
+
     def autotune(self, trial_steps: int = 20) -> int:
         """Pick the fastest step-kernel launch shape for this grid (0 = tile
-        kernel, 1..4 = strip kernel with 8/16/32/64 rows); state unchanged."""
+        kernel, 1..4 = strip kernel with 8/16/32/64 rows, 5 = TMA-staged tile
+        kernel); state unchanged."""
         c = ctypes.c_int()
         self._check(self._lib.maclab_autotune(self._h, int(trial_steps), ctypes.byref(c)))
         info = _abi.Info()

@@ -67,6 +67,7 @@ PROTOTYPES = [
     ("maclab_set_tile_rows", c_int, [c_void_p, c_int]),
     ("maclab_set_launch", c_int, [c_void_p, c_int, c_int]),
     ("maclab_autotune", c_int, [c_void_p, c_int, P(c_int)]),
+    ("maclab_set_step_kernel", c_int, [c_void_p, c_int]),
     ("maclab_set_profiling", c_int, [c_void_p, c_int]),
     ("maclab_get_profile", c_int, [c_void_p, P(c_double), P(c_int64)]),
     ("maclab_get_info", c_int, [c_void_p, P(Info)]),

@@ -9,6 +9,8 @@
 #include "maclab.h"
 #include "maclab_kernels.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -66,7 +68,11 @@ struct maclab_s {
     int ncb = 0, nrb = 0, ty = 0;
     int fmode = 0;             // force terms present: F_WIND | F_FRICTION | F_CORIOLIS
     int grid_blocks = 0;       // cap on step-kernel blocks (0 = one warp per strip)
-    bool use_tile = true;      // tile kernel (default) or warp-strip kernel
+    int kernel = MACLAB_KERNEL_TILE;  // step kernel: tile, warp strip or TMA-staged tile
+    bool tma_ok = false;       // tensor maps encoded (FP32, 16-byte aligned buffers)
+    TmaMaps tma_maps[2];       // per buffer parity of the state being read
+    int tma_grid = 0;          // persistent blocks of the TMA-staged kernel
+    int* tma_err = nullptr;    // set by the TMA-staged kernel when a wait timed out
     int graph_steps = 64;      // steps per CUDA-graph replay (even; 0 = no graphs)
     bool steady_bc = true;     // no boundary value depends on time
     cudaStream_t capture_stream = nullptr;
@@ -193,17 +199,34 @@ int launch_step(maclab_t s)
         }
     }
     const int b = 1 - s->cur;
-    if (s->use_tile) {
+    if (s->kernel != MACLAB_KERNEL_STRIP) {
         // fast nodes and (when fused) Dirichlet nodes in one launch; nodes with a
         // bounce-back link in a second launch when there are any
         const int tx = (s->grid.nx + tile::TX - 1) / tile::TX, ty = (s->grid.ny + tile::TY - 1) / tile::TY;
-        const size_t smem = tile::smem_bytes<T>();
         const TileDirichlet td{s->dir_fused ? s->dir_tile_start : nullptr, s->dir, s->D64, bv};
-        switch (s->fmode) {  // compile-time variants for the force terms present
+        if constexpr (std::is_same<T, float>::value) {
+            if (s->kernel == MACLAB_KERNEL_TMA) {
+                const TmaMaps& mp = s->tma_maps[s->cur];
+                switch (s->fmode) {
+#define MACLAB_FM(m)                                                                                \
+    case m:                                                                                         \
+        step_tile_tma_kernel<m><<<s->tma_grid, tile::THREADS, tma::SMEM, s->stream>>>(f, mp, tx, tx * ty, td, \
+                                                                                   s->tma_err);     \
+        break;
+                    MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6)
+                    MACLAB_FM(7)
+#undef MACLAB_FM
+                }
+            }
+        }
+        if (s->kernel == MACLAB_KERNEL_TILE) {
+            const size_t smem = tile::smem_bytes<T>();
+            switch (s->fmode) {  // compile-time variants for the force terms present
 #define MACLAB_FM(m) \
     case m: step_tile_kernel<T, m><<<tx * ty, tile::THREADS, smem, s->stream>>>(f, tx, td); break;
-            MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
+                MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
 #undef MACLAB_FM
+            }
         }
         if (s->n_general > 0)
             step_general_kernel<T><<<(s->n_general + 127) / 128, 128, 0, s->stream>>>(f, s->general,
@@ -223,7 +246,7 @@ int launch_step(maclab_t s)
                                                                                       s->n_general);
     }
     if (s->profiling) cudaEventRecord(ev1, s->stream);
-    if (s->n_dir > 0 && !(s->use_tile && s->dir_fused))
+    if (s->n_dir > 0 && !(s->kernel != MACLAB_KERNEL_STRIP && s->dir_fused))
         dirichlet_kernel<T><<<(s->n_dir + 127) / 128, 128, 0, s->stream>>>(
             (T*)s->eta[b], (T*)s->u[b], (T*)s->v[b], (const T*)s->D, s->D64, s->dir, s->n_dir, bv);
     cudaError_t e = cudaGetLastError();
@@ -245,6 +268,60 @@ int launch_residual(maclab_t s)
     residual_final_kernel<<<1, 32 * RED_NVAL, 0, s->stream>>>(s->partial, s->red_blocks, s->red_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(s, e, "residual launch");
+    return MACLAB_OK;
+}
+
+// Tensor maps of the TMA-staged kernel: 2D [ny][pitch] views of eta, u, v
+// (both buffers), D and the types; boxes of 72 floats / 96 bytes by 18 rows
+// (a tile and its halo).  Reads past the grid fill zeros, which only land in
+// staged columns the kernel does not use.  Returns false (and leaves the
+// TMA kernel off) when the driver entry point is missing, a buffer is not
+// 16-byte aligned or an encode fails.
+bool encode_tma_maps(maclab_t s)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+        cudaGetLastError();
+    });
+    if (!encode || s->prec != MACLAB_F32) return false;
+    auto make = [&](CUtensorMap* m, void* base, CUtensorMapDataType dt, size_t esize, uint32_t box_x) {
+        if (((uintptr_t)base & 15) != 0) return false;
+        const cuuint64_t dims[2] = {(cuuint64_t)s->grid.nx, (cuuint64_t)s->grid.ny};
+        const cuuint64_t strides[1] = {(cuuint64_t)s->pitch * esize};
+        const cuuint32_t box[2] = {box_x, (cuuint32_t)tile::IR};
+        const cuuint32_t estr[2] = {1, 1};
+        return encode(m, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    bool ok = true;
+    for (int a = 0; a < 2 && ok; ++a) {
+        TmaMaps& m = s->tma_maps[a];
+        ok = make(&m.eta, s->eta[a], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, tma::SRW) &&
+             make(&m.u, s->u[a], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, tma::SRW) &&
+             make(&m.v, s->v[a], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, tma::SRW) &&
+             make(&m.D, s->D, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, tma::SRW) &&
+             make(&m.type, s->type, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, tma::STW);
+    }
+    return ok;
+}
+
+// Nonzero when a TMA-staged step gave up waiting for a copy.
+int check_tma_err(maclab_t s)
+{
+    if (!s->tma_err) return MACLAB_OK;
+    int flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, s->tma_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "step status");
+    if (flag) return fail(s, MACLAB_E_CUDA, "TMA-staged step: a tensor copy did not arrive in time");
     return MACLAB_OK;
 }
 
@@ -510,6 +587,7 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
          (s->type = (uint8_t*)dev_alloc(s, NP + 64)) && (s->stage = (double*)dev_alloc(s, 3 * N * 8)) &&
          (s->partial = (double*)dev_alloc(s, (size_t)s->red_blocks * RED_NVAL * 8)) &&
          (s->red_out = (double*)dev_alloc(s, RED_NVAL * 8));
+    if (ok && s->prec == MACLAB_F32) ok = (s->tma_err = (int*)dev_alloc(s, sizeof(int))) != nullptr;
     if (ok && !general.empty()) ok = (s->general = (int*)dev_alloc(s, general.size() * sizeof(int))) != nullptr;
     if (ok && !dirs.empty()) ok = (s->dir = (DirNode*)dev_alloc(s, dirs.size() * sizeof(DirNode))) != nullptr;
     if (ok && s->dir_fused)
@@ -543,6 +621,7 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
     if (!general.empty()) put(s->general, general.data(), general.size() * sizeof(int));
     if (!dirs.empty()) put(s->dir, dirs.data(), dirs.size() * sizeof(DirNode));
     if (s->dir_fused) put(s->dir_tile_start, dir_start.data(), dir_start.size() * sizeof(int));
+    if (s->tma_err && ce == cudaSuccess) ce = cudaMemsetAsync(s->tma_err, 0, sizeof(int), s->stream);
     for (int k = 0; k < 2 && ce == cudaSuccess; ++k) {
         ce = cudaMemsetAsync(s->eta[k], 0, NP * s->esize, s->stream);
         if (ce == cudaSuccess) ce = cudaMemsetAsync(s->u[k], 0, NP * s->esize, s->stream);
@@ -568,7 +647,7 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
     // ---- shared memory of the tile kernel (above the 48 KB default for FP64) ----
     {
 #ifdef MACLAB_STRIP_KERNEL
-        s->use_tile = false;
+        s->kernel = MACLAB_KERNEL_STRIP;
 #endif
         cudaError_t ae = cudaSuccess;
 #define MACLAB_ATTR(T, m)                                                                                  \
@@ -583,6 +662,25 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
             MACLAB_ATTR(double, 4) MACLAB_ATTR(double, 5) MACLAB_ATTR(double, 6) MACLAB_ATTR(double, 7)
         }
 #undef MACLAB_ATTR
+        if (ae == cudaSuccess && s->prec == MACLAB_F32 && encode_tma_maps(s)) {
+            // the TMA-staged kernel: opt in to its shared memory, size its persistent grid
+            int per_sm = 0;
+#define MACLAB_ATTR(m)                                                                                    \
+    if (ae == cudaSuccess)                                                                                \
+        ae = cudaFuncSetAttribute(step_tile_tma_kernel<m>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  (int)tma::SMEM);
+            MACLAB_ATTR(0) MACLAB_ATTR(1) MACLAB_ATTR(2) MACLAB_ATTR(3) MACLAB_ATTR(4) MACLAB_ATTR(5)
+            MACLAB_ATTR(6) MACLAB_ATTR(7)
+#undef MACLAB_ATTR
+            if (ae == cudaSuccess)
+                ae = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_tile_tma_kernel<7>, tile::THREADS,
+                                                                   tma::SMEM);
+            const int ntiles = P.tiles_x * P.tiles_y;
+            if (ae == cudaSuccess && per_sm > 0) {
+                s->tma_ok = true;
+                s->tma_grid = std::max(1, std::min(ntiles, per_sm * sms));
+            }
+        }
         if (ae != cudaSuccess) {
             cuda_fail(nullptr, ae, "cudaFuncSetAttribute");
             release_all(s);
@@ -703,11 +801,13 @@ int maclab_autotune(maclab_t s, int trial_steps, int* choice)
     const int cur = s->cur;
     const int64_t n0 = s->n;
     const bool hp = s->have_prev;
-    const bool tile0 = s->use_tile;
+    const int kernel0 = s->kernel;
     const int ty0 = s->ty;
     const int prof0 = s->profiling;
-    // candidates: 0 = tile kernel; k >= 1 = strip kernel with 4 << k rows
+    // candidates: 0 = tile kernel; k = 1..4 strip kernel with 4 << k rows;
+    // 5 = TMA-staged tile kernel
     const int rows[5] = {0, 8, 16, 32, 64};
+    const int ncand = s->tma_ok ? 6 : 5;
     double best = 1e300;
     int best_k = 0;
     cudaEvent_t e0, e1;
@@ -715,9 +815,9 @@ int maclab_autotune(maclab_t s, int trial_steps, int* choice)
     cudaEventCreate(&e1);
     s->profiling = true;  // one launch per step (no graph replay) while timing
     int rc = MACLAB_OK;
-    for (int k = 0; k < 5 && rc == MACLAB_OK; ++k) {
-        s->use_tile = k == 0;
-        if (k > 0) {
+    for (int k = 0; k < ncand && rc == MACLAB_OK; ++k) {
+        s->kernel = k == 0 ? MACLAB_KERNEL_TILE : k == 5 ? MACLAB_KERNEL_TMA : MACLAB_KERNEL_STRIP;
+        if (k >= 1 && k <= 4) {
             s->ty = std::min(rows[k], s->grid.ny);
             s->nrb = (s->grid.ny + s->ty - 1) / s->ty;
         }
@@ -737,14 +837,14 @@ int maclab_autotune(maclab_t s, int trial_steps, int* choice)
     s->profiling = prof0;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    s->use_tile = best_k == 0;
-    if (best_k > 0) {
+    s->kernel = best_k == 0 ? MACLAB_KERNEL_TILE : best_k == 5 ? MACLAB_KERNEL_TMA : MACLAB_KERNEL_STRIP;
+    if (best_k >= 1 && best_k <= 4) {
         s->ty = std::min(rows[best_k], s->grid.ny);
     } else {
         s->ty = ty0;
     }
     s->nrb = (s->grid.ny + s->ty - 1) / s->ty;
-    (void)tile0;
+    (void)kernel0;
     drop_graphs(s);
     for (int k = 0; k < 6; ++k) cudaMemcpyAsync(src[k], keep[k], bytes, cudaMemcpyDeviceToDevice, s->stream);
     cudaStreamSynchronize(s->stream);
@@ -778,6 +878,8 @@ int maclab_set_graph_steps(maclab_t s, int steps)
 int maclab_get_state(maclab_t s, double* h, double* u, double* v)
 {
     if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    const int rc = check_tma_err(s);
+    if (rc != MACLAB_OK) return rc;
     return s->prec == MACLAB_F32 ? download_state<float>(s, h, u, v) : download_state<double>(s, h, u, v);
 }
 
@@ -792,7 +894,9 @@ int maclab_residual(maclab_t s, double out[4])
 {
     if (!s || !out) return fail(s, MACLAB_E_ARG, "NULL argument");
     if (!s->have_prev) return fail(s, MACLAB_E_STATE, "no step taken since create / set_state");
-    int rc = s->prec == MACLAB_F32 ? launch_residual<float>(s) : launch_residual<double>(s);
+    int rc = check_tma_err(s);
+    if (rc != MACLAB_OK) return rc;
+    rc = s->prec == MACLAB_F32 ? launch_residual<float>(s) : launch_residual<double>(s);
     if (rc != MACLAB_OK) return rc;
     double r[RED_NVAL];
     cudaError_t e = cudaMemcpyAsync(r, s->red_out, sizeof(r), cudaMemcpyDeviceToHost, s->stream);
@@ -946,6 +1050,18 @@ int maclab_set_launch(maclab_t s, int rows, int blocks)
     return MACLAB_OK;
 }
 
+int maclab_set_step_kernel(maclab_t s, int kernel)
+{
+    if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    if (kernel != MACLAB_KERNEL_TILE && kernel != MACLAB_KERNEL_STRIP && kernel != MACLAB_KERNEL_TMA)
+        return fail(s, MACLAB_E_ARG, "unknown step kernel");
+    if (kernel == MACLAB_KERNEL_TMA && !s->tma_ok)
+        return fail(s, MACLAB_E_ARG, "the TMA-staged kernel needs an FP32 handle with 16-byte aligned buffers");
+    s->kernel = kernel;
+    drop_graphs(s);
+    return MACLAB_OK;
+}
+
 int maclab_set_profiling(maclab_t s, int on)
 {
     if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
@@ -988,8 +1104,8 @@ int maclab_get_info(maclab_t s, maclab_info* info)
     info->n_fast = s->n_fast;
     info->device_bytes = s->device_bytes;
     info->tile_rows = s->ty;
-    info->step_kernel = s->use_tile ? 0 : 1;
-    info->dirichlet_fused = (s->use_tile && s->dir_fused) ? 1 : 0;
+    info->step_kernel = s->kernel;
+    info->dirichlet_fused = (s->kernel != MACLAB_KERNEL_STRIP && s->dir_fused) ? 1 : 0;
     return MACLAB_OK;
 }
 
@@ -1522,13 +1638,13 @@ int maclab_batch_get_state(maclab_batch_t b, int i, double* h, double* u, double
         state_out_kernel<double><<<grid_blocks(N, 256, 4096), 256, 0, b->stream>>>(
             (const double*)b->eta[c] + o, (const double*)b->u[c] + o, (const double*)b->v[c] + o, b->D64 + o,
             b->stage, b->stage + N, b->stage + 2 * N, b->nx[i], b->ny[i], b->pitch[i]);
-    if ((e = cudaGetLastError()) != cudaSuccess) return bfail(b, MACLAB_E_CUDA, "batch get_state");
+    if ((e = cudaGetLastError()) != cudaSuccess) return bfail(b, MACLAB_E_CUDA, std::string("batch get_state: ") + cudaGetErrorString(e));
     double* dst[3] = {h, u, v};
     for (int k = 0; k < 3; ++k)
         if (dst[k] && (e = cudaMemcpyAsync(dst[k], b->stage + k * N, N * 8, cudaMemcpyDeviceToHost, b->stream)) !=
                           cudaSuccess)
-            return bfail(b, MACLAB_E_CUDA, "batch get_state");
-    if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return bfail(b, MACLAB_E_CUDA, "batch get_state");
+            return bfail(b, MACLAB_E_CUDA, std::string("batch get_state: ") + cudaGetErrorString(e));
+    if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return bfail(b, MACLAB_E_CUDA, std::string("batch get_state: ") + cudaGetErrorString(e));
     return MACLAB_OK;
 }
 
@@ -1541,7 +1657,7 @@ int maclab_batch_set_state(maclab_batch_t b, int i, const double* h, const doubl
     if ((e = cudaMemcpyAsync(b->stage, h, N * 8, cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(b->stage + N, u, N * 8, cudaMemcpyHostToDevice, b->stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(b->stage + 2 * N, v, N * 8, cudaMemcpyHostToDevice, b->stream)) != cudaSuccess)
-        return bfail(b, MACLAB_E_CUDA, "batch set_state");
+        return bfail(b, MACLAB_E_CUDA, std::string("batch set_state: ") + cudaGetErrorString(e));
     const int c = b->cur, d = 1 - b->cur;
     // both buffers: the instance is consistent whatever the parity
     if (b->prec == MACLAB_F32)
@@ -1554,11 +1670,11 @@ int maclab_batch_set_state(maclab_batch_t b, int i, const double* h, const doubl
             b->stage, b->stage + N, b->stage + 2 * N, b->D64 + o, b->type + o, (double*)b->eta[c] + o,
             (double*)b->u[c] + o, (double*)b->v[c] + o, (double*)b->eta[d] + o, (double*)b->u[d] + o,
             (double*)b->v[d] + o, b->nx[i], b->ny[i], b->pitch[i]);
-    if ((e = cudaGetLastError()) != cudaSuccess) return bfail(b, MACLAB_E_CUDA, "batch set_state");
-    if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return bfail(b, MACLAB_E_CUDA, "batch set_state");
+    if ((e = cudaGetLastError()) != cudaSuccess) return bfail(b, MACLAB_E_CUDA, std::string("batch set_state: ") + cudaGetErrorString(e));
+    if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return bfail(b, MACLAB_E_CUDA, std::string("batch set_state: ") + cudaGetErrorString(e));
     int rc = batch_freeze(b, i);
     if (rc == MACLAB_OK && (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
-        return bfail(b, MACLAB_E_CUDA, "batch set_state");
+        return bfail(b, MACLAB_E_CUDA, std::string("batch set_state: ") + cudaGetErrorString(e));
     b->have_prev = false;
     return rc;
 }

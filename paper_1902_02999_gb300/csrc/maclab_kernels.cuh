@@ -30,6 +30,8 @@
 // e sum_a lambda_a KF c_a (c_a.F(x)) = dt F(x) / 2).
 #pragma once
 #include <cstdint>
+#include <type_traits>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace maclab {
@@ -780,49 +782,102 @@ __device__ __forceinline__ void store_pair(tile::Derived<T>& sm, int pr, int lc,
     sm.ed[pr][lc + 1] = V2{b.eta, b.D};
 }
 
-// Update of one tile whose top-left updated node is (x0, y0); `tile` indexes
-// the per-tile Dirichlet ranges.
+// Raw rows of an interior tile staged in shared memory by tensor copies
+// (FP32): eta, u, v and D over global columns x0 - 4 .. x0 + 67 (a 16-byte
+// aligned start) and the node types over x0 - 16 .. x0 + 79, for tile rows
+// y0 - 1 .. y0 + 16.  A tensor copy writes to a 128-byte aligned shared
+// address, so each staged field starts on 128 bytes.
+namespace tma {
+constexpr int SRW = tile::TX + 8;     // 72 staged float columns
+constexpr int STW = tile::TX + 32;    // 96 staged type columns
+constexpr int FOFF = 2;               // staged float column of tile column 0
+constexpr int TOFF = 14;              // staged type column of tile column 0
+constexpr int FBOX = tile::IR * SRW;  // floats per staged field (5184 bytes)
+constexpr int FSTRIDE = (FBOX * 4 + 127) / 128 * 128 / 4;  // floats between fields (5248 bytes)
+struct Stage {
+    float f[4][FSTRIDE];              // eta, u, v, D: [IR][SRW] each
+    uint8_t type[tile::IR * STW];     // [IR][STW]
+};
+constexpr uint32_t BYTES = 4u * FBOX * 4u + tile::IR * STW;
+constexpr size_t STAGE_OFF = (sizeof(tile::Derived<float>) + 127) / 128 * 128;
+constexpr size_t SMEM = 128 + STAGE_OFF + sizeof(Stage);  // 128: room to align the base
+}  // namespace tma
+
+// Pair at tile row lr and tile column lc (even) of a staged tile.
+__device__ __forceinline__ void staged_pair(const tma::Stage& st, int lr, int lc, Raw<float> (&raw)[2],
+                                            uint32_t& types)
+{
+    const int s = lr * tma::SRW + lc + tma::FOFF;
+    const float2 e2 = *reinterpret_cast<const float2*>(&st.f[0][s]);
+    const float2 u2 = *reinterpret_cast<const float2*>(&st.f[1][s]);
+    const float2 v2 = *reinterpret_cast<const float2*>(&st.f[2][s]);
+    const float2 d2 = *reinterpret_cast<const float2*>(&st.f[3][s]);
+    types = *reinterpret_cast<const uint16_t*>(&st.type[lr * tma::STW + lc + tma::TOFF]);
+    raw[0] = Raw<float>{e2.x, u2.x, v2.x, d2.x, 0};
+    raw[1] = Raw<float>{e2.y, u2.y, v2.y, d2.y, 0};
+}
+
+// Phase A of a tile: raw values of the thread's own pairs (tile pair
+// column 1 + tx, tile rows 1 + 2 tyy + r) and of one halo pair, derived and
+// stored to shared memory.  `st` (FP32 only) holds the staged rows of an
+// interior tile; null means load through the edge rules.
 template <typename T, int FM>
-__device__ __forceinline__ void tile_update(const Fields<T>& f, int x0, int y0, int tile, const int* dir_start,
-                                            const DirNode* dir_list, const double* D64, const DirValues& bv,
-                                            tile::Derived<T>& sm)
+__device__ __forceinline__ void tile_phase_a(const Fields<T>& f, int x0, int y0, const tma::Stage* st,
+                                             tile::Derived<T>& sm, Src<T> (&own)[2][2], uint32_t (&own_types)[2])
+{
+    using namespace tile;
+    const int tx = threadIdx.x & 31, tyy = threadIdx.x >> 5;
+    Raw<T> raw[2][2];
+    Raw<T> hraw[2];
+    uint32_t htypes;
+    int hpr = 0, hpc = 0;
+    const bool has_halo = threadIdx.x < HALO_PAIRS;
+    if (has_halo) {
+        const int h = threadIdx.x;
+        if (h < 2 * IR) { hpc = h < IR ? 0 : PC - 1; hpr = h % IR; }
+        else { const int u = h - 2 * IR; hpr = u < PC - 2 ? 0 : IR - 1; hpc = 1 + u % (PC - 2); }
+    }
+    bool staged = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (st) {
+            staged = true;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) staged_pair(*st, 1 + 2 * tyy + r, 2 + 2 * tx, raw[r], own_types[r]);
+            if (has_halo) staged_pair(*st, hpr, 2 * hpc, hraw, htypes);
+        }
+    }
+    if (!staged) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) load_pair(f, y0 + 2 * tyy + r, x0 + 2 * tx, raw[r], own_types[r]);
+        if (has_halo) load_pair(f, y0 - 1 + hpr, x0 - 2 + 2 * hpc, hraw, htypes);
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        derive<T, FM>(f.c, raw[r][0], own[r][0]);
+        derive<T, FM>(f.c, raw[r][1], own[r][1]);
+        store_pair(sm, 1 + 2 * tyy + r, 2 + 2 * tx, own[r][0], own[r][1]);
+    }
+    if (has_halo) {
+        Src<T> h0, h1;
+        derive<T, FM>(f.c, hraw[0], h0);
+        derive<T, FM>(f.c, hraw[1], h1);
+        store_pair(sm, hpr, 2 * hpc, h0, h1);
+    }
+}
+
+// Phases B and C of a tile whose phase A is complete and visible; `tile`
+// indexes the per-tile Dirichlet ranges.
+template <typename T>
+__device__ __forceinline__ void tile_phase_bc(const Fields<T>& f, int x0, int y0, int tile, const int* dir_start,
+                                              const DirNode* dir_list, const double* D64, const DirValues& bv,
+                                              const tile::Derived<T>& sm, const Src<T> (&own)[2][2],
+                                              const uint32_t (&own_types)[2])
 {
     using namespace tile;
     using O = Op<T>;
     using V2 = typename Vec2<T>::type;
     const int tx = threadIdx.x & 31, tyy = threadIdx.x >> 5;
     const Coef<T>& K = f.c;
-    // ---- phase A: own pairs (tile pair column 1 + tx, tile rows 1 + 2 tyy + r)
-    Src<T> own[2][2];
-    uint32_t own_types[2];
-    {
-        Raw<T> raw[2][2];
-#pragma unroll
-        for (int r = 0; r < 2; ++r) load_pair(f, y0 + 2 * tyy + r, x0 + 2 * tx, raw[r], own_types[r]);
-        Raw<T> hraw[2];
-        uint32_t htypes;
-        int hpr = 0, hpc = 0;
-        const bool has_halo = threadIdx.x < HALO_PAIRS;
-        if (has_halo) {
-            const int h = threadIdx.x;
-            if (h < 2 * IR) { hpc = h < IR ? 0 : PC - 1; hpr = h % IR; }
-            else { const int u = h - 2 * IR; hpr = u < PC - 2 ? 0 : IR - 1; hpc = 1 + u % (PC - 2); }
-            load_pair(f, y0 - 1 + hpr, x0 - 2 + 2 * hpc, hraw, htypes);
-        }
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            derive<T, FM>(f.c, raw[r][0], own[r][0]);
-            derive<T, FM>(f.c, raw[r][1], own[r][1]);
-            store_pair(sm, 1 + 2 * tyy + r, 2 + 2 * tx, own[r][0], own[r][1]);
-        }
-        if (has_halo) {
-            Src<T> h0, h1;
-            derive<T, FM>(f.c, hraw[0], h0);
-            derive<T, FM>(f.c, hraw[1], h1);
-            store_pair(sm, hpr, 2 * hpc, h0, h1);
-        }
-    }
-    __syncthreads();
     // ---- phase B: nodes (x0 + 2 tx + k, y0 + 2 tyy + r)
     const T q = T(0.25);
 #pragma unroll
@@ -899,6 +954,19 @@ __device__ __forceinline__ void tile_update(const Fields<T>& f, int x0, int y0, 
     }
 }
 
+// Update of one tile whose top-left updated node is (x0, y0); `tile` indexes
+// the per-tile Dirichlet ranges.
+template <typename T, int FM>
+__device__ __forceinline__ void tile_update(const Fields<T>& f, int x0, int y0, int tile, const int* dir_start,
+                                            const DirNode* dir_list, const double* D64, const DirValues& bv,
+                                            tile::Derived<T>& sm)
+{
+    Src<T> own[2][2];
+    uint32_t own_types[2];
+    tile_phase_a<T, FM>(f, x0, y0, nullptr, sm, own, own_types);
+    __syncthreads();
+    tile_phase_bc<T>(f, x0, y0, tile, dir_start, dir_list, D64, bv, sm, own, own_types);
+}
 
 template <typename T, int FM>
 __global__ void __launch_bounds__(tile::THREADS, tile::MinBlocks<T>::value)
@@ -908,6 +976,122 @@ step_tile_kernel(const __grid_constant__ Fields<T> f, int tiles_x, const __grid_
     tile::Derived<T>& sm = *reinterpret_cast<tile::Derived<T>*>(smem_raw);
     const int x0 = (blockIdx.x % tiles_x) * tile::TX, y0 = (blockIdx.x / tiles_x) * tile::TY;
     tile_update<T, FM>(f, x0, y0, blockIdx.x, td.start, td.list, td.D64, td.bv, sm);
+}
+
+// ---------------------------------------------------------------------------
+// TMA-staged tile kernel (FP32).  Blocks are persistent (three per SM) and
+// walk the tiles blockIdx.x, blockIdx.x + gridDim.x, ...  The raw rows of an
+// interior tile (every row and column its phase A reads lies inside the
+// grid, so no edge rule applies) arrive in shared memory by five 2D tensor
+// copies that one thread issues while the block still works on the previous
+// tile's gather; an mbarrier counts the bytes.  Edge tiles load through the
+// edge rules as in step_tile_kernel.  Every mbarrier wait is bounded: on
+// timeout the block sets *err, waits (bounded again) for its copy and leaves.
+struct TmaMaps {
+    CUtensorMap eta, u, v, D, type;   // 2D maps of the state being read, D and the types
+};
+constexpr uint32_t TMA_WAIT_LIMIT = 1u << 22;   // try_wait rounds before giving up
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+// true once the phase of parity `phase` has completed; false after `limit` rounds
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, uint32_t limit)
+{
+    for (uint32_t k = 0; k < limit; ++k) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+// Stage the rows of the tile at (x0, y0).  x0 is a multiple of 64, so both
+// inner coordinates (x0 - 4 floats, x0 - 16 bytes) start on 16 bytes.
+__device__ __forceinline__ void tma_stage(const TmaMaps& m, tma::Stage& st, uint32_t bar, int x0, int y0)
+{
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // earlier reads of the buffer come first
+    mbar_expect_tx(bar, tma::BYTES);
+    tma_load_2d((uint32_t)__cvta_generic_to_shared(&st.f[0][0]), &m.eta, x0 - 4, y0 - 1, bar);
+    tma_load_2d((uint32_t)__cvta_generic_to_shared(&st.f[1][0]), &m.u, x0 - 4, y0 - 1, bar);
+    tma_load_2d((uint32_t)__cvta_generic_to_shared(&st.f[2][0]), &m.v, x0 - 4, y0 - 1, bar);
+    tma_load_2d((uint32_t)__cvta_generic_to_shared(&st.f[3][0]), &m.D, x0 - 4, y0 - 1, bar);
+    tma_load_2d((uint32_t)__cvta_generic_to_shared(&st.type[0]), &m.type, x0 - 16, y0 - 1, bar);
+}
+// Phase A of the tile at (x0, y0) reads grid columns x0 - 2 .. x0 + 65 and
+// rows y0 - 1 .. y0 + 16 only.
+__device__ __forceinline__ bool tile_interior(int nx, int ny, int x0, int y0)
+{
+    return x0 >= 2 && x0 + tile::TX + 2 <= nx && y0 >= 1 && y0 + tile::TY + 1 <= ny;
+}
+
+template <int FM>
+__global__ void __launch_bounds__(tile::THREADS, 3)
+step_tile_tma_kernel(const __grid_constant__ Fields<float> f, const __grid_constant__ TmaMaps maps, int tiles_x,
+                     int ntiles, const __grid_constant__ TileDirichlet td, int* __restrict__ err)
+{
+    extern __shared__ __align__(128) unsigned char smem_tma[];
+    // the base rounded up to 128 bytes (tma::SMEM holds the slack)
+    unsigned char* base = smem_tma + ((128u - ((uint32_t)__cvta_generic_to_shared(smem_tma) & 127u)) & 127u);
+    tile::Derived<float>& sm = *reinterpret_cast<tile::Derived<float>*>(base);
+    tma::Stage& st = *reinterpret_cast<tma::Stage*>(base + tma::STAGE_OFF);
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ int abort_flag;
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    int t = blockIdx.x;
+    if (threadIdx.x == 0 && t < ntiles) {
+        const int x0 = (t % tiles_x) * tile::TX, y0 = (t / tiles_x) * tile::TY;
+        if (tile_interior(f.nx, f.ny, x0, y0)) tma_stage(maps, st, bar, x0, y0);
+    }
+    for (; t < ntiles; t += gridDim.x) {
+        const int x0 = (t % tiles_x) * tile::TX, y0 = (t / tiles_x) * tile::TY;
+        const bool staged = tile_interior(f.nx, f.ny, x0, y0);
+        if (staged) {
+            if (!mbar_wait(bar, phase, TMA_WAIT_LIMIT)) atomicOr(&abort_flag, 1);
+            __syncthreads();
+            if (abort_flag) {
+                if (threadIdx.x == 0) atomicOr(err, 1);
+                mbar_wait(bar, phase, TMA_WAIT_LIMIT);  // the copy lands before the block leaves
+                return;
+            }
+            phase ^= 1u;
+        }
+        Src<float> own[2][2];
+        uint32_t own_types[2];
+        tile_phase_a<float, FM>(f, x0, y0, staged ? &st : nullptr, sm, own, own_types);
+        __syncthreads();  // derived values visible; the staging buffer is free again
+        if (threadIdx.x == 0) {
+            const int tn = t + gridDim.x;
+            if (tn < ntiles) {
+                const int xn = (tn % tiles_x) * tile::TX, yn = (tn / tiles_x) * tile::TY;
+                if (tile_interior(f.nx, f.ny, xn, yn)) tma_stage(maps, st, bar, xn, yn);
+            }
+        }
+        tile_phase_bc<float>(f, x0, y0, t, td.start, td.list, td.D64, td.bv, sm, own, own_types);
+        __syncthreads();  // phase B reads of `sm` end before the next phase A writes it
+    }
 }
 
 // ---------------------------------------------------------------------------
