@@ -147,6 +147,7 @@ Coef<T> make_coef(const maclab_params& p, double e, double dt)
     c.wfy = (T)(p.rho_a * p.Cw * p.wind_v * wmag / p.rho_w);
     c.Cb = (T)p.Cb;
     c.Om = (T)p.Omega;
+    c.nz = (T)-0.0;
     return c;
 }
 

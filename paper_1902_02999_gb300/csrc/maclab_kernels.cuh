@@ -57,6 +57,7 @@ struct Coef {
     T wfy;
     T Cb;    // C_b (Eq. bed-stress)
     T Om;    // Omega (Eq. SWE-force)
+    T nz;    // -0.0, read at run time (see Op2::mul)
 };
 
 template <typename T>
@@ -132,6 +133,48 @@ template <> struct Op<double> {
     static __device__ __forceinline__ double sqrt(double a) { return ::sqrt(a); }
 };
 
+// Paired FP32 arithmetic on sm_100-class GPUs: one instruction applies the
+// same operation to two lanes (.x, .y), each rounded to nearest as the
+// scalar Op<float> operation would be, so a node's result is the same
+// whether its arithmetic ran paired or alone.
+struct Op2 {
+    // The lanes travel as two f32 registers and are packed inside the asm,
+    // so no float2 is reinterpreted as an integer in C++.
+    static __device__ __forceinline__ float2 add(float2 a, float2 c)
+    {
+        float2 d;
+        asm("{\n .reg .b64 a, c, d;\n mov.b64 a, {%2, %3};\n mov.b64 c, {%4, %5};\n"
+            " add.rn.f32x2 d, a, c;\n mov.b64 {%0, %1}, d;\n}\n"
+            : "=f"(d.x), "=f"(d.y)
+            : "f"(a.x), "f"(a.y), "f"(c.x), "f"(c.y));
+        return d;
+    }
+    static __device__ __forceinline__ float2 sub(float2 a, float2 c)
+    {
+        float2 d;
+        asm("{\n .reg .b64 a, c, d;\n mov.b64 a, {%2, %3};\n mov.b64 c, {%4, %5};\n"
+            " sub.rn.f32x2 d, a, c;\n mov.b64 {%0, %1}, d;\n}\n"
+            : "=f"(d.x), "=f"(d.y)
+            : "f"(a.x), "f"(a.y), "f"(c.x), "f"(c.y));
+        return d;
+    }
+    // a * c as fma(a, c, z) with z = -0.0 from the kernel's parameters: the
+    // same rounding as a plain multiply (signed zeros included), but the
+    // compiler cannot fuse it into a following add, which it does for a
+    // paired multiply even when both carry an explicit rounding mode.
+    static __device__ __forceinline__ float2 mul(float2 a, float2 c, float2 z) { return fma(a, c, z); }
+    static __device__ __forceinline__ float2 fma(float2 a, float2 c, float2 e)
+    {
+        float2 d;
+        asm("{\n .reg .b64 a, c, e, d;\n mov.b64 a, {%2, %3};\n mov.b64 c, {%4, %5};\n mov.b64 e, {%6, %7};\n"
+            " fma.rn.f32x2 d, a, c, e;\n mov.b64 {%0, %1}, d;\n}\n"
+            : "=f"(d.x), "=f"(d.y)
+            : "f"(a.x), "f"(a.y), "f"(c.x), "f"(c.y), "f"(e.x), "f"(e.y));
+        return d;
+    }
+};
+__device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
+
 // Which force terms of Eq. SWE-force are present (compile-time variants).
 enum : int { F_WIND = 1, F_FRICTION = 2, F_CORIOLIS = 4 };
 
@@ -191,6 +234,86 @@ __device__ __forceinline__ void derive(const Coef<T>& c, const Raw<T>& r, Src<T>
     s.o6 = O::sub(dp, s4);
     s.o8 = O::add(dm, t4);
     s.o4 = O::sub(dm, t4);
+    s.eta = eta;
+    s.D = D;
+}
+
+// Source quantities of two nodes at once (FP32): the operations of derive,
+// paired.  Negated products are formed with negated constants, which
+// rounds to the same value as negating the product.
+struct Src2 {
+    float2 eta, D;
+    float2 o1, o2, o3, o4, o5, o6, o7, o8;
+    float2 ownh;
+    float2 hFx, hFy;
+};
+
+__device__ __forceinline__ void flip_lane(uint8_t fl, float& u, float& v, float& wfx, float& wfy, float& Om)
+{
+    if (fl & 1) { u = -u; wfx = -wfx; }
+    if (fl & 2) { v = -v; wfy = -wfy; }
+    if (fl && (fl & 3) != 3) Om = -Om;
+}
+
+template <int FM>
+__device__ __forceinline__ void derive2(const Coef<float>& c, const Raw<float>& r0, const Raw<float>& r1, Src2& s)
+{
+    using P = Op2;
+    using O = Op<float>;
+    const float2 z = splat(c.nz);
+    float2 u = make_float2(r0.u, r1.u), v = make_float2(r0.v, r1.v);
+    float2 wfx = splat(c.wfx), wfy = splat(c.wfy), Om = splat(c.Om);
+    if (r0.flip | r1.flip) {  // specular ghosts: normal components reversed, rotation sense too
+        flip_lane(r0.flip, u.x, v.x, wfx.x, wfy.x, Om.x);
+        flip_lane(r1.flip, u.y, v.y, wfx.y, wfy.y, Om.y);
+    }
+    const float2 eta = make_float2(r0.eta, r1.eta), D = make_float2(r0.D, r1.D);
+    const float2 h = P::add(D, eta);
+    const float2 uu = P::fma(u, u, P::mul(v, v, z));
+    const float2 ge = P::mul(splat(c.G6), eta, z);
+    const float2 ku = P::mul(splat(c.K6), uu, z);
+    const float2 ap = P::mul(h, P::sub(ge, ku), z);
+    // eta - h (5 ge + 4 ku)
+    s.ownh = P::fma(h, P::fma(splat(-5.f), ge, P::mul(splat(-4.f), ku, z)), eta);
+    float2 Fx = (FM & F_WIND) ? wfx : splat(0.f), Fy = (FM & F_WIND) ? wfy : splat(0.f);
+    if (FM & F_CORIOLIS) {
+        const float2 omh = P::mul(Om, h, z);
+        const float2 nomh = P::mul(make_float2(-Om.x, -Om.y), h, z);
+        Fx = P::fma(omh, v, Fx);
+        Fy = P::fma(nomh, u, Fy);
+    }
+    if (FM & F_FRICTION) {
+        const float2 ncbs = P::mul(splat(-c.Cb), make_float2(O::sqrt(uu.x), O::sqrt(uu.y)), z);
+        Fx = P::fma(ncbs, u, Fx);
+        Fy = P::fma(ncbs, v, Fy);
+    }
+    const float2 hu = P::mul(h, u, z), hv = P::mul(h, v, z);
+    float2 qx = P::mul(hu, splat(c.k3), z), qy = P::mul(hv, splat(c.k3), z);
+    if (FM) {
+        s.hFx = P::mul(splat(c.hdt), Fx, z);
+        s.hFy = P::mul(splat(c.hdt), Fy, z);
+        qx = P::fma(splat(c.KF), Fx, qx);
+        qy = P::fma(splat(c.KF), Fy, qy);
+    } else {
+        s.hFx = splat(0.f);
+        s.hFy = splat(0.f);
+    }
+    const float2 sxx = P::mul(P::mul(hu, u, z), splat(c.k2), z);
+    const float2 syy = P::mul(P::mul(hv, v, z), splat(c.k2), z);
+    const float2 sxy = P::mul(P::mul(hu, v, z), splat(c.k1), z);
+    const float2 ax = P::add(ap, sxx), ay = P::add(ap, syy);
+    s.o1 = P::add(ax, qx);
+    s.o5 = P::sub(ax, qx);
+    s.o3 = P::add(ay, qy);
+    s.o7 = P::sub(ay, qy);
+    const float2 d = P::add(ax, syy);
+    const float2 q4 = splat(0.25f);
+    const float2 dp = P::mul(q4, P::add(d, sxy), z), dm = P::mul(q4, P::sub(d, sxy), z);
+    const float2 s4 = P::mul(q4, P::add(qx, qy), z), t4 = P::mul(q4, P::sub(qx, qy), z);
+    s.o2 = P::add(dp, s4);
+    s.o6 = P::sub(dp, s4);
+    s.o8 = P::add(dm, t4);
+    s.o4 = P::sub(dm, t4);
     s.eta = eta;
     s.D = D;
 }
@@ -954,6 +1077,83 @@ __device__ __forceinline__ void tile_phase_bc(const Fields<T>& f, int x0, int y0
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 tile phase A with paired arithmetic: a thread's two nodes of a row
+// are the two lanes of every operation of derive.  Same operations, same
+// results as tile_phase_a.
+__device__ __forceinline__ void store_pair2(tile::Derived<float>& sm, int pr, int lc, const Src2& s)
+{
+    *reinterpret_cast<float2*>(&sm.o[0][pr][lc]) = s.o1;
+    *reinterpret_cast<float2*>(&sm.o[1][pr][lc]) = s.o2;
+    *reinterpret_cast<float2*>(&sm.o[2][pr][lc]) = s.o3;
+    *reinterpret_cast<float2*>(&sm.o[3][pr][lc]) = s.o4;
+    *reinterpret_cast<float2*>(&sm.o[4][pr][lc]) = s.o5;
+    *reinterpret_cast<float2*>(&sm.o[5][pr][lc]) = s.o6;
+    *reinterpret_cast<float2*>(&sm.o[6][pr][lc]) = s.o7;
+    *reinterpret_cast<float2*>(&sm.o[7][pr][lc]) = s.o8;
+    *reinterpret_cast<float4*>(&sm.ed[pr][lc]) = make_float4(s.eta.x, s.D.x, s.eta.y, s.D.y);
+}
+
+template <int FM>
+__device__ __forceinline__ void tile_phase_a_f32(const Fields<float>& f, int x0, int y0, const tma::Stage* st,
+                                                 tile::Derived<float>& sm, Src2 (&own)[2], uint32_t (&own_types)[2])
+{
+    using namespace tile;
+    const int tx = threadIdx.x & 31, tyy = threadIdx.x >> 5;
+    Raw<float> raw[2][2];
+    Raw<float> hraw[2];
+    uint32_t htypes;
+    int hpr = 0, hpc = 0;
+    const bool has_halo = threadIdx.x < HALO_PAIRS;
+    if (has_halo) {
+        const int h = threadIdx.x;
+        if (h < 2 * IR) { hpc = h < IR ? 0 : PC - 1; hpr = h % IR; }
+        else { const int u = h - 2 * IR; hpr = u < PC - 2 ? 0 : IR - 1; hpc = 1 + u % (PC - 2); }
+    }
+    if (st) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) staged_pair(*st, 1 + 2 * tyy + r, 2 + 2 * tx, raw[r], own_types[r]);
+        if (has_halo) staged_pair(*st, hpr, 2 * hpc, hraw, htypes);
+    } else {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) load_pair(f, y0 + 2 * tyy + r, x0 + 2 * tx, raw[r], own_types[r]);
+        if (has_halo) load_pair(f, y0 - 1 + hpr, x0 - 2 + 2 * hpc, hraw, htypes);
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        derive2<FM>(f.c, raw[r][0], raw[r][1], own[r]);
+        store_pair2(sm, 1 + 2 * tyy + r, 2 + 2 * tx, own[r]);
+    }
+    if (has_halo) {
+        Src2 hs;
+        derive2<FM>(f.c, hraw[0], hraw[1], hs);
+        store_pair2(sm, hpr, 2 * hpc, hs);
+    }
+}
+
+__device__ __forceinline__ Src<float> lane_of(const Src2& s, int k)
+{
+    Src<float> o;
+#define MACLAB_LANE(m) o.m = k ? s.m.y : s.m.x;
+    MACLAB_LANE(eta) MACLAB_LANE(D) MACLAB_LANE(o1) MACLAB_LANE(o2) MACLAB_LANE(o3) MACLAB_LANE(o4)
+    MACLAB_LANE(o5) MACLAB_LANE(o6) MACLAB_LANE(o7) MACLAB_LANE(o8) MACLAB_LANE(ownh) MACLAB_LANE(hFx)
+    MACLAB_LANE(hFy)
+#undef MACLAB_LANE
+    return o;
+}
+
+__device__ __forceinline__ void tile_phase_bc_f32(const Fields<float>& f, int x0, int y0, int tile,
+                                                  const int* dir_start, const DirNode* dir_list, const double* D64,
+                                                  const DirValues& bv, const tile::Derived<float>& sm,
+                                                  const Src2 (&own)[2], const uint32_t (&own_types)[2])
+{
+    // phase B stays one node per instruction: pairing it needs the
+    // neighbours' (eta, D) regrouped by lane, which costs more moves and
+    // loads than the paired arithmetic saves
+    const Src<float> o[2][2] = {{lane_of(own[0], 0), lane_of(own[0], 1)}, {lane_of(own[1], 0), lane_of(own[1], 1)}};
+    tile_phase_bc<float>(f, x0, y0, tile, dir_start, dir_list, D64, bv, sm, o, own_types);
+}
+
 // Update of one tile whose top-left updated node is (x0, y0); `tile` indexes
 // the per-tile Dirichlet ranges.
 template <typename T, int FM>
@@ -961,11 +1161,23 @@ __device__ __forceinline__ void tile_update(const Fields<T>& f, int x0, int y0, 
                                             const DirNode* dir_list, const double* D64, const DirValues& bv,
                                             tile::Derived<T>& sm)
 {
-    Src<T> own[2][2];
     uint32_t own_types[2];
-    tile_phase_a<T, FM>(f, x0, y0, nullptr, sm, own, own_types);
-    __syncthreads();
-    tile_phase_bc<T>(f, x0, y0, tile, dir_start, dir_list, D64, bv, sm, own, own_types);
+#ifdef MACLAB_NO_PAIRED_A
+    constexpr bool paired = false;
+#else
+    constexpr bool paired = std::is_same<T, float>::value;
+#endif
+    if constexpr (paired) {
+        Src2 own[2];
+        tile_phase_a_f32<FM>(f, x0, y0, nullptr, sm, own, own_types);
+        __syncthreads();
+        tile_phase_bc_f32(f, x0, y0, tile, dir_start, dir_list, D64, bv, sm, own, own_types);
+    } else {
+        Src<T> own[2][2];
+        tile_phase_a<T, FM>(f, x0, y0, nullptr, sm, own, own_types);
+        __syncthreads();
+        tile_phase_bc<T>(f, x0, y0, tile, dir_start, dir_list, D64, bv, sm, own, own_types);
+    }
 }
 
 template <typename T, int FM>
@@ -1078,9 +1290,15 @@ step_tile_tma_kernel(const __grid_constant__ Fields<float> f, const __grid_const
             }
             phase ^= 1u;
         }
+#ifdef MACLAB_NO_PAIRED_A
         Src<float> own[2][2];
         uint32_t own_types[2];
         tile_phase_a<float, FM>(f, x0, y0, staged ? &st : nullptr, sm, own, own_types);
+#else
+        Src2 own[2];
+        uint32_t own_types[2];
+        tile_phase_a_f32<FM>(f, x0, y0, staged ? &st : nullptr, sm, own, own_types);
+#endif
         __syncthreads();  // derived values visible; the staging buffer is free again
         if (threadIdx.x == 0) {
             const int tn = t + gridDim.x;
@@ -1089,7 +1307,11 @@ step_tile_tma_kernel(const __grid_constant__ Fields<float> f, const __grid_const
                 if (tile_interior(f.nx, f.ny, xn, yn)) tma_stage(maps, st, bar, xn, yn);
             }
         }
+#ifdef MACLAB_NO_PAIRED_A
         tile_phase_bc<float>(f, x0, y0, t, td.start, td.list, td.D64, td.bv, sm, own, own_types);
+#else
+        tile_phase_bc_f32(f, x0, y0, t, td.start, td.list, td.D64, td.bv, sm, own, own_types);
+#endif
         __syncthreads();  // phase B reads of `sm` end before the next phase A writes it
     }
 }

@@ -1,7 +1,9 @@
 """The TMA-staged tile kernel (persistent blocks; interior tiles staged in
-shared memory by tensor copies) against the one-block-per-tile kernel
-(bitwise: both spell out every rounding the same way) and against the FP64
-oracle (within the FP32 tolerance of the parity tests)."""
+shared memory by tensor copies) against the one-block-per-tile kernel and
+the warp-strip kernel (bitwise: all spell out every rounding the same way;
+the tile kernels pair two nodes per FP32 instruction, the strip kernel does
+not) and against the FP64 oracle (within the FP32 tolerance of the parity
+tests)."""
 import numpy as np
 import pytest
 
@@ -30,15 +32,15 @@ def sim_of(case, kernel=None, precision="f32"):
     return sim
 
 
-def run_pair(case, steps, graph_steps=None):
+def run_pair(case, steps, graph_steps=None, kernels=("tile", "tma")):
     out = []
-    for kernel in ("tile", "tma"):
+    for kernel in kernels:
         sim = sim_of(case, kernel)
         if graph_steps is not None:
             sim.set_graph_steps(graph_steps)
         sim.step(steps)
         out.append(sim.get_state())
-        assert sim.info["step_kernel"] == (2 if kernel == "tma" else 0)
+        assert sim.info["step_kernel"] == {"tile": 0, "strip": 1, "tma": 2}[kernel]
         sim.close()
     return out
 
@@ -54,6 +56,17 @@ def test_tma_kernel_equals_tile_kernel(nx, ny, seed, edges):
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("edges", EDGES)
+def test_paired_and_scalar_kernels_agree_bitwise(edges):
+    """Paired FP32 arithmetic (tile kernels) against one node per
+    instruction (strip kernel), specular ghosts and ragged tails included."""
+    case = inputs.random_case(517, 131, 40, edges=edges)
+    runs = run_pair(case, 80, kernels=("strip", "tile", "tma"))
+    for other in runs[1:]:
+        for x, y in zip(runs[0], other):
+            assert np.array_equal(x, y)
+
+
 def test_tma_kernel_force_variants_equal_tile_kernel():
     """Every compile-time force variant: wind, friction, Coriolis on / off."""
     for fm in range(8):
@@ -64,9 +77,10 @@ def test_tma_kernel_force_variants_equal_tile_kernel():
             case.cb = 0.0
         if not fm & 4:
             case.omega = 0.0
-        a, b = run_pair(case, 40)
-        for x, y in zip(a, b):
-            assert np.array_equal(x, y), fm
+        runs = run_pair(case, 40, kernels=("strip", "tile", "tma"))
+        for other in runs[1:]:
+            for x, y in zip(runs[0], other):
+                assert np.array_equal(x, y), fm
 
 
 def test_tma_kernel_with_graph_replay():
