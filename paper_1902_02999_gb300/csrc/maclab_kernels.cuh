@@ -843,11 +843,23 @@ constexpr int IW = 2 * PC;                 // 68 tile columns: global x0 - 2 .. 
 constexpr int HALO_PAIRS = 2 * IR + 2 * (PC - 2);  // 100
 template <typename T>
 struct Derived {
-    T o[8][IR][IW];                        // outgoing values o_1 .. o_8
-    typename Vec2<T>::type ed[IR][IW];     // (eta, D)
+    T o_[8][IR][IW];                       // outgoing values o_1 .. o_8
+    __device__ __forceinline__ T& o(int d, int r, int c) { return o_[d][r][c]; }
+    __device__ __forceinline__ const T& o(int d, int r, int c) const { return o_[d][r][c]; }
+    // (eta, D), even and odd tile columns apart: a warp reading column
+    // 2 tx + k (k fixed) then touches consecutive 8-byte words
+    typename Vec2<T>::type ed_[2][IR][IW / 2];
+    __device__ __forceinline__ typename Vec2<T>::type& ed(int r, int c) { return ed_[c & 1][r][c >> 1]; }
+    __device__ __forceinline__ const typename Vec2<T>::type& ed(int r, int c) const { return ed_[c & 1][r][c >> 1]; }
 };
-template <typename T> struct MinBlocks { static constexpr int value = 3; };
+#ifndef MACLAB_TILE_MINB
+#define MACLAB_TILE_MINB 4
+#endif
+template <typename T> struct MinBlocks { static constexpr int value = MACLAB_TILE_MINB; };
 template <> struct MinBlocks<double> { static constexpr int value = 2; };
+// the batch kernel carries per-instance state: three blocks keep it in registers
+template <typename T> struct BatchMinBlocks { static constexpr int value = 3; };
+template <> struct BatchMinBlocks<double> { static constexpr int value = 2; };
 template <typename T>
 __host__ __device__ constexpr size_t smem_bytes() { return sizeof(Derived<T>); }
 }  // namespace tile
@@ -900,9 +912,9 @@ __device__ __forceinline__ void store_pair(tile::Derived<T>& sm, int pr, int lc,
     const T oa[8] = {a.o1, a.o2, a.o3, a.o4, a.o5, a.o6, a.o7, a.o8};
     const T ob[8] = {b.o1, b.o2, b.o3, b.o4, b.o5, b.o6, b.o7, b.o8};
 #pragma unroll
-    for (int d = 0; d < 8; ++d) *reinterpret_cast<V2*>(&sm.o[d][pr][lc]) = V2{oa[d], ob[d]};
-    sm.ed[pr][lc] = V2{a.eta, a.D};
-    sm.ed[pr][lc + 1] = V2{b.eta, b.D};
+    for (int d = 0; d < 8; ++d) *reinterpret_cast<V2*>(&sm.o(d, pr, lc)) = V2{oa[d], ob[d]};
+    sm.ed(pr, lc) = V2{a.eta, a.D};
+    sm.ed(pr, lc + 1) = V2{b.eta, b.D};
 }
 
 // Raw rows of an interior tile staged in shared memory by tensor copies
@@ -941,12 +953,12 @@ __device__ __forceinline__ void staged_pair(const tma::Stage& st, int lr, int lc
 }
 
 // Phase A of a tile: raw values of the thread's own pairs (tile pair
-// column 1 + tx, tile rows 1 + 2 tyy + r) and of one halo pair, derived and
-// stored to shared memory.  `st` (FP32 only) holds the staged rows of an
-// interior tile; null means load through the edge rules.
+// column 1 + tx, tile rows 1 + 2 tyy + r) and of one halo pair, loaded
+// through the edge rules, derived one node at a time and stored to shared
+// memory (FP64; FP32 uses the paired tile_phase_a_f32).
 template <typename T, int FM>
-__device__ __forceinline__ void tile_phase_a(const Fields<T>& f, int x0, int y0, const tma::Stage* st,
-                                             tile::Derived<T>& sm, Src<T> (&own)[2][2], uint32_t (&own_types)[2])
+__device__ __forceinline__ void tile_phase_a(const Fields<T>& f, int x0, int y0, tile::Derived<T>& sm,
+                                             Src<T> (&own)[2][2], uint32_t (&own_types)[2])
 {
     using namespace tile;
     const int tx = threadIdx.x & 31, tyy = threadIdx.x >> 5;
@@ -960,20 +972,9 @@ __device__ __forceinline__ void tile_phase_a(const Fields<T>& f, int x0, int y0,
         if (h < 2 * IR) { hpc = h < IR ? 0 : PC - 1; hpr = h % IR; }
         else { const int u = h - 2 * IR; hpr = u < PC - 2 ? 0 : IR - 1; hpc = 1 + u % (PC - 2); }
     }
-    bool staged = false;
-    if constexpr (std::is_same<T, float>::value) {
-        if (st) {
-            staged = true;
 #pragma unroll
-            for (int r = 0; r < 2; ++r) staged_pair(*st, 1 + 2 * tyy + r, 2 + 2 * tx, raw[r], own_types[r]);
-            if (has_halo) staged_pair(*st, hpr, 2 * hpc, hraw, htypes);
-        }
-    }
-    if (!staged) {
-#pragma unroll
-        for (int r = 0; r < 2; ++r) load_pair(f, y0 + 2 * tyy + r, x0 + 2 * tx, raw[r], own_types[r]);
-        if (has_halo) load_pair(f, y0 - 1 + hpr, x0 - 2 + 2 * hpc, hraw, htypes);
-    }
+    for (int r = 0; r < 2; ++r) load_pair(f, y0 + 2 * tyy + r, x0 + 2 * tx, raw[r], own_types[r]);
+    if (has_halo) load_pair(f, y0 - 1 + hpr, x0 - 2 + 2 * hpc, hraw, htypes);
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         derive<T, FM>(f.c, raw[r][0], own[r][0]);
@@ -1016,12 +1017,12 @@ __device__ __forceinline__ void tile_phase_bc(const Fields<T>& f, int x0, int y0
             const uint8_t ty = (uint8_t)(own_types[r] >> (8 * k));
             const bool ok = x < f.nx && y < f.ny && (ty & KIND_MASK) != K_SOLID && !(ty & GENERAL_BIT);
             okmask |= (ok ? 1u : 0u) << k;
-            const T cL_o1 = sm.o[0][lr][lc - 1], mL_o2 = sm.o[1][lr - 1][lc - 1], pL_o8 = sm.o[7][lr + 1][lc - 1];
-            const T cR_o5 = sm.o[4][lr][lc + 1], mR_o4 = sm.o[3][lr - 1][lc + 1], pR_o6 = sm.o[5][lr + 1][lc + 1];
-            const T mC_o3 = sm.o[2][lr - 1][lc], pC_o7 = sm.o[6][lr + 1][lc];
-            const V2 mL = sm.ed[lr - 1][lc - 1], mC = sm.ed[lr - 1][lc], mR = sm.ed[lr - 1][lc + 1];
-            const V2 cL = sm.ed[lr][lc - 1], cR = sm.ed[lr][lc + 1];
-            const V2 pL = sm.ed[lr + 1][lc - 1], pC = sm.ed[lr + 1][lc], pR = sm.ed[lr + 1][lc + 1];
+            const T cL_o1 = sm.o(0, lr, lc - 1), mL_o2 = sm.o(1, lr - 1, lc - 1), pL_o8 = sm.o(7, lr + 1, lc - 1);
+            const T cR_o5 = sm.o(4, lr, lc + 1), mR_o4 = sm.o(3, lr - 1, lc + 1), pR_o6 = sm.o(5, lr + 1, lc + 1);
+            const T mC_o3 = sm.o(2, lr - 1, lc), pC_o7 = sm.o(6, lr + 1, lc);
+            const V2 mL = sm.ed(lr - 1, lc - 1), mC = sm.ed(lr - 1, lc), mR = sm.ed(lr - 1, lc + 1);
+            const V2 cL = sm.ed(lr, lc - 1), cR = sm.ed(lr, lc + 1);
+            const V2 pL = sm.ed(lr + 1, lc - 1), pC = sm.ed(lr + 1, lc), pR = sm.ed(lr + 1, lc + 1);
             const T OL = O::add(O::add(cL_o1, mL_o2), pL_o8);
             const T OR = O::add(O::add(cR_o5, mR_o4), pR_o6);
             const T Sh = O::add(O::add(OL, OR), O::add(mC_o3, pC_o7));
@@ -1083,15 +1084,11 @@ __device__ __forceinline__ void tile_phase_bc(const Fields<T>& f, int x0, int y0
 // results as tile_phase_a.
 __device__ __forceinline__ void store_pair2(tile::Derived<float>& sm, int pr, int lc, const Src2& s)
 {
-    *reinterpret_cast<float2*>(&sm.o[0][pr][lc]) = s.o1;
-    *reinterpret_cast<float2*>(&sm.o[1][pr][lc]) = s.o2;
-    *reinterpret_cast<float2*>(&sm.o[2][pr][lc]) = s.o3;
-    *reinterpret_cast<float2*>(&sm.o[3][pr][lc]) = s.o4;
-    *reinterpret_cast<float2*>(&sm.o[4][pr][lc]) = s.o5;
-    *reinterpret_cast<float2*>(&sm.o[5][pr][lc]) = s.o6;
-    *reinterpret_cast<float2*>(&sm.o[6][pr][lc]) = s.o7;
-    *reinterpret_cast<float2*>(&sm.o[7][pr][lc]) = s.o8;
-    *reinterpret_cast<float4*>(&sm.ed[pr][lc]) = make_float4(s.eta.x, s.D.x, s.eta.y, s.D.y);
+    const float2 od[8] = {s.o1, s.o2, s.o3, s.o4, s.o5, s.o6, s.o7, s.o8};
+#pragma unroll
+    for (int d = 0; d < 8; ++d) *reinterpret_cast<float2*>(&sm.o(d, pr, lc)) = od[d];
+    sm.ed(pr, lc) = make_float2(s.eta.x, s.D.x);
+    sm.ed(pr, lc + 1) = make_float2(s.eta.y, s.D.y);
 }
 
 template <int FM>
@@ -1162,19 +1159,14 @@ __device__ __forceinline__ void tile_update(const Fields<T>& f, int x0, int y0, 
                                             tile::Derived<T>& sm)
 {
     uint32_t own_types[2];
-#ifdef MACLAB_NO_PAIRED_A
-    constexpr bool paired = false;
-#else
-    constexpr bool paired = std::is_same<T, float>::value;
-#endif
-    if constexpr (paired) {
+    if constexpr (std::is_same<T, float>::value) {
         Src2 own[2];
         tile_phase_a_f32<FM>(f, x0, y0, nullptr, sm, own, own_types);
         __syncthreads();
         tile_phase_bc_f32(f, x0, y0, tile, dir_start, dir_list, D64, bv, sm, own, own_types);
     } else {
         Src<T> own[2][2];
-        tile_phase_a<T, FM>(f, x0, y0, nullptr, sm, own, own_types);
+        tile_phase_a<T, FM>(f, x0, y0, sm, own, own_types);
         __syncthreads();
         tile_phase_bc<T>(f, x0, y0, tile, dir_start, dir_list, D64, bv, sm, own, own_types);
     }
@@ -1290,15 +1282,9 @@ step_tile_tma_kernel(const __grid_constant__ Fields<float> f, const __grid_const
             }
             phase ^= 1u;
         }
-#ifdef MACLAB_NO_PAIRED_A
-        Src<float> own[2][2];
-        uint32_t own_types[2];
-        tile_phase_a<float, FM>(f, x0, y0, staged ? &st : nullptr, sm, own, own_types);
-#else
         Src2 own[2];
         uint32_t own_types[2];
         tile_phase_a_f32<FM>(f, x0, y0, staged ? &st : nullptr, sm, own, own_types);
-#endif
         __syncthreads();  // derived values visible; the staging buffer is free again
         if (threadIdx.x == 0) {
             const int tn = t + gridDim.x;
@@ -1307,11 +1293,7 @@ step_tile_tma_kernel(const __grid_constant__ Fields<float> f, const __grid_const
                 if (tile_interior(f.nx, f.ny, xn, yn)) tma_stage(maps, st, bar, xn, yn);
             }
         }
-#ifdef MACLAB_NO_PAIRED_A
-        tile_phase_bc<float>(f, x0, y0, t, td.start, td.list, td.D64, td.bv, sm, own, own_types);
-#else
         tile_phase_bc_f32(f, x0, y0, t, td.start, td.list, td.D64, td.bv, sm, own, own_types);
-#endif
         __syncthreads();  // phase B reads of `sm` end before the next phase A writes it
     }
 }
@@ -1333,7 +1315,7 @@ struct BatchInst {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(tile::THREADS, tile::MinBlocks<T>::value)
+__global__ void __launch_bounds__(tile::THREADS, tile::BatchMinBlocks<T>::value)
 step_batch_kernel(const BatchInst<T>* __restrict__ insts, const int* __restrict__ tile_inst,
                   const uint8_t* __restrict__ active, int parity, const int* __restrict__ dir_start,
                   const DirNode* __restrict__ dirs)
