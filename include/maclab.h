@@ -351,6 +351,11 @@ int maclab_batch_get_state(maclab_batch_t batch, int i, double* h, double* u, do
 int maclab_batch_set_state(maclab_batch_t batch, int i, const double* h, const double* u,
                            const double* v);
 
+/* Device pointers of instance i's current state arrays (eta, u, v), each
+ * [ny_i][*pitch] in the batch's precision; valid until the next step,
+ * set_state or destroy.  For zero-copy reads by the caller. */
+int maclab_batch_device_state(maclab_batch_t batch, int i, void** eta, void** u, void** v, int* pitch);
+
 /* Instance count, total nodes, total tiles and steps taken. */
 int maclab_batch_info(maclab_batch_t batch, int* count, int64_t* nodes, int64_t* tiles, int64_t* steps);
 

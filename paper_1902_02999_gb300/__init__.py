@@ -409,6 +409,15 @@ class Batch:
         h, u, v = _f64(h, N), _f64(u, N), _f64(v, N)
         self._check(self._lib.maclab_batch_set_state(self._h, int(i), _dptr(h), _dptr(u), _dptr(v)))
 
+    def device_state(self, i: int):
+        """Device pointers (eta, u, v) of instance i's current state and the
+        row pitch (elements); valid until the next step or set_state."""
+        ptrs = [ctypes.c_void_p() for _ in range(3)]
+        pitch = ctypes.c_int()
+        self._check(self._lib.maclab_batch_device_state(self._h, int(i), *[ctypes.byref(p) for p in ptrs],
+                                                        ctypes.byref(pitch)))
+        return ptrs[0].value, ptrs[1].value, ptrs[2].value, pitch.value
+
     def info(self):
         c, nodes, tiles, steps = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         self._check(self._lib.maclab_batch_info(self._h, ctypes.byref(c), ctypes.byref(nodes),

@@ -1,4 +1,5 @@
-"""ctypes declarations of include/maclab.h (argument marshalling only)."""
+"""ctypes declarations of include/maclab.h and include/maclab_ws.h
+(argument marshalling only)."""
 from __future__ import annotations
 
 import ctypes
@@ -47,7 +48,14 @@ class Info(ctypes.Structure):
                 ("dirichlet_fused", c_int)]
 
 
-# (name, restype, argtypes) of every exported entry point of include/maclab.h
+class WSConfig(ctypes.Structure):
+    _fields_ = [("res", c_int), ("channels", c_int), ("blocks", c_int), ("dilation", c_int * 64),
+                ("max_batch", c_int), ("seed", ctypes.c_uint64)]
+
+
+c_float = ctypes.c_float
+
+# (name, restype, argtypes) of every exported entry point of include/*.h
 PROTOTYPES = [
     ("maclab_abi_version", c_int, []),
     ("maclab_create", c_int, [P(Grid), P(Params), P(BC), P(c_double), P(ctypes.c_uint8),
@@ -85,9 +93,26 @@ PROTOTYPES = [
     ("maclab_batch_get_state", c_int, [c_void_p, c_int, P(c_double), P(c_double), P(c_double)]),
     ("maclab_batch_set_state", c_int, [c_void_p, c_int, P(c_double), P(c_double), P(c_double)]),
     ("maclab_batch_info", c_int, [c_void_p, P(c_int), P(c_int64), P(c_int64), P(c_int64)]),
+    ("maclab_batch_device_state", c_int, [c_void_p, c_int, P(c_void_p), P(c_void_p), P(c_void_p), P(c_int)]),
     ("maclab_batch_last_error", ctypes.c_char_p, [c_void_p]),
     ("maclab_batch_destroy", None, [c_void_p]),
     ("maclab_destroy", None, [c_void_p]),
+    # learned warm start (maclab_ws.h)
+    ("maclab_ws_create", c_int, [P(WSConfig), c_void_p, P(c_void_p)]),
+    ("maclab_ws_destroy", None, [c_void_p]),
+    ("maclab_ws_param_count", c_int, [c_void_p, P(c_int64)]),
+    ("maclab_ws_get_params", c_int, [c_void_p, P(c_float), c_int64]),
+    ("maclab_ws_set_params", c_int, [c_void_p, P(c_float), c_int64]),
+    ("maclab_ws_forward", c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    ("maclab_ws_gradients", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, P(c_float), c_int64,
+                                    P(c_double)]),
+    ("maclab_ws_train_step", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_float,
+                                     P(c_double)]),
+    ("maclab_ws_encode", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_double, c_double, c_double,
+                                 c_void_p,
+                                 c_void_p, c_void_p, c_int, P(c_double), c_void_p, c_void_p, c_void_p]),
+    ("maclab_ws_decode", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, P(c_double), c_void_p, c_void_p,
+                                 c_void_p]),
 ]
 
 _lock = threading.Lock()

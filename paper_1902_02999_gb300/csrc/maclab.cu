@@ -524,6 +524,14 @@ extern "C" {
 
 int maclab_abi_version(void) { return MACLAB_ABI_VERSION; }
 
+}  // extern "C"
+
+// Thread-local message for maclab_last_error(NULL), set by other
+// translation units of the library.
+void maclab_note_error(const std::string& msg) { g_last_error = msg; }
+
+extern "C" {
+
 const char* maclab_last_error(maclab_t sim)
 {
     if (sim) return sim->err.c_str();
@@ -1646,6 +1654,18 @@ int maclab_batch_get_state(maclab_batch_t b, int i, double* h, double* u, double
                           cudaSuccess)
             return bfail(b, MACLAB_E_CUDA, std::string("batch get_state: ") + cudaGetErrorString(e));
     if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return bfail(b, MACLAB_E_CUDA, std::string("batch get_state: ") + cudaGetErrorString(e));
+    return MACLAB_OK;
+}
+
+int maclab_batch_device_state(maclab_batch_t b, int i, void** eta, void** u, void** v, int* pitch)
+{
+    if (!b || i < 0 || i >= b->count) return bfail(b, MACLAB_E_ARG, "bad instance");
+    const int c = b->cur;
+    const size_t o = b->off[i] * b->esize;
+    if (eta) *eta = (char*)b->eta[c] + o;
+    if (u) *u = (char*)b->u[c] + o;
+    if (v) *v = (char*)b->v[c] + o;
+    if (pitch) *pitch = b->pitch[i];
     return MACLAB_OK;
 }
 

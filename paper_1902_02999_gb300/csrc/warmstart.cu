@@ -1,0 +1,896 @@
+// warmstart.cu -- learned warm start (include/maclab_ws.h): a residual
+// convolutional network on a coarse grid, trained on steady states of the
+// plain iteration, proposing the starting state of a steady-state run.
+//
+// Every convolution is an implicit GEMM on the tensor cores: bfloat16
+// operands staged in shared memory by cp.async, fragments loaded with
+// ldmatrix, mma.sync m16n8k16 with float accumulators.
+//   forward / input gradient: M = pixels of one image row segment (64),
+//     N = output channels, K = 9 taps x input channels;
+//   weight gradient: M = output channels, N = input channels, K = pixels
+//     (split over blocks, float atomics into the gradient).
+#include "maclab.h"
+#include "maclab_ws.h"
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+void maclab_note_error(const std::string& msg);
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+constexpr int IO = MACLAB_WS_IO;
+constexpr int CELL = MACLAB_WS_CELL;
+constexpr int THREADS = 256;
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp16(uint32_t dst, const void* src, bool valid)
+{
+    const int n = valid ? 16 : 0;  // 0: the 16 bytes are filled with zeros
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void ldsm4(uint32_t (&r)[4], uint32_t a)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+__device__ __forceinline__ void ldsm2(uint32_t (&r)[2], uint32_t a)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+__device__ __forceinline__ void ldsm4t(uint32_t (&r)[4], uint32_t a)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+__device__ __forceinline__ void ldsm2t(uint32_t (&r)[2], uint32_t a)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(a));
+}
+// D += A B, A 16 x 16 (row), B 16 x 8 (col), bfloat16 in, float accumulate
+__device__ __forceinline__ void mma(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ uint32_t relu2(uint32_t x)
+{
+    __nv_bfloat162 v;
+    memcpy(&v, &x, 4);
+    v = __hmax2(v, __float2bfloat162_rn(0.f));
+    uint32_t r;
+    memcpy(&r, &v, 4);
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Convolution as implicit GEMM (forward, and input gradient with flipped,
+// transposed weights).  A block computes 64 pixels of one image row
+// (x0 .. x0 + 63 of row y of image b) times NT output channels.
+//   X  [B][R][R][Cin] bf16;  Wk [9][Cout][Cin] bf16 (the B operand, K
+//   contiguous per output channel)
+//   epilogue: v = acc + bias; v = gate > 0 ? v : 0 (gate [B][R][R][Cout]);
+//   v += res; Y (bf16) and / or Yf (float) [B][R][R][Cout]
+struct ConvArgs {
+    const bf16* X;
+    const bf16* Wk;
+    const float* bias;
+    const bf16* gate;
+    const bf16* res;
+    bf16* Y;
+    float* Yf;
+    int R, Cin, Cout, dil, relu_in;
+};
+
+constexpr int CONV_M = 64;
+constexpr int CONV_STAGES = 3;
+
+// 16-byte chunk h (0, 1) of 32-byte row r, swizzled so that ldmatrix rows
+// r .. r + 7 fall in distinct bank groups
+__device__ __forceinline__ int swz32(int r, int h) { return r * 32 + ((h ^ ((r >> 2) & 1)) << 4); }
+
+template <int NT>
+__global__ void __launch_bounds__(THREADS) ws_conv_kernel(const ConvArgs a)
+{
+    constexpr int WN = NT / 2;           // output channels per warp (2 warps along N)
+    constexpr int NJ = WN / 8;           // n8 tiles per warp
+    __shared__ __align__(128) unsigned char sA[CONV_STAGES][CONV_M * 32];
+    __shared__ __align__(128) unsigned char sB[CONV_STAGES][NT * 32];
+    const int R = a.R, Cin = a.Cin, Cout = a.Cout, dil = a.dil;
+    const int segs = R / CONV_M;
+    const int row = blockIdx.x / segs;   // b * R + y
+    const int x0 = (blockIdx.x % segs) * CONV_M;
+    const int b = row / R, y = row % R;
+    const int n0 = blockIdx.y * NT;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 3, wn = warp >> 2;
+    const int kci = Cin / 16;
+    const int KT = 9 * kci;
+
+    auto load = [&](int stage, int kk) {
+        const int tap = kk / kci, ci0 = (kk % kci) * 16;
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        if (tid < CONV_M * 2) {
+            const int m = tid >> 1, h = tid & 1;
+            const int yy = y + dy * dil, xx = x0 + m + dx * dil;
+            const bool ok = yy >= 0 && yy < R && xx >= 0 && xx < R;
+            const bf16* src = ok ? a.X + ((size_t)(b * R + yy) * R + xx) * Cin + ci0 + h * 8 : a.X;
+            cp16(smem_addr(&sA[stage][swz32(m, h)]), src, ok);
+        }
+        for (int i = tid; i < NT * 2; i += THREADS) {
+            const int n = i >> 1, h = i & 1;
+            const bf16* src = a.Wk + ((size_t)tap * Cout + n0 + n) * Cin + ci0 + h * 8;
+            cp16(smem_addr(&sB[stage][swz32(n, h)]), src, true);
+        }
+    };
+
+    float acc[NJ][4];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+
+#pragma unroll
+    for (int s = 0; s < CONV_STAGES - 1; ++s) {
+        if (s < KT) load(s, s);
+        cp_commit();
+    }
+    for (int kk = 0; kk < KT; ++kk) {
+        cp_wait<CONV_STAGES - 2>();
+        __syncthreads();
+        const int pf = kk + CONV_STAGES - 1;
+        if (pf < KT) load(pf % CONV_STAGES, pf);
+        cp_commit();
+        const int st = kk % CONV_STAGES;
+        uint32_t af[4];
+        {
+            const int r = wm * 16 + (lane & 15), h = lane >> 4;
+            ldsm4(af, smem_addr(&sA[st][swz32(r, h)]));
+        }
+        if (a.relu_in) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) af[q] = relu2(af[q]);
+        }
+        if constexpr (NJ >= 2) {
+#pragma unroll
+            for (int j = 0; j < NJ; j += 2) {
+                const int n = wn * WN + j * 8 + (lane & 7) + ((lane >> 4) << 3), h = (lane >> 3) & 1;
+                uint32_t bq[4];
+                ldsm4(bq, smem_addr(&sB[st][swz32(n, h)]));
+                const uint32_t b0[2] = {bq[0], bq[1]}, b1[2] = {bq[2], bq[3]};
+                mma(acc[j], af, b0);
+                mma(acc[j + 1], af, b1);
+            }
+        } else {
+            const int n = wn * WN + (lane & 7), h = (lane >> 3) & 1;
+            uint32_t bq[2];
+            ldsm2(bq, smem_addr(&sB[st][swz32(n, h)]));
+            mma(acc[0], af, bq);
+        }
+    }
+    cp_wait<0>();
+
+    // epilogue: fragment (row g / g + 8, columns 2c, 2c + 1) of each n8 tile
+    const int g = lane >> 2, c = lane & 3;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int n = n0 + wn * WN + j * 8 + 2 * c;
+        const float b0 = a.bias ? a.bias[n] : 0.f, b1 = a.bias ? a.bias[n + 1] : 0.f;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int m = wm * 16 + g + 8 * hh;
+            const size_t o = ((size_t)row * R + x0 + m) * Cout + n;
+            float v0 = acc[j][2 * hh] + b0, v1 = acc[j][2 * hh + 1] + b1;
+            if (a.gate) {
+                const __nv_bfloat162 gt = *reinterpret_cast<const __nv_bfloat162*>(a.gate + o);
+                if (!(__bfloat162float(gt.x) > 0.f)) v0 = 0.f;
+                if (!(__bfloat162float(gt.y) > 0.f)) v1 = 0.f;
+            }
+            if (a.res) {
+                const __nv_bfloat162 rr = *reinterpret_cast<const __nv_bfloat162*>(a.res + o);
+                v0 += __bfloat162float(rr.x);
+                v1 += __bfloat162float(rr.y);
+            }
+            if (a.Y) *reinterpret_cast<__nv_bfloat162*>(a.Y + o) = __floats2bfloat162_rn(v0, v1);
+            if (a.Yf) *reinterpret_cast<float2*>(a.Yf + o) = make_float2(v0, v1);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient: dW[tap][co][ci] += sum_p dY[p][co] * act(X)[p + off(tap)][ci]
+// A block owns one tap, an MT x NT tile of (co, ci) and every split-th
+// chunk of 32 pixels.
+struct WgradArgs {
+    const bf16* dY;   // [B][R][R][Cout]
+    const bf16* X;    // [B][R][R][Cin]
+    float* dW;        // [9][Cout][Cin]
+    int B, R, Cin, Cout, dil, relu_in, splits;
+};
+constexpr int WG_K = 32;  // pixels per stage
+
+// 16-byte chunk h of row r when a row holds `chunks` chunks (2 or 8)
+__device__ __forceinline__ int swz_rows(int r, int h, int chunks)
+{
+    return chunks == 8 ? r * 128 + ((h ^ (r & 7)) << 4) : r * 32 + ((h ^ ((r >> 2) & 1)) << 4);
+}
+
+template <int MT, int NT>
+__global__ void __launch_bounds__(THREADS) ws_wgrad_kernel(const WgradArgs a)
+{
+    constexpr int WMW = MT / 16;         // warps along M
+    constexpr int WNW = 8 / WMW;         // warps along N
+    constexpr int WN = NT / WNW;         // ci per warp
+    constexpr int NJ = WN / 8;
+    constexpr int CA = MT / 8, CB = NT / 8;  // 16-byte chunks per staged row
+    __shared__ __align__(128) unsigned char sA[2][WG_K * MT * 2];
+    __shared__ __align__(128) unsigned char sB[2][WG_K * NT * 2];
+    const int R = a.R, Cin = a.Cin, Cout = a.Cout, dil = a.dil;
+    const int mt = Cout / MT;
+    const int tile = blockIdx.x;
+    const int m0 = (tile % mt) * MT, k0 = (tile / mt) * NT;
+    const int tap = blockIdx.y, split = blockIdx.z;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp % WMW, wn = warp / WMW;
+    const int chunks_total = a.B * R * R / WG_K;
+
+    auto load = [&](int stage, int ch) {
+        const int p0 = ch * WG_K;            // first pixel (b, y, x0)
+        const int rowi = p0 / R, x0 = p0 % R;
+        const int b = rowi / R, y = rowi % R;
+        for (int i = tid; i < WG_K * CA; i += THREADS) {
+            const int r = i / CA, h = i % CA;
+            const bf16* src = a.dY + (size_t)(p0 + r) * Cout + m0 + h * 8;
+            cp16(smem_addr(&sA[stage][swz_rows(r, h, CA)]), src, true);
+        }
+        const int yy = y + dy * dil;
+        for (int i = tid; i < WG_K * CB; i += THREADS) {
+            const int r = i / CB, h = i % CB;
+            const int xx = x0 + r + dx * dil;
+            const bool ok = yy >= 0 && yy < R && xx >= 0 && xx < R;
+            const bf16* src = ok ? a.X + ((size_t)(b * R + yy) * R + xx) * Cin + k0 + h * 8 : a.X;
+            cp16(smem_addr(&sB[stage][swz_rows(r, h, CB)]), src, ok);
+        }
+    };
+
+    float acc[NJ][4];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+
+    int ch = split;
+    if (ch < chunks_total) load(0, ch);
+    cp_commit();
+    int st = 0;
+    for (; ch < chunks_total; ch += a.splits) {
+        const int nx = ch + a.splits;
+        if (nx < chunks_total) load(st ^ 1, nx);
+        cp_commit();
+        cp_wait<1>();
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < WG_K / 16; ++ks) {
+            uint32_t af[4];
+            {
+                // A = dY^T: rows co, columns pixels; staged [pixel][co]
+                const int r = ks * 16 + (lane & 7) + ((lane >> 4) << 3);
+                const int h = (wm * 16 + ((lane >> 3) & 1) * 8) / 8;
+                ldsm4t(af, smem_addr(&sA[st][swz_rows(r, h, CA)]));
+            }
+            if constexpr (NJ >= 2) {
+#pragma unroll
+                for (int j = 0; j < NJ; j += 2) {
+                    const int r = ks * 16 + (lane & 7) + (((lane >> 3) & 1) << 3);
+                    const int h = (wn * WN + j * 8 + ((lane >> 4) << 3)) / 8;
+                    uint32_t bq[4];
+                    ldsm4t(bq, smem_addr(&sB[st][swz_rows(r, h, CB)]));
+                    if (a.relu_in) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) bq[q] = relu2(bq[q]);
+                    }
+                    const uint32_t b0[2] = {bq[0], bq[1]}, b1[2] = {bq[2], bq[3]};
+                    mma(acc[j], af, b0);
+                    mma(acc[j + 1], af, b1);
+                }
+            } else {
+                const int r = ks * 16 + (lane & 7) + (((lane >> 3) & 1) << 3);
+                const int h = (wn * WN) / 8;
+                uint32_t bq[2];
+                ldsm2t(bq, smem_addr(&sB[st][swz_rows(r, h, CB)]));
+                if (a.relu_in) {
+                    bq[0] = relu2(bq[0]);
+                    bq[1] = relu2(bq[1]);
+                }
+                mma(acc[0], af, bq);
+            }
+        }
+        __syncthreads();  // stage st is free before the next load into it
+        st ^= 1;
+    }
+    cp_wait<0>();
+    const int g = lane >> 2, c = lane & 3;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int n = k0 + wn * WN + j * 8 + 2 * c;
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int m = m0 + wm * 16 + g + 8 * hh;
+            float* d = a.dW + ((size_t)tap * Cout + m) * Cin + n;
+            atomicAdd(d, acc[j][2 * hh]);
+            atomicAdd(d + 1, acc[j][2 * hh + 1]);
+        }
+    }
+}
+
+// db[c] += sum_p dY[p][c]
+__global__ void __launch_bounds__(THREADS) ws_bias_grad_kernel(const bf16* dY, int P, int C, float* db)
+{
+    __shared__ float part[THREADS];
+    const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int lanes = THREADS / 32;
+    float s = 0.f;
+    if (c < C)
+        for (int p = blockIdx.y * lanes + (threadIdx.x >> 5); p < P; p += gridDim.y * lanes)
+            s += __bfloat162float(dY[(size_t)p * C + c]);
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < 32 && c < C) {
+        float t = 0.f;
+        for (int k = 0; k < lanes; ++k) t += part[k * 32 + threadIdx.x];
+        atomicAdd(db + c, t);
+    }
+}
+
+// loss = sum_p w_p sum_{c < oc} (Y - T)^2 (block partials in double);
+// dY = 2 w (Y - T) for c < oc, 0 otherwise
+__global__ void __launch_bounds__(THREADS) ws_loss_kernel(const float* Y, const float* T, const float* W, int P,
+                                                          int oc, bf16* dY, double* loss)
+{
+    __shared__ double part[THREADS];
+    double s = 0.0;
+    for (int i = blockIdx.x * THREADS + threadIdx.x; i < P * IO; i += gridDim.x * THREADS) {
+        const int p = i / IO, c = i % IO;
+        float g = 0.f;
+        if (c < oc) {
+            const float d = Y[i] - T[i];
+            s += (double)W[p] * d * d;
+            g = 2.f * W[p] * d;
+        }
+        dY[i] = __float2bfloat16_rn(g);
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = THREADS / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) part[threadIdx.x] += part[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, part[0]);
+}
+
+// float -> bf16
+__global__ void ws_to_bf16_kernel(const float* x, bf16* y, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = __float2bfloat16_rn(x[i]);
+}
+
+// Adam on the flat parameter vector; lr_t carries the bias corrections
+__global__ void ws_adam_kernel(float* p, const float* g, float* m, float* v, size_t n, float lr_t, float b1,
+                               float b2, float eps)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr_t * mi / (sqrtf(vi) + eps);
+    }
+}
+
+// bf16 copies of one layer's weights: forward layout [9][co][ci] and the
+// input-gradient layout Wb[t][ci][co] = W[8 - t][co][ci]
+__global__ void ws_pack_kernel(const float* W, int Cout, int Cin, bf16* Wf, bf16* Wb)
+{
+    const size_t n = (size_t)9 * Cout * Cin;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int ci = (int)(i % Cin);
+        const int co = (int)((i / Cin) % Cout);
+        const int t = (int)(i / ((size_t)Cin * Cout));
+        const bf16 w = __float2bfloat16_rn(W[i]);
+        Wf[i] = w;
+        Wb[((size_t)(8 - t) * Cin + ci) * Cout + co] = w;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fine grid <-> coarse grid
+__global__ void ws_encode_kernel(int n, int R, const float* D, const uint8_t* mask, float wu, float wv, float cb,
+                                 float dx, const float* eta, const float* u, const float* v, int pitch, float s0, float s1,
+                                 float s2, float s3, float* X, float* T, float* Wt)
+{
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= R * R) return;
+    const int I = cell % R, J = cell / R;
+    float cnt = 0.f, sd = 0.f, se = 0.f, su = 0.f, sv = 0.f;
+    for (int j = J * CELL; j < J * CELL + CELL; ++j)
+        for (int i = I * CELL; i < I * CELL + CELL; ++i) {
+            const size_t k = (size_t)j * n + i;
+            if (mask[k] == MACLAB_SOLID) continue;
+            cnt += 1.f;
+            sd += D[k];
+            if (eta) {
+                const size_t q = (size_t)j * pitch + i;
+                se += eta[q];
+                su += u[q];
+                sv += v[q];
+            }
+        }
+    const float inv = cnt > 0.f ? 1.f / cnt : 0.f;
+    float* x = X + (size_t)cell * IO;
+    x[0] = cnt / (CELL * CELL);
+    x[1] = sd * inv / s0;
+    x[2] = wu / 5.f;
+    x[3] = wv / 5.f;
+    x[4] = 100.f * cb;
+    x[5] = 2.f * (I + 0.5f) / R - 1.f;
+    x[6] = 2.f * (J + 0.5f) / R - 1.f;
+    x[7] = 0.5f * dx;
+    for (int c = 8; c < IO; ++c) x[c] = 0.f;
+    if (T) {
+        float* t = T + (size_t)cell * IO;
+        t[0] = se * inv / s1;
+        t[1] = su * inv / s2;
+        t[2] = sv * inv / s3;
+        for (int c = 3; c < IO; ++c) t[c] = 0.f;
+        Wt[cell] = cnt / (CELL * CELL);
+    }
+}
+
+__global__ void ws_decode_kernel(int n, int R, const float* Y, const float* D, const uint8_t* mask, double s1,
+                                 double s2, double s3, double* h, double* u, double* v)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n * n) return;
+    const int i = k % n, j = k / n;
+    const uint8_t t = mask[k];
+    if (t == MACLAB_SOLID) {
+        h[k] = D[k];
+        u[k] = 0.0;
+        v[k] = 0.0;
+        return;
+    }
+    // coarse coordinates of the node (cell centres at integers), clamped
+    const float fx = fminf(fmaxf((i + 0.5f) / CELL - 0.5f, 0.f), R - 1.f);
+    const float fy = fminf(fmaxf((j + 0.5f) / CELL - 0.5f, 0.f), R - 1.f);
+    const int x0 = min((int)fx, R - 2), y0 = min((int)fy, R - 2);
+    const int x1 = x0 + 1, y1 = y0 + 1;
+    const float ax = fx - x0, ay = fy - y0;
+    float out[3];
+    for (int c = 0; c < 3; ++c) {
+        const float a00 = Y[((size_t)y0 * R + x0) * IO + c], a10 = Y[((size_t)y0 * R + x1) * IO + c];
+        const float a01 = Y[((size_t)y1 * R + x0) * IO + c], a11 = Y[((size_t)y1 * R + x1) * IO + c];
+        out[c] = (1.f - ay) * ((1.f - ax) * a00 + ax * a10) + ay * ((1.f - ax) * a01 + ax * a11);
+    }
+    h[k] = (double)D[k] + out[0] * s1;
+    const bool still = t == MACLAB_NOSLIP;
+    u[k] = still ? 0.0 : out[1] * s2;
+    v[k] = still ? 0.0 : out[2] * s3;
+}
+
+int grid_for(size_t n, int cap = 4096) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, cap)); }
+
+uint64_t splitmix(uint64_t& s)
+{
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+
+// ===========================================================================
+struct maclab_ws_s {
+    maclab_ws_config cfg{};
+    cudaStream_t stream = nullptr;
+    struct Layer {
+        int cin, cout, dil, relu_in;
+        int64_t w_off, b_off;   // offsets into the parameter vector
+        bf16* Wf = nullptr;     // [9][cout][cin]
+        bf16* Wb = nullptr;     // [9][cin][cout], flipped
+    };
+    std::vector<Layer> layers;  // lift, blocks, head
+    int64_t nparam = 0;
+    float* param = nullptr;     // master weights
+    float* grad = nullptr;
+    float* m1 = nullptr;
+    float* m2 = nullptr;
+    int64_t step = 0;
+    bf16* X = nullptr;          // [B][R][R][16]
+    std::vector<bf16*> H;       // H_1 .. H_{L+1}, [B][R][R][C]
+    bf16* G[2] = {nullptr, nullptr};  // gradient ping-pong [B][R][R][C]
+    bf16* dY = nullptr;         // [B][R][R][16]
+    float* Yf = nullptr;        // [B][R][R][16]
+    double* loss = nullptr;
+    std::vector<void*> bufs;
+    std::string err;
+};
+
+namespace {
+
+int wfail(maclab_ws_t w, int code, const std::string& msg)
+{
+    if (w) w->err = msg;
+    maclab_note_error(msg);
+    return code;
+}
+
+template <typename T>
+bool walloc(maclab_ws_t w, T** p, size_t count)
+{
+    void* q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(count * sizeof(T), 256)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    w->bufs.push_back(q);
+    *p = (T*)q;
+    return true;
+}
+
+void launch_conv(maclab_ws_t w, const ConvArgs& a, int batch)
+{
+    const int segs = a.R / CONV_M;
+    if (a.Cout % 128 == 0) {
+        dim3 grid(batch * a.R * segs, a.Cout / 128);
+        ws_conv_kernel<128><<<grid, THREADS, 0, w->stream>>>(a);
+    } else {
+        dim3 grid(batch * a.R * segs, a.Cout / 16);
+        ws_conv_kernel<16><<<grid, THREADS, 0, w->stream>>>(a);
+    }
+}
+
+void launch_wgrad(maclab_ws_t w, const WgradArgs& a0)
+{
+    WgradArgs a = a0;
+    const int chunks = a.B * a.R * a.R / WG_K;
+    const int MT = a.Cout % 64 == 0 ? 64 : 16, NT = a.Cin % 64 == 0 ? 64 : 16;
+    const int tiles = (a.Cout / MT) * (a.Cin / NT);
+    // about two blocks per SM over all (tile, tap, split) blocks
+    a.splits = std::max(1, std::min(chunks, 304 / std::max(1, tiles * 9) + 1));
+    dim3 grid(tiles, 9, a.splits);
+    if (MT == 64 && NT == 64) ws_wgrad_kernel<64, 64><<<grid, THREADS, 0, w->stream>>>(a);
+    else if (MT == 64) ws_wgrad_kernel<64, 16><<<grid, THREADS, 0, w->stream>>>(a);
+    else ws_wgrad_kernel<16, 64><<<grid, THREADS, 0, w->stream>>>(a);
+}
+
+void pack_all(maclab_ws_t w)
+{
+    for (auto& L : w->layers)
+        ws_pack_kernel<<<grid_for((size_t)9 * L.cout * L.cin), 256, 0, w->stream>>>(w->param + L.w_off, L.cout, L.cin,
+                                                                                 L.Wf, L.Wb);
+}
+
+// forward of `batch` samples from w->X; head output to w->Yf
+void forward(maclab_ws_t w, int batch)
+{
+    const int R = w->cfg.res;
+    const int nl = (int)w->layers.size();
+    const bf16* in = w->X;
+    for (int l = 0; l < nl; ++l) {
+        const auto& L = w->layers[l];
+        ConvArgs a{};
+        a.X = in;
+        a.Wk = L.Wf;
+        a.bias = w->param + L.b_off;
+        a.R = R;
+        a.Cin = L.cin;
+        a.Cout = L.cout;
+        a.dil = L.dil;
+        a.relu_in = L.relu_in;
+        if (l == nl - 1) {
+            a.Yf = w->Yf;
+        } else {
+            a.Y = w->H[l];
+            if (l > 0) a.res = w->H[l - 1];  // residual block
+        }
+        launch_conv(w, a, batch);
+        if (l < nl - 1) in = w->H[l];
+    }
+}
+
+// gradients of the loss into w->grad (zeroed first); dY from the loss kernel
+void backward(maclab_ws_t w, int batch)
+{
+    const int R = w->cfg.res;
+    const int nl = (int)w->layers.size();
+    const int P = batch * R * R;
+    cudaMemsetAsync(w->grad, 0, (size_t)w->nparam * sizeof(float), w->stream);
+    const bf16* gout = w->dY;  // gradient w.r.t. the output of layer l
+    int ping = 0;
+    for (int l = nl - 1; l >= 0; --l) {
+        const auto& L = w->layers[l];
+        const bf16* xin = l == 0 ? w->X : w->H[l - 1];
+        WgradArgs g{};
+        g.dY = gout;
+        g.X = xin;
+        g.dW = w->grad + L.w_off;
+        g.B = batch;
+        g.R = R;
+        g.Cin = L.cin;
+        g.Cout = L.cout;
+        g.dil = L.dil;
+        g.relu_in = L.relu_in;
+        launch_wgrad(w, g);
+        dim3 bg((L.cout + 31) / 32, 64);
+        ws_bias_grad_kernel<<<bg, THREADS, 0, w->stream>>>(gout, P, L.cout, w->grad + L.b_off);
+        if (l == 0) break;
+        // gradient w.r.t. this layer's input H_{l-1}:
+        //   head:  relu'(H) * conv^T(gout)
+        //   block: gout + relu'(H) * conv^T(gout)
+        ConvArgs a{};
+        a.X = gout;
+        a.Wk = L.Wb;
+        a.R = R;
+        a.Cin = L.cout;
+        a.Cout = L.cin;
+        a.dil = L.dil;
+        a.relu_in = 0;
+        a.gate = w->H[l - 1];
+        a.res = l < nl - 1 ? gout : nullptr;
+        a.Y = w->G[ping];
+        launch_conv(w, a, batch);
+        gout = w->G[ping];
+        ping ^= 1;
+    }
+}
+
+int check_batch(maclab_ws_t w, int batch)
+{
+    if (!w) return wfail(nullptr, MACLAB_E_ARG, "NULL warm-start handle");
+    if (batch < 1 || batch > w->cfg.max_batch) return wfail(w, MACLAB_E_ARG, "batch must be 1..max_batch");
+    return MACLAB_OK;
+}
+
+int loss_and_grad(maclab_ws_t w, int batch, int oc, const float* x, const float* t, const float* wt)
+{
+    const int R = w->cfg.res;
+    const size_t P = (size_t)batch * R * R;
+    ws_to_bf16_kernel<<<grid_for(P * IO), 256, 0, w->stream>>>(x, w->X, P * IO);
+    forward(w, batch);
+    cudaMemsetAsync(w->loss, 0, sizeof(double), w->stream);
+    ws_loss_kernel<<<grid_for(P * IO, 1024), THREADS, 0, w->stream>>>(w->Yf, t, wt, (int)P, oc, w->dY, w->loss);
+    backward(w, batch);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("warm-start launch: ") + cudaGetErrorString(e));
+    return MACLAB_OK;
+}
+
+int read_loss(maclab_ws_t w, double* loss)
+{
+    if (!loss) return MACLAB_OK;
+    cudaError_t e = cudaMemcpyAsync(loss, w->loss, sizeof(double), cudaMemcpyDeviceToHost, w->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
+    if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("warm-start loss: ") + cudaGetErrorString(e));
+    return MACLAB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int maclab_ws_create(const maclab_ws_config* cfg, void* stream, maclab_ws_t* out)
+{
+    if (!cfg || !out) return wfail(nullptr, MACLAB_E_ARG, "NULL argument");
+    *out = nullptr;
+    if (cfg->res < 64 || cfg->res % 64 || cfg->channels < 64 || cfg->channels % 64 || cfg->blocks < 0 ||
+        cfg->blocks > 64 || cfg->max_batch < 1)
+        return wfail(nullptr, MACLAB_E_ARG, "need res and channels multiples of 64, 0 <= blocks <= 64, max_batch >= 1");
+    for (int l = 0; l < cfg->blocks; ++l)
+        if (cfg->dilation[l] < 1 || cfg->dilation[l] >= cfg->res)
+            return wfail(nullptr, MACLAB_E_ARG, "dilations must be in 1..res-1");
+    maclab_ws_t w = new maclab_ws_s;
+    w->cfg = *cfg;
+    w->stream = (cudaStream_t)stream;
+    const int C = cfg->channels, R = cfg->res;
+    auto add = [&](int cin, int cout, int dil, int relu) {
+        maclab_ws_s::Layer L;
+        L.cin = cin;
+        L.cout = cout;
+        L.dil = dil;
+        L.relu_in = relu;
+        L.w_off = w->nparam;
+        w->nparam += (int64_t)9 * cin * cout;
+        L.b_off = w->nparam;
+        w->nparam += cout;
+        w->layers.push_back(L);
+    };
+    add(IO, C, 1, 0);
+    for (int l = 0; l < cfg->blocks; ++l) add(C, C, cfg->dilation[l], 1);
+    add(C, IO, 1, 1);
+    const size_t P = (size_t)cfg->max_batch * R * R;
+    bool ok = walloc(w, &w->param, w->nparam) && walloc(w, &w->grad, w->nparam) && walloc(w, &w->m1, w->nparam) &&
+              walloc(w, &w->m2, w->nparam) && walloc(w, &w->X, P * IO) && walloc(w, &w->dY, P * IO) &&
+              walloc(w, &w->Yf, P * IO) && walloc(w, &w->loss, 1) && walloc(w, &w->G[0], P * C) &&
+              walloc(w, &w->G[1], P * C);
+    w->H.assign(w->layers.size() - 1, nullptr);
+    for (size_t l = 0; ok && l < w->H.size(); ++l) ok = walloc(w, &w->H[l], P * C);
+    for (auto& L : w->layers) {
+        if (!ok) break;
+        ok = walloc(w, &L.Wf, (size_t)9 * L.cin * L.cout) && walloc(w, &L.Wb, (size_t)9 * L.cin * L.cout);
+    }
+    if (!ok) {
+        maclab_ws_destroy(w);
+        return wfail(nullptr, MACLAB_E_NOMEM, "warm-start device allocation failed");
+    }
+    // initial weights: normal(0, sqrt(2 / fan_in)) by Box-Muller on SplitMix64;
+    // the residual branches start small and the head at zero
+    std::vector<float> h(w->nparam, 0.f);
+    uint64_t s = cfg->seed;
+    for (size_t li = 0; li < w->layers.size(); ++li) {
+        const auto& L = w->layers[li];
+        const bool head = li + 1 == w->layers.size();
+        const double sd = head ? 0.0 : std::sqrt(2.0 / (9.0 * L.cin)) * (li == 0 ? 1.0 : 0.2);
+        for (int64_t k = 0; k < (int64_t)9 * L.cin * L.cout; ++k) {
+            const double u1 = ((splitmix(s) >> 11) + 1) * (1.0 / 9007199254740993.0);
+            const double u2 = (splitmix(s) >> 11) * (1.0 / 9007199254740992.0);
+            h[L.w_off + k] = (float)(sd * std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2));
+        }
+    }
+    cudaError_t e = cudaMemcpyAsync(w->param, h.data(), h.size() * 4, cudaMemcpyHostToDevice, w->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w->m1, 0, (size_t)w->nparam * 4, w->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w->m2, 0, (size_t)w->nparam * 4, w->stream);
+    if (e == cudaSuccess) {
+        pack_all(w);
+        e = cudaStreamSynchronize(w->stream);
+    }
+    if (e != cudaSuccess) {
+        maclab_ws_destroy(w);
+        return wfail(nullptr, MACLAB_E_CUDA, std::string("warm-start init: ") + cudaGetErrorString(e));
+    }
+    *out = w;
+    return MACLAB_OK;
+}
+
+void maclab_ws_destroy(maclab_ws_t w)
+{
+    if (!w) return;
+    cudaStreamSynchronize(w->stream);
+    for (void* p : w->bufs) cudaFree(p);
+    delete w;
+}
+
+int maclab_ws_param_count(maclab_ws_t w, int64_t* n)
+{
+    if (!w || !n) return wfail(w, MACLAB_E_ARG, "NULL argument");
+    *n = w->nparam;
+    return MACLAB_OK;
+}
+
+int maclab_ws_get_params(maclab_ws_t w, float* host, int64_t n)
+{
+    if (!w || !host || n != w->nparam) return wfail(w, MACLAB_E_ARG, "need the handle's parameter count");
+    cudaError_t e = cudaMemcpyAsync(host, w->param, n * 4, cudaMemcpyDeviceToHost, w->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
+    if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("get_params: ") + cudaGetErrorString(e));
+    return MACLAB_OK;
+}
+
+int maclab_ws_set_params(maclab_ws_t w, const float* host, int64_t n)
+{
+    if (!w || !host || n != w->nparam) return wfail(w, MACLAB_E_ARG, "need the handle's parameter count");
+    cudaError_t e = cudaMemcpyAsync(w->param, host, n * 4, cudaMemcpyHostToDevice, w->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w->m1, 0, (size_t)n * 4, w->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w->m2, 0, (size_t)n * 4, w->stream);
+    if (e == cudaSuccess) {
+        pack_all(w);
+        e = cudaStreamSynchronize(w->stream);
+    }
+    if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("set_params: ") + cudaGetErrorString(e));
+    w->step = 0;
+    return MACLAB_OK;
+}
+
+int maclab_ws_forward(maclab_ws_t w, int batch, const float* x, float* y)
+{
+    int rc = check_batch(w, batch);
+    if (rc != MACLAB_OK) return rc;
+    if (!x || !y) return wfail(w, MACLAB_E_ARG, "NULL tensor");
+    const int R = w->cfg.res;
+    const size_t P = (size_t)batch * R * R;
+    ws_to_bf16_kernel<<<grid_for(P * IO), 256, 0, w->stream>>>(x, w->X, P * IO);
+    forward(w, batch);
+    cudaError_t e = cudaMemcpyAsync(y, w->Yf, P * IO * 4, cudaMemcpyDeviceToDevice, w->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("warm-start forward: ") + cudaGetErrorString(e));
+    return MACLAB_OK;
+}
+
+int maclab_ws_gradients(maclab_ws_t w, int batch, int oc, const float* x, const float* t, const float* wt,
+                        float* grad_host, int64_t n, double* loss)
+{
+    int rc = check_batch(w, batch);
+    if (rc != MACLAB_OK) return rc;
+    if (!x || !t || !wt || !grad_host || n != w->nparam || oc < 1 || oc > IO)
+        return wfail(w, MACLAB_E_ARG, "NULL tensor, wrong parameter count or out_ch");
+    if ((rc = loss_and_grad(w, batch, oc, x, t, wt)) != MACLAB_OK) return rc;
+    cudaError_t e = cudaMemcpyAsync(grad_host, w->grad, n * 4, cudaMemcpyDeviceToHost, w->stream);
+    if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("gradients: ") + cudaGetErrorString(e));
+    if (loss) return read_loss(w, loss);
+    e = cudaStreamSynchronize(w->stream);
+    if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("gradients: ") + cudaGetErrorString(e));
+    return MACLAB_OK;
+}
+
+int maclab_ws_train_step(maclab_ws_t w, int batch, int oc, const float* x, const float* t, const float* wt, float lr,
+                         double* loss)
+{
+    int rc = check_batch(w, batch);
+    if (rc != MACLAB_OK) return rc;
+    if (!x || !t || !wt || oc < 1 || oc > IO || !(lr >= 0.f)) return wfail(w, MACLAB_E_ARG, "bad train_step argument");
+    if ((rc = loss_and_grad(w, batch, oc, x, t, wt)) != MACLAB_OK) return rc;
+    w->step += 1;
+    const double b1 = 0.9, b2 = 0.999;
+    const double lr_t = lr * std::sqrt(1.0 - std::pow(b2, (double)w->step)) / (1.0 - std::pow(b1, (double)w->step));
+    ws_adam_kernel<<<grid_for((size_t)w->nparam), 256, 0, w->stream>>>(w->param, w->grad, w->m1, w->m2,
+                                                                      (size_t)w->nparam, (float)lr_t, (float)b1,
+                                                                      (float)b2, 1e-8f);
+    pack_all(w);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("train_step: ") + cudaGetErrorString(e));
+    return read_loss(w, loss);
+}
+
+int maclab_ws_encode(maclab_ws_t w, int n, const float* D, const uint8_t* mask, double wind_u, double wind_v,
+                     double Cb, double dx, const float* eta, const float* u, const float* v, int pitch, const double scale[4],
+                     float* x, float* t, float* wt)
+{
+    if (!w || !D || !mask || !scale || !x) return wfail(w, MACLAB_E_ARG, "NULL argument");
+    if (!(dx > 0)) return wfail(w, MACLAB_E_ARG, "dx must be positive");
+    const int R = w->cfg.res;
+    if (n != R * CELL) return wfail(w, MACLAB_E_ARG, "fine grid must be res * MACLAB_WS_CELL per side");
+    if (eta && (!u || !v || !t || !wt || pitch < n)) return wfail(w, MACLAB_E_ARG, "state needs u, v, targets, pitch");
+    for (int k = 0; k < 4; ++k)
+        if (!(scale[k] > 0)) return wfail(w, MACLAB_E_ARG, "scales must be positive");
+    ws_encode_kernel<<<(R * R + 255) / 256, 256, 0, w->stream>>>(n, R, D, mask, (float)wind_u, (float)wind_v,
+                                                                 (float)Cb, (float)dx, eta, u, v, pitch, (float)scale[0],
+                                                                 (float)scale[1], (float)scale[2], (float)scale[3], x,
+                                                                 eta ? t : nullptr, wt);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("encode: ") + cudaGetErrorString(e));
+    return MACLAB_OK;
+}
+
+int maclab_ws_decode(maclab_ws_t w, int n, const float* y, const float* D, const uint8_t* mask, const double scale[4],
+                     double* h, double* u, double* v)
+{
+    if (!w || !y || !D || !mask || !scale || !h || !u || !v) return wfail(w, MACLAB_E_ARG, "NULL argument");
+    const int R = w->cfg.res;
+    if (n != R * CELL) return wfail(w, MACLAB_E_ARG, "fine grid must be res * MACLAB_WS_CELL per side");
+    ws_decode_kernel<<<(n * n + 255) / 256, 256, 0, w->stream>>>(n, R, y, D, mask, scale[1], scale[2], scale[3], h,
+                                                                 u, v);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("decode: ") + cudaGetErrorString(e));
+    return MACLAB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,318 @@
+"""Learned warm start for steady-state runs (include/maclab_ws.h).
+
+A residual convolutional network proposes the starting state of a steady
+run; the plain MacLABSWE iteration then converges from it and decides the
+answer.  The network runs on a coarse grid (4 x 4 fine nodes per cell) and
+is trained on steady states that the library's own batch solver produces.
+
+Binding only: the network, its training step, the coarse encoding and the
+fine decoding run in the library's kernels (warmstart.cu); torch provides
+device memory.
+
+    python -m paper_1902_02999_gb300.warmstart --train 1024 --test 32
+
+trains on seeded dish lakes and reports steps and wall time to residual
+1e-8 from rest and from the proposal.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import time
+
+import numpy as np
+
+from . import Batch, MaclabError, _abi, lib
+
+IO = 16
+CELL = 4
+# dilations of the residual blocks: receptive field wider than the 64 x 64 grid
+DEFAULT_DILATIONS = (1, 2, 4, 8, 16, 32, 1, 2, 4, 8, 16, 1)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class WarmStartNet:
+    """One network handle (maclab_ws_t) with its own weights and buffers."""
+
+    def __init__(self, res: int = 64, channels: int = 128, dilations=DEFAULT_DILATIONS, max_batch: int = 32,
+                 seed: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the warm start needs a CUDA GPU; no CPU fallback exists")
+        self._lib = lib()
+        self.res, self.channels, self.dilations = res, channels, tuple(dilations)
+        self.max_batch = max_batch
+        cfg = _abi.WSConfig()
+        cfg.res, cfg.channels, cfg.blocks, cfg.max_batch, cfg.seed = res, channels, len(dilations), max_batch, seed
+        for k, d in enumerate(dilations):
+            cfg.dilation[k] = int(d)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        rc = self._lib.maclab_ws_create(ctypes.byref(cfg), ctypes.c_void_p(int(stream.cuda_stream)), ctypes.byref(h))
+        if rc != 0:
+            raise MaclabError(rc, self._lib.maclab_last_error(None).decode())
+        self._h = h
+        n = ctypes.c_int64()
+        self._check(self._lib.maclab_ws_param_count(self._h, ctypes.byref(n)))
+        self.nparam = n.value
+
+    def _check(self, rc):
+        if rc != 0:
+            raise MaclabError(rc, self._lib.maclab_last_error(None).decode())
+
+    # ---- parameters
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.nparam, dtype=np.float32)
+        self._check(self._lib.maclab_ws_get_params(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                   self.nparam))
+        return out
+
+    def set_params(self, theta) -> None:
+        t = np.ascontiguousarray(np.asarray(theta, dtype=np.float32))
+        assert t.size == self.nparam
+        self._check(self._lib.maclab_ws_set_params(self._h, t.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                   self.nparam))
+
+    # ---- network
+    def forward(self, x):
+        import torch
+        y = torch.empty_like(x)
+        self._check(self._lib.maclab_ws_forward(self._h, x.shape[0], _ptr(x), _ptr(y)))
+        return y
+
+    def gradients(self, x, t, w, out_ch: int = 3):
+        g = np.empty(self.nparam, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(self._lib.maclab_ws_gradients(self._h, x.shape[0], out_ch, _ptr(x), _ptr(t), _ptr(w),
+                                                  g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), self.nparam,
+                                                  ctypes.byref(loss)))
+        return loss.value, g
+
+    def train_step(self, x, t, w, lr: float, out_ch: int = 3, want_loss: bool = True):
+        loss = ctypes.c_double()
+        self._check(self._lib.maclab_ws_train_step(self._h, x.shape[0], out_ch, _ptr(x), _ptr(t), _ptr(w),
+                                                   float(lr), ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    # ---- fine <-> coarse
+    def encode(self, D, mask, case, scale, state=None):
+        """Coarse input x [R][R][16] (and, with state = (eta, u, v, pitch)
+        device pointers, targets t [R][R][16] and weights w [R][R])."""
+        import torch
+        R = self.res
+        dev = D.device
+        x = torch.empty((R, R, IO), dtype=torch.float32, device=dev)
+        t = w = None
+        sc = (ctypes.c_double * 4)(*scale)
+        if state is not None:
+            t = torch.empty((R, R, IO), dtype=torch.float32, device=dev)
+            w = torch.empty((R, R), dtype=torch.float32, device=dev)
+            eta, u, v, pitch = state
+        else:
+            eta = u = v = None
+            pitch = 0
+        self._check(self._lib.maclab_ws_encode(
+            self._h, R * CELL, _ptr(D), _ptr(mask), float(case.wind_u), float(case.wind_v), float(case.cb),
+            float(case.dx), ctypes.c_void_p(eta), ctypes.c_void_p(u), ctypes.c_void_p(v), int(pitch), sc,
+            _ptr(x), _ptr(t) if t is not None else None, _ptr(w) if w is not None else None))
+        return x, t, w
+
+    def decode(self, y, D, mask, scale):
+        """Fine proposal (h, u, v) as float64 device tensors [n][n]."""
+        import torch
+        n = self.res * CELL
+        h, u, v = (torch.empty((n, n), dtype=torch.float64, device=D.device) for _ in range(3))
+        sc = (ctypes.c_double * 4)(*scale)
+        self._check(self._lib.maclab_ws_decode(self._h, n, _ptr(y), _ptr(D), _ptr(mask), sc, _ptr(h), _ptr(u),
+                                               _ptr(v)))
+        return h, u, v
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.maclab_ws_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+def lake_fields(case, device):
+    """Still-water depth D = h_ref - z_b (float32) and the mask on the device."""
+    import torch
+    D = torch.tensor(np.asarray(case.h_ref - case.zb, dtype=np.float32), device=device)
+    M = torch.tensor(np.asarray(case.mask, dtype=np.uint8), device=device)
+    return D, M
+
+
+def steady_batch(cases, tol=1e-8, max_steps=200000, check_every=1000):
+    """Plain iteration of every case to residual tol in one batch; returns
+    the batch (kept alive for its device states) and steps / seconds."""
+    b = Batch(cases, precision="f32")
+    steps, r, sec = b.run_to_steady(tol=tol, max_steps=max_steps, check_every=check_every)
+    return b, steps, r, sec
+
+
+def make_dataset(net, cases, tol=1e-7, max_steps=120000, chunk=1024, scale=None):
+    """Steady states of `cases` (plain iteration, FP32) encoded for training:
+    X, T [N][R][R][16], W [N][R][R] on the device, the scales used and the
+    per-case steps.  Targets are taken at residual `tol` (or max_steps)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    R = net.res
+    N = len(cases)
+    X = torch.empty((N, R, R, IO), dtype=torch.float32, device=dev)
+    T = torch.empty_like(X)
+    W = torch.empty((N, R, R), dtype=torch.float32, device=dev)
+    raw = scale is None
+    sc = (1.0, 1.0, 1.0, 1.0) if raw else scale
+    all_steps = np.zeros(N, dtype=np.int64)
+    for c0 in range(0, N, chunk):
+        part = cases[c0:c0 + chunk]
+        b, steps, _, _ = steady_batch(part, tol=tol, max_steps=max_steps)
+        all_steps[c0:c0 + len(part)] = steps
+        for k, case in enumerate(part):
+            D, M = lake_fields(case, dev)
+            x, t, w = net.encode(D, M, case, sc, state=b.device_state(k))
+            X[c0 + k], T[c0 + k], W[c0 + k] = x, t, w
+        torch.cuda.synchronize()
+        b.close()
+    if raw:
+        # divisors that make the target channels O(1) and the depth channel O(1)
+        live = W > 0
+        s_eta = float(T[..., 0][live].std().item()) or 1.0
+        s_u = float(torch.sqrt((T[..., 1][live] ** 2 + T[..., 2][live] ** 2).mean()).item()) or 1.0
+        dmax = float(max(np.max(c.h_ref - c.zb) for c in cases))
+        sc = (dmax, s_eta, s_u, s_u)
+        X[..., 1] /= sc[0]
+        T[..., 0] /= sc[1]
+        T[..., 1] /= sc[2]
+        T[..., 2] /= sc[3]
+    return X, T, W, sc, all_steps
+
+
+def train(net, X, T, W, epochs=30, batch=16, lr=1e-3, seed=0, log=None):
+    """Adam over shuffled mini-batches with a cosine learning rate; the
+    sample weights are normalised to sum to one per batch."""
+    import torch
+    N = X.shape[0]
+    rng = np.random.default_rng(seed)
+    steps_total = epochs * max(1, N // batch)
+    k = 0
+    losses = []
+    for ep in range(epochs):
+        order = rng.permutation(N)
+        ep_loss = 0.0
+        for i in range(0, N - batch + 1, batch):
+            idx = torch.as_tensor(order[i:i + batch], device=X.device)
+            xb, tb, wb = X[idx].contiguous(), T[idx].contiguous(), W[idx]
+            wb = (wb / wb.sum()).contiguous()
+            lr_k = 0.5 * lr * (1.0 + math.cos(math.pi * k / steps_total))
+            ep_loss += net.train_step(xb, tb, wb, lr_k)
+            k += 1
+        losses.append(ep_loss / max(1, N // batch))
+        if log:
+            log("epoch %d loss %.4e" % (ep, losses[-1]))
+    return losses
+
+
+def propose(net, case, scale):
+    """Warm-start state (h, u, v) of one case as host float64 arrays."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    D, M = lake_fields(case, dev)
+    x, _, _ = net.encode(D, M, case, scale)
+    y = net.forward(x.unsqueeze(0))[0].contiguous()
+    h, u, v = net.decode(y, D, M, scale)
+    return h.cpu().numpy(), u.cpu().numpy(), v.cpu().numpy()
+
+
+def compare(net, cases, scale, tol=1e-8, max_steps=400000, check_every=500):
+    """Steps and wall time to residual tol from rest and from the proposal,
+    both batches of the same cases on the same GPU.  The warm start's wall
+    time includes encoding, the network and the decoding."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = Batch(cases, precision="f32")
+    sp, _, secp = plain.run_to_steady(tol=tol, max_steps=max_steps, check_every=check_every)
+    torch.cuda.synchronize()
+    wall_plain = time.perf_counter() - t0
+    states_plain = [plain.get_state(i) for i in range(len(cases))]
+    plain.close()
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    warm = Batch(cases, precision="f32")
+    proposals = []
+    for i, c in enumerate(cases):
+        h, u, v = propose(net, c, scale)
+        proposals.append((h, u, v))
+        warm.set_state(i, h, u, v)
+    t_prop = time.perf_counter() - t0
+    sw, _, secw = warm.run_to_steady(tol=tol, max_steps=max_steps, check_every=check_every)
+    torch.cuda.synchronize()
+    wall_warm = time.perf_counter() - t0
+    states_warm = [warm.get_state(i) for i in range(len(cases))]
+    warm.close()
+    # proposal error against the converged plain state (relative, fluid nodes)
+    err = []
+    agree = []
+    for c, p, s, q in zip(cases, proposals, states_plain, states_warm):
+        live = c.mask != 0
+        eta_p, eta_s = p[0] - (c.h_ref - c.zb), s[0] - (c.h_ref - c.zb)
+        e_eta = np.abs(eta_p - eta_s)[live].max() / max(np.abs(eta_s)[live].max(), 1e-30)
+        sp_ = np.hypot(s[1], s[2])[live].max()
+        e_u = max(np.abs(p[1] - s[1])[live].max(), np.abs(p[2] - s[2])[live].max()) / max(sp_, 1e-30)
+        err.append((e_eta, e_u))
+        agree.append(max(np.abs(q[0] - s[0])[live].max() / np.abs(s[0])[live].max(),
+                         np.abs(q[1] - s[1])[live].max() / max(sp_, 1e-30)))
+    return {"plain_steps": sp, "warm_steps": sw, "plain_seconds": secp, "warm_seconds": secw,
+            "wall_plain": wall_plain, "wall_warm": wall_warm, "proposal_seconds": t_prop,
+            "proposal_error": np.array(err), "final_agreement": np.array(agree)}
+
+
+def main():
+    import torch
+    import inputs
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=1024)
+    ap.add_argument("--test", type=int, default=32)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--target-tol", type=float, default=1e-7)
+    args = ap.parse_args()
+    torch.cuda.set_device(0)
+    net = WarmStartNet(max_batch=args.batch)
+    t0 = time.perf_counter()
+    train_cases = [inputs.dish_lake(256, seed=1000 + k) for k in range(args.train)]
+    X, T, W, scale, steps = make_dataset(net, train_cases, tol=args.target_tol)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = train(net, X, T, W, epochs=args.epochs, batch=args.batch, lr=args.lr, log=print)
+    t_train = time.perf_counter() - t0
+    test_cases = [inputs.dish_lake(256, seed=k) for k in range(args.test)]
+    res = compare(net, test_cases, scale)
+    out = {"train": args.train, "params": net.nparam, "data_s": t_data, "train_s": t_train,
+           "loss_first": losses[0], "loss_last": losses[-1], "scale": scale,
+           "plain_steps_median": float(np.median(res["plain_steps"])),
+           "warm_steps_median": float(np.median(res["warm_steps"])),
+           "wall_plain": res["wall_plain"], "wall_warm": res["wall_warm"],
+           "proposal_error_median": np.median(res["proposal_error"], axis=0).tolist(),
+           "final_agreement_max": float(res["final_agreement"].max())}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,6 +1,6 @@
 """The C-ABI library builds for sm_103a, loads without a GPU, exports every
-entry point include/maclab.h declares, and its structs match the ctypes
-layouts of the binding.  No compute call is made here."""
+entry point include/*.h declares, and its structs match the ctypes layouts
+of the binding.  No compute call is made here."""
 import ctypes
 import os
 import re
@@ -11,11 +11,12 @@ import pytest
 from paper_1902_02999_gb300 import _abi, build as buildmod
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "maclab.h")
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(maclab_[a-z0-9_]+)\s*\(", text)))
 
@@ -62,6 +63,23 @@ def test_struct_layouts_match_header(tmp_path):
             ctypes.sizeof(_abi.BC), ctypes.sizeof(_abi.Allocator), ctypes.sizeof(_abi.Info),
             _abi.Info.device_bytes.offset, _abi.Params.h_ref.offset]
     assert got == want
+
+
+def test_warm_start_config_layout_and_argument_checks(tmp_path):
+    src = tmp_path / "ws.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "maclab_ws.h"\n'
+                   "int main(void){printf(\"%zu %zu %zu\\n\",sizeof(maclab_ws_config),"
+                   "offsetof(maclab_ws_config,max_batch),offsetof(maclab_ws_config,seed));return 0;}\n")
+    exe = tmp_path / "ws"
+    subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert got == [ctypes.sizeof(_abi.WSConfig), _abi.WSConfig.max_batch.offset, _abi.WSConfig.seed.offset]
+    lib = _abi.load()
+    cfg = _abi.WSConfig(res=48, channels=128, blocks=2, max_batch=1)   # res not a multiple of 64
+    h = ctypes.c_void_p()
+    assert lib.maclab_ws_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1 and not h.value
+    assert b"multiples of 64" in lib.maclab_last_error(None)
+    assert lib.maclab_ws_forward(None, 1, None, None) == -1
 
 
 def test_build_targets_sm103a_only():
