@@ -197,6 +197,9 @@ def main():
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--batch-max-steps", type=int, default=50_000)
+    ap.add_argument("--ws-train", type=int, default=1024, help="lakes the warm-start network trains on (0: skip)")
+    ap.add_argument("--ws-epochs", type=int, default=20)
+    ap.add_argument("--ws-test", type=int, default=16, help="unseen lakes timed from rest and from the proposal")
     args = ap.parse_args()
     workload = "bump_channel_%dx%d_%s" % (args.nx, args.ny, args.precision)
 
@@ -295,6 +298,27 @@ def main():
            "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 3 * 8 * N,
            "steps": args.e2e_steps}
 
+    # temporal blocking: the same workload with clean tiles advanced two
+    # steps per launch (bitwise the same states); 29 B per node update are
+    # still counted per step, so a fraction above 1 is possible in principle
+    tblock = None
+    if not args.no_extra and args.precision == "f32":
+        sim.set_temporal_block(2)
+        sim.step(max(args.warmup, 3))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tms = e0.elapsed_time(e1) / args.steps
+        tb_peak, _ = hbm_peak()
+        tblock = {"k": 2, "clean_tiles": sim.info["clean_tiles"], "ms_per_step": tms,
+                  "mlups": nodes / (tms / 1e3) / 1e6,
+                  "frac_of_hbm_roofline": BYTES_PER_NODE[args.precision] * nodes / (tms / 1e3) / 1e9 / tb_peak,
+                  "note": "per step of the whole job: 29 B/node algorithmic bytes over the step time"}
+        sim.set_temporal_block(1)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(case)
@@ -372,6 +396,35 @@ def main():
                               "p99_steps": float(np.percentile(st[conv], 99)) if conv.any() else None}}
         bt.close()
 
+    # learned warm start: wall time to residual 1e-8 from rest vs from the
+    # network's proposal on unseen seeded 256 x 256 dish lakes (both FP32
+    # batches of the plain iteration on this GPU); the network trains here,
+    # on steady states of the same solver
+    warm = None
+    if not args.no_extra and args.ws_train > 0 and rank == 0:
+        from paper_1902_02999_gb300 import warmstart as ws
+        net = ws.WarmStartNet(max_batch=16)
+        t0 = time.perf_counter()
+        train_cases = [inputs.dish_lake(256, seed=1000 + k) for k in range(args.ws_train)]
+        X, T, W, scale, data_steps = ws.make_dataset(net, train_cases, tol=1e-7)
+        torch.cuda.synchronize()
+        t_data = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        losses = ws.train(net, X, T, W, epochs=args.ws_epochs, batch=16, lr=1e-3)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        del X, T, W
+        res = ws.compare(net, [inputs.dish_lake(256, seed=k) for k in range(args.ws_test)], scale)
+        warm = {"workload": "dish_lake_256 seeds 0..%d (unseen)" % (args.ws_test - 1), "tol": 1e-8,
+                "accuracy": "warm run stops when within the plain run's final error of the fp64 steady state",
+                "network": {"params": net.nparam, "grid": "64x64 cells of 4x4 nodes", "channels": net.channels,
+                            "blocks": len(net.dilations), "precision": "bf16 activations, fp32 accumulate"},
+                "train": {"lakes": args.ws_train, "epochs": args.ws_epochs, "data_s": t_data,
+                          "train_s": t_train, "loss_first": losses[0], "loss_last": losses[-1]},
+                "error_reference": "fp64 plain iteration to residual 1e-11"}
+        warm.update(ws.summary(res))
+        net.close()
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -383,7 +436,8 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single-gpu",
                            "step_kernel": KERNEL_LABEL[info["step_kernel"]]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "steady_state": steady, "f64": f64, "batched": batched,
+                "steady_state": steady, "f64": f64, "batched": batched, "warm_start": warm,
+                "temporal_block": tblock,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)
     sim.close()

@@ -147,6 +147,9 @@ typedef struct {
     int tile_rows;           /* rows per warp strip of the strip kernel        */
     int step_kernel;         /* maclab_step_kernel in use                      */
     int dirichlet_fused;     /* 1 when Dirichlet nodes are set inside the step kernel */
+    int temporal_block;      /* steps per launch of interior tiles: 1 or 2     */
+    int64_t clean_tiles;     /* tiles that can take two steps per launch (0 until
+                                maclab_set_temporal_block(sim, 2) classifies them) */
 } maclab_info;
 
 /* Create a simulation (procedure steps (a)-(b) of Section 3).
@@ -266,11 +269,25 @@ int maclab_set_launch(maclab_t sim, int rows, int blocks);
  * return MACLAB_E_CUDA. */
 int maclab_set_step_kernel(maclab_t sim, int kernel);
 
+/* Temporal blocking (FP32): with k = 2, maclab_step advances "clean"
+ * 64 x 16 tiles two steps per launch (a tile is clean when the tile and two
+ * nodes of halo on every side lie inside the grid and hold only fluid and
+ * no-slip nodes without bounce-back links).  The other tiles, bounce-back
+ * links and Dirichlet nodes take two single steps through a scratch state.
+ * The results are bitwise identical to k = 1.  The last step of every
+ * maclab_step call (and of every captured graph) is a single step, so the
+ * residual always compares consecutive steps.  The first call with k = 2
+ * classifies the tiles and allocates the scratch state (synchronises).
+ * MACLAB_E_ARG for k outside 1..2 or k = 2 on an FP64 handle. */
+int maclab_set_temporal_block(maclab_t sim, int k);
+
 /* Kernel timing for benchmarks.  While enabled (on != 0), every step
  * records a CUDA event pair around the launch of the fused step kernel on
  * the handle's stream.  maclab_get_profile synchronises, adds up the
- * recorded durations (milliseconds) and the number of step-kernel launches
- * since profiling was enabled, and clears the record.  Enabling resets it. */
+ * recorded durations (milliseconds) and the number of steps those launches
+ * advanced since profiling was enabled, and clears the record.  Enabling
+ * resets it.  With temporal blocking a two-step launch and its companion
+ * single-step launches are timed as one record of two steps. */
 int maclab_set_profiling(maclab_t sim, int on);
 int maclab_get_profile(maclab_t sim, double* step_kernel_ms, int64_t* launches);
 

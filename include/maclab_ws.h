@@ -99,9 +99,13 @@ int maclab_ws_encode(maclab_ws_t ws, int n, const float* D_dev, const uint8_t* m
 /* Coarse output y_dev [R][R][16] -> fine proposal (h, u, v) as double
  * [n][n] device arrays: channels 0..2 times scale[1..3], bilinear between
  * cell centres (clamped at the border), h = D + eta; solid nodes get
- * h = D, u = v = 0 and no-slip nodes u = v = 0. */
+ * h = D, u = v = 0 and no-slip nodes u = v = 0.  When mass_eta is finite,
+ * eta is then shifted by one constant over the non-solid nodes so that it
+ * sums to mass_eta there: the iteration conserves mass exactly in a closed
+ * basin, so its steady state depends on the initial volume (mass_eta = 0
+ * for a basin filled to its still-water level h_ref). */
 int maclab_ws_decode(maclab_ws_t ws, int n, const float* y_dev, const float* D_dev, const uint8_t* mask_dev,
-                     const double scale[4], double* h_dev, double* u_dev, double* v_dev);
+                     const double scale[4], double mass_eta, double* h_dev, double* u_dev, double* v_dev);
 
 #ifdef __cplusplus
 }

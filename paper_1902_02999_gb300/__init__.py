@@ -233,6 +233,13 @@ class Simulation:
         self._check(self._lib.maclab_set_step_kernel(self._h, code))
         self.info["step_kernel"] = code
 
+    def set_temporal_block(self, k: int) -> None:
+        """Steps per launch of clean interior tiles: 1, or 2 (FP32)."""
+        self._check(self._lib.maclab_set_temporal_block(self._h, int(k)))
+        info = _abi.Info()
+        self._check(self._lib.maclab_get_info(self._h, ctypes.byref(info)))
+        self.info = {f: getattr(info, f) for f, _ in _abi.Info._fields_}
+
     def autotune(self, trial_steps: int = 20) -> int:
         """Pick the fastest step-kernel launch shape for this grid (0 = tile
         kernel, 1..4 = strip kernel with 8/16/32/64 rows, 5 = TMA-staged tile

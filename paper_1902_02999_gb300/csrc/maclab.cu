@@ -83,6 +83,14 @@ struct maclab_s {
     double sumD = 0;           // sum of D64 over non-solid nodes
     size_t device_bytes = 0;
     bool profiling = false;
+    int64_t prof_steps = 0;    // steps covered by the recorded event pairs
+    int tblock = 1;            // temporal blocking: steps per launch of clean tiles
+    bool tiles_classified = false;
+    int n_clean = 0, n_other = 0;
+    int* clean_list = nullptr; // tiles that take two steps per launch
+    int* other_list = nullptr; // the rest
+    void* mid[3] = {nullptr, nullptr, nullptr};  // scratch state (eta, u, v) at the middle step
+    int graph_end[2] = {0, 1}; // buffer parity after a replay of graph[parity]
     std::vector<cudaEvent_t> events;  // pairs around step-kernel launches
     size_t events_used = 0;
     std::string err;
@@ -172,6 +180,20 @@ Fields<T> make_fields(const maclab_s* s)
     return f;
 }
 
+// Fields reading the state (ie, iu, iv) and writing (oe, ou, ov)
+template <typename T>
+Fields<T> fields_io(const maclab_s* s, void* ie, void* iu, void* iv, void* oe, void* ou, void* ov)
+{
+    Fields<T> f = make_fields<T>(s);
+    f.eta = (const T*)ie;
+    f.u = (const T*)iu;
+    f.v = (const T*)iv;
+    f.eta1 = (T*)oe;
+    f.u1 = (T*)ou;
+    f.v1 = (T*)ov;
+    return f;
+}
+
 double wave(const maclab_wave& w, double t) { return w.mean + w.amp * std::sin(w.omega * t + w.phase); }
 
 template <typename T>
@@ -188,6 +210,7 @@ int launch_step(maclab_t s)
         ev0 = s->events[s->events_used];
         ev1 = s->events[s->events_used + 1];
         s->events_used += 2;
+        s->prof_steps += 1;
         cudaEventRecord(ev0, s->stream);
     }
     DirValues bv{};
@@ -255,6 +278,104 @@ int launch_step(maclab_t s)
     s->cur = 1 - s->cur;
     s->n += 1;
     s->have_prev = true;
+    return MACLAB_OK;
+}
+
+DirValues dir_values(const maclab_s* s, int64_t step)
+{
+    DirValues bv{};
+    if (s->n_dir > 0) {
+        const double t1 = (double)step * s->dt;
+        for (int k = 0; k < 4; ++k) {
+            bv.h[k] = wave(s->bc.h[k], t1);
+            bv.qx[k] = wave(s->bc.qx[k], t1);
+            bv.qy[k] = wave(s->bc.qy[k], t1);
+        }
+    }
+    return bv;
+}
+
+// One single step of the tiles that are not clean, with the bounce-back-link
+// and Dirichlet companions, from the state (ie, iu, iv) to (oe, ou, ov).
+void other_tiles_step(maclab_t s, void* ie, void* iu, void* iv, void* oe, void* ou, void* ov, int64_t to_step)
+{
+    const Fields<float> f = fields_io<float>(s, ie, iu, iv, oe, ou, ov);
+    const DirValues bv = dir_values(s, to_step);
+    const int tx = (s->grid.nx + tile::TX - 1) / tile::TX;
+    const TileDirichlet td{s->dir_fused ? s->dir_tile_start : nullptr, s->dir, s->D64, bv};
+    if (s->n_other > 0) {
+        const size_t smem = tile::smem_bytes<float>();
+        switch (s->fmode) {
+#define MACLAB_FM(m) \
+    case m: step_tile_list_kernel<float, m><<<s->n_other, tile::THREADS, smem, s->stream>>>(f, tx, td, s->other_list); break;
+            MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
+#undef MACLAB_FM
+        }
+    }
+    if (s->n_general > 0)
+        step_general_kernel<float><<<(s->n_general + 127) / 128, 128, 0, s->stream>>>(f, s->general, s->n_general);
+    if (s->n_dir > 0 && !s->dir_fused)
+        dirichlet_kernel<float><<<(s->n_dir + 127) / 128, 128, 0, s->stream>>>(
+            (float*)oe, (float*)ou, (float*)ov, (const float*)s->D, s->D64, s->dir, s->n_dir, bv);
+}
+
+// Two steps: clean tiles in one launch (step_tile2_kernel), the other tiles
+// in two single steps through the scratch state s->mid (which also receives
+// the clean tiles' outer rings at the middle step).
+int launch_pair(maclab_t s)
+{
+    const int a = s->cur, b = 1 - s->cur;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (s->profiling) {
+        while (s->events.size() < s->events_used + 2) {
+            cudaEvent_t ev;
+            if (cudaEventCreate(&ev) != cudaSuccess) return cuda_fail(s, cudaGetLastError(), "event");
+            s->events.push_back(ev);
+        }
+        ev0 = s->events[s->events_used];
+        ev1 = s->events[s->events_used + 1];
+        s->events_used += 2;
+        s->prof_steps += 2;
+        cudaEventRecord(ev0, s->stream);
+    }
+    if (s->n_clean > 0) {
+        const Fields<float> f = fields_io<float>(s, s->eta[a], s->u[a], s->v[a], s->mid[0], s->mid[1], s->mid[2]);
+        const int tx = (s->grid.nx + tile::TX - 1) / tile::TX;
+        const size_t smem = sizeof(tile2::Smem);
+        switch (s->fmode) {
+#define MACLAB_FM(m)                                                                                             \
+    case m:                                                                                                      \
+        step_tile2_kernel<m><<<s->n_clean, tile::THREADS, smem, s->stream>>>(f, (float*)s->eta[b], (float*)s->u[b], \
+                                                                            (float*)s->v[b], tx, s->clean_list);   \
+        break;
+            MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
+#undef MACLAB_FM
+        }
+    }
+    other_tiles_step(s, s->eta[a], s->u[a], s->v[a], s->mid[0], s->mid[1], s->mid[2], s->n + 1);
+    other_tiles_step(s, s->mid[0], s->mid[1], s->mid[2], s->eta[b], s->u[b], s->v[b], s->n + 2);
+    if (s->profiling) cudaEventRecord(ev1, s->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(s, e, "two-step launch");
+    s->cur = b;
+    s->n += 2;
+    s->have_prev = false;  // the middle state is not kept whole
+    return MACLAB_OK;
+}
+
+// n steps: pairs where temporal blocking is on, the last step always single
+int advance(maclab_t s, int64_t n)
+{
+    const bool pairs_on = s->tblock == 2 && s->prec == MACLAB_F32;
+    const int64_t pairs = pairs_on && n >= 3 ? (n - 1) / 2 : 0;
+    for (int64_t k = 0; k < pairs; ++k) {
+        int rc = launch_pair(s);
+        if (rc != MACLAB_OK) return rc;
+    }
+    for (int64_t k = 2 * pairs; k < n; ++k) {
+        int rc = s->prec == MACLAB_F32 ? launch_step<float>(s) : launch_step<double>(s);
+        if (rc != MACLAB_OK) return rc;
+    }
     return MACLAB_OK;
 }
 
@@ -744,10 +865,10 @@ int capture_graph(maclab_t s)
     e = cudaStreamBeginCapture(s->capture_stream, cudaStreamCaptureModeThreadLocal);
     int rc = MACLAB_OK;
     if (e == cudaSuccess) {
-        for (int k = 0; k < s->graph_steps && rc == MACLAB_OK; ++k)
-            rc = s->prec == MACLAB_F32 ? launch_step<float>(s) : launch_step<double>(s);
+        rc = advance(s, s->graph_steps);
         e = cudaStreamEndCapture(s->capture_stream, &g);
     }
+    s->graph_end[cur] = s->cur;
     s->stream = user;
     s->cur = cur;
     s->n = n;
@@ -783,15 +904,12 @@ int maclab_step(maclab_t s, int64_t n)
         }
         cudaError_t e = cudaGraphLaunch(s->graph[s->cur], s->stream);
         if (e != cudaSuccess) return cuda_fail(s, e, "graph launch");
-        s->n += s->graph_steps;  // an even number of steps: the parity is unchanged
-        s->have_prev = true;
+        s->n += s->graph_steps;
+        s->cur = s->graph_end[s->cur];  // the buffer the captured steps ended in
+        s->have_prev = true;            // a graph ends with a single step
         n -= s->graph_steps;
     }
-    for (int64_t k = 0; k < n; ++k) {
-        int rc = s->prec == MACLAB_F32 ? launch_step<float>(s) : launch_step<double>(s);
-        if (rc != MACLAB_OK) return rc;
-    }
-    return MACLAB_OK;
+    return advance(s, n);
 }
 
 int maclab_autotune(maclab_t s, int trial_steps, int* choice)
@@ -1071,11 +1189,72 @@ int maclab_set_step_kernel(maclab_t s, int kernel)
     return MACLAB_OK;
 }
 
+int maclab_set_temporal_block(maclab_t s, int k)
+{
+    if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    if (k < 1 || k > 2) return fail(s, MACLAB_E_ARG, "temporal block must be 1 or 2");
+    if (k == 2 && s->prec != MACLAB_F32) return fail(s, MACLAB_E_ARG, "temporal blocking needs an FP32 handle");
+    if (k == 2 && !s->tiles_classified) {
+        // classify the tiles from the node types on the device
+        const int nx = s->grid.nx, ny = s->grid.ny, pitch = s->pitch;
+        std::vector<uint8_t> type((size_t)pitch * ny);
+        cudaError_t e = cudaMemcpyAsync(type.data(), s->type, type.size(), cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "temporal block setup");
+        const int tiles_x = (nx + tile::TX - 1) / tile::TX, tiles_y = (ny + tile::TY - 1) / tile::TY;
+        std::vector<int> clean, other;
+        for (int t = 0; t < tiles_x * tiles_y; ++t) {
+            const int x0 = (t % tiles_x) * tile::TX, y0 = (t / tiles_x) * tile::TY;
+            bool ok = x0 - 2 >= 0 && y0 - 2 >= 0 && x0 + tile::TX + 2 <= nx && y0 + tile::TY + 2 <= ny;
+            for (int y = y0 - 2; ok && y < y0 + tile::TY + 2; ++y)
+                for (int x = x0 - 2; ok && x < x0 + tile::TX + 2; ++x) {
+                    const uint8_t ty = type[(size_t)y * pitch + x];
+                    const int kind = ty & KIND_MASK;
+                    ok = (kind == K_FLUID || kind == K_NOSLIP) && !(ty & GENERAL_BIT);
+                }
+            (ok ? clean : other).push_back(t);
+        }
+        const size_t NP = (size_t)pitch * ny;
+        for (int q = 0; q < 3; ++q)
+            if (!(s->mid[q] = dev_alloc(s, NP * sizeof(float)))) return fail(s, MACLAB_E_NOMEM, "temporal block scratch");
+        if ((!clean.empty() && !(s->clean_list = (int*)dev_alloc(s, clean.size() * sizeof(int)))) ||
+            (!other.empty() && !(s->other_list = (int*)dev_alloc(s, other.size() * sizeof(int)))))
+            return fail(s, MACLAB_E_NOMEM, "temporal block lists");
+        if (!clean.empty()) e = cudaMemcpyAsync(s->clean_list, clean.data(), clean.size() * sizeof(int),
+                                                cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess && !other.empty())
+            e = cudaMemcpyAsync(s->other_list, other.data(), other.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                s->stream);
+        for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaMemsetAsync(s->mid[q], 0, NP * sizeof(float), s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "temporal block setup");
+        cudaError_t ae = cudaSuccess;
+#define MACLAB_ATTR(m)                                                                                      \
+    if (ae == cudaSuccess)                                                                                  \
+        ae = cudaFuncSetAttribute(step_tile2_kernel<m>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                                  (int)sizeof(tile2::Smem));                                                \
+    if (ae == cudaSuccess)                                                                                  \
+        ae = cudaFuncSetAttribute(step_tile_list_kernel<float, m>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  (int)tile::smem_bytes<float>());
+        MACLAB_ATTR(0) MACLAB_ATTR(1) MACLAB_ATTR(2) MACLAB_ATTR(3) MACLAB_ATTR(4) MACLAB_ATTR(5) MACLAB_ATTR(6)
+        MACLAB_ATTR(7)
+#undef MACLAB_ATTR
+        if (ae != cudaSuccess) return cuda_fail(s, ae, "cudaFuncSetAttribute");
+        s->n_clean = (int)clean.size();
+        s->n_other = (int)other.size();
+        s->tiles_classified = true;
+    }
+    s->tblock = k;
+    drop_graphs(s);
+    return MACLAB_OK;
+}
+
 int maclab_set_profiling(maclab_t s, int on)
 {
     if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
     s->profiling = on != 0;
     s->events_used = 0;
+    s->prof_steps = 0;
     return MACLAB_OK;
 }
 
@@ -1092,8 +1271,9 @@ int maclab_get_profile(maclab_t s, double* ms, int64_t* launches)
         total += t;
     }
     if (ms) *ms = total;
-    if (launches) *launches = (int64_t)(s->events_used / 2);
+    if (launches) *launches = s->prof_steps;
     s->events_used = 0;
+    s->prof_steps = 0;
     return MACLAB_OK;
 }
 
@@ -1115,6 +1295,8 @@ int maclab_get_info(maclab_t s, maclab_info* info)
     info->tile_rows = s->ty;
     info->step_kernel = s->kernel;
     info->dirichlet_fused = (s->kernel != MACLAB_KERNEL_STRIP && s->dir_fused) ? 1 : 0;
+    info->temporal_block = s->tblock;
+    info->clean_tiles = s->n_clean;
     return MACLAB_OK;
 }
 

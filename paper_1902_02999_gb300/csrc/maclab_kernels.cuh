@@ -841,14 +841,14 @@ constexpr int PC = TX / 2 + 2;             // 34 node pairs per tile row (with h
 constexpr int IR = TY + 2;                 // 18 tile rows (with halo)
 constexpr int IW = 2 * PC;                 // 68 tile columns: global x0 - 2 .. x0 + 65
 constexpr int HALO_PAIRS = 2 * IR + 2 * (PC - 2);  // 100
-template <typename T>
+template <typename T, int ROWS = IR>
 struct Derived {
-    T o_[8][IR][IW];                       // outgoing values o_1 .. o_8
+    T o_[8][ROWS][IW];                     // outgoing values o_1 .. o_8
     __device__ __forceinline__ T& o(int d, int r, int c) { return o_[d][r][c]; }
     __device__ __forceinline__ const T& o(int d, int r, int c) const { return o_[d][r][c]; }
     // (eta, D), even and odd tile columns apart: a warp reading column
     // 2 tx + k (k fixed) then touches consecutive 8-byte words
-    typename Vec2<T>::type ed_[2][IR][IW / 2];
+    typename Vec2<T>::type ed_[2][ROWS][IW / 2];
     __device__ __forceinline__ typename Vec2<T>::type& ed(int r, int c) { return ed_[c & 1][r][c >> 1]; }
     __device__ __forceinline__ const typename Vec2<T>::type& ed(int r, int c) const { return ed_[c & 1][r][c >> 1]; }
 };
@@ -989,6 +989,50 @@ __device__ __forceinline__ void tile_phase_a(const Fields<T>& f, int x0, int y0,
     }
 }
 
+// New eta, u, v of the node at tile row lr, column lc from the derived values
+// of its eight neighbours in shared memory (Eqs. Mac.lb.6 / Mac.lb.7 in the
+// perturbation form); eta, D, ownh, hFx, hFy are the node's own source
+// quantities.  Every kernel that gathers from shared memory calls this one
+// function, so their results agree bitwise.
+template <typename T, typename DR>
+__device__ __forceinline__ void node_update(const DR& sm, int lr, int lc, const Coef<T>& K, T eta, T D, T ownh,
+                                            T hFx, T hFy, bool noslip, T& oe, T& ou, T& ov)
+{
+    using O = Op<T>;
+    using V2 = typename Vec2<T>::type;
+    const T q = T(0.25);
+    const T cL_o1 = sm.o(0, lr, lc - 1), mL_o2 = sm.o(1, lr - 1, lc - 1), pL_o8 = sm.o(7, lr + 1, lc - 1);
+    const T cR_o5 = sm.o(4, lr, lc + 1), mR_o4 = sm.o(3, lr - 1, lc + 1), pR_o6 = sm.o(5, lr + 1, lc + 1);
+    const T mC_o3 = sm.o(2, lr - 1, lc), pC_o7 = sm.o(6, lr + 1, lc);
+    const V2 mL = sm.ed(lr - 1, lc - 1), mC = sm.ed(lr - 1, lc), mR = sm.ed(lr - 1, lc + 1);
+    const V2 cL = sm.ed(lr, lc - 1), cR = sm.ed(lr, lc + 1);
+    const V2 pL = sm.ed(lr + 1, lc - 1), pC = sm.ed(lr + 1, lc), pR = sm.ed(lr + 1, lc + 1);
+    const T OL = O::add(O::add(cL_o1, mL_o2), pL_o8);
+    const T OR = O::add(O::add(cR_o5, mR_o4), pR_o6);
+    const T Sh = O::add(O::add(OL, OR), O::add(mC_o3, pC_o7));
+    const T Sx = O::sub(OL, OR);
+    const T Sy = O::sub(O::add(O::add(mL_o2, mR_o4), mC_o3), O::add(O::add(pL_o8, pR_o6), pC_o7));
+    // lambda-weighted stencils of eta (.x) and D (.y): sum, x-moment, y-moment
+    const T MLe = O::fma(q, O::add(mL.x, pL.x), cL.x);
+    const T MRe = O::fma(q, O::add(mR.x, pR.x), cR.x);
+    const T MLd = O::fma(q, O::add(mL.y, pL.y), cL.y);
+    const T MRd = O::fma(q, O::add(mR.y, pR.y), cR.y);
+    const T Se = O::add(O::add(MLe, MRe), O::add(mC.x, pC.x));
+    const T Sd = O::add(O::add(MLd, MRd), O::add(mC.y, pC.y));
+    const T Xe = O::sub(MLe, MRe), Xd = O::sub(MLd, MRd);
+    const T Ye = O::fma(q, O::sub(O::add(mL.x, mR.x), O::add(pL.x, pR.x)), O::sub(mC.x, pC.x));
+    const T Yd = O::fma(q, O::sub(O::add(mL.y, mR.y), O::add(pL.y, pR.y)), O::sub(mC.y, pC.y));
+    const T A = O::mul(K.G6, D), B = O::mul(K.G6, eta);
+    // ownh already holds the receiver-only bed part 5 G6 eta_x D_x
+    const T eta1 = O::add(O::add(ownh, Sh), O::fma(A, Se, O::mul(-B, Sd)));
+    const T hu1 = O::fma(K.e, O::add(Sx, O::fma(A, Xe, O::mul(-B, Xd))), hFx);
+    const T hv1 = O::fma(K.e, O::add(Sy, O::fma(A, Ye, O::mul(-B, Yd))), hFy);
+    const T inv = O::rcp(O::add(D, eta1));
+    oe = eta1;
+    ou = noslip ? T(0) : O::mul(hu1, inv);
+    ov = noslip ? T(0) : O::mul(hv1, inv);
+}
+
 // Phases B and C of a tile whose phase A is complete and visible; `tile`
 // indexes the per-tile Dirichlet ranges.
 template <typename T>
@@ -998,12 +1042,10 @@ __device__ __forceinline__ void tile_phase_bc(const Fields<T>& f, int x0, int y0
                                               const uint32_t (&own_types)[2])
 {
     using namespace tile;
-    using O = Op<T>;
     using V2 = typename Vec2<T>::type;
     const int tx = threadIdx.x & 31, tyy = threadIdx.x >> 5;
     const Coef<T>& K = f.c;
     // ---- phase B: nodes (x0 + 2 tx + k, y0 + 2 tyy + r)
-    const T q = T(0.25);
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         const int lr = 1 + 2 * tyy + r;    // tile row of the node
@@ -1017,38 +1059,9 @@ __device__ __forceinline__ void tile_phase_bc(const Fields<T>& f, int x0, int y0
             const uint8_t ty = (uint8_t)(own_types[r] >> (8 * k));
             const bool ok = x < f.nx && y < f.ny && (ty & KIND_MASK) != K_SOLID && !(ty & GENERAL_BIT);
             okmask |= (ok ? 1u : 0u) << k;
-            const T cL_o1 = sm.o(0, lr, lc - 1), mL_o2 = sm.o(1, lr - 1, lc - 1), pL_o8 = sm.o(7, lr + 1, lc - 1);
-            const T cR_o5 = sm.o(4, lr, lc + 1), mR_o4 = sm.o(3, lr - 1, lc + 1), pR_o6 = sm.o(5, lr + 1, lc + 1);
-            const T mC_o3 = sm.o(2, lr - 1, lc), pC_o7 = sm.o(6, lr + 1, lc);
-            const V2 mL = sm.ed(lr - 1, lc - 1), mC = sm.ed(lr - 1, lc), mR = sm.ed(lr - 1, lc + 1);
-            const V2 cL = sm.ed(lr, lc - 1), cR = sm.ed(lr, lc + 1);
-            const V2 pL = sm.ed(lr + 1, lc - 1), pC = sm.ed(lr + 1, lc), pR = sm.ed(lr + 1, lc + 1);
-            const T OL = O::add(O::add(cL_o1, mL_o2), pL_o8);
-            const T OR = O::add(O::add(cR_o5, mR_o4), pR_o6);
-            const T Sh = O::add(O::add(OL, OR), O::add(mC_o3, pC_o7));
-            const T Sx = O::sub(OL, OR);
-            const T Sy = O::sub(O::add(O::add(mL_o2, mR_o4), mC_o3), O::add(O::add(pL_o8, pR_o6), pC_o7));
-            // lambda-weighted stencils of eta (.x) and D (.y): sum, x-moment, y-moment
-            const T MLe = O::fma(q, O::add(mL.x, pL.x), cL.x);
-            const T MRe = O::fma(q, O::add(mR.x, pR.x), cR.x);
-            const T MLd = O::fma(q, O::add(mL.y, pL.y), cL.y);
-            const T MRd = O::fma(q, O::add(mR.y, pR.y), cR.y);
-            const T Se = O::add(O::add(MLe, MRe), O::add(mC.x, pC.x));
-            const T Sd = O::add(O::add(MLd, MRd), O::add(mC.y, pC.y));
-            const T Xe = O::sub(MLe, MRe), Xd = O::sub(MLd, MRd);
-            const T Ye = O::fma(q, O::sub(O::add(mL.x, mR.x), O::add(pL.x, pR.x)), O::sub(mC.x, pC.x));
-            const T Yd = O::fma(q, O::sub(O::add(mL.y, mR.y), O::add(pL.y, pR.y)), O::sub(mC.y, pC.y));
             const Src<T>& me = own[r][k];
-            const T A = O::mul(K.G6, me.D), B = O::mul(K.G6, me.eta);
-            // ownh already holds the receiver-only bed part 5 G6 eta_x D_x
-            const T eta1 = O::add(O::add(me.ownh, Sh), O::fma(A, Se, O::mul(-B, Sd)));
-            const T hu1 = O::fma(K.e, O::add(Sx, O::fma(A, Xe, O::mul(-B, Xd))), me.hFx);
-            const T hv1 = O::fma(K.e, O::add(Sy, O::fma(A, Ye, O::mul(-B, Yd))), me.hFy);
-            const T inv = O::rcp(O::add(me.D, eta1));
-            const bool noslip = (ty & KIND_MASK) == K_NOSLIP;
-            oe[k] = eta1;
-            ou[k] = noslip ? T(0) : O::mul(hu1, inv);
-            ov[k] = noslip ? T(0) : O::mul(hv1, inv);
+            node_update<T>(sm, lr, lc, K, me.eta, me.D, me.ownh, me.hFx, me.hFy,
+                           (ty & KIND_MASK) == K_NOSLIP, oe[k], ou[k], ov[k]);
         }
         if (okmask == 0) continue;
         const size_t idx = (size_t)y * f.pitch + x0 + 2 * tx;
@@ -1180,6 +1193,155 @@ step_tile_kernel(const __grid_constant__ Fields<T> f, int tiles_x, const __grid_
     tile::Derived<T>& sm = *reinterpret_cast<tile::Derived<T>*>(smem_raw);
     const int x0 = (blockIdx.x % tiles_x) * tile::TX, y0 = (blockIdx.x / tiles_x) * tile::TY;
     tile_update<T, FM>(f, x0, y0, blockIdx.x, td.start, td.list, td.D64, td.bv, sm);
+}
+
+// Single step over a list of tiles (the tiles a two-step launch leaves out).
+template <typename T, int FM>
+__global__ void __launch_bounds__(tile::THREADS, tile::MinBlocks<T>::value)
+step_tile_list_kernel(const __grid_constant__ Fields<T> f, int tiles_x, const __grid_constant__ TileDirichlet td,
+                      const int* __restrict__ list)
+{
+    extern __shared__ __align__(16) unsigned char smem_list[];
+    tile::Derived<T>& sm = *reinterpret_cast<tile::Derived<T>*>(smem_list);
+    const int t = list[blockIdx.x];
+    const int x0 = (t % tiles_x) * tile::TX, y0 = (t / tiles_x) * tile::TY;
+    tile_update<T, FM>(f, x0, y0, t, td.start, td.list, td.D64, td.bv, sm);
+}
+
+// ---------------------------------------------------------------------------
+// Two steps per launch (temporal blocking, FP32) for "clean" tiles: the
+// 68 x 20 window of the tile (two nodes of halo on every side) lies inside
+// the grid and holds only fluid and no-slip nodes without bounce-back links,
+// so no edge rule, bounce-back link or Dirichlet node enters either step.
+//   A1  derive the window at step n           (rows 0..19 of the window)
+//   B1  update rows 1..18 to step n + 1, kept in registers; the tile's
+//       outer ring of nodes is also written to the step-n+1 buffer for the
+//       tiles that take two single steps
+//   A2  derive those rows at step n + 1
+//   B2  update the 64 x 16 tile to step n + 2 and store it
+// Window column c is global x0 - 2 + c, window row r global y0 - 2 + r.
+// Every node value equals that of two single steps bitwise (same
+// derive2 / node_update arithmetic).
+namespace tile2 {
+constexpr int R2 = tile::TY + 4;            // 20 window rows
+constexpr int PAIRS = R2 * tile::PC;        // 680 pairs of the window
+constexpr int MID = (R2 - 2) * tile::PC;    // 612 pairs of rows 1..18
+constexpr int HOLD = (MID + tile::THREADS - 1) / tile::THREADS;  // 3
+struct Smem {
+    tile::Derived<float, R2> d;
+    float2 own[3][R2][tile::PC];            // ownh, hFx, hFy of pair (r, j): columns 2j, 2j + 1
+    uint16_t type[R2][tile::PC];
+};
+}  // namespace tile2
+
+__device__ __forceinline__ void store_window_pair(tile2::Smem& sm, int r, int j, const Src2& s, uint32_t types)
+{
+    const float2 od[8] = {s.o1, s.o2, s.o3, s.o4, s.o5, s.o6, s.o7, s.o8};
+#pragma unroll
+    for (int d = 0; d < 8; ++d) *reinterpret_cast<float2*>(&sm.d.o(d, r, 2 * j)) = od[d];
+    sm.d.ed(r, 2 * j) = make_float2(s.eta.x, s.D.x);
+    sm.d.ed(r, 2 * j + 1) = make_float2(s.eta.y, s.D.y);
+    sm.own[0][r][j] = s.ownh;
+    sm.own[1][r][j] = s.hFx;
+    sm.own[2][r][j] = s.hFy;
+    sm.type[r][j] = (uint16_t)types;
+}
+
+__device__ __forceinline__ void window_node(const tile2::Smem& sm, const Coef<float>& K, int r, int c, float& oe,
+                                            float& ou, float& ov)
+{
+    const int j = c >> 1, k = c & 1;
+    const float2 ed = sm.d.ed(r, c);
+    const float2 oh = sm.own[0][r][j], fx = sm.own[1][r][j], fy = sm.own[2][r][j];
+    const uint8_t ty = (uint8_t)(sm.type[r][j] >> (8 * k));
+    node_update<float>(sm.d, r, c, K, ed.x, ed.y, k ? oh.y : oh.x, k ? fx.y : fx.x, k ? fy.y : fy.x,
+                       (ty & KIND_MASK) == K_NOSLIP, oe, ou, ov);
+}
+
+// f: eta, u, v at step n; eta1, u1, v1 the step-n+1 buffer (outer ring only);
+// out_* the step-n+2 buffer.  Blocks walk the list of clean tiles.
+template <int FM>
+__global__ void __launch_bounds__(tile::THREADS, 3)
+step_tile2_kernel(const __grid_constant__ Fields<float> f, float* __restrict__ out_eta, float* __restrict__ out_u,
+                  float* __restrict__ out_v, int tiles_x, const int* __restrict__ list)
+{
+    using namespace tile;
+    using namespace tile2;
+    extern __shared__ __align__(16) unsigned char smem_t2[];
+    Smem& sm = *reinterpret_cast<Smem*>(smem_t2);
+    const int t = list[blockIdx.x];
+    const int x0 = (t % tiles_x) * TX, y0 = (t / tiles_x) * TY;
+    const Coef<float>& K = f.c;
+    // ---- A1: the window at step n (inside the grid: plain vector loads)
+    for (int p = threadIdx.x; p < PAIRS; p += THREADS) {
+        const int r = p / PC, j = p % PC;
+        const size_t base = (size_t)(y0 - 2 + r) * f.pitch + x0 - 2 + 2 * j;
+        const float2 e2 = *reinterpret_cast<const float2*>(f.eta + base);
+        const float2 u2 = *reinterpret_cast<const float2*>(f.u + base);
+        const float2 v2 = *reinterpret_cast<const float2*>(f.v + base);
+        const float2 d2 = *reinterpret_cast<const float2*>(f.D + base);
+        const uint32_t types = *reinterpret_cast<const uint16_t*>(f.type + base);
+        Src2 s;
+        derive2<FM>(K, Raw<float>{e2.x, u2.x, v2.x, d2.x, 0}, Raw<float>{e2.y, u2.y, v2.y, d2.y, 0}, s);
+        store_window_pair(sm, r, j, s, types);
+    }
+    __syncthreads();
+    // ---- B1: rows 1..18 at step n + 1 (window columns 0 and 67 have no
+    // update; they are computed from in-window neighbours and never read)
+    float2 he[HOLD], hu[HOLD], hv[HOLD], hd[HOLD];
+    uint32_t ht[HOLD];
+#pragma unroll
+    for (int k = 0; k < HOLD; ++k) {
+        const int p = threadIdx.x + k * THREADS;
+        if (p >= MID) break;
+        const int r = 1 + p / PC, j = p % PC;
+        float oe[2], ou[2], ov[2];
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const int c = min(max(2 * j + l, 1), IW - 2);
+            window_node(sm, K, r, c, oe[l], ou[l], ov[l]);
+            // outer ring of the tile -> the step-n+1 buffer
+            const int cc = 2 * j + l;
+            if (r >= 2 && r <= R2 - 3 && cc >= 2 && cc <= IW - 3 &&
+                (r == 2 || r == R2 - 3 || cc == 2 || cc == IW - 3)) {
+                const size_t idx = (size_t)(y0 - 2 + r) * f.pitch + x0 - 2 + cc;
+                f.eta1[idx] = oe[l];
+                f.u1[idx] = ou[l];
+                f.v1[idx] = ov[l];
+            }
+        }
+        he[k] = make_float2(oe[0], oe[1]);
+        hu[k] = make_float2(ou[0], ou[1]);
+        hv[k] = make_float2(ov[0], ov[1]);
+        hd[k] = make_float2(sm.d.ed(r, 2 * j).y, sm.d.ed(r, 2 * j + 1).y);
+        ht[k] = sm.type[r][j];
+    }
+    __syncthreads();
+    // ---- A2: derive rows 1..18 at step n + 1
+#pragma unroll
+    for (int k = 0; k < HOLD; ++k) {
+        const int p = threadIdx.x + k * THREADS;
+        if (p >= MID) break;
+        const int r = 1 + p / PC, j = p % PC;
+        Src2 s;
+        derive2<FM>(K, Raw<float>{he[k].x, hu[k].x, hv[k].x, hd[k].x, 0},
+                    Raw<float>{he[k].y, hu[k].y, hv[k].y, hd[k].y, 0}, s);
+        store_window_pair(sm, r, j, s, ht[k]);
+    }
+    __syncthreads();
+    // ---- B2: the tile (window rows 2..17, columns 2..65) at step n + 2
+    const int tx = threadIdx.x & 31, tyy = threadIdx.x >> 5;
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+        const int r = 2 + 2 * tyy + rr;
+        float oe[2], ou[2], ov[2];
+#pragma unroll
+        for (int l = 0; l < 2; ++l) window_node(sm, K, r, 2 + 2 * tx + l, oe[l], ou[l], ov[l]);
+        const size_t idx = (size_t)(y0 - 2 + r) * f.pitch + x0 + 2 * tx;
+        *reinterpret_cast<float2*>(out_eta + idx) = make_float2(oe[0], oe[1]);
+        *reinterpret_cast<float2*>(out_u + idx) = make_float2(ou[0], ou[1]);
+        *reinterpret_cast<float2*>(out_v + idx) = make_float2(ov[0], ov[1]);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -496,6 +496,42 @@ __global__ void ws_decode_kernel(int n, int R, const float* Y, const float* D, c
     v[k] = still ? 0.0 : out[2] * s3;
 }
 
+// sum over non-solid nodes of (h - D) and their count, block partials
+// added into acc[0..1]
+__global__ void __launch_bounds__(THREADS) ws_eta_sum_kernel(int nn, const double* h, const float* D,
+                                                             const uint8_t* mask, double* acc)
+{
+    __shared__ double ps[THREADS], pc[THREADS];
+    double s = 0.0, c = 0.0;
+    for (int k = blockIdx.x * THREADS + threadIdx.x; k < nn; k += gridDim.x * THREADS)
+        if (mask[k] != MACLAB_SOLID) {
+            s += h[k] - (double)D[k];
+            c += 1.0;
+        }
+    ps[threadIdx.x] = s;
+    pc[threadIdx.x] = c;
+    __syncthreads();
+    for (int k = THREADS / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) {
+            ps[threadIdx.x] += ps[threadIdx.x + k];
+            pc[threadIdx.x] += pc[threadIdx.x + k];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(acc, ps[0]);
+        atomicAdd(acc + 1, pc[0]);
+    }
+}
+
+// h -= (sum - target) / count on non-solid nodes
+__global__ void ws_eta_shift_kernel(int nn, double* h, const uint8_t* mask, const double* acc, double target)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nn || mask[k] == MACLAB_SOLID || !(acc[1] > 0.0)) return;
+    h[k] -= (acc[0] - target) / acc[1];
+}
+
 int grid_for(size_t n, int cap = 4096) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, cap)); }
 
 uint64_t splitmix(uint64_t& s)
@@ -531,6 +567,7 @@ struct maclab_ws_s {
     bf16* dY = nullptr;         // [B][R][R][16]
     float* Yf = nullptr;        // [B][R][R][16]
     double* loss = nullptr;
+    double* acc = nullptr;      // decode's (sum of eta, count)
     std::vector<void*> bufs;
     std::string err;
 };
@@ -730,7 +767,7 @@ int maclab_ws_create(const maclab_ws_config* cfg, void* stream, maclab_ws_t* out
     const size_t P = (size_t)cfg->max_batch * R * R;
     bool ok = walloc(w, &w->param, w->nparam) && walloc(w, &w->grad, w->nparam) && walloc(w, &w->m1, w->nparam) &&
               walloc(w, &w->m2, w->nparam) && walloc(w, &w->X, P * IO) && walloc(w, &w->dY, P * IO) &&
-              walloc(w, &w->Yf, P * IO) && walloc(w, &w->loss, 1) && walloc(w, &w->G[0], P * C) &&
+              walloc(w, &w->Yf, P * IO) && walloc(w, &w->loss, 1) && walloc(w, &w->acc, 2) && walloc(w, &w->G[0], P * C) &&
               walloc(w, &w->G[1], P * C);
     w->H.assign(w->layers.size() - 1, nullptr);
     for (size_t l = 0; ok && l < w->H.size(); ++l) ok = walloc(w, &w->H[l], P * C);
@@ -881,13 +918,18 @@ int maclab_ws_encode(maclab_ws_t w, int n, const float* D, const uint8_t* mask, 
 }
 
 int maclab_ws_decode(maclab_ws_t w, int n, const float* y, const float* D, const uint8_t* mask, const double scale[4],
-                     double* h, double* u, double* v)
+                     double mass_eta, double* h, double* u, double* v)
 {
     if (!w || !y || !D || !mask || !scale || !h || !u || !v) return wfail(w, MACLAB_E_ARG, "NULL argument");
     const int R = w->cfg.res;
     if (n != R * CELL) return wfail(w, MACLAB_E_ARG, "fine grid must be res * MACLAB_WS_CELL per side");
     ws_decode_kernel<<<(n * n + 255) / 256, 256, 0, w->stream>>>(n, R, y, D, mask, scale[1], scale[2], scale[3], h,
                                                                  u, v);
+    if (std::isfinite(mass_eta)) {
+        cudaMemsetAsync(w->acc, 0, 2 * sizeof(double), w->stream);
+        ws_eta_sum_kernel<<<grid_for((size_t)n * n, 1024), THREADS, 0, w->stream>>>(n * n, h, D, mask, w->acc);
+        ws_eta_shift_kernel<<<(n * n + 255) / 256, 256, 0, w->stream>>>(n * n, h, mask, w->acc, mass_eta);
+    }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("decode: ") + cudaGetErrorString(e));
     return MACLAB_OK;

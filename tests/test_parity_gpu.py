@@ -222,6 +222,27 @@ def test_paper_tidal_case_on_gpu():
     assert np.abs(h[0] + case.zb[0] - eta).max() / eta < 5e-5
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_coriolis_inertial_oscillation(precision):
+    """Uniform flow on a flat periodic domain with Coriolis only: every node
+    follows w_{n+1} = (1 - i dt Omega) w_n for w = u + i v (the centred force
+    of a uniform state, Eq. SWE-force), so after n steps the velocity has
+    turned by n atan(dt Omega) and grown by (1 + (dt Omega)^2)^(n/2)."""
+    n, steps = 64, 3000
+    z = np.zeros((n, n))
+    c = inputs.Case("inertial", n, n, 10.0, 20.0, z, np.full((n, n), FLUID, np.uint8), np.full((n, n), 3.0),
+                    np.full((n, n), 0.2), np.full((n, n), -0.1), edges=(PERIODIC,) * 4, h_ref=3.0)
+    c.omega = 1.0e-4
+    sim = sim_of(c, precision)
+    sim.step(steps)
+    h, u, v = sim.get_state()
+    w = (0.2 - 0.1j) * (1 - 1j * c.dt * c.omega) ** steps
+    assert abs(np.angle(w / (0.2 - 0.1j))) > 0.05          # a visible turn
+    th, tu = TOL[precision]
+    assert np.abs(h - 3.0).max() <= th * 3.0
+    assert np.abs(u - w.real).max() <= tu * abs(w) and np.abs(v - w.imag).max() <= tu * abs(w)
+
+
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 def test_tidal_strip_400x3(precision):
     """The 400 x 3 strip with free-slip side walls, 2000 steps."""

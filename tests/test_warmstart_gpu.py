@@ -123,21 +123,30 @@ def test_encode_and_decode_constant_fields():
     assert np.allclose(h[fl], Dn[fl] + 0.25, atol=1e-6)
     assert np.allclose(uu[fl], -0.5) and np.allclose(vv[fl], 2.0)
     assert (uu[case.mask == inputs.NOSLIP] == 0).all() and (uu[case.mask == 0] == 0).all()
+    # volume constraint: eta shifted by one constant to sum to the target
+    live = case.mask != 0
+    Df = D.cpu().numpy().astype(np.float64)
+    for target in (0.0, 3.0):
+        h2 = net.decode(y, D, M, scale, target)[0].cpu().numpy()
+        assert abs((h2 - Df)[live].sum() - target) <= 1e-9 * live.sum()
+        d = (h2 - h)[live]
+        assert np.allclose(d, d[0], rtol=0, atol=1e-12)
+        assert (h2[~live] == h[~live]).all()
     net.close()
 
 
-def test_warm_start_reaches_the_same_steady_state_in_fewer_steps():
+def test_warm_start_reaches_the_plain_accuracy_in_fewer_steps():
     """Train on 256 seeded lakes; on 8 unseen lakes the plain iteration from
-    the proposal reaches residual 1e-8 in fewer steps than from rest, and
-    ends at the state the plain run from rest reaches."""
+    the network's proposal gets as close to the FP64 steady state (residual
+    1e-11) as the iteration from rest gets at residual 1e-8, in fewer steps."""
     from paper_1902_02999_gb300.warmstart import WarmStartNet, compare, make_dataset, train
     net = WarmStartNet(res=64, channels=64, dilations=(1, 2, 4, 8, 16, 1), max_batch=16, seed=0)
     cases = [inputs.dish_lake(256, seed=2000 + k) for k in range(256)]
-    X, T, W, scale, _ = make_dataset(net, cases, tol=1e-6, max_steps=80000, chunk=256)
+    X, T, W, scale, _ = make_dataset(net, cases, tol=1e-7, max_steps=80000, chunk=256)
     losses = train(net, X, T, W, epochs=12, batch=16, lr=2e-3)
     assert losses[-1] < 0.3 * losses[0]
     res = compare(net, [inputs.dish_lake(256, seed=k) for k in range(8)], scale, max_steps=200000)
-    assert (res["plain_steps"] > 0).all() and (res["warm_steps"] > 0).all()
-    assert np.median(res["warm_steps"]) < np.median(res["plain_steps"]), res
-    assert res["final_agreement"].max() < 1e-3, res["final_agreement"]
+    assert (res["plain_steps"] > 0).all() and (res["matched_steps"] > 0).all(), res
+    assert np.median(res["matched_steps"]) < np.median(res["plain_steps"]), res
+    assert (res["proposal_error"].max(axis=0) < 1.0).all()
     net.close()
