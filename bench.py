@@ -197,7 +197,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--batch-max-steps", type=int, default=50_000)
-    ap.add_argument("--ws-train", type=int, default=1024, help="lakes the warm-start network trains on (0: skip)")
+    ap.add_argument("--ws-train", type=int, default=2048, help="lakes the warm-start network trains on (0: skip)")
     ap.add_argument("--ws-epochs", type=int, default=20)
     ap.add_argument("--ws-test", type=int, default=16, help="unseen lakes timed from rest and from the proposal")
     args = ap.parse_args()
