@@ -15,7 +15,10 @@ from Eqs. feq-full and Mac.lb.6/7, lake at rest over an arbitrary bed,
 exact mass conservation in closed basins, the uniform-flow fixed point, the
 uniform-force closed form, the viscosity of Eq. mlb-viscosity, mirror
 symmetry, the push form of Eq. lb.1 at tau = 1, and the asymptotic tidal
-solution of Section 4.1 within the paper's level bound.
+solution of Section 4.1 within the paper's level bound.  The distribution
+form with a general relaxation time (``elab_run``) is pinned by its
+reduction to MacLABSWE at tau = 1, the viscosity of Eq. viscosity and exact
+mass conservation (tests/test_oracle_elab.py).
 """
 from __future__ import annotations
 
@@ -74,6 +77,9 @@ def _load():
             lib.oracle_run.argtypes = [pp, d, u8, d, d, d, ctypes.c_int64, ctypes.c_int64]
             lib.oracle_residual.argtypes = [pp, u8, d, d, d, d, d, d, d]
             lib.oracle_step_push.argtypes = [pp, d, d, d, d, d, d, d]
+            lib.oracle_elab_step.argtypes = [pp, d, u8, ctypes.c_double, d, d]
+            lib.oracle_elab_init.argtypes = [pp, d, d, d, d]
+            lib.oracle_elab_moments.argtypes = [pp, d, d, d, d]
             _lib = lib
     return _lib
 
@@ -170,3 +176,30 @@ def step_push(case, h, u, v):
     if rc != 0:
         raise MemoryError("oracle_step_push")
     return h1, u1, v1
+
+
+def elab_run(case, tau: float, nsteps: int, f=None):
+    """eLABSWE (Eq. lb.1) with relaxation time tau: ``nsteps`` steps from the
+    distributions f [9, ny, nx] (default: the equilibrium of the case's
+    initial state).  Returns (h, u, v, f)."""
+    lib = _load()
+    prob = _problem(case)
+    N = case.nx * case.ny
+    if f is None:
+        f = np.empty((9, case.ny, case.nx))
+        h0, u0, v0 = (_arr(a, case) for a in (case.h0, case.u0, case.v0))
+        lib.oracle_elab_init(ctypes.byref(prob), _dp(h0), _dp(u0), _dp(v0), _dp(f))
+    f = np.ascontiguousarray(f, dtype=np.float64).copy()
+    f1 = np.empty_like(f)
+    zb = np.ascontiguousarray(case.zb, dtype=np.float64)
+    mask = np.ascontiguousarray(case.mask, dtype=np.uint8)
+    for _ in range(nsteps):
+        rc = lib.oracle_elab_step(ctypes.byref(prob), _dp(zb), mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                  float(tau), _dp(f), _dp(f1))
+        if rc != 0:
+            raise ValueError("oracle_elab_step: only fluid and solid nodes (%d)" % rc)
+        f, f1 = f1, f
+    h, u, v = (np.empty((case.ny, case.nx)) for _ in range(3))
+    lib.oracle_elab_moments(ctypes.byref(prob), _dp(f), _dp(h), _dp(u), _dp(v))
+    assert f.size == 9 * N
+    return h, u, v, f

@@ -369,3 +369,109 @@ int oracle_step_push(const oracle_problem* p, const double* zb,
     free(f);
     return 0;
 }
+
+/*
+ * eLABSWE with a general relaxation time tau (Eq. lb.1, Section 3), the
+ * distribution form that MacLABSWE reduces when tau = 1 (Eq. Mac.lb.3).
+ * Nine distributions per node, f[a * N + x].  One step, pulled at every
+ * non-solid node x, direction a, source y = x - c_a:
+ *
+ *   f_a(x, t + dt) = f*_a(y) - (g hbar / e^2) C_a [z_b(x) - z_b(y)]
+ *                    + (dt / e^2) C_a e_aj Fbar_j
+ *   f*_a(y)        = f_a(y) - [f_a(y) - f^eq_a(y)] / tau     (collision at y)
+ *
+ * with hbar and Fbar at the old level (R2).  A source that is solid or
+ * behind a bounce-back edge returns the node's own post-collision value of
+ * the opposite direction, f*_abar(x), without bed or force term (R3 with
+ * general tau); a specular source is the mirror image of the node inside,
+ * so it supplies f*_{mirror(a)} there (R4); periodic sources wrap.  No-slip
+ * and Dirichlet nodes are not part of this form: returns -3 if any exists.
+ * Solid nodes keep their distributions.
+ */
+static void elab_moments_at(const double* f, size_t N, size_t x, double e, double* h, double* u, double* v)
+{
+    int a;
+    double hs = 0.0, mx = 0.0, my = 0.0;
+    for (a = 0; a < 9; ++a) {
+        hs += f[(size_t)a * N + x];                  /* Eq. fea-0-h */
+        mx += e * CX[a] * f[(size_t)a * N + x];      /* Eq. fea-0-v */
+        my += e * CY[a] * f[(size_t)a * N + x];
+    }
+    *h = hs;
+    *u = mx / hs;
+    *v = my / hs;
+}
+
+static double elab_post(const oracle_problem* p, const double* f, size_t N, size_t x, int a, double tau)
+{
+    double h, u, v, fe[9];
+    elab_moments_at(f, N, x, p->e, &h, &u, &v);
+    oracle_feq(h, u, v, p->e, p->g, fe);
+    return f[(size_t)a * N + x] - (f[(size_t)a * N + x] - fe[a]) / tau;
+}
+
+int oracle_elab_step(const oracle_problem* p, const double* zb, const uint8_t* type, double tau,
+                     const double* f, double* f1)
+{
+    const int nx = p->nx, ny = p->ny;
+    const double e = p->e, g = p->g, dt = p->dx / p->e;
+    const size_t N = (size_t)nx * ny;
+    int i, j, a;
+    for (j = 0; j < ny; ++j)
+        for (i = 0; i < nx; ++i) {
+            size_t x = (size_t)j * nx + i;
+            if (type[x] != OT_SOLID && type[x] != OT_FLUID) return -3;
+        }
+    for (j = 0; j < ny; ++j) {
+        for (i = 0; i < nx; ++i) {
+            size_t x = (size_t)j * nx + i;
+            double hx, ux, vx, Fx[2];
+            if (type[x] == OT_SOLID) {
+                for (a = 0; a < 9; ++a) f1[(size_t)a * N + x] = f[(size_t)a * N + x];
+                continue;
+            }
+            elab_moments_at(f, N, x, e, &hx, &ux, &vx);
+            oracle_force(p, hx, ux, vx, Fx);
+            f1[x] = elab_post(p, f, N, x, 0, tau);  /* a = 0: no streaming, no terms */
+            for (a = 1; a < 9; ++a) {
+                int si, sj, sx, sy;
+                double val;
+                if (!resolve_source(p, type, i, j, a, &si, &sj, &sx, &sy)) {
+                    val = elab_post(p, f, N, x, opposite(a), tau);
+                } else {
+                    size_t s = (size_t)sj * nx + si;
+                    double hs, us, vs, Fs[2], hbar, Fbx, Fby;
+                    elab_moments_at(f, N, s, e, &hs, &us, &vs);
+                    oracle_force(p, hs, us, vs, Fs);
+                    val = elab_post(p, f, N, s, mirrored(a, sx, sy), tau);
+                    hbar = 0.5 * (hx + hs);
+                    val += -(g * hbar / (e * e)) * coef_C(a) * (zb[x] - zb[s]);
+                    Fbx = 0.5 * (Fx[0] + sx * Fs[0]);
+                    Fby = 0.5 * (Fx[1] + sy * Fs[1]);
+                    val += (dt / (e * e)) * coef_C(a) * (e * CX[a] * Fbx + e * CY[a] * Fby);
+                }
+                f1[(size_t)a * N + x] = val;
+            }
+        }
+    }
+    return 0;
+}
+
+/* f = f^eq(h, u, v) at every node (the equilibrium start of a run) */
+void oracle_elab_init(const oracle_problem* p, const double* h, const double* u, const double* v, double* f)
+{
+    size_t N = (size_t)p->nx * p->ny, x;
+    int a;
+    for (x = 0; x < N; ++x) {
+        double fe[9];
+        oracle_feq(h[x], u[x], v[x], p->e, p->g, fe);
+        for (a = 0; a < 9; ++a) f[(size_t)a * N + x] = fe[a];
+    }
+}
+
+/* h, u, v of every node from the distributions (Eqs. fea-0-h, fea-0-v) */
+void oracle_elab_moments(const oracle_problem* p, const double* f, double* h, double* u, double* v)
+{
+    size_t N = (size_t)p->nx * p->ny, x;
+    for (x = 0; x < N; ++x) elab_moments_at(f, N, x, p->e, &h[x], &u[x], &v[x]);
+}
