@@ -150,6 +150,8 @@ typedef struct {
     int temporal_block;      /* steps per launch of interior tiles: 1 or 2     */
     int64_t clean_tiles;     /* tiles that can take two steps per launch (0 until
                                 maclab_set_temporal_block(sim, 2) classifies them) */
+    double tau;              /* relaxation time: 1 = MacLABSWE, otherwise the
+                                distribution form (maclab_set_relaxation)      */
 } maclab_info;
 
 /* Create a simulation (procedure steps (a)-(b) of Section 3).
@@ -268,6 +270,19 @@ int maclab_set_launch(maclab_t sim, int rows, int blocks);
  * at about a second) makes the next maclab_residual / maclab_get_state
  * return MACLAB_E_CUDA. */
 int maclab_set_step_kernel(maclab_t sim, int kernel);
+
+/* Relaxation time tau of Eq. lb.1 (Section 3).  tau = 1 (the default) is
+ * MacLABSWE: only h, u, v are stored.  Any other tau > 0.5 switches the
+ * handle to the eLABSWE distribution form: nine distributions per node
+ * (stored as perturbations about the rest equilibrium f^eq(D, 0)), started
+ * at the equilibrium of the current state; e and dt stay, so the viscosity
+ * becomes nu = e^2 dt (2 tau - 1) / 6 (Eq. viscosity).  The form has no
+ * no-slip override and no Dirichlet rule: MACLAB_E_ARG on a handle with
+ * no-slip or Dirichlet nodes, or for tau <= 0.5.  maclab_set_state restarts
+ * the distributions at the equilibrium of the new state.  Per node and step
+ * the FP32 form reads 41 bytes and writes 48 (MacLABSWE: 17 and 12).
+ * Synchronises. */
+int maclab_set_relaxation(maclab_t sim, double tau);
 
 /* Temporal blocking (FP32): with k = 2, maclab_step advances "clean"
  * 64 x 16 tiles two steps per launch (a tile is clean when the tile and two

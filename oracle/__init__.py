@@ -77,6 +77,7 @@ def _load():
             lib.oracle_run.argtypes = [pp, d, u8, d, d, d, ctypes.c_int64, ctypes.c_int64]
             lib.oracle_residual.argtypes = [pp, u8, d, d, d, d, d, d, d]
             lib.oracle_step_push.argtypes = [pp, d, d, d, d, d, d, d]
+            lib.oracle_step_newlevel.argtypes = [pp, d, u8, d, d, d, d, d, d, ctypes.c_double]
             lib.oracle_elab_step.argtypes = [pp, d, u8, ctypes.c_double, d, d]
             lib.oracle_elab_init.argtypes = [pp, d, d, d, d]
             lib.oracle_elab_moments.argtypes = [pp, d, d, d, d]
@@ -203,3 +204,26 @@ def elab_run(case, tau: float, nsteps: int, f=None):
     lib.oracle_elab_moments(ctypes.byref(prob), _dp(f), _dp(h), _dp(u), _dp(v))
     assert f.size == 9 * N
     return h, u, v, f
+
+
+def run_newlevel(case, nsteps: int, state=None, n0: int = 0):
+    """Like run(), with hbar at the new time level (Eq. h-bar as written,
+    solved node by node).  Returns (h, u, v)."""
+    lib = _load()
+    if state is None:
+        state = (case.h0, case.u0, case.v0)
+    h, u, v = (_arr(a, case) for a in state)
+    h1, u1, v1 = np.empty_like(h), np.empty_like(h), np.empty_like(h)
+    zb = np.ascontiguousarray(case.zb, dtype=np.float64)
+    mask = np.ascontiguousarray(case.mask, dtype=np.uint8)
+    for k in range(nsteps):
+        rc = lib.oracle_step_newlevel(ctypes.byref(_problem(case)), _dp(zb),
+                                      mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                      _dp(h), _dp(u), _dp(v), _dp(h1), _dp(u1), _dp(v1),
+                                      float((n0 + k + 1) * case.dt))
+        if rc != 0:
+            raise ValueError("oracle_step_newlevel failed (%d)" % rc)
+        h, h1 = h1, h
+        u, u1 = u1, u
+        v, v1 = v1, v
+    return h, u, v

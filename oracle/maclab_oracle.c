@@ -475,3 +475,108 @@ void oracle_elab_moments(const oracle_problem* p, const double* f, double* h, do
     size_t N = (size_t)p->nx * p->ny, x;
     for (x = 0; x < N; ++x) elab_moments_at(f, N, x, p->e, &h[x], &u[x], &v[x]);
 }
+
+/*
+ * Variant: hbar at the new time level, as Eq. h-bar writes it for the link
+ * that carries f_a from y = x - c_a into x:
+ *     hbar_a = (h(x, t + dt) + h(y, t)) / 2.
+ * The bed term is the only place h(x, t + dt) enters, and it enters
+ * linearly, so the new depth of each node solves one linear equation:
+ *     h1 = A - (1/2) sum_a k_a h(y_a) - (1/2) h1 sum_a k_a,
+ *     k_a = (g / e^2) C_a [z_b(x) - z_b(y_a)]   (usable links only),
+ * A being every other term of Eq. Mac.lb.6; the momentum of Eq. Mac.lb.7
+ * follows with the same hbar.  Everything else (links, forces, no-slip and
+ * Dirichlet rules) is as in oracle_step.
+ */
+int oracle_step_newlevel(const oracle_problem* p, const double* zb, const uint8_t* type,
+                         const double* h, const double* u, const double* v,
+                         double* h1, double* u1, double* v1, double t_next)
+{
+    const int nx = p->nx, ny = p->ny;
+    const double e = p->e, g = p->g, dt = p->dx / p->e;
+    int i, j, a;
+    for (j = 0; j < ny; ++j) {
+        for (i = 0; i < nx; ++i) {
+            size_t x = (size_t)j * nx + i;
+            double fx[9], Fx[2], A, Ax, Ay, Pk, Px, Py, K, Kx, Ky, hn;
+            if (type[x] == OT_SOLID) {
+                h1[x] = h[x];
+                u1[x] = u[x];
+                v1[x] = v[x];
+                continue;
+            }
+            oracle_feq(h[x], u[x], v[x], e, g, fx);
+            oracle_force(p, h[x], u[x], v[x], Fx);
+            A = fx[0];
+            Ax = Ay = 0.0;
+            Pk = Px = Py = 0.0;   /* -(1/2) sum k_a h(y_a), weighted by 1, e c_ax, e c_ay */
+            K = Kx = Ky = 0.0;    /* sum k_a, weighted likewise */
+            for (a = 1; a < 9; ++a) {
+                double ex = e * CX[a], ey = e * CY[a];
+                int si, sj, sx, sy;
+                double fa, k;
+                if (!resolve_source(p, type, i, j, a, &si, &sj, &sx, &sy)) {
+                    fa = fx[opposite(a)];            /* R3 bounce-back */
+                    A += fa;
+                    Ax += ex * fa;
+                    Ay += ey * fa;
+                    continue;
+                }
+                {
+                    size_t s = (size_t)sj * nx + si;
+                    double fs[9], Fs[2], Fbar_x, Fbar_y;
+                    oracle_feq(h[s], u[s], v[s], e, g, fs);
+                    oracle_force(p, h[s], u[s], v[s], Fs);
+                    Fbar_x = 0.5 * (Fx[0] + sx * Fs[0]);
+                    Fbar_y = 0.5 * (Fx[1] + sy * Fs[1]);
+                    fa = fs[mirrored(a, sx, sy)] +
+                         (dt / (e * e)) * coef_C(a) * (ex * Fbar_x + ey * Fbar_y);
+                    A += fa;
+                    Ax += ex * fa;
+                    Ay += ey * fa;
+                    k = (g / (e * e)) * coef_C(a) * (zb[x] - zb[s]);
+                    Pk += -0.5 * k * h[s];
+                    Px += -0.5 * ex * k * h[s];
+                    Py += -0.5 * ey * k * h[s];
+                    K += k;
+                    Kx += ex * k;
+                    Ky += ey * k;
+                }
+            }
+            hn = (A + Pk) / (1.0 + 0.5 * K);
+            h1[x] = hn;
+            u1[x] = (Ax + Px - 0.5 * hn * Kx) / hn;
+            v1[x] = (Ay + Py - 0.5 * hn * Ky) / hn;
+            if (type[x] == OT_NOSLIP) {              /* R5 */
+                u1[x] = 0.0;
+                v1[x] = 0.0;
+            }
+        }
+    }
+    /* R5 second pass, as in oracle_step */
+    for (j = 0; j < ny; ++j) {
+        for (i = 0; i < nx; ++i) {
+            size_t x = (size_t)j * nx + i, n1;
+            int di, dj, ed;
+            if (type[x] < OT_DIR_H || type[x] > OT_DIR_HU) continue;
+            ed = dirichlet_edge(p, i, j, &di, &dj);
+            if (ed < 0 || i + di < 0 || i + di >= nx || j + dj < 0 || j + dj >= ny) return -1;
+            n1 = (size_t)(j + dj) * nx + (i + di);
+            if (type[n1] == OT_SOLID || type[n1] >= OT_DIR_H) return -1;
+            if (type[x] == OT_DIR_H) {
+                h1[x] = wave(p->bc[ed][0], t_next);
+                u1[x] = u1[n1];
+                v1[x] = v1[n1];
+            } else {
+                double qx = wave(p->bc[ed][1], t_next), qy = wave(p->bc[ed][2], t_next);
+                if (type[x] == OT_DIR_Q)
+                    h1[x] = h1[n1];
+                else
+                    h1[x] = wave(p->bc[ed][0], t_next);
+                u1[x] = qx / h1[x];
+                v1[x] = qy / h1[x];
+            }
+        }
+    }
+    return 0;
+}

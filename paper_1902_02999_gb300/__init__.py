@@ -233,6 +233,14 @@ class Simulation:
         self._check(self._lib.maclab_set_step_kernel(self._h, code))
         self.info["step_kernel"] = code
 
+    def set_relaxation(self, tau: float) -> None:
+        """Relaxation time of Eq. lb.1: 1 = MacLABSWE, otherwise the
+        distribution form (fluid and solid nodes only)."""
+        self._check(self._lib.maclab_set_relaxation(self._h, float(tau)))
+        info = _abi.Info()
+        self._check(self._lib.maclab_get_info(self._h, ctypes.byref(info)))
+        self.info = {f: getattr(info, f) for f, _ in _abi.Info._fields_}
+
     def set_temporal_block(self, k: int) -> None:
         """Steps per launch of clean interior tiles: 1, or 2 (FP32)."""
         self._check(self._lib.maclab_set_temporal_block(self._h, int(k)))

@@ -91,6 +91,9 @@ struct maclab_s {
     int* other_list = nullptr; // the rest
     void* mid[3] = {nullptr, nullptr, nullptr};  // scratch state (eta, u, v) at the middle step
     int graph_end[2] = {0, 1}; // buffer parity after a replay of graph[parity]
+    double tau = 1.0;          // relaxation time; != 1: distribution form
+    bool elab = false;
+    void* gdist[2] = {nullptr, nullptr};  // 9 planes of [ny][pitch] per buffer
     std::vector<cudaEvent_t> events;  // pairs around step-kernel launches
     size_t events_used = 0;
     std::string err;
@@ -223,7 +226,21 @@ int launch_step(maclab_t s)
         }
     }
     const int b = 1 - s->cur;
-    if (s->kernel != MACLAB_KERNEL_STRIP) {
+    if (s->elab) {
+        const int tx = (s->grid.nx + tile::TX - 1) / tile::TX, ty = (s->grid.ny + tile::TY - 1) / tile::TY;
+        const size_t plane = (size_t)s->pitch * s->grid.ny;
+        const size_t smem = sizeof(elab::Smem<T>);
+        const T omega = (T)(1.0 / s->tau);
+        switch (s->fmode) {
+#define MACLAB_FM(m)                                                                                        \
+    case m:                                                                                                 \
+        step_elab_kernel<T, m><<<tx * ty, tile::THREADS, smem, s->stream>>>(f, (const T*)s->gdist[s->cur], \
+                                                                          (T*)s->gdist[b], plane, omega, tx); \
+        break;
+            MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
+#undef MACLAB_FM
+        }
+    } else if (s->kernel != MACLAB_KERNEL_STRIP) {
         // fast nodes and (when fused) Dirichlet nodes in one launch; nodes with a
         // bounce-back link in a second launch when there are any
         const int tx = (s->grid.nx + tile::TX - 1) / tile::TX, ty = (s->grid.ny + tile::TY - 1) / tile::TY;
@@ -366,7 +383,7 @@ int launch_pair(maclab_t s)
 // n steps: pairs where temporal blocking is on, the last step always single
 int advance(maclab_t s, int64_t n)
 {
-    const bool pairs_on = s->tblock == 2 && s->prec == MACLAB_F32;
+    const bool pairs_on = s->tblock == 2 && s->prec == MACLAB_F32 && !s->elab;
     const int64_t pairs = pairs_on && n >= 3 ? (n - 1) / 2 : 0;
     for (int64_t k = 0; k < pairs; ++k) {
         int rc = launch_pair(s);
@@ -451,6 +468,26 @@ int grid_blocks(size_t total, int threads, int cap)
 {
     size_t b = (total + threads - 1) / threads;
     return (int)std::max<size_t>(1, std::min<size_t>(b, (size_t)cap));
+}
+
+// Distribution form: restart the distributions at the equilibrium of the
+// current macroscopic state (buffer s->cur).
+int elab_restart(maclab_t s)
+{
+    const size_t plane = (size_t)s->pitch * s->grid.ny;
+    const int a = s->cur;
+    if (s->prec == MACLAB_F32)
+        elab_init_kernel<float><<<grid_blocks(plane, 256, 4096), 256, 0, s->stream>>>(
+            (const float*)s->eta[a], (const float*)s->u[a], (const float*)s->v[a], (const float*)s->D, s->type,
+            s->grid.nx, s->grid.ny, s->pitch, make_coef<float>(s->params, s->e, s->dt), (float*)s->gdist[a], plane);
+    else
+        elab_init_kernel<double><<<grid_blocks(plane, 256, 4096), 256, 0, s->stream>>>(
+            (const double*)s->eta[a], (const double*)s->u[a], (const double*)s->v[a], (const double*)s->D, s->type,
+            s->grid.nx, s->grid.ny, s->pitch, make_coef<double>(s->params, s->e, s->dt), (double*)s->gdist[a], plane);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "distribution restart");
+    return MACLAB_OK;
 }
 
 template <typename T>
@@ -1014,7 +1051,9 @@ int maclab_set_state(maclab_t s, const double* h, const double* u, const double*
 {
     if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
     if (!h || !u || !v) return fail(s, MACLAB_E_ARG, "h, u and v are required");
-    return s->prec == MACLAB_F32 ? upload_state<float>(s, h, u, v) : upload_state<double>(s, h, u, v);
+    const int rc = s->prec == MACLAB_F32 ? upload_state<float>(s, h, u, v) : upload_state<double>(s, h, u, v);
+    if (rc != MACLAB_OK || !s->elab) return rc;
+    return elab_restart(s);
 }
 
 int maclab_residual(maclab_t s, double out[4])
@@ -1189,6 +1228,50 @@ int maclab_set_step_kernel(maclab_t s, int kernel)
     return MACLAB_OK;
 }
 
+int maclab_set_relaxation(maclab_t s, double tau)
+{
+    if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    if (!(tau > 0.5) || !std::isfinite(tau)) return fail(s, MACLAB_E_ARG, "tau must be finite and > 0.5");
+    if (tau == 1.0) {
+        s->tau = 1.0;
+        s->elab = false;
+        drop_graphs(s);
+        return MACLAB_OK;
+    }
+    const int nx = s->grid.nx, ny = s->grid.ny, pitch = s->pitch;
+    const size_t NP = (size_t)pitch * ny;
+    std::vector<uint8_t> type(NP);
+    cudaError_t e = cudaMemcpyAsync(type.data(), s->type, NP, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "relaxation setup");
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const int kind = type[(size_t)y * pitch + x] & KIND_MASK;
+            if (kind != K_SOLID && kind != K_FLUID)
+                return fail(s, MACLAB_E_ARG, "the distribution form takes fluid and solid nodes only");
+        }
+    for (int k = 0; k < 2; ++k)
+        if (!s->gdist[k] && !(s->gdist[k] = dev_alloc(s, 9 * NP * s->esize)))
+            return fail(s, MACLAB_E_NOMEM, "distribution buffers");
+    cudaError_t ae = cudaSuccess;
+    const size_t smem = s->prec == MACLAB_F32 ? sizeof(elab::Smem<float>) : sizeof(elab::Smem<double>);
+#define MACLAB_ATTR(m)                                                                                        \
+    if (ae == cudaSuccess)                                                                                    \
+        ae = s->prec == MACLAB_F32                                                                            \
+                 ? cudaFuncSetAttribute(step_elab_kernel<float, m>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                        (int)smem)                                                            \
+                 : cudaFuncSetAttribute(step_elab_kernel<double, m>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                        (int)smem);
+    MACLAB_ATTR(0) MACLAB_ATTR(1) MACLAB_ATTR(2) MACLAB_ATTR(3) MACLAB_ATTR(4) MACLAB_ATTR(5) MACLAB_ATTR(6)
+    MACLAB_ATTR(7)
+#undef MACLAB_ATTR
+    if (ae != cudaSuccess) return cuda_fail(s, ae, "cudaFuncSetAttribute");
+    s->tau = tau;
+    s->elab = true;
+    drop_graphs(s);
+    return elab_restart(s);
+}
+
 int maclab_set_temporal_block(maclab_t s, int k)
 {
     if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
@@ -1297,6 +1380,7 @@ int maclab_get_info(maclab_t s, maclab_info* info)
     info->dirichlet_fused = (s->kernel != MACLAB_KERNEL_STRIP && s->dir_fused) ? 1 : 0;
     info->temporal_block = s->tblock;
     info->clean_tiles = s->n_clean;
+    info->tau = s->tau;
     return MACLAB_OK;
 }
 

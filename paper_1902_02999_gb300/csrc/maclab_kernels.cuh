@@ -1461,6 +1461,175 @@ step_tile_tma_kernel(const __grid_constant__ Fields<float> f, const __grid_const
 }
 
 // ---------------------------------------------------------------------------
+// eLABSWE with a general relaxation time tau (Eq. lb.1): nine distributions
+// per node, stored as g_a = f_a - f^eq_a(D, 0) (perturbations about the rest
+// equilibrium, so that a lake at rest is g = 0 exactly).  In these variables
+// one step of Eq. lb.1, pulled at node x from y = x - c_a, reads
+//   g_a(x, t + dt) = g*_a(y) + lambda_a [ -G6 (eta_x + eta_y)(D_y - D_x)
+//                                          + KF c_a . (F_x + F_y) ]
+//   g*_a(y)        = g_a(y) + (o_a(y) - g_a(y)) / tau,
+//   o_a            = f^eq_a(h, u) - f^eq_a(D, 0)      (Eq. feq-full),
+// the rest-equilibrium difference f^eq_a(D_y, 0) - f^eq_a(D_x, 0) having
+// cancelled the D-only part of the bed term.  A source that is solid or
+// behind a bounce-back edge gives g*_abar(x); a specular source is the
+// mirror node, supplying g*_{mirror(a)} there with its force mirrored.
+// h = D + sum_a g_a and h u = e sum_a c_a g_a (Eqs. fea-0-h, fea-0-v).
+// A block owns a 64 x 16 tile; phase A collides the tile and its one-node
+// halo into shared memory, phase B streams.
+namespace elab {
+template <typename T>
+struct Smem {
+    T gs[9][tile::IR][tile::IW];                   // post-collision g*, direction-mapped for mirrors
+    typename Vec2<T>::type ed[tile::IR][tile::IW]; // (eta, D)
+    typename Vec2<T>::type F[tile::IR][tile::IW];  // force, mirrored for specular ghosts
+    uint8_t use[tile::IR][tile::IW];               // usable source
+};
+template <typename T> struct MinBlocks { static constexpr int value = 3; };
+template <> struct MinBlocks<double> { static constexpr int value = 1; };
+}  // namespace elab
+
+// direction with lattice vector (sx c_x, sy c_y) for mirror bits (1: x, 2: y)
+__device__ __forceinline__ int mirror_dir(int a, uint8_t fl)
+{
+    const int cx = (fl & 1) ? -c_cx[a] : c_cx[a], cy = (fl & 2) ? -c_cy[a] : c_cy[a];
+#pragma unroll
+    for (int b = 0; b < 9; ++b)
+        if (c_cx[b] == cx && c_cy[b] == cy) return b;
+    return a;
+}
+
+// o_a = f^eq_a(h, u, v) - f^eq_a(D, 0), a = 0..8, and the force at a node
+template <typename T, int FM>
+__device__ __forceinline__ void elab_equilibrium(const Coef<T>& c, T eta, T D, T u, T v, T (&o)[9], T& Fx, T& Fy)
+{
+    const T h = D + eta;
+    const T uu = u * u + v * v;
+    const T ge = c.G6 * eta * (T(2) * D + eta);
+    const T ku = c.K6 * h * uu;
+    o[0] = eta - T(5) * ge - T(4) * ku;
+#pragma unroll
+    for (int a = 1; a < 9; ++a) {
+        const T cu = T(c_cx[a]) * u + T(c_cy[a]) * v;
+        const T lam = (a & 1) ? T(1) : T(0.25);
+        o[a] = lam * (ge + h * cu * c.k3 + h * cu * cu * c.k2 - ku);
+    }
+    Fx = (FM & F_WIND) ? c.wfx : T(0);
+    Fy = (FM & F_WIND) ? c.wfy : T(0);
+    if (FM & F_CORIOLIS) {
+        Fx += c.Om * h * v;
+        Fy -= c.Om * h * u;
+    }
+    if (FM & F_FRICTION) {
+        const T cbs = c.Cb * sqrt(uu);
+        Fx -= cbs * u;
+        Fy -= cbs * v;
+    }
+}
+
+// gin / gout: 9 planes of [ny][pitch]; f.eta1 / u1 / v1 receive the new
+// macroscopic state; omega = 1 / tau
+template <typename T, int FM>
+__global__ void __launch_bounds__(tile::THREADS, elab::MinBlocks<T>::value)
+step_elab_kernel(const __grid_constant__ Fields<T> f, const T* __restrict__ gin, T* __restrict__ gout, size_t plane,
+                 T omega, int tiles_x)
+{
+    using namespace tile;
+    using V2 = typename Vec2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_elab[];
+    elab::Smem<T>& sm = *reinterpret_cast<elab::Smem<T>*>(smem_elab);
+    const Coef<T>& K = f.c;
+    const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY;
+    // ---- phase A: collide the tile and its halo (window rows y0-1 .. y0+16,
+    // columns x0-2 .. x0+65)
+    for (int p = threadIdx.x; p < IR * IW; p += THREADS) {
+        const int r = p / IW, c = p % IW;
+        uint8_t fl = 0;
+        const int rr = resolve_index(y0 - 1 + r, f.ny, f.edge[2], f.edge[3], 2, fl);
+        const int cc = resolve_index(x0 - 2 + c, f.nx, f.edge[0], f.edge[1], 1, fl);
+        bool ok = rr >= 0 && cc >= 0;
+        const size_t m = ok ? (size_t)rr * f.pitch + cc : 0;
+        ok = ok && (f.type[m] & KIND_MASK) != K_SOLID;
+        sm.use[r][c] = ok ? 1 : 0;
+        if (!ok) continue;
+        T g[9];
+#pragma unroll
+        for (int b = 0; b < 9; ++b) g[b] = gin[b * plane + m];
+        T eta = T(0), mx = T(0), my = T(0);
+#pragma unroll
+        for (int b = 0; b < 9; ++b) {
+            eta += g[b];
+            mx += T(c_cx[b]) * g[b];
+            my += T(c_cy[b]) * g[b];
+        }
+        const T D = f.D[m];
+        const T inv = T(1) / (D + eta);
+        const T u = K.e * mx * inv, v = K.e * my * inv;
+        T o[9], Fx, Fy;
+        elab_equilibrium<T, FM>(K, eta, D, u, v, o, Fx, Fy);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const int b = fl ? mirror_dir(a, fl) : a;
+            sm.gs[a][r][c] = g[b] + omega * (o[b] - g[b]);
+        }
+        sm.ed[r][c] = V2{eta, D};
+        sm.F[r][c] = V2{(fl & 1) ? -Fx : Fx, (fl & 2) ? -Fy : Fy};
+    }
+    __syncthreads();
+    // ---- phase B: stream into the tile's nodes
+    for (int q = threadIdx.x; q < TX * TY; q += THREADS) {
+        const int r = 1 + q / TX, c = 2 + q % TX;
+        const int x = x0 + q % TX, y = y0 + q / TX;
+        if (x >= f.nx || y >= f.ny || !sm.use[r][c]) continue;
+        const V2 me = sm.ed[r][c], Fm = sm.F[r][c];
+        T gn[9];
+        gn[0] = sm.gs[0][r][c];
+#pragma unroll
+        for (int a = 1; a < 9; ++a) {
+            const int pr = r - c_cy[a], pc = c - c_cx[a];
+            if (sm.use[pr][pc]) {
+                const V2 ep = sm.ed[pr][pc], Fp = sm.F[pr][pc];
+                const T lam = (a & 1) ? T(1) : T(0.25);
+                const T bed = -K.G6 * (me.x + ep.x) * (ep.y - me.y);
+                const T frc = K.KF * (T(c_cx[a]) * (Fm.x + Fp.x) + T(c_cy[a]) * (Fm.y + Fp.y));
+                gn[a] = sm.gs[a][pr][pc] + lam * (bed + frc);
+            } else {
+                gn[a] = sm.gs[a == 0 ? 0 : ((a + 3) & 7) + 1][r][c];
+            }
+        }
+        T eta = T(0), mx = T(0), my = T(0);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            eta += gn[a];
+            mx += T(c_cx[a]) * gn[a];
+            my += T(c_cy[a]) * gn[a];
+        }
+        const size_t idx = (size_t)y * f.pitch + x;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) gout[a * plane + idx] = gn[a];
+        const T inv = T(1) / (me.y + eta);
+        f.eta1[idx] = eta;
+        f.u1[idx] = K.e * mx * inv;
+        f.v1[idx] = K.e * my * inv;
+    }
+}
+
+// g = o(eta, u, v) at every non-solid node (the equilibrium start), 0 at solids
+template <typename T>
+__global__ void elab_init_kernel(const T* eta, const T* u, const T* v, const T* D, const uint8_t* type, int nx, int ny,
+                                 int pitch, Coef<T> c, T* g, size_t plane)
+{
+    const size_t n = (size_t)ny * pitch;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(k % pitch);
+        T o[9], Fx, Fy;
+        const bool live = x < nx && (type[k] & KIND_MASK) != K_SOLID;
+        if (live) elab_equilibrium<T, 0>(c, eta[k], D[k], u[k], v[k], o, Fx, Fy);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) g[a * plane + k] = live ? o[a] : T(0);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Batched step: one launch advances every active instance of a batch.  The
 // tiles of all instances form one list; block b updates tile tile_local[b]
 // of instance tile_inst[b] with that instance's fields and coefficients.
