@@ -322,7 +322,7 @@ def main():
     # the eLABSWE distribution form (Eq. lb.1, tau = 0.8) against MacLABSWE
     # on the same grid made periodic along x and all fluid (the form has no
     # Dirichlet rule): bytes and time per node update
-    dist = None
+    dform = None
     if not args.no_extra and args.precision == "f32":
         import numpy as np
         pc = inputs.bump_channel(args.nx, args.ny, seed=0)
@@ -330,7 +330,7 @@ def main():
         pc.edges = (inputs.PERIODIC, inputs.PERIODIC, inputs.SPECULAR, inputs.SPECULAR)
         pc.bc = np.zeros_like(np.asarray(pc.bc, dtype=np.float64))
         ds = Simulation.from_case(pc, precision="f32")
-        dist = {"workload": "bump_channel_%dx%d, periodic in x, all fluid" % (args.nx, args.ny)}
+        dform = {"workload": "bump_channel_%dx%d, periodic in x, all fluid" % (args.nx, args.ny)}
         n_dist = max(200, args.steps // 10)
         for label, tau, bpn in (("macroscopic", 1.0, 29), ("distribution_tau_0.8", 0.8, 89)):
             ds.set_relaxation(tau)
@@ -341,7 +341,7 @@ def main():
             kms, kl = ds.get_profile()
             ds.set_profiling(False)
             per = kms / max(1, kl)
-            dist[label] = {"ms_per_step": per, "mlups": pc.nodes / (per / 1e3) / 1e6, "bytes_per_node": bpn,
+            dform[label] = {"ms_per_step": per, "mlups": pc.nodes / (per / 1e3) / 1e6, "bytes_per_node": bpn,
                            "achieved_gbs": bpn * pc.nodes / (per / 1e3) / 1e9}
         ds.close()
 
@@ -463,7 +463,7 @@ def main():
                            "step_kernel": KERNEL_LABEL[info["step_kernel"]]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "steady_state": steady, "f64": f64, "batched": batched, "warm_start": warm,
-                "temporal_block": tblock, "distribution_form": dist,
+                "temporal_block": tblock, "distribution_form": dform,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)
     sim.close()

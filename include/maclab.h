@@ -152,6 +152,7 @@ typedef struct {
                                 maclab_set_temporal_block(sim, 2) classifies them) */
     double tau;              /* relaxation time: 1 = MacLABSWE, otherwise the
                                 distribution form (maclab_set_relaxation)      */
+    int hbar_level;          /* 0: hbar at the old level, 1: at the new level */
 } maclab_info;
 
 /* Create a simulation (procedure steps (a)-(b) of Section 3).
@@ -283,6 +284,16 @@ int maclab_set_step_kernel(maclab_t sim, int kernel);
  * the FP32 form reads 41 bytes and writes 48 (MacLABSWE: 17 and 12).
  * Synchronises. */
 int maclab_set_relaxation(maclab_t sim, double tau);
+
+/* Time level of hbar in the bed-slope term (Eq. h-bar).  0 (default): both
+ * depths at the old level, hbar = (h(x, t) + h(y, t)) / 2, which keeps the
+ * step explicit.  1: as Eq. h-bar writes it, hbar = (h(x, t + dt) + h(y, t))
+ * / 2 on the link from y into x; the bed terms are linear in the node's new
+ * depth, which is solved for node by node (no iteration).  Level 1 runs
+ * every node through the per-link kernel (slower than the fused tile
+ * kernel) and is refused (MACLAB_E_ARG) in the distribution form.  The first
+ * call with level 1 lists the nodes (synchronises). */
+int maclab_set_hbar_level(maclab_t sim, int level);
 
 /* Temporal blocking (FP32): with k = 2, maclab_step advances "clean"
  * 64 x 16 tiles two steps per launch (a tile is clean when the tile and two

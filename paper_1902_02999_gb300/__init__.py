@@ -233,6 +233,11 @@ class Simulation:
         self._check(self._lib.maclab_set_step_kernel(self._h, code))
         self.info["step_kernel"] = code
 
+    def set_hbar_level(self, level: int) -> None:
+        """hbar of the bed term at the old (0) or the new (1) time level."""
+        self._check(self._lib.maclab_set_hbar_level(self._h, int(level)))
+        self.info["hbar_level"] = int(level)
+
     def set_relaxation(self, tau: float) -> None:
         """Relaxation time of Eq. lb.1: 1 = MacLABSWE, otherwise the
         distribution form (fluid and solid nodes only)."""

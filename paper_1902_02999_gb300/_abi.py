@@ -46,7 +46,7 @@ class Info(ctypes.Structure):
                 ("n_dirichlet", c_int64), ("n_fluid", c_int64), ("n_fast", c_int64),
                 ("device_bytes", c_size_t), ("tile_rows", c_int), ("step_kernel", c_int),
                 ("dirichlet_fused", c_int), ("temporal_block", c_int), ("clean_tiles", c_int64),
-                ("tau", c_double)]
+                ("tau", c_double), ("hbar_level", c_int)]
 
 
 class WSConfig(ctypes.Structure):
@@ -79,6 +79,7 @@ PROTOTYPES = [
     ("maclab_set_step_kernel", c_int, [c_void_p, c_int]),
     ("maclab_set_temporal_block", c_int, [c_void_p, c_int]),
     ("maclab_set_relaxation", c_int, [c_void_p, c_double]),
+    ("maclab_set_hbar_level", c_int, [c_void_p, c_int]),
     ("maclab_set_profiling", c_int, [c_void_p, c_int]),
     ("maclab_get_profile", c_int, [c_void_p, P(c_double), P(c_int64)]),
     ("maclab_get_info", c_int, [c_void_p, P(Info)]),

@@ -92,6 +92,9 @@ struct maclab_s {
     void* mid[3] = {nullptr, nullptr, nullptr};  // scratch state (eta, u, v) at the middle step
     int graph_end[2] = {0, 1}; // buffer parity after a replay of graph[parity]
     double tau = 1.0;          // relaxation time; != 1: distribution form
+    bool newlevel = false;     // hbar at the new time level (per-link kernel for every node)
+    int* all_list = nullptr;   // every non-solid node (j * nx + i)
+    int n_all = 0;
     bool elab = false;
     void* gdist[2] = {nullptr, nullptr};  // 9 planes of [ny][pitch] per buffer
     std::vector<cudaEvent_t> events;  // pairs around step-kernel launches
@@ -240,6 +243,9 @@ int launch_step(maclab_t s)
             MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
 #undef MACLAB_FM
         }
+    } else if (s->newlevel) {
+        if (s->n_all > 0)
+            step_general_kernel<T, true><<<(s->n_all + 127) / 128, 128, 0, s->stream>>>(f, s->all_list, s->n_all);
     } else if (s->kernel != MACLAB_KERNEL_STRIP) {
         // fast nodes and (when fused) Dirichlet nodes in one launch; nodes with a
         // bounce-back link in a second launch when there are any
@@ -287,7 +293,7 @@ int launch_step(maclab_t s)
                                                                                       s->n_general);
     }
     if (s->profiling) cudaEventRecord(ev1, s->stream);
-    if (s->n_dir > 0 && !(s->kernel != MACLAB_KERNEL_STRIP && s->dir_fused))
+    if (s->n_dir > 0 && !s->elab && (s->newlevel || !(s->kernel != MACLAB_KERNEL_STRIP && s->dir_fused)))
         dirichlet_kernel<T><<<(s->n_dir + 127) / 128, 128, 0, s->stream>>>(
             (T*)s->eta[b], (T*)s->u[b], (T*)s->v[b], (const T*)s->D, s->D64, s->dir, s->n_dir, bv);
     cudaError_t e = cudaGetLastError();
@@ -383,7 +389,7 @@ int launch_pair(maclab_t s)
 // n steps: pairs where temporal blocking is on, the last step always single
 int advance(maclab_t s, int64_t n)
 {
-    const bool pairs_on = s->tblock == 2 && s->prec == MACLAB_F32 && !s->elab;
+    const bool pairs_on = s->tblock == 2 && s->prec == MACLAB_F32 && !s->elab && !s->newlevel;
     const int64_t pairs = pairs_on && n >= 3 ? (n - 1) / 2 : 0;
     for (int64_t k = 0; k < pairs; ++k) {
         int rc = launch_pair(s);
@@ -1228,9 +1234,39 @@ int maclab_set_step_kernel(maclab_t s, int kernel)
     return MACLAB_OK;
 }
 
+int maclab_set_hbar_level(maclab_t s, int level)
+{
+    if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    if (level != 0 && level != 1) return fail(s, MACLAB_E_ARG, "hbar level must be 0 or 1");
+    if (level == 1 && s->elab) return fail(s, MACLAB_E_ARG, "the new-level hbar is not offered in the distribution form");
+    if (level == 1 && !s->all_list) {
+        const int nx = s->grid.nx, ny = s->grid.ny, pitch = s->pitch;
+        std::vector<uint8_t> type((size_t)pitch * ny);
+        cudaError_t e = cudaMemcpyAsync(type.data(), s->type, type.size(), cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "hbar level setup");
+        std::vector<int> all;
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x)
+                if ((type[(size_t)y * pitch + x] & KIND_MASK) != K_SOLID) all.push_back(y * nx + x);
+        if (!all.empty()) {
+            if (!(s->all_list = (int*)dev_alloc(s, all.size() * sizeof(int))))
+                return fail(s, MACLAB_E_NOMEM, "node list");
+            e = cudaMemcpyAsync(s->all_list, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, s->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+            if (e != cudaSuccess) return cuda_fail(s, e, "hbar level setup");
+        }
+        s->n_all = (int)all.size();
+    }
+    s->newlevel = level == 1;
+    drop_graphs(s);
+    return MACLAB_OK;
+}
+
 int maclab_set_relaxation(maclab_t s, double tau)
 {
     if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    if (s->newlevel && tau != 1.0) return fail(s, MACLAB_E_ARG, "the distribution form takes the old-level hbar");
     if (!(tau > 0.5) || !std::isfinite(tau)) return fail(s, MACLAB_E_ARG, "tau must be finite and > 0.5");
     if (tau == 1.0) {
         s->tau = 1.0;
@@ -1381,6 +1417,7 @@ int maclab_get_info(maclab_t s, maclab_info* info)
     info->temporal_block = s->tblock;
     info->clean_tiles = s->n_clean;
     info->tau = s->tau;
+    info->hbar_level = s->newlevel ? 1 : 0;
     return MACLAB_OK;
 }
 

@@ -722,8 +722,10 @@ __device__ __forceinline__ T feq_diff(const Coef<T>& c, const NodeQ<T>& n, int c
 
 // Update of one node (i, j) with the links resolved one by one.  Every
 // rounding is spelled out, so the result does not depend on which kernel
-// the code is inlined into.
-template <typename T>
+// the code is inlined into.  NEW: hbar at the new time level (Eq. h-bar as
+// written, hbar = (h(x, t + dt) + h(y, t)) / 2): the bed terms are linear in
+// the new eta of the node, which is then solved for directly.
+template <typename T, bool NEW = false>
 __device__ __forceinline__ void general_node(const Fields<T>& f, int i, int j)
 {
     using O = Op<T>;
@@ -733,6 +735,7 @@ __device__ __forceinline__ void general_node(const Fields<T>& f, int i, int j)
     T Sh = O::fma(-O::mul(T(5), O::mul(c.G6, X.eta)), O::fma(T(2), X.D, X.eta), X.eta);
     Sh = O::fma(-O::mul(T(4), c.K6), O::mul(X.h, X.uu), Sh);
     T Sx = T(0), Sy = T(0);
+    T Q = T(0), Qx = T(0), Qy = T(0);  // new level: sum of lambda G6 (D_x - D_y), weighted by 1, c_x, c_y
 #pragma unroll 1
     for (int a = 1; a < 9; ++a) {
         const int cx = c_cx[a], cy = c_cy[a];
@@ -751,7 +754,16 @@ __device__ __forceinline__ void general_node(const Fields<T>& f, int i, int j)
             w = feq_diff(c, X, -cx, -cy);
         } else {
             const NodeQ<T> Y = node_q(f, s, flip);  // the mirrored node when flip != 0
-            const T bed = O::mul(O::mul(lam, c.G6), O::mul(O::add(X.eta, Y.eta), O::sub(X.D, Y.D)));
+            T bed;
+            if (NEW) {
+                const T q = O::mul(O::mul(lam, c.G6), O::sub(X.D, Y.D));
+                bed = O::mul(q, Y.eta);  // the source half; the node's half waits for its new eta
+                Q = O::add(Q, q);
+                Qx = O::fma(T(cx), q, Qx);
+                Qy = O::fma(T(cy), q, Qy);
+            } else {
+                bed = O::mul(O::mul(lam, c.G6), O::mul(O::add(X.eta, Y.eta), O::sub(X.D, Y.D)));
+            }
             const T frc = O::mul(O::mul(lam, c.KF),
                                  O::fma(T(cx), O::add(X.Fx, Y.Fx), O::mul(T(cy), O::add(X.Fy, Y.Fy))));
             w = O::add(O::add(feq_diff(c, Y, cx, cy), bed), frc);
@@ -759,6 +771,11 @@ __device__ __forceinline__ void general_node(const Fields<T>& f, int i, int j)
         Sh = O::add(Sh, w);
         Sx = O::fma(T(cx), w, Sx);
         Sy = O::fma(T(cy), w, Sy);
+    }
+    if (NEW) {  // eta1 = Sh + eta1 Q
+        Sh = Sh / O::sub(T(1), Q);
+        Sx = O::fma(Sh, Qx, Sx);
+        Sy = O::fma(Sh, Qy, Sy);
     }
     const T hu1 = O::mul(c.e, Sx), hv1 = O::mul(c.e, Sy);
     const T inv = T(1) / O::add(X.D, Sh);
@@ -769,14 +786,14 @@ __device__ __forceinline__ void general_node(const Fields<T>& f, int i, int j)
     f.v1[xi] = v1;
 }
 
-template <typename T>
+template <typename T, bool NEW = false>
 __global__ void __launch_bounds__(128) step_general_kernel(const Fields<T> f, const int* __restrict__ list,
                                                            int count)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count) return;
     const int node = list[t];
-    general_node(f, node % f.nx, node / f.nx);
+    general_node<T, NEW>(f, node % f.nx, node / f.nx);
 }
 
 // ---------------------------------------------------------------------------
