@@ -26,8 +26,9 @@
  * handle owns its weights, moments and activation buffers.  Every call runs
  * on the handle's stream; calls that return a host value synchronise.
  * Errors: MACLAB_E_ARG for bad sizes or NULL pointers, MACLAB_E_CUDA for a
- * failed launch, MACLAB_E_NOMEM when device memory runs out (status codes
- * of maclab.h); maclab_last_error(NULL) gives the message.
+ * failed launch or a tensor-core wait that timed out (reported by the next
+ * call that synchronises), MACLAB_E_NOMEM when device memory runs out
+ * (status codes of maclab.h); maclab_last_error(NULL) gives the message.
  */
 #ifndef MACLAB_WS_H
 #define MACLAB_WS_H
@@ -51,6 +52,8 @@ typedef struct {
     int dilation[64];  /* d_l >= 1 of block l (entries past L unused) */
     int max_batch;     /* largest batch the activation buffers hold */
     uint64_t seed;     /* weight initialisation (SplitMix64 stream) */
+    int tensor_path;   /* 0: tcgen05 for the 128 -> 128 convolutions (default),
+                          1: mma.sync for every convolution */
 } maclab_ws_config;
 
 /* Create a network with freshly initialised weights (He-scaled normal

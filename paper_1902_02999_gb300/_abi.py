@@ -51,7 +51,7 @@ class Info(ctypes.Structure):
 
 class WSConfig(ctypes.Structure):
     _fields_ = [("res", c_int), ("channels", c_int), ("blocks", c_int), ("dilation", c_int * 64),
-                ("max_batch", c_int), ("seed", ctypes.c_uint64)]
+                ("max_batch", c_int), ("seed", ctypes.c_uint64), ("tensor_path", c_int)]
 
 
 c_float = ctypes.c_float

@@ -2,11 +2,17 @@
 // convolutional network on a coarse grid, trained on steady states of the
 // plain iteration, proposing the starting state of a steady-state run.
 //
-// Every convolution is an implicit GEMM on the tensor cores: bfloat16
-// operands staged in shared memory by cp.async, fragments loaded with
-// ldmatrix, mma.sync m16n8k16 with float accumulators.
-//   forward / input gradient: M = pixels of one image row segment (64),
-//     N = output channels, K = 9 taps x input channels;
+// Every convolution is an implicit GEMM on the tensor cores with bfloat16
+// operands and float accumulators:
+//   the 128 -> 128 channel convolutions of the residual blocks (forward and
+//     input gradient, most of the work) use tcgen05.mma: operands staged by
+//     cp.async in shared memory in the canonical K-major layout, the
+//     128 x 128 accumulator in tensor memory, one thread issuing, completion
+//     through an mbarrier (ws_conv_tc_kernel);
+//   the other shapes (16-channel lift and head) and the weight gradient use
+//     mma.sync m16n8k16 with ldmatrix fragment loads.
+//   forward / input gradient: M = pixels, N = output channels,
+//     K = 9 taps x input channels;
 //   weight gradient: M = output channels, N = input channels, K = pixels
 //     (split over blocks, float atomics into the gradient).
 #include "maclab.h"
@@ -213,6 +219,207 @@ __global__ void __launch_bounds__(THREADS) ws_conv_kernel(const ConvArgs a)
             if (a.Yf) *reinterpret_cast<float2*>(a.Yf + o) = make_float2(v0, v1);
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// The same convolution on tcgen05: a block owns 128 consecutive pixels of
+// one image (M = 128) and 128 output channels (N = 128); K runs over the 9
+// taps x input channels in stages of 64 channels of one tap (4 MMAs of
+// K = 16).  Two stages of operands alternate: while the tensor core works on
+// one, the block stages the next; tcgen05.commit signals on the stage's
+// mbarrier when its MMAs are done with it.
+//   shared-memory operand layout (K-major, no swizzle): 8 x 8 core matrices
+//   of 128 bytes (8 rows of 16 bytes); core matrix (row group g, K chunk kc)
+//   at kc * 2048 + g * 128, so the descriptor's leading (K) byte offset is
+//   2048 and its stride (8-row group) byte offset 128.
+constexpr int TC_M = 128, TC_N = 128, TC_KS = 64, TC_THREADS = 128;
+constexpr uint32_t TC_OPER = TC_M * TC_KS * 2;          // 16 KB per operand and stage
+constexpr size_t TC_SMEM = 2 * 2 * TC_OPER + 1024;      // 2 stages x (A, B) + alignment slack
+constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
+// instruction descriptor, kind::f16: f32 accumulate, bf16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                              ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ uint32_t tc_off(int row, int kc) { return kc * 2048 + (row >> 3) * 128 + (row & 7) * 16; }
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)(2048 >> 4) << 16;  // leading byte offset: next core matrix along K
+    d |= (uint64_t)(128 >> 4) << 32;   // stride byte offset: next group of 8 rows
+    d |= (uint64_t)1 << 46;            // descriptor version of this tensor-core generation
+    return d;                          // base offset 0, no swizzle
+}
+
+__device__ __forceinline__ void tc_mbar_init(uint32_t bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool tc_mbar_wait(uint32_t bar, uint32_t phase)
+{
+    for (uint32_t k = 0; k < TC_WAIT_LIMIT; ++k) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(TC_THREADS) ws_conv_tc_kernel(const ConvArgs a, int* err)
+{
+    extern __shared__ __align__(16) unsigned char tsm_raw[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    // operand stages on a 1024-byte boundary
+    const uint32_t raw = smem_addr(tsm_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char* tsm = tsm_raw + (base - raw);
+    const int R = a.R, Cin = a.Cin, Cout = a.Cout, dil = a.dil;
+    const int P = R * R, tiles = P / TC_M;
+    const int b = blockIdx.x / tiles, p0 = (blockIdx.x % tiles) * TC_M;
+    const int n0 = blockIdx.y * TC_N;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t bar0 = smem_addr(&mbar[0]), bar1 = smem_addr(&mbar[1]);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(TC_N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        tc_mbar_init(bar0);
+        tc_mbar_init(bar1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const int kch = Cin / TC_KS;
+    const int KT = 9 * kch;
+    uint32_t phase[2] = {0, 0};
+    bool ok = true;
+    for (int kk = 0; kk < KT; ++kk) {
+        const int buf = kk & 1;
+        if (kk >= 2) {  // the MMAs of stage kk - 2 are done with this buffer
+            if (!tc_mbar_wait(buf ? bar1 : bar0, phase[buf])) atomicOr(&abort_flag, 1);
+            phase[buf] ^= 1u;
+            __syncthreads();
+            if (abort_flag) {
+                ok = false;
+                break;
+            }
+        }
+        const int tap = kk / kch, ci0 = (kk % kch) * TC_KS;
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        unsigned char* A = tsm + buf * 2 * TC_OPER;
+        unsigned char* Bm = A + TC_OPER;
+        for (int i = tid; i < TC_M * (TC_KS / 8); i += TC_THREADS) {
+            const int m = i >> 3, kc = i & 7;
+            const int p = p0 + m, y = p / R, x = p % R;
+            const int yy = y + dy * dil, xx = x + dx * dil;
+            const bool in = yy >= 0 && yy < R && xx >= 0 && xx < R;
+            const bf16* src = in ? a.X + ((size_t)(b * R + yy) * R + xx) * Cin + ci0 + kc * 8 : a.X;
+            cp16(smem_addr(A + tc_off(m, kc)), src, in);
+            const bf16* wsrc = a.Wk + ((size_t)tap * Cout + n0 + m) * Cin + ci0 + kc * 8;
+            cp16(smem_addr(Bm + tc_off(m, kc)), wsrc, true);
+        }
+        cp_commit();
+        cp_wait<0>();
+        if (a.relu_in) {  // each thread rectifies the chunks it staged
+            for (int i = tid; i < TC_M * (TC_KS / 8); i += TC_THREADS) {
+                uint4* q = reinterpret_cast<uint4*>(A + tc_off(i >> 3, i & 7));
+                uint4 v = *q;
+                v.x = relu2(v.x);
+                v.y = relu2(v.y);
+                v.z = relu2(v.z);
+                v.w = relu2(v.w);
+                *q = v;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // staged data visible to the tensor core
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t sa = smem_addr(A), sb = smem_addr(Bm);
+#pragma unroll
+            for (int k16 = 0; k16 < TC_KS / 16; ++k16) {
+                const uint64_t ad = tc_desc(sa + k16 * 2 * 2048), bd = tc_desc(sb + k16 * 2 * 2048);
+                const uint32_t acc = (kk > 0 || k16 > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             buf ? bar1 : bar0)
+                         : "memory");
+        }
+    }
+    // the last commit covers every MMA issued before it
+    if (ok && KT > 0) {
+        const int lb = (KT - 1) & 1;
+        if (!tc_mbar_wait(lb ? bar1 : bar0, phase[lb])) atomicOr(&abort_flag, 1);
+        __syncthreads();
+        ok = !abort_flag;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok) {
+        // epilogue: warp w reads tensor-memory lanes 32 w .. 32 w + 31 (pixels)
+        const int m = warp * 32 + lane;
+        const size_t orow = ((size_t)b * P + p0 + m) * Cout + n0;
+#pragma unroll 1
+        for (int c0 = 0; c0 < TC_N; c0 += 16) {
+            uint32_t r[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15}, [%16];\n"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+                const int n = n0 + c0 + j;
+                const size_t o = orow + c0 + j;
+                float v0 = __uint_as_float(r[j]) + (a.bias ? a.bias[n] : 0.f);
+                float v1 = __uint_as_float(r[j + 1]) + (a.bias ? a.bias[n + 1] : 0.f);
+                if (a.gate) {
+                    const __nv_bfloat162 gt = *reinterpret_cast<const __nv_bfloat162*>(a.gate + o);
+                    if (!(__bfloat162float(gt.x) > 0.f)) v0 = 0.f;
+                    if (!(__bfloat162float(gt.y) > 0.f)) v1 = 0.f;
+                }
+                if (a.res) {
+                    const __nv_bfloat162 rr = *reinterpret_cast<const __nv_bfloat162*>(a.res + o);
+                    v0 += __bfloat162float(rr.x);
+                    v1 += __bfloat162float(rr.y);
+                }
+                if (a.Y) *reinterpret_cast<__nv_bfloat162*>(a.Y + o) = __floats2bfloat162_rn(v0, v1);
+                if (a.Yf) *reinterpret_cast<float2*>(a.Yf + o) = make_float2(v0, v1);
+            }
+        }
+    } else {
+        // a wait gave up: let the MMAs already issued finish (bounded) before
+        // the accumulator is released
+        if (tid == 0) {
+            atomicOr(err, 1);
+            tc_mbar_wait(bar0, phase[0]);
+            tc_mbar_wait(bar1, phase[1]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_N) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -568,6 +775,7 @@ struct maclab_ws_s {
     float* Yf = nullptr;        // [B][R][R][16]
     double* loss = nullptr;
     double* acc = nullptr;      // decode's (sum of eta, count)
+    int* tc_err = nullptr;      // set when a tensor-core wait timed out
     std::vector<void*> bufs;
     std::string err;
 };
@@ -597,7 +805,10 @@ bool walloc(maclab_ws_t w, T** p, size_t count)
 void launch_conv(maclab_ws_t w, const ConvArgs& a, int batch)
 {
     const int segs = a.R / CONV_M;
-    if (a.Cout % 128 == 0) {
+    if (w->cfg.tensor_path == 0 && a.Cin % TC_KS == 0 && a.Cout % TC_N == 0 && (a.R * a.R) % TC_M == 0) {
+        dim3 grid(batch * (a.R * a.R / TC_M), a.Cout / TC_N);
+        ws_conv_tc_kernel<<<grid, TC_THREADS, TC_SMEM, w->stream>>>(a, w->tc_err);
+    } else if (a.Cout % 128 == 0) {
         dim3 grid(batch * a.R * segs, a.Cout / 128);
         ws_conv_kernel<128><<<grid, THREADS, 0, w->stream>>>(a);
     } else {
@@ -722,13 +933,23 @@ int loss_and_grad(maclab_ws_t w, int batch, int oc, const float* x, const float*
     return MACLAB_OK;
 }
 
+int check_tc(maclab_ws_t w)
+{
+    int flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, w->tc_err, sizeof(int), cudaMemcpyDeviceToHost, w->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
+    if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("warm-start status: ") + cudaGetErrorString(e));
+    if (flag) return wfail(w, MACLAB_E_CUDA, "warm start: a tensor-core wait timed out");
+    return MACLAB_OK;
+}
+
 int read_loss(maclab_ws_t w, double* loss)
 {
     if (!loss) return MACLAB_OK;
     cudaError_t e = cudaMemcpyAsync(loss, w->loss, sizeof(double), cudaMemcpyDeviceToHost, w->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
     if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("warm-start loss: ") + cudaGetErrorString(e));
-    return MACLAB_OK;
+    return check_tc(w);
 }
 
 }  // namespace
@@ -767,7 +988,7 @@ int maclab_ws_create(const maclab_ws_config* cfg, void* stream, maclab_ws_t* out
     const size_t P = (size_t)cfg->max_batch * R * R;
     bool ok = walloc(w, &w->param, w->nparam) && walloc(w, &w->grad, w->nparam) && walloc(w, &w->m1, w->nparam) &&
               walloc(w, &w->m2, w->nparam) && walloc(w, &w->X, P * IO) && walloc(w, &w->dY, P * IO) &&
-              walloc(w, &w->Yf, P * IO) && walloc(w, &w->loss, 1) && walloc(w, &w->acc, 2) && walloc(w, &w->G[0], P * C) &&
+              walloc(w, &w->Yf, P * IO) && walloc(w, &w->loss, 1) && walloc(w, &w->acc, 2) && walloc(w, &w->tc_err, 1) && walloc(w, &w->G[0], P * C) &&
               walloc(w, &w->G[1], P * C);
     w->H.assign(w->layers.size() - 1, nullptr);
     for (size_t l = 0; ok && l < w->H.size(); ++l) ok = walloc(w, &w->H[l], P * C);
@@ -796,6 +1017,9 @@ int maclab_ws_create(const maclab_ws_config* cfg, void* stream, maclab_ws_t* out
     cudaError_t e = cudaMemcpyAsync(w->param, h.data(), h.size() * 4, cudaMemcpyHostToDevice, w->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(w->m1, 0, (size_t)w->nparam * 4, w->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(w->m2, 0, (size_t)w->nparam * 4, w->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w->tc_err, 0, sizeof(int), w->stream);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ws_conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
     if (e == cudaSuccess) {
         pack_all(w);
         e = cudaStreamSynchronize(w->stream);
@@ -873,9 +1097,7 @@ int maclab_ws_gradients(maclab_ws_t w, int batch, int oc, const float* x, const 
     cudaError_t e = cudaMemcpyAsync(grad_host, w->grad, n * 4, cudaMemcpyDeviceToHost, w->stream);
     if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("gradients: ") + cudaGetErrorString(e));
     if (loss) return read_loss(w, loss);
-    e = cudaStreamSynchronize(w->stream);
-    if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("gradients: ") + cudaGetErrorString(e));
-    return MACLAB_OK;
+    return check_tc(w);
 }
 
 int maclab_ws_train_step(maclab_ws_t w, int batch, int oc, const float* x, const float* t, const float* wt, float lr,

@@ -40,7 +40,7 @@ class WarmStartNet:
     """One network handle (maclab_ws_t) with its own weights and buffers."""
 
     def __init__(self, res: int = 64, channels: int = 128, dilations=DEFAULT_DILATIONS, max_batch: int = 32,
-                 seed: int = 0, stream=None):
+                 seed: int = 0, stream=None, tensor_path: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the warm start needs a CUDA GPU; no CPU fallback exists")
@@ -49,6 +49,7 @@ class WarmStartNet:
         self.max_batch = max_batch
         cfg = _abi.WSConfig()
         cfg.res, cfg.channels, cfg.blocks, cfg.max_batch, cfg.seed = res, channels, len(dilations), max_batch, seed
+        cfg.tensor_path = tensor_path  # 0: tcgen05 for the 128 -> 128 convolutions, 1: mma.sync only
         for k, d in enumerate(dilations):
             cfg.dilation[k] = int(d)
         if stream is None:

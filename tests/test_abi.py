@@ -68,12 +68,14 @@ def test_struct_layouts_match_header(tmp_path):
 def test_warm_start_config_layout_and_argument_checks(tmp_path):
     src = tmp_path / "ws.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "maclab_ws.h"\n'
-                   "int main(void){printf(\"%zu %zu %zu\\n\",sizeof(maclab_ws_config),"
-                   "offsetof(maclab_ws_config,max_batch),offsetof(maclab_ws_config,seed));return 0;}\n")
+                   "int main(void){printf(\"%zu %zu %zu %zu\\n\",sizeof(maclab_ws_config),"
+                   "offsetof(maclab_ws_config,max_batch),offsetof(maclab_ws_config,seed),"
+                   "offsetof(maclab_ws_config,tensor_path));return 0;}\n")
     exe = tmp_path / "ws"
     subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
-    assert got == [ctypes.sizeof(_abi.WSConfig), _abi.WSConfig.max_batch.offset, _abi.WSConfig.seed.offset]
+    assert got == [ctypes.sizeof(_abi.WSConfig), _abi.WSConfig.max_batch.offset, _abi.WSConfig.seed.offset,
+                   _abi.WSConfig.tensor_path.offset]
     lib = _abi.load()
     cfg = _abi.WSConfig(res=48, channels=128, blocks=2, max_batch=1)   # res not a multiple of 64
     h = ctypes.c_void_p()

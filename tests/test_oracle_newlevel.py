@@ -89,3 +89,16 @@ def test_lake_at_rest_and_flat_bed():
     c = oracle.run_newlevel(case, 20)
     d = oracle.run(case, 20)
     assert np.abs(c[0] - d[0])[live].max() > 1e-9
+
+
+def test_mass_exact_at_the_old_level_only():
+    """The old-level bed terms of opposite links cancel in pairs (exact mass
+    in a closed basin); with the new level they do not, and a closed basin
+    gains or loses mass at the truncation level."""
+    case = inputs.random_case(40, 30, 3, edges=(BOUNCEBACK,) * 4, dirichlet=False)
+    live = case.mask != SOLID
+    m0 = case.h0[live].sum()
+    old = oracle.run(case, 200)[0][live].sum()
+    new = oracle.run_newlevel(case, 200)[0][live].sum()
+    assert abs(old - m0) <= 1e-13 * m0
+    assert 1e-12 * m0 < abs(new - m0) < 1e-5 * m0

@@ -25,9 +25,9 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def make(C, dil, batch, seed=0):
+def make(C, dil, batch, seed=0, tensor_path=0):
     from paper_1902_02999_gb300.warmstart import WarmStartNet
-    return WarmStartNet(res=64, channels=C, dilations=dil, max_batch=batch, seed=seed)
+    return WarmStartNet(res=64, channels=C, dilations=dil, max_batch=batch, seed=seed, tensor_path=tensor_path)
 
 
 def random_setup(net, C, dil, batch, seed):
@@ -76,6 +76,24 @@ def test_gradients_match_reference(C, dil):
             assert e <= 6e-2, (ci, co, size, e)
             k += size
     net.close()
+
+
+def test_tcgen05_and_mma_sync_paths_agree():
+    """The 128 -> 128 convolutions on tcgen05 (default) and on mma.sync give
+    the same outputs and gradients up to the order of float summation and
+    the rounding of the stored bfloat16 activations."""
+    C, dil = 128, (1, 2, 4)
+    nets = [make(C, dil, 2, tensor_path=t) for t in (0, 1)]
+    theta, X, T, w = random_setup(nets[0], C, dil, 2, 4)
+    dev = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    outs, grads = [], []
+    for net in nets:
+        net.set_params(theta)
+        outs.append(net.forward(dev(X)).cpu().numpy())
+        grads.append(net.gradients(dev(X), dev(T), dev(w))[1])
+        net.close()
+    assert rel(outs[0], outs[1]) <= 1e-2, rel(outs[0], outs[1])
+    assert rel(grads[0], grads[1]) <= 2e-2, rel(grads[0], grads[1])
 
 
 def test_training_fits_a_small_set():
