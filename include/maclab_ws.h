@@ -52,8 +52,9 @@ typedef struct {
     int dilation[64];  /* d_l >= 1 of block l (entries past L unused) */
     int max_batch;     /* largest batch the activation buffers hold */
     uint64_t seed;     /* weight initialisation (SplitMix64 stream) */
-    int tensor_path;   /* 0: tcgen05 for the 128 -> 128 convolutions (default),
-                          1: mma.sync for every convolution */
+    int tensor_path;   /* 0: mma.sync for every convolution (default; the
+                          faster of the two as measured), 1: tcgen05 for
+                          the 128 -> 128 convolutions */
 } maclab_ws_config;
 
 /* Create a network with freshly initialised weights (He-scaled normal

@@ -4,13 +4,15 @@
 //
 // Every convolution is an implicit GEMM on the tensor cores with bfloat16
 // operands and float accumulators:
-//   the 128 -> 128 channel convolutions of the residual blocks (forward and
-//     input gradient, most of the work) use tcgen05.mma: operands staged by
-//     cp.async in shared memory in the canonical K-major layout, the
-//     128 x 128 accumulator in tensor memory, one thread issuing, completion
-//     through an mbarrier (ws_conv_tc_kernel);
-//   the other shapes (16-channel lift and head) and the weight gradient use
-//     mma.sync m16n8k16 with ldmatrix fragment loads.
+//   by default mma.sync m16n8k16 with ldmatrix fragment loads
+//     (ws_conv_kernel, ws_wgrad_kernel);
+//   optionally (tensor_path = 1) the 128 -> 128 channel convolutions of the
+//     residual blocks (forward and input gradient, most of the work) run on
+//     tcgen05.mma: operands staged by cp.async in shared memory in the
+//     canonical K-major layout, the 128 x 128 accumulator in tensor memory,
+//     one thread issuing, completion through mbarriers (ws_conv_tc_kernel).
+//     It gives the same results; in its present form it is slower (its
+//     operand copies, not the tensor core, set its pace).
 //   forward / input gradient: M = pixels, N = output channels,
 //     K = 9 taps x input channels;
 //   weight gradient: M = output channels, N = input channels, K = pixels
@@ -224,17 +226,25 @@ __global__ void __launch_bounds__(THREADS) ws_conv_kernel(const ConvArgs a)
 // ---------------------------------------------------------------------------
 // The same convolution on tcgen05: a block owns 128 consecutive pixels of
 // one image (M = 128) and 128 output channels (N = 128); K runs over the 9
-// taps x input channels in stages of 64 channels of one tap (4 MMAs of
-// K = 16).  Two stages of operands alternate: while the tensor core works on
-// one, the block stages the next; tcgen05.commit signals on the stage's
-// mbarrier when its MMAs are done with it.
+// taps x input channels in stages of TC_KS channels of one tap (TC_KS / 16
+// MMAs of K = 16).  TC_STAGES operand buffers rotate: the copies of a stage
+// are issued TC_STAGES - 1 stages ahead (the MMAs of a stage take far less
+// time than its copies), one thread issues each stage's MMAs, and
+// tcgen05.commit signals the stage's mbarrier when its MMAs are done with
+// the buffer.
 //   shared-memory operand layout (K-major, no swizzle): 8 x 8 core matrices
 //   of 128 bytes (8 rows of 16 bytes); core matrix (row group g, K chunk kc)
 //   at kc * 2048 + g * 128, so the descriptor's leading (K) byte offset is
 //   2048 and its stride (8-row group) byte offset 128.
-constexpr int TC_M = 128, TC_N = 128, TC_KS = 64, TC_THREADS = 128;
-constexpr uint32_t TC_OPER = TC_M * TC_KS * 2;          // 16 KB per operand and stage
-constexpr size_t TC_SMEM = 2 * 2 * TC_OPER + 1024;      // 2 stages x (A, B) + alignment slack
+#ifndef MACLAB_TC_KS
+#define MACLAB_TC_KS 32
+#endif
+#ifndef MACLAB_TC_STAGES
+#define MACLAB_TC_STAGES 6
+#endif
+constexpr int TC_M = 128, TC_N = 128, TC_KS = MACLAB_TC_KS, TC_THREADS = 256, TC_STAGES = MACLAB_TC_STAGES;
+constexpr uint32_t TC_OPER = TC_M * TC_KS * 2;          // bytes per operand and stage
+constexpr size_t TC_SMEM = TC_STAGES * 2 * TC_OPER + 1024;  // stages x (A, B) + alignment slack
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
 // instruction descriptor, kind::f16: f32 accumulate, bf16 A and B, both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24
@@ -273,10 +283,10 @@ __device__ __forceinline__ bool tc_mbar_wait(uint32_t bar, uint32_t phase)
 __global__ void __launch_bounds__(TC_THREADS) ws_conv_tc_kernel(const ConvArgs a, int* err)
 {
     extern __shared__ __align__(16) unsigned char tsm_raw[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar[TC_STAGES];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
-    // operand stages on a 1024-byte boundary
+    // operand buffers on a 1024-byte boundary
     const uint32_t raw = smem_addr(tsm_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char* tsm = tsm_raw + (base - raw);
@@ -285,7 +295,6 @@ __global__ void __launch_bounds__(TC_THREADS) ws_conv_tc_kernel(const ConvArgs a
     const int b = blockIdx.x / tiles, p0 = (blockIdx.x % tiles) * TC_M;
     const int n0 = blockIdx.y * TC_N;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t bar0 = smem_addr(&mbar[0]), bar1 = smem_addr(&mbar[1]);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&tmem_slot)),
                      "r"(TC_N)
@@ -293,8 +302,7 @@ __global__ void __launch_bounds__(TC_THREADS) ws_conv_tc_kernel(const ConvArgs a
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (tid == 0) {
-        tc_mbar_init(bar0);
-        tc_mbar_init(bar1);
+        for (int k = 0; k < TC_STAGES; ++k) tc_mbar_init(smem_addr(&mbar[k]));
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -304,25 +312,18 @@ __global__ void __launch_bounds__(TC_THREADS) ws_conv_tc_kernel(const ConvArgs a
     const uint32_t tmem = tmem_slot;
     const int kch = Cin / TC_KS;
     const int KT = 9 * kch;
-    uint32_t phase[2] = {0, 0};
-    bool ok = true;
-    for (int kk = 0; kk < KT; ++kk) {
-        const int buf = kk & 1;
-        if (kk >= 2) {  // the MMAs of stage kk - 2 are done with this buffer
-            if (!tc_mbar_wait(buf ? bar1 : bar0, phase[buf])) atomicOr(&abort_flag, 1);
-            phase[buf] ^= 1u;
-            __syncthreads();
-            if (abort_flag) {
-                ok = false;
-                break;
-            }
-        }
+    uint32_t phase[TC_STAGES];
+#pragma unroll
+    for (int k = 0; k < TC_STAGES; ++k) phase[k] = 0;
+
+    auto load = [&](int kk) {
+        const int buf = kk % TC_STAGES;
         const int tap = kk / kch, ci0 = (kk % kch) * TC_KS;
         const int dy = tap / 3 - 1, dx = tap % 3 - 1;
         unsigned char* A = tsm + buf * 2 * TC_OPER;
         unsigned char* Bm = A + TC_OPER;
         for (int i = tid; i < TC_M * (TC_KS / 8); i += TC_THREADS) {
-            const int m = i >> 3, kc = i & 7;
+            const int m = i / (TC_KS / 8), kc = i % (TC_KS / 8);
             const int p = p0 + m, y = p / R, x = p % R;
             const int yy = y + dy * dil, xx = x + dx * dil;
             const bool in = yy >= 0 && yy < R && xx >= 0 && xx < R;
@@ -331,11 +332,37 @@ __global__ void __launch_bounds__(TC_THREADS) ws_conv_tc_kernel(const ConvArgs a
             const bf16* wsrc = a.Wk + ((size_t)tap * Cout + n0 + m) * Cin + ci0 + kc * 8;
             cp16(smem_addr(Bm + tc_off(m, kc)), wsrc, true);
         }
+    };
+
+    bool ok = true;
+#pragma unroll
+    for (int s = 0; s < TC_STAGES - 1; ++s) {
+        if (s < KT) load(s);
         cp_commit();
-        cp_wait<0>();
+    }
+    for (int kk = 0; kk < KT; ++kk) {
+        const int pf = kk + TC_STAGES - 1;
+        if (pf < KT) {
+            // buffer pf % TC_STAGES was last read by the MMAs of stage kk - 1
+            if (kk >= 1) {
+                const int pb = (kk - 1) % TC_STAGES;
+                if (!tc_mbar_wait(smem_addr(&mbar[pb]), phase[pb])) atomicOr(&abort_flag, 1);
+                phase[pb] ^= 1u;
+                __syncthreads();
+                if (abort_flag) {
+                    ok = false;
+                    break;
+                }
+            }
+            load(pf);
+        }
+        cp_commit();
+        cp_wait<TC_STAGES - 1>();  // this thread's copies of stage kk have landed
+        const int buf = kk % TC_STAGES;
+        unsigned char* A = tsm + buf * 2 * TC_OPER;
         if (a.relu_in) {  // each thread rectifies the chunks it staged
             for (int i = tid; i < TC_M * (TC_KS / 8); i += TC_THREADS) {
-                uint4* q = reinterpret_cast<uint4*>(A + tc_off(i >> 3, i & 7));
+                uint4* q = reinterpret_cast<uint4*>(A + tc_off(i / (TC_KS / 8), i % (TC_KS / 8)));
                 uint4 v = *q;
                 v.x = relu2(v.x);
                 v.y = relu2(v.y);
@@ -348,7 +375,7 @@ __global__ void __launch_bounds__(TC_THREADS) ws_conv_tc_kernel(const ConvArgs a
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t sa = smem_addr(A), sb = smem_addr(Bm);
+            const uint32_t sa = smem_addr(A), sb = sa + TC_OPER;
 #pragma unroll
             for (int k16 = 0; k16 < TC_KS / 16; ++k16) {
                 const uint64_t ad = tc_desc(sa + k16 * 2 * 2048), bd = tc_desc(sb + k16 * 2 * 2048);
@@ -360,24 +387,27 @@ __global__ void __launch_bounds__(TC_THREADS) ws_conv_tc_kernel(const ConvArgs a
                     : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                             buf ? bar1 : bar0)
+                             smem_addr(&mbar[buf]))
                          : "memory");
         }
     }
+    cp_wait<0>();
     // the last commit covers every MMA issued before it
     if (ok && KT > 0) {
-        const int lb = (KT - 1) & 1;
-        if (!tc_mbar_wait(lb ? bar1 : bar0, phase[lb])) atomicOr(&abort_flag, 1);
+        const int lb = (KT - 1) % TC_STAGES;
+        if (!tc_mbar_wait(smem_addr(&mbar[lb]), phase[lb])) atomicOr(&abort_flag, 1);
         __syncthreads();
         ok = !abort_flag;
     }
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (ok) {
-        // epilogue: warp w reads tensor-memory lanes 32 w .. 32 w + 31 (pixels)
-        const int m = warp * 32 + lane;
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31
+        // (pixels), columns 64 (w / 4) .. + 63
+        const int m = (warp & 3) * 32 + lane;
+        const int cbase = (warp >> 2) * (TC_N / 2);
         const size_t orow = ((size_t)b * P + p0 + m) * Cout + n0;
 #pragma unroll 1
-        for (int c0 = 0; c0 < TC_N; c0 += 16) {
+        for (int c0 = cbase; c0 < cbase + TC_N / 2; c0 += 16) {
             uint32_t r[16];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
@@ -385,7 +415,7 @@ __global__ void __launch_bounds__(TC_THREADS) ws_conv_tc_kernel(const ConvArgs a
                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
                   "=r"(r[15])
-                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+                : "r"(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0));
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
             for (int j = 0; j < 16; j += 2) {
@@ -407,14 +437,11 @@ __global__ void __launch_bounds__(TC_THREADS) ws_conv_tc_kernel(const ConvArgs a
                 if (a.Yf) *reinterpret_cast<float2*>(a.Yf + o) = make_float2(v0, v1);
             }
         }
-    } else {
+    } else if (tid == 0) {
         // a wait gave up: let the MMAs already issued finish (bounded) before
         // the accumulator is released
-        if (tid == 0) {
-            atomicOr(err, 1);
-            tc_mbar_wait(bar0, phase[0]);
-            tc_mbar_wait(bar1, phase[1]);
-        }
+        atomicOr(err, 1);
+        for (int k = 0; k < TC_STAGES; ++k) tc_mbar_wait(smem_addr(&mbar[k]), phase[k]);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -805,7 +832,7 @@ bool walloc(maclab_ws_t w, T** p, size_t count)
 void launch_conv(maclab_ws_t w, const ConvArgs& a, int batch)
 {
     const int segs = a.R / CONV_M;
-    if (w->cfg.tensor_path == 0 && a.Cin % TC_KS == 0 && a.Cout % TC_N == 0 && (a.R * a.R) % TC_M == 0) {
+    if (w->cfg.tensor_path == 1 && a.Cin % TC_KS == 0 && a.Cout % TC_N == 0 && (a.R * a.R) % TC_M == 0) {
         dim3 grid(batch * (a.R * a.R / TC_M), a.Cout / TC_N);
         ws_conv_tc_kernel<<<grid, TC_THREADS, TC_SMEM, w->stream>>>(a, w->tc_err);
     } else if (a.Cout % 128 == 0) {
