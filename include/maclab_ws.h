@@ -52,9 +52,11 @@ typedef struct {
     int dilation[64];  /* d_l >= 1 of block l (entries past L unused) */
     int max_batch;     /* largest batch the activation buffers hold */
     uint64_t seed;     /* weight initialisation (SplitMix64 stream) */
-    int tensor_path;   /* 0: mma.sync for every convolution (default; the
-                          faster of the two as measured), 1: tcgen05 for
-                          the 128 -> 128 convolutions */
+    int tensor_path;   /* the 128 -> 128 convolutions (residual blocks) on
+                          0: tcgen05, operands staged by TMA (default),
+                          1: tcgen05, operands staged by cp.async,
+                          2: mma.sync; the other convolutions always run on
+                          mma.sync.  Other values are rejected. */
 } maclab_ws_config;
 
 /* Create a network with freshly initialised weights (He-scaled normal

@@ -4,15 +4,18 @@
 //
 // Every convolution is an implicit GEMM on the tensor cores with bfloat16
 // operands and float accumulators:
-//   by default mma.sync m16n8k16 with ldmatrix fragment loads
-//     (ws_conv_kernel, ws_wgrad_kernel);
-//   optionally (tensor_path = 1) the 128 -> 128 channel convolutions of the
+//   by default (tensor_path = 0) the 128 -> 128 channel convolutions of the
 //     residual blocks (forward and input gradient, most of the work) run on
-//     tcgen05.mma: operands staged by cp.async in shared memory in the
-//     canonical K-major layout, the 128 x 128 accumulator in tensor memory,
-//     one thread issuing, completion through mbarriers (ws_conv_tc_kernel).
-//     It gives the same results; in its present form it is slower (its
-//     operand copies, not the tensor core, set its pace).
+//     tcgen05.mma with operands brought in by TMA tensor copies into
+//     128-byte swizzled shared memory, the 128 x 128 accumulator in tensor
+//     memory, one thread issuing, completion through mbarriers
+//     (ws_conv_tma_kernel);
+//   tensor_path = 1 stages the same operands with cp.async in the canonical
+//     no-swizzle K-major layout instead (ws_conv_tc_kernel, slower: its
+//     per-thread copies set its pace);
+//   the other convolutions (16-channel input and output layers), the weight
+//     gradient, and every convolution under tensor_path = 2, run on mma.sync
+//     m16n8k16 with ldmatrix fragment loads (ws_conv_kernel, ws_wgrad_kernel);
 //   forward / input gradient: M = pixels, N = output channels,
 //     K = 9 taps x input channels;
 //   weight gradient: M = output channels, N = input channels, K = pixels
@@ -20,6 +23,8 @@
 #include "maclab.h"
 #include "maclab_ws.h"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -27,6 +32,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -450,6 +456,240 @@ __global__ void __launch_bounds__(TC_THREADS) ws_conv_tc_kernel(const ConvArgs a
 }
 
 // ---------------------------------------------------------------------------
+// tcgen05 with TMA-fed operands (tensor_path = 0, the default).  Per stage (one tap, 64
+// input channels) one thread issues two tensor copies into 128-byte
+// swizzled shared memory: the 128 pixels of the block shifted by the tap
+// (a 4D box over [batch][y][x][c]; pixels outside the image arrive as
+// zeros) and the 128 x 64 weight slice (a 2D box).  A "full" mbarrier per
+// buffer counts the bytes, an "empty" one receives the tcgen05.commit of
+// the stage's MMAs; copies run two stages ahead of the MMAs in four buffers.
+//   operand layout: rows of 128 bytes (64 bf16), 16-byte chunk j of row r at
+//   chunk j ^ (r % 8) (the 128-byte swizzle of the tensor copy), 8-row
+//   groups 1024 bytes apart: descriptor stride byte offset 1024, swizzle
+//   mode 128B, and each K = 16 step advances the start address by 32 bytes.
+struct TmaOperands {
+    CUtensorMap A;   // activations [batch][R][R][Cin], box {64, bx, by, 1}
+    CUtensorMap B;   // weights [9 Cout][Cin], box {64, 128}
+};
+#ifndef MACLAB_TT_STAGES
+#define MACLAB_TT_STAGES 3
+#endif
+#ifndef MACLAB_TT_AHEAD
+#define MACLAB_TT_AHEAD 2
+#endif
+constexpr int TT_STAGES = MACLAB_TT_STAGES, TT_AHEAD = MACLAB_TT_AHEAD, TT_THREADS = 128;
+constexpr uint32_t TT_OPER = 128 * 64 * 2;                    // 16 KB per operand and stage
+constexpr size_t TT_SMEM = TT_STAGES * 2 * TT_OPER + 1024;
+
+__device__ __forceinline__ uint64_t tt_desc(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;            // leading byte offset (unused by swizzled K-major operands)
+    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset: next group of 8 rows
+    d |= (uint64_t)1 << 46;            // descriptor version of this tensor-core generation
+    d |= (uint64_t)2 << 61;            // 128-byte swizzle
+    return d;
+}
+__device__ __forceinline__ void tt_expect(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__global__ void __launch_bounds__(TT_THREADS) ws_conv_tma_kernel(const __grid_constant__ TmaOperands maps,
+                                                                  const ConvArgs a, int* err)
+{
+    extern __shared__ __align__(16) unsigned char ttm_raw[];
+    __shared__ __align__(8) uint64_t full[TT_STAGES], empty[TT_STAGES];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    const uint32_t raw = smem_addr(ttm_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char* tsm = ttm_raw + (base - raw);
+    const int R = a.R, Cin = a.Cin, Cout = a.Cout, dil = a.dil;
+    const int P = R * R, tiles = P / TC_M;
+    const int b = blockIdx.x / tiles, p0 = (blockIdx.x % tiles) * TC_M;
+    const int y0 = p0 / R, x0 = p0 % R;
+    const int n0 = blockIdx.y * TC_N;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(TC_N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int k = 0; k < TT_STAGES; ++k) {
+            tc_mbar_init(smem_addr(&full[k]));
+            tc_mbar_init(smem_addr(&empty[k]));
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const int kch = Cin / 64;
+    const int KT = 9 * kch;
+    uint32_t pf[TT_STAGES], pe[TT_STAGES];
+#pragma unroll
+    for (int k = 0; k < TT_STAGES; ++k) pf[k] = pe[k] = 0;
+
+    auto issue = [&](int kk) {  // thread 0: the two tensor copies of stage kk
+        const int buf = kk % TT_STAGES;
+        const int tap = kk / kch, ci0 = (kk % kch) * 64;
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        const uint32_t sa = smem_addr(tsm + buf * 2 * TT_OPER), sb = sa + TT_OPER;
+        const uint32_t bar = smem_addr(&full[buf]);
+        tt_expect(bar, 2 * TT_OPER);
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+            "[%6];\n" ::"r"(sa),
+            "l"(reinterpret_cast<uint64_t>(&maps.A)), "r"(ci0), "r"(x0 + dx * dil), "r"(y0 + dy * dil), "r"(b),
+            "r"(bar)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::
+                "r"(sb),
+            "l"(reinterpret_cast<uint64_t>(&maps.B)), "r"(ci0), "r"(tap * Cout + n0), "r"(bar)
+            : "memory");
+    };
+
+    bool ok = true;
+    if (tid == 0)
+        for (int s = 0; s < TT_AHEAD && s < KT; ++s) issue(s);
+    for (int kk = 0; kk < KT; ++kk) {
+        if (tid == 0 && kk + TT_AHEAD < KT) {
+            const int nb = (kk + TT_AHEAD) % TT_STAGES;
+            if (kk + TT_AHEAD >= TT_STAGES) {  // that buffer's last MMAs must be done
+                if (!tc_mbar_wait(smem_addr(&empty[nb]), pe[nb])) atomicOr(&abort_flag, 1);
+                pe[nb] ^= 1u;
+            }
+            issue(kk + TT_AHEAD);
+        }
+        const int buf = kk % TT_STAGES;
+        if (!tc_mbar_wait(smem_addr(&full[buf]), pf[buf])) atomicOr(&abort_flag, 1);
+        pf[buf] ^= 1u;
+        unsigned char* A = tsm + buf * 2 * TT_OPER;
+        if (a.relu_in) {
+            for (int i = tid; i < (int)(TT_OPER / 16); i += TT_THREADS) {
+                uint4* q = reinterpret_cast<uint4*>(A + i * 16);
+                uint4 v = *q;
+                v.x = relu2(v.x);
+                v.y = relu2(v.y);
+                v.z = relu2(v.z);
+                v.w = relu2(v.w);
+                *q = v;
+            }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        }
+        __syncthreads();
+        if (abort_flag) {
+            ok = false;
+            break;
+        }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t sa = smem_addr(A), sb = sa + TT_OPER;
+#pragma unroll
+            for (int k16 = 0; k16 < 4; ++k16) {
+                const uint64_t ad = tt_desc(sa + k16 * 32), bd = tt_desc(sb + k16 * 32);
+                const uint32_t acc = (kk > 0 || k16 > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_addr(&empty[buf]))
+                         : "memory");
+        }
+    }
+    if (tid == 0) {
+        if (ok && KT > 0) {
+            // the commit of the last stage covers every MMA issued before it;
+            // the earlier commits of its buffer were waited for by the producer
+            const int lb = (KT - 1) % TT_STAGES;
+            if (!tc_mbar_wait(smem_addr(&empty[lb]), pe[lb])) atomicOr(&abort_flag, 1);
+        } else if (!ok) {
+            // gave up: let copies and MMAs in flight finish (bounded) before
+            // shared and tensor memory are released
+            for (int k = 0; k < TT_STAGES; ++k) {
+                tc_mbar_wait(smem_addr(&full[k]), pf[k]);
+                tc_mbar_wait(smem_addr(&empty[k]), pe[k]);
+            }
+        }
+    }
+    __syncthreads();
+    ok = ok && !abort_flag;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok) {
+        const int m = warp * 32 + lane;
+        const size_t orow = ((size_t)b * P + p0 + m) * Cout + n0;
+#pragma unroll 1
+        for (int c0 = 0; c0 < TC_N; c0 += 16) {
+            uint32_t r[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15}, [%16];\n"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            // a thread owns 16 consecutive channels of its pixel: 32-byte
+            // (bf16) and 64-byte (float) runs, moved as 16-byte vectors
+            const size_t o = orow + c0;
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]) + (a.bias ? a.bias[n0 + c0 + j] : 0.f);
+            if (a.gate) {
+                uint4 g2[2];
+                g2[0] = *reinterpret_cast<const uint4*>(a.gate + o);
+                g2[1] = *reinterpret_cast<const uint4*>(a.gate + o + 8);
+                const __nv_bfloat162* gt = reinterpret_cast<const __nv_bfloat162*>(g2);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (!(__bfloat162float(gt[j].x) > 0.f)) v[2 * j] = 0.f;
+                    if (!(__bfloat162float(gt[j].y) > 0.f)) v[2 * j + 1] = 0.f;
+                }
+            }
+            if (a.res) {
+                uint4 r2[2];
+                r2[0] = *reinterpret_cast<const uint4*>(a.res + o);
+                r2[1] = *reinterpret_cast<const uint4*>(a.res + o + 8);
+                const __nv_bfloat162* rr = reinterpret_cast<const __nv_bfloat162*>(r2);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    v[2 * j] += __bfloat162float(rr[j].x);
+                    v[2 * j + 1] += __bfloat162float(rr[j].y);
+                }
+            }
+            if (a.Y) {
+                uint4 w2[2];
+                __nv_bfloat162* wb = reinterpret_cast<__nv_bfloat162*>(w2);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) wb[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                *reinterpret_cast<uint4*>(a.Y + o) = w2[0];
+                *reinterpret_cast<uint4*>(a.Y + o + 8) = w2[1];
+            }
+            if (a.Yf) {
+#pragma unroll
+                for (int j = 0; j < 16; j += 4)
+                    *reinterpret_cast<float4*>(a.Yf + o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_N) : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Weight gradient: dW[tap][co][ci] += sum_p dY[p][co] * act(X)[p + off(tap)][ci]
 // A block owns one tap, an MT x NT tile of (co, ci) and every split-th
 // chunk of 32 pixels.
@@ -829,10 +1069,55 @@ bool walloc(maclab_ws_t w, T** p, size_t count)
     return true;
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+        cudaGetLastError();
+    });
+    return encode;
+}
+
+// tensor maps of one convolution for ws_conv_tma_kernel; false if the
+// driver entry point is missing or an encode fails
+bool tma_operands(const ConvArgs& a, int batch, TmaOperands& m)
+{
+    const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return false;
+    const int bx = a.R < 128 ? a.R : 128, by = 128 / bx;
+    const cuuint64_t adims[4] = {(cuuint64_t)a.Cin, (cuuint64_t)a.R, (cuuint64_t)a.R, (cuuint64_t)batch};
+    const cuuint64_t astr[3] = {(cuuint64_t)a.Cin * 2, (cuuint64_t)a.R * a.Cin * 2, (cuuint64_t)a.R * a.R * a.Cin * 2};
+    const cuuint32_t abox[4] = {64, (cuuint32_t)bx, (cuuint32_t)by, 1};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    if (encode(&m.A, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)a.X, adims, astr, abox, one,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const cuuint64_t bdims[2] = {(cuuint64_t)a.Cin, (cuuint64_t)9 * a.Cout};
+    const cuuint64_t bstr[1] = {(cuuint64_t)a.Cin * 2};
+    const cuuint32_t bbox[2] = {64, 128};
+    return encode(&m.B, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)a.Wk, bdims, bstr, bbox, one,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 void launch_conv(maclab_ws_t w, const ConvArgs& a, int batch)
 {
     const int segs = a.R / CONV_M;
-    if (w->cfg.tensor_path == 1 && a.Cin % TC_KS == 0 && a.Cout % TC_N == 0 && (a.R * a.R) % TC_M == 0) {
+    const bool tc_shape = a.Cin % 64 == 0 && a.Cout % TC_N == 0 && (a.R * a.R) % TC_M == 0 &&
+                          (a.R < 128 ? 128 % a.R == 0 : a.R % 128 == 0);
+    TmaOperands maps;
+    if (w->cfg.tensor_path == 0 && tc_shape && tma_operands(a, batch, maps)) {
+        dim3 grid(batch * (a.R * a.R / TC_M), a.Cout / TC_N);
+        ws_conv_tma_kernel<<<grid, TT_THREADS, TT_SMEM, w->stream>>>(maps, a, w->tc_err);
+    } else if (w->cfg.tensor_path == 1 && a.Cin % TC_KS == 0 && a.Cout % TC_N == 0 && (a.R * a.R) % TC_M == 0) {
         dim3 grid(batch * (a.R * a.R / TC_M), a.Cout / TC_N);
         ws_conv_tc_kernel<<<grid, TC_THREADS, TC_SMEM, w->stream>>>(a, w->tc_err);
     } else if (a.Cout % 128 == 0) {
@@ -990,6 +1275,8 @@ int maclab_ws_create(const maclab_ws_config* cfg, void* stream, maclab_ws_t* out
     if (cfg->res < 64 || cfg->res % 64 || cfg->channels < 64 || cfg->channels % 64 || cfg->blocks < 0 ||
         cfg->blocks > 64 || cfg->max_batch < 1)
         return wfail(nullptr, MACLAB_E_ARG, "need res and channels multiples of 64, 0 <= blocks <= 64, max_batch >= 1");
+    if (cfg->tensor_path < 0 || cfg->tensor_path > 2)
+        return wfail(nullptr, MACLAB_E_ARG, "tensor_path must be 0, 1 or 2");
     for (int l = 0; l < cfg->blocks; ++l)
         if (cfg->dilation[l] < 1 || cfg->dilation[l] >= cfg->res)
             return wfail(nullptr, MACLAB_E_ARG, "dilations must be in 1..res-1");
@@ -1047,6 +1334,8 @@ int maclab_ws_create(const maclab_ws_config* cfg, void* stream, maclab_ws_t* out
     if (e == cudaSuccess) e = cudaMemsetAsync(w->tc_err, 0, sizeof(int), w->stream);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(ws_conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ws_conv_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT_SMEM);
     if (e == cudaSuccess) {
         pack_all(w);
         e = cudaStreamSynchronize(w->stream);

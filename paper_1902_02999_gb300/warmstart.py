@@ -49,7 +49,9 @@ class WarmStartNet:
         self.max_batch = max_batch
         cfg = _abi.WSConfig()
         cfg.res, cfg.channels, cfg.blocks, cfg.max_batch, cfg.seed = res, channels, len(dilations), max_batch, seed
-        cfg.tensor_path = tensor_path  # 0: mma.sync, 1: tcgen05 for the 128 -> 128 convolutions
+        # the 128 -> 128 convolutions on 0: tcgen05 fed by TMA, 1: tcgen05 fed
+        # by cp.async, 2: mma.sync
+        cfg.tensor_path = tensor_path
         for k, d in enumerate(dilations):
             cfg.dilation[k] = int(d)
         if stream is None:

@@ -81,6 +81,10 @@ def test_warm_start_config_layout_and_argument_checks(tmp_path):
     h = ctypes.c_void_p()
     assert lib.maclab_ws_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1 and not h.value
     assert b"multiples of 64" in lib.maclab_last_error(None)
+    cfg = _abi.WSConfig(res=64, channels=128, blocks=2, max_batch=1, tensor_path=3)
+    cfg.dilation[0] = cfg.dilation[1] = 1
+    assert lib.maclab_ws_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1 and not h.value
+    assert b"tensor_path" in lib.maclab_last_error(None)
     assert lib.maclab_ws_forward(None, 1, None, None) == -1
 
 

@@ -49,7 +49,7 @@ def random_setup(net, C, dil, batch, seed):
     return theta, X, T, w
 
 
-@pytest.mark.parametrize("C,dil,path", [(128, (1, 2), 0), (128, (1, 2), 1), (64, (3,), 0)])
+@pytest.mark.parametrize("C,dil,path", [(128, (1, 2), 0), (128, (1, 2), 1), (128, (1, 2), 2), (64, (3,), 0)])
 def test_forward_matches_reference(C, dil, path):
     net = make(C, dil, 2, tensor_path=path)
     theta, X, _, _ = random_setup(net, C, dil, 2, 1)
@@ -60,7 +60,7 @@ def test_forward_matches_reference(C, dil, path):
     net.close()
 
 
-@pytest.mark.parametrize("C,dil,path", [(128, (1, 4), 0), (128, (1, 4), 1), (64, (2,), 0)])
+@pytest.mark.parametrize("C,dil,path", [(128, (1, 4), 0), (128, (1, 4), 1), (128, (1, 4), 2), (64, (2,), 0)])
 def test_gradients_match_reference(C, dil, path):
     net = make(C, dil, 2, tensor_path=path)
     theta, X, T, w = random_setup(net, C, dil, 2, 2)
@@ -78,12 +78,14 @@ def test_gradients_match_reference(C, dil, path):
     net.close()
 
 
-def test_tcgen05_and_mma_sync_paths_agree():
-    """The 128 -> 128 convolutions on mma.sync (default) and on tcgen05 give
-    the same outputs and gradients up to the order of float summation and
-    the rounding of the stored bfloat16 activations."""
+@pytest.mark.parametrize("path", [0, 1])
+def test_tcgen05_and_mma_sync_paths_agree(path):
+    """The 128 -> 128 convolutions on tcgen05 (operands staged by TMA, the
+    default, or by cp.async) and on mma.sync give the same outputs and
+    gradients up to the order of float summation and the rounding of the
+    stored bfloat16 activations."""
     C, dil = 128, (1, 2, 4)
-    nets = [make(C, dil, 2, tensor_path=t) for t in (0, 1)]
+    nets = [make(C, dil, 2, tensor_path=t) for t in (2, path)]
     theta, X, T, w = random_setup(nets[0], C, dil, 2, 4)
     dev = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
     outs, grads = [], []
