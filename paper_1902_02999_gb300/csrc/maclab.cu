@@ -181,6 +181,7 @@ Fields<T> make_fields(const maclab_s* s)
     f.nx = s->grid.nx;
     f.ny = s->grid.ny;
     f.pitch = s->pitch;
+    f.idx32 = (int64_t)s->pitch * s->grid.ny < ((int64_t)1 << 31) ? 1 : 0;
     for (int k = 0; k < 4; ++k) f.edge[k] = s->bc.edge[k];
     f.c = make_coef<T>(s->params, s->e, s->dt);
     return f;
@@ -268,9 +269,10 @@ int launch_step(maclab_t s)
         }
         if (s->kernel == MACLAB_KERNEL_TILE) {
             const size_t smem = tile::smem_bytes<T>();
+            const dim3 grid(tx, std::min(ty, 65535), (ty + 65534) / 65535);
             switch (s->fmode) {  // compile-time variants for the force terms present
 #define MACLAB_FM(m) \
-    case m: step_tile_kernel<T, m><<<tx * ty, tile::THREADS, smem, s->stream>>>(f, tx, td); break;
+    case m: step_tile_kernel<T, m><<<grid, tile::THREADS, smem, s->stream>>>(f, tx, ty, td); break;
                 MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
 #undef MACLAB_FM
             }
@@ -1552,6 +1554,7 @@ void fill_insts(maclab_batch_t b, const std::vector<Prepared>& P, std::vector<Ba
             f.nx = P[i].nx;
             f.ny = P[i].ny;
             f.pitch = P[i].pitch;
+            f.idx32 = (int64_t)P[i].pitch * P[i].ny < ((int64_t)1 << 31) ? 1 : 0;
             for (int k = 0; k < 4; ++k) f.edge[k] = P[i].bc.edge[k];
             f.c = make_coef<T>(P[i].params, P[i].e, P[i].dt);
         }

@@ -71,6 +71,7 @@ struct Fields {
     T* u1;
     T* v1;
     int nx, ny, pitch;
+    int idx32;    // 1 when pitch * ny < 2^31: node offsets fit in an int
     int edge[4];  // W, E, S, N
     Coef<T> c;
 };
@@ -850,10 +851,15 @@ __global__ void dirichlet_kernel(T* __restrict__ eta, T* __restrict__ u, T* __re
 //      has no bounce-back link, the tile's Dirichlet nodes are set from the
 //      new values after a second barrier.
 // Thread (tx, ty) of 32 x 8 owns the node pairs at tile columns 2 + 2 tx,
-// 3 + 2 tx of tile rows 1 + 2 ty and 2 + 2 ty.
+// 3 + 2 tx of tile rows 1 + 2 ty and 2 + 2 ty.  Tiles whose reads and
+// writes all lie inside the grid (every tile but the outermost ring) load
+// without edge rules or bounds tests, with 32-bit node offsets.
 namespace tile {
-constexpr int TX = 64, TY = 16;            // nodes updated per tile
-constexpr int THREADS = 256;               // 32 x 8
+#ifndef MACLAB_TILE_TY
+#define MACLAB_TILE_TY 16
+#endif
+constexpr int TX = 64, TY = MACLAB_TILE_TY;  // nodes updated per tile
+constexpr int THREADS = 16 * TY;           // 32 x TY / 2
 constexpr int PC = TX / 2 + 2;             // 34 node pairs per tile row (with halo)
 constexpr int IR = TY + 2;                 // 18 tile rows (with halo)
 constexpr int IW = 2 * PC;                 // 68 tile columns: global x0 - 2 .. x0 + 65
@@ -922,6 +928,34 @@ __device__ __forceinline__ void load_pair(const Fields<T>& f, int y, int x, Raw<
     }
 }
 
+// Phase A of the tile at (x0, y0) reads grid rows y0 - 1 .. y0 + 16 and
+// columns x0 - 2 .. x0 + 65 only.
+__device__ __forceinline__ bool tile_interior(int nx, int ny, int x0, int y0)
+{
+    return x0 >= 2 && x0 + tile::TX + 2 <= nx && y0 >= 1 && y0 + tile::TY + 1 <= ny;
+}
+// A tile whose reads and writes all lie inside the grid (no edge rule, no
+// bounds test) and whose offsets fit in 32 bits.
+template <typename T>
+__device__ __forceinline__ bool tile_inside(const Fields<T>& f, int x0, int y0)
+{
+    return f.idx32 && tile_interior(f.nx, f.ny, x0, y0);
+}
+
+// The pair at node offset `off` of an inside tile.
+template <typename T>
+__device__ __forceinline__ void load_pair_in(const Fields<T>& f, int off, Raw<T> (&raw)[2], uint32_t& types)
+{
+    using V2 = typename Vec2<T>::type;
+    const V2 e2 = *reinterpret_cast<const V2*>(f.eta + off);
+    const V2 u2 = *reinterpret_cast<const V2*>(f.u + off);
+    const V2 v2 = *reinterpret_cast<const V2*>(f.v + off);
+    const V2 d2 = *reinterpret_cast<const V2*>(f.D + off);
+    types = *reinterpret_cast<const uint16_t*>(f.type + off);
+    raw[0] = Raw<T>{e2.x, u2.x, v2.x, d2.x, 0};
+    raw[1] = Raw<T>{e2.y, u2.y, v2.y, d2.y, 0};
+}
+
 template <typename T>
 __device__ __forceinline__ void store_pair(tile::Derived<T>& sm, int pr, int lc, const Src<T>& a, const Src<T>& b)
 {
@@ -974,7 +1008,7 @@ __device__ __forceinline__ void staged_pair(const tma::Stage& st, int lr, int lc
 // through the edge rules, derived one node at a time and stored to shared
 // memory (FP64; FP32 uses the paired tile_phase_a_f32).
 template <typename T, int FM>
-__device__ __forceinline__ void tile_phase_a(const Fields<T>& f, int x0, int y0, tile::Derived<T>& sm,
+__device__ __forceinline__ void tile_phase_a(const Fields<T>& f, int x0, int y0, bool inside, tile::Derived<T>& sm,
                                              Src<T> (&own)[2][2], uint32_t (&own_types)[2])
 {
     using namespace tile;
@@ -989,9 +1023,16 @@ __device__ __forceinline__ void tile_phase_a(const Fields<T>& f, int x0, int y0,
         if (h < 2 * IR) { hpc = h < IR ? 0 : PC - 1; hpr = h % IR; }
         else { const int u = h - 2 * IR; hpr = u < PC - 2 ? 0 : IR - 1; hpc = 1 + u % (PC - 2); }
     }
+    if (inside) {
+        const int off = (y0 + 2 * tyy) * f.pitch + x0 + 2 * tx;
+        load_pair_in(f, off, raw[0], own_types[0]);
+        load_pair_in(f, off + f.pitch, raw[1], own_types[1]);
+        if (has_halo) load_pair_in(f, (y0 - 1 + hpr) * f.pitch + x0 - 2 + 2 * hpc, hraw, htypes);
+    } else {
 #pragma unroll
-    for (int r = 0; r < 2; ++r) load_pair(f, y0 + 2 * tyy + r, x0 + 2 * tx, raw[r], own_types[r]);
-    if (has_halo) load_pair(f, y0 - 1 + hpr, x0 - 2 + 2 * hpc, hraw, htypes);
+        for (int r = 0; r < 2; ++r) load_pair(f, y0 + 2 * tyy + r, x0 + 2 * tx, raw[r], own_types[r]);
+        if (has_halo) load_pair(f, y0 - 1 + hpr, x0 - 2 + 2 * hpc, hraw, htypes);
+    }
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         derive<T, FM>(f.c, raw[r][0], own[r][0]);
@@ -1053,10 +1094,10 @@ __device__ __forceinline__ void node_update(const DR& sm, int lr, int lc, const 
 // Phases B and C of a tile whose phase A is complete and visible; `tile`
 // indexes the per-tile Dirichlet ranges.
 template <typename T>
-__device__ __forceinline__ void tile_phase_bc(const Fields<T>& f, int x0, int y0, int tile, const int* dir_start,
-                                              const DirNode* dir_list, const double* D64, const DirValues& bv,
-                                              const tile::Derived<T>& sm, const Src<T> (&own)[2][2],
-                                              const uint32_t (&own_types)[2])
+__device__ __forceinline__ void tile_phase_bc(const Fields<T>& f, int x0, int y0, bool inside, int tile,
+                                              const int* dir_start, const DirNode* dir_list, const double* D64,
+                                              const DirValues& bv, const tile::Derived<T>& sm,
+                                              const Src<T> (&own)[2][2], const uint32_t (&own_types)[2])
 {
     using namespace tile;
     using V2 = typename Vec2<T>::type;
@@ -1074,14 +1115,14 @@ __device__ __forceinline__ void tile_phase_bc(const Fields<T>& f, int x0, int y0
             const int lc = 2 + 2 * tx + k;  // tile column of the node
             const int x = x0 + 2 * tx + k;
             const uint8_t ty = (uint8_t)(own_types[r] >> (8 * k));
-            const bool ok = x < f.nx && y < f.ny && (ty & KIND_MASK) != K_SOLID && !(ty & GENERAL_BIT);
+            const bool ok = (inside || (x < f.nx && y < f.ny)) && (ty & KIND_MASK) != K_SOLID && !(ty & GENERAL_BIT);
             okmask |= (ok ? 1u : 0u) << k;
             const Src<T>& me = own[r][k];
             node_update<T>(sm, lr, lc, K, me.eta, me.D, me.ownh, me.hFx, me.hFy,
                            (ty & KIND_MASK) == K_NOSLIP, oe[k], ou[k], ov[k]);
         }
         if (okmask == 0) continue;
-        const size_t idx = (size_t)y * f.pitch + x0 + 2 * tx;
+        const size_t idx = inside ? (size_t)(y * f.pitch + x0 + 2 * tx) : (size_t)y * f.pitch + x0 + 2 * tx;
         if (okmask == 3u) {
             *reinterpret_cast<V2*>(f.eta1 + idx) = V2{oe[0], oe[1]};
             *reinterpret_cast<V2*>(f.u1 + idx) = V2{ou[0], ou[1]};
@@ -1122,8 +1163,9 @@ __device__ __forceinline__ void store_pair2(tile::Derived<float>& sm, int pr, in
 }
 
 template <int FM>
-__device__ __forceinline__ void tile_phase_a_f32(const Fields<float>& f, int x0, int y0, const tma::Stage* st,
-                                                 tile::Derived<float>& sm, Src2 (&own)[2], uint32_t (&own_types)[2])
+__device__ __forceinline__ void tile_phase_a_f32(const Fields<float>& f, int x0, int y0, bool inside,
+                                                 const tma::Stage* st, tile::Derived<float>& sm, Src2 (&own)[2],
+                                                 uint32_t (&own_types)[2])
 {
     using namespace tile;
     const int tx = threadIdx.x & 31, tyy = threadIdx.x >> 5;
@@ -1141,6 +1183,11 @@ __device__ __forceinline__ void tile_phase_a_f32(const Fields<float>& f, int x0,
 #pragma unroll
         for (int r = 0; r < 2; ++r) staged_pair(*st, 1 + 2 * tyy + r, 2 + 2 * tx, raw[r], own_types[r]);
         if (has_halo) staged_pair(*st, hpr, 2 * hpc, hraw, htypes);
+    } else if (inside) {
+        const int off = (y0 + 2 * tyy) * f.pitch + x0 + 2 * tx;
+        load_pair_in(f, off, raw[0], own_types[0]);
+        load_pair_in(f, off + f.pitch, raw[1], own_types[1]);
+        if (has_halo) load_pair_in(f, (y0 - 1 + hpr) * f.pitch + x0 - 2 + 2 * hpc, hraw, htypes);
     } else {
 #pragma unroll
         for (int r = 0; r < 2; ++r) load_pair(f, y0 + 2 * tyy + r, x0 + 2 * tx, raw[r], own_types[r]);
@@ -1169,7 +1216,7 @@ __device__ __forceinline__ Src<float> lane_of(const Src2& s, int k)
     return o;
 }
 
-__device__ __forceinline__ void tile_phase_bc_f32(const Fields<float>& f, int x0, int y0, int tile,
+__device__ __forceinline__ void tile_phase_bc_f32(const Fields<float>& f, int x0, int y0, bool inside, int tile,
                                                   const int* dir_start, const DirNode* dir_list, const double* D64,
                                                   const DirValues& bv, const tile::Derived<float>& sm,
                                                   const Src2 (&own)[2], const uint32_t (&own_types)[2])
@@ -1178,7 +1225,7 @@ __device__ __forceinline__ void tile_phase_bc_f32(const Fields<float>& f, int x0
     // neighbours' (eta, D) regrouped by lane, which costs more moves and
     // loads than the paired arithmetic saves
     const Src<float> o[2][2] = {{lane_of(own[0], 0), lane_of(own[0], 1)}, {lane_of(own[1], 0), lane_of(own[1], 1)}};
-    tile_phase_bc<float>(f, x0, y0, tile, dir_start, dir_list, D64, bv, sm, o, own_types);
+    tile_phase_bc<float>(f, x0, y0, inside, tile, dir_start, dir_list, D64, bv, sm, o, own_types);
 }
 
 // Update of one tile whose top-left updated node is (x0, y0); `tile` indexes
@@ -1189,27 +1236,31 @@ __device__ __forceinline__ void tile_update(const Fields<T>& f, int x0, int y0, 
                                             tile::Derived<T>& sm)
 {
     uint32_t own_types[2];
+    const bool inside = tile_inside(f, x0, y0);
     if constexpr (std::is_same<T, float>::value) {
         Src2 own[2];
-        tile_phase_a_f32<FM>(f, x0, y0, nullptr, sm, own, own_types);
+        tile_phase_a_f32<FM>(f, x0, y0, inside, nullptr, sm, own, own_types);
         __syncthreads();
-        tile_phase_bc_f32(f, x0, y0, tile, dir_start, dir_list, D64, bv, sm, own, own_types);
+        tile_phase_bc_f32(f, x0, y0, inside, tile, dir_start, dir_list, D64, bv, sm, own, own_types);
     } else {
         Src<T> own[2][2];
-        tile_phase_a<T, FM>(f, x0, y0, sm, own, own_types);
+        tile_phase_a<T, FM>(f, x0, y0, inside, sm, own, own_types);
         __syncthreads();
-        tile_phase_bc<T>(f, x0, y0, tile, dir_start, dir_list, D64, bv, sm, own, own_types);
+        tile_phase_bc<T>(f, x0, y0, inside, tile, dir_start, dir_list, D64, bv, sm, own, own_types);
     }
 }
 
 template <typename T, int FM>
 __global__ void __launch_bounds__(tile::THREADS, tile::MinBlocks<T>::value)
-step_tile_kernel(const __grid_constant__ Fields<T> f, int tiles_x, const __grid_constant__ TileDirichlet td)
+step_tile_kernel(const __grid_constant__ Fields<T> f, int tiles_x, int tiles_y, const __grid_constant__ TileDirichlet td)
 {
+    // block (bx, by, bz) updates tile column bx of tile row bz * gridDim.y + by
     extern __shared__ __align__(16) unsigned char smem_raw[];
     tile::Derived<T>& sm = *reinterpret_cast<tile::Derived<T>*>(smem_raw);
-    const int x0 = (blockIdx.x % tiles_x) * tile::TX, y0 = (blockIdx.x / tiles_x) * tile::TY;
-    tile_update<T, FM>(f, x0, y0, blockIdx.x, td.start, td.list, td.D64, td.bv, sm);
+    const int ty = blockIdx.z * gridDim.y + blockIdx.y;
+    if (ty >= tiles_y) return;  // whole block
+    tile_update<T, FM>(f, blockIdx.x * tile::TX, ty * tile::TY, ty * tiles_x + blockIdx.x, td.start, td.list, td.D64,
+                       td.bv, sm);
 }
 
 // Single step over a list of tiles (the tiles a two-step launch leaves out).
@@ -1416,13 +1467,6 @@ __device__ __forceinline__ void tma_stage(const TmaMaps& m, tma::Stage& st, uint
     tma_load_2d((uint32_t)__cvta_generic_to_shared(&st.f[3][0]), &m.D, x0 - 4, y0 - 1, bar);
     tma_load_2d((uint32_t)__cvta_generic_to_shared(&st.type[0]), &m.type, x0 - 16, y0 - 1, bar);
 }
-// Phase A of the tile at (x0, y0) reads grid columns x0 - 2 .. x0 + 65 and
-// rows y0 - 1 .. y0 + 16 only.
-__device__ __forceinline__ bool tile_interior(int nx, int ny, int x0, int y0)
-{
-    return x0 >= 2 && x0 + tile::TX + 2 <= nx && y0 >= 1 && y0 + tile::TY + 1 <= ny;
-}
-
 template <int FM>
 __global__ void __launch_bounds__(tile::THREADS, 3)
 step_tile_tma_kernel(const __grid_constant__ Fields<float> f, const __grid_constant__ TmaMaps maps, int tiles_x,
@@ -1463,7 +1507,7 @@ step_tile_tma_kernel(const __grid_constant__ Fields<float> f, const __grid_const
         }
         Src2 own[2];
         uint32_t own_types[2];
-        tile_phase_a_f32<FM>(f, x0, y0, staged ? &st : nullptr, sm, own, own_types);
+        tile_phase_a_f32<FM>(f, x0, y0, false, staged ? &st : nullptr, sm, own, own_types);
         __syncthreads();  // derived values visible; the staging buffer is free again
         if (threadIdx.x == 0) {
             const int tn = t + gridDim.x;
@@ -1472,7 +1516,7 @@ step_tile_tma_kernel(const __grid_constant__ Fields<float> f, const __grid_const
                 if (tile_interior(f.nx, f.ny, xn, yn)) tma_stage(maps, st, bar, xn, yn);
             }
         }
-        tile_phase_bc_f32(f, x0, y0, t, td.start, td.list, td.D64, td.bv, sm, own, own_types);
+        tile_phase_bc_f32(f, x0, y0, staged && f.idx32, t, td.start, td.list, td.D64, td.bv, sm, own, own_types);
         __syncthreads();  // phase B reads of `sm` end before the next phase A writes it
     }
 }
