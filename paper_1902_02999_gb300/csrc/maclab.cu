@@ -235,11 +235,12 @@ int launch_step(maclab_t s)
         const size_t plane = (size_t)s->pitch * s->grid.ny;
         const size_t smem = sizeof(elab::Smem<T>);
         const T omega = (T)(1.0 / s->tau);
+        const dim3 grid(tx, std::min(ty, 65535), (ty + 65534) / 65535);
         switch (s->fmode) {
 #define MACLAB_FM(m)                                                                                        \
     case m:                                                                                                 \
-        step_elab_kernel<T, m><<<tx * ty, tile::THREADS, smem, s->stream>>>(f, (const T*)s->gdist[s->cur], \
-                                                                          (T*)s->gdist[b], plane, omega, tx); \
+        step_elab_kernel<T, m><<<grid, tile::THREADS, smem, s->stream>>>(f, (const T*)s->gdist[s->cur], \
+                                                                       (T*)s->gdist[b], plane, omega, ty); \
         break;
             MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
 #undef MACLAB_FM
