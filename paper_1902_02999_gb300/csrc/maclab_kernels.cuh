@@ -1632,46 +1632,66 @@ step_elab_kernel(const __grid_constant__ Fields<T> f, const T* __restrict__ gin,
     const int x0 = blockIdx.x * TX, y0 = tyi * TY;
     const bool inside = tile_inside(f, x0, y0);
     // ---- phase A: collide the tile and its halo (window rows y0-1 .. y0+16,
-    // columns x0-2 .. x0+65)
-    for (int p = threadIdx.x; p < IR * IW; p += THREADS) {
-        const int r = p / IW, c = p - r * IW;
-        uint8_t fl = 0;
-        size_t m;
-        bool ok;
-        if (inside) {
-            m = (size_t)((y0 - 1 + r) * f.pitch + x0 - 2 + c);
-            ok = true;
-        } else {
-            const int rr = resolve_index(y0 - 1 + r, f.ny, f.edge[2], f.edge[3], 2, fl);
-            const int cc = resolve_index(x0 - 2 + c, f.nx, f.edge[0], f.edge[1], 1, fl);
-            ok = rr >= 0 && cc >= 0;
-            m = ok ? (size_t)rr * f.pitch + cc : 0;
+    // columns x0-2 .. x0+65), two window nodes per thread and round: the
+    // loads of both (type, D and the nine planes) are issued before either
+    // is used, so that they are in flight together
+    constexpr int NA = IR * IW;
+    for (int p0 = threadIdx.x; p0 < NA; p0 += 2 * THREADS) {
+        T g[2][9], Dn[2];
+        uint8_t fl[2] = {0, 0}, ty[2] = {0, 0};
+        bool in[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int p = p0 + k * THREADS;
+            const int r = p / IW, c = p - r * IW;
+            size_t m = 0;
+            in[k] = p < NA;
+            if (inside) {
+                m = (size_t)((y0 - 1 + r) * f.pitch + x0 - 2 + c);
+            } else if (in[k]) {
+                const int rr = resolve_index(y0 - 1 + r, f.ny, f.edge[2], f.edge[3], 2, fl[k]);
+                const int cc = resolve_index(x0 - 2 + c, f.nx, f.edge[0], f.edge[1], 1, fl[k]);
+                if (rr >= 0 && cc >= 0)
+                    m = (size_t)rr * f.pitch + cc;
+                else
+                    in[k] = false;  // behind a bounce-back edge: unusable
+            }
+            if (in[k]) {  // solid nodes are loaded too and dropped below
+                ty[k] = f.type[m];
+                Dn[k] = f.D[m];
+#pragma unroll
+                for (int b = 0; b < 9; ++b) g[k][b] = gin[b * plane + m];
+            }
         }
-        ok = ok && (f.type[m] & KIND_MASK) != K_SOLID;
-        sm.use[r][c] = ok ? 1 : 0;
-        if (!ok) continue;
-        T g[9];
 #pragma unroll
-        for (int b = 0; b < 9; ++b) g[b] = gin[b * plane + m];
-        const T D = f.D[m];
-        T eta, mx, my;
-        elab_moments(g, eta, mx, my);
-        const T inv = O::rcp(D + eta);
-        const T u = K.e * mx * inv, v = K.e * my * inv;
-        T o[9], Fx, Fy;
-        elab_equilibrium<T, FM>(K, eta, D, u, v, o, Fx, Fy);
-        T post[9];
+        for (int k = 0; k < 2; ++k) {
+            const int p = p0 + k * THREADS;
+            if (p >= NA) continue;
+            const int r = p / IW, c = p - r * IW;
+            const bool ok = in[k] && (ty[k] & KIND_MASK) != K_SOLID;
+            sm.use[r][c] = ok ? 1 : 0;
+            if (!ok) continue;
+            const T D = Dn[k];
+            T eta, mx, my;
+            elab_moments(g[k], eta, mx, my);
+            const T inv = O::rcp(D + eta);
+            const T u = K.e * mx * inv, v = K.e * my * inv;
+            T o[9], Fx, Fy;
+            elab_equilibrium<T, FM>(K, eta, D, u, v, o, Fx, Fy);
+            T post[9];
 #pragma unroll
-        for (int b = 0; b < 9; ++b) post[b] = g[b] + omega * (o[b] - g[b]);
-        if (fl == 0) {
+            for (int b = 0; b < 9; ++b) post[b] = g[k][b] + omega * (o[b] - g[k][b]);
+            const uint8_t m8 = fl[k];
+            if (m8 == 0) {
 #pragma unroll
-            for (int b = 0; b < 9; ++b) sm.gs[b][r][c] = post[b];
-        } else {  // specular ghost: its g*_b serves the mirrored direction
+                for (int b = 0; b < 9; ++b) sm.gs[b][r][c] = post[b];
+            } else {  // specular ghost: its g*_b serves the mirrored direction
 #pragma unroll
-            for (int b = 0; b < 9; ++b) sm.gs[mirror_of(b, fl)][r][c] = post[b];
+                for (int b = 0; b < 9; ++b) sm.gs[mirror_of(b, m8)][r][c] = post[b];
+            }
+            sm.ed[r][c] = V2{eta, D};
+            sm.F[r][c] = V2{K.KF * ((m8 & 1) ? -Fx : Fx), K.KF * ((m8 & 2) ? -Fy : Fy)};
         }
-        sm.ed[r][c] = V2{eta, D};
-        sm.F[r][c] = V2{K.KF * ((fl & 1) ? -Fx : Fx), K.KF * ((fl & 2) ? -Fy : Fy)};
     }
     __syncthreads();
     // ---- phase B: stream into the tile's nodes
