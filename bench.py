@@ -34,6 +34,12 @@ sys.path.insert(0, ROOT)
 METRIC = ("MLUPS & % of HBM roofline (FP32 step); wall time to residual 1e-8, "
           "warm-start vs plain")
 BYTES_PER_NODE = {"f32": 29, "f64": 57}   # read eta,u,v,D + type, write eta,u,v
+HBM_NOMINAL_GBS = 7900.0                   # GB300 HBM3e, nominal
+# FP64 arithmetic of one node update, multiply-add counted as two: the
+# source quantities (53, with the friction term) and the gather / update (67),
+# plus one square root and one reciprocal
+F64_FLOPS_PER_NODE = 120
+F64_NOMINAL_TFLOPS = 1.25                  # GB300 dense FP64, nominal (no measured FP64 peak)
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_JSON = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
 # step-kernel codes of the library (maclab_step_kernel)
@@ -267,6 +273,7 @@ def main():
     peak, peak_src = hbm_peak()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src,
+                "frac_of_nominal_7900": achieved / HBM_NOMINAL_GBS,
                 "kernel": KERNEL_SYMBOL[info["step_kernel"]] % ("float" if args.precision == "f32" else "double"),
                 "dirichlet_fused": bool(info["dirichlet_fused"]),
                 "bytes_per_node": BYTES_PER_NODE[args.precision],
@@ -380,8 +387,13 @@ def main():
         torch.cuda.synchronize()
         k64, n64 = s64.get_profile()
         ms64 = e0.elapsed_time(e1) / args.f64_steps
+        k64_s = k64 / max(1, n64) / 1e3
         f64 = {"value": nodes / (ms64 / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms64,
-               "kernel_ms_per_launch": k64 / max(1, n64),
+               "kernel_ms_per_launch": k64_s * 1e3,
+               "alu_roofline": {"bound": "alu", "flops_per_node": F64_FLOPS_PER_NODE,
+                                "achieved": F64_FLOPS_PER_NODE * nodes / k64_s / 1e12,
+                                "peak": F64_NOMINAL_TFLOPS, "unit": "TFLOP/s", "peak_source": "nominal",
+                                "frac": F64_FLOPS_PER_NODE * nodes / k64_s / 1e12 / F64_NOMINAL_TFLOPS},
                "achieved_gbs": BYTES_PER_NODE["f64"] * nodes / (k64 / max(1, n64) / 1e3) / 1e9,
                "bytes_per_node": BYTES_PER_NODE["f64"],
                "step_kernel": ("tile 64x16" if choice64 == 0 else "TMA-staged tile 64x16" if choice64 == 5
@@ -454,6 +466,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "fluid_mlups": world * info["n_fluid"] * args.steps / (ms / 1e3) / 1e6,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": args.precision, "data": "synthetic",
                 "config": {"workload": workload, "nodes": nodes,

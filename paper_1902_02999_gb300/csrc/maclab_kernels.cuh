@@ -1636,12 +1636,17 @@ step_elab_kernel(const __grid_constant__ Fields<T> f, const T* __restrict__ gin,
     // loads of both (type, D and the nine planes) are issued before either
     // is used, so that they are in flight together
     constexpr int NA = IR * IW;
-    for (int p0 = threadIdx.x; p0 < NA; p0 += 2 * THREADS) {
-        T g[2][9], Dn[2];
-        uint8_t fl[2] = {0, 0}, ty[2] = {0, 0};
-        bool in[2];
+#ifndef MACLAB_ELAB_PA
+#define MACLAB_ELAB_PA 3
+#endif
+    constexpr int PA = MACLAB_ELAB_PA;
+    int all_use = 1;  // every window node this thread visits is usable
+    for (int p0 = threadIdx.x; p0 < NA; p0 += PA * THREADS) {
+        T g[PA][9], Dn[PA];
+        uint8_t fl[PA] = {}, ty[PA] = {};
+        bool in[PA];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < PA; ++k) {
             const int p = p0 + k * THREADS;
             const int r = p / IW, c = p - r * IW;
             size_t m = 0;
@@ -1664,12 +1669,13 @@ step_elab_kernel(const __grid_constant__ Fields<T> f, const T* __restrict__ gin,
             }
         }
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < PA; ++k) {
             const int p = p0 + k * THREADS;
             if (p >= NA) continue;
             const int r = p / IW, c = p - r * IW;
             const bool ok = in[k] && (ty[k] & KIND_MASK) != K_SOLID;
             sm.use[r][c] = ok ? 1 : 0;
+            all_use &= ok ? 1 : 0;
             if (!ok) continue;
             const T D = Dn[k];
             T eta, mx, my;
@@ -1693,14 +1699,15 @@ step_elab_kernel(const __grid_constant__ Fields<T> f, const T* __restrict__ gin,
             sm.F[r][c] = V2{K.KF * ((m8 & 1) ? -Fx : Fx), K.KF * ((m8 & 2) ? -Fy : Fy)};
         }
     }
-    __syncthreads();
+    // a tile whose whole window is usable streams without per-link checks
+    const bool dense = __syncthreads_and(all_use) != 0;
     // ---- phase B: stream into the tile's nodes
     for (int q = threadIdx.x; q < TX * TY; q += THREADS) {
         const int qr = q / TX, qc = q % TX;
         const int r = 1 + qr, c = 2 + qc;
         const int x = x0 + qc, y = y0 + qr;
         if (!inside && (x >= f.nx || y >= f.ny)) continue;
-        if (!sm.use[r][c]) continue;
+        if (!dense && !sm.use[r][c]) continue;
         const V2 me = sm.ed[r][c], Fm = sm.F[r][c];
         T gn[9];
         gn[0] = sm.gs[0][r][c];
@@ -1708,7 +1715,7 @@ step_elab_kernel(const __grid_constant__ Fields<T> f, const T* __restrict__ gin,
         for (int a = 1; a < 9; ++a) {
             const int cx = lat_cx(a), cy = lat_cy(a);
             const int pr = r - cy, pc = c - cx;
-            if (sm.use[pr][pc]) {
+            if (dense || sm.use[pr][pc]) {
                 const V2 ep = sm.ed[pr][pc], Fp = sm.F[pr][pc];
                 const T lam = (a & 1) ? T(1) : T(0.25);
                 const T bed = -K.G6 * (me.x + ep.x) * (ep.y - me.y);
