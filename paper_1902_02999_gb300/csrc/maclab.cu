@@ -8,6 +8,7 @@
 // memory, classifies nodes, and sequences the launches.
 #include "maclab.h"
 #include "maclab_kernels.cuh"
+#include "maclab_elab.cuh"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
