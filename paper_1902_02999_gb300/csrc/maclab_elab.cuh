@@ -30,7 +30,7 @@ template <typename T>
 struct Smem {
     T gs[9][tile::IR][tile::IW];                   // post-collision g*, direction-mapped for mirrors
     typename Vec2<T>::type ed[tile::IR][tile::IW]; // (eta, D)
-    typename Vec2<T>::type F[tile::IR][tile::IW];  // force, mirrored for specular ghosts
+    typename Vec2<T>::type F[tile::IR][tile::IW];  // KF F (source half already in gs)
     uint8_t use[tile::IR][tile::IW];               // usable source
 };
 template <typename T> struct MinBlocks { static constexpr int value = 3; };
@@ -89,6 +89,16 @@ __device__ __forceinline__ void elab_equilibrium(const Coef<T>& c, T eta, T D, T
     }
 }
 
+// c_a . (fx, fy) for a = 1 .. 8 (a known at compile time)
+template <typename T>
+__device__ __forceinline__ T lat_dot(int a, T fx, T fy)
+{
+    const int cx = lat_cx(a), cy = lat_cy(a);
+    if (cx != 0 && cy != 0) return (cx > 0 ? fx : -fx) + (cy > 0 ? fy : -fy);
+    if (cx != 0) return cx > 0 ? fx : -fx;
+    return cy > 0 ? fy : -fy;
+}
+
 // Zeroth and first moments of the nine distributions.
 template <typename T>
 __device__ __forceinline__ void elab_moments(const T (&g)[9], T& eta, T& mx, T& my)
@@ -100,8 +110,14 @@ __device__ __forceinline__ void elab_moments(const T (&g)[9], T& eta, T& mx, T& 
 
 // gin / gout: 9 planes of [ny][pitch]; f.eta1 / u1 / v1 receive the new
 // macroscopic state; omega = 1 / tau.  Block (bx, by, bz) owns tile column
-// bx of tile row bz * gridDim.y + by.  The force is kept in shared memory
-// pre-multiplied by KF.
+// bx of tile row bz * gridDim.y + by.  The centred force term of a link,
+// lambda_a KF c_a . (F_x + F_y), is split in two halves: the source half
+// joins the stored post-collision value g*_a(y) (for a mirror ghost
+// c_mirror(a) . F_mirrored = c_a . F, so it is formed in the node's own
+// frame), the receiver half is added at x from the node's own force.  A
+// bounced link takes g*_abar(x), whose source half is lambda_a KF c_abar . F_x;
+// adding the receiver half lambda_a KF c_a . F_x cancels it, as the rule
+// wants.
 template <typename T, int FM>
 __global__ void __launch_bounds__(tile::THREADS, elab::MinBlocks<T>::value)
 step_elab_kernel(const __grid_constant__ Fields<T> f, const T* __restrict__ gin, T* __restrict__ gout, size_t plane,
@@ -170,9 +186,12 @@ step_elab_kernel(const __grid_constant__ Fields<T> f, const T* __restrict__ gin,
             const T u = K.e * mx * inv, v = K.e * my * inv;
             T o[9], Fx, Fy;
             elab_equilibrium<T, FM>(K, eta, D, u, v, o, Fx, Fy);
+            const T fxs = K.KF * Fx, fys = K.KF * Fy;
             T post[9];
+            post[0] = g[k][0] + omega * (o[0] - g[k][0]);
 #pragma unroll
-            for (int b = 0; b < 9; ++b) post[b] = g[k][b] + omega * (o[b] - g[k][b]);
+            for (int b = 1; b < 9; ++b)
+                post[b] = g[k][b] + omega * (o[b] - g[k][b]) + ((b & 1) ? T(1) : T(0.25)) * lat_dot(b, fxs, fys);
             const uint8_t m8 = fl[k];
             if (m8 == 0) {
 #pragma unroll
@@ -182,7 +201,7 @@ step_elab_kernel(const __grid_constant__ Fields<T> f, const T* __restrict__ gin,
                 for (int b = 0; b < 9; ++b) sm.gs[mirror_of(b, m8)][r][c] = post[b];
             }
             sm.ed[r][c] = V2{eta, D};
-            sm.F[r][c] = V2{K.KF * ((m8 & 1) ? -Fx : Fx), K.KF * ((m8 & 2) ? -Fy : Fy)};
+            sm.F[r][c] = V2{fxs, fys};  // read by the node itself only (receivers lie in the grid)
         }
     }
     // a tile whose whole window is usable streams without per-link checks
@@ -201,20 +220,14 @@ step_elab_kernel(const __grid_constant__ Fields<T> f, const T* __restrict__ gin,
         for (int a = 1; a < 9; ++a) {
             const int cx = lat_cx(a), cy = lat_cy(a);
             const int pr = r - cy, pc = c - cx;
+            const T lam = (a & 1) ? T(1) : T(0.25);
+            const T frc = lat_dot(a, Fm.x, Fm.y);  // receiver half of KF c_a . (F_x + F_y)
             if (dense || sm.use[pr][pc]) {
-                const V2 ep = sm.ed[pr][pc], Fp = sm.F[pr][pc];
-                const T lam = (a & 1) ? T(1) : T(0.25);
+                const V2 ep = sm.ed[pr][pc];
                 const T bed = -K.G6 * (me.x + ep.x) * (ep.y - me.y);
-                T frc;  // KF c_a . (F_x + F_y)
-                if (cx != 0 && cy != 0)
-                    frc = (cx > 0 ? (Fm.x + Fp.x) : -(Fm.x + Fp.x)) + (cy > 0 ? (Fm.y + Fp.y) : -(Fm.y + Fp.y));
-                else if (cx != 0)
-                    frc = cx > 0 ? (Fm.x + Fp.x) : -(Fm.x + Fp.x);
-                else
-                    frc = cy > 0 ? (Fm.y + Fp.y) : -(Fm.y + Fp.y);
                 gn[a] = sm.gs[a][pr][pc] + lam * (bed + frc);
             } else {
-                gn[a] = sm.gs[((a + 3) & 7) + 1][r][c];
+                gn[a] = sm.gs[((a + 3) & 7) + 1][r][c] + lam * frc;
             }
         }
         T eta, mx, my;
