@@ -102,3 +102,23 @@ def test_back_to_macroscopic_and_argument_checks():
     with pytest.raises(MaclabError):
         walled.set_relaxation(1.2)   # no-slip nodes
     walled.close()
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_all_fluid_tiles_match_oracle(precision):
+    """No solid node anywhere: every tile whose window lies in the grid
+    streams without per-link checks; periodic x and specular y edges."""
+    edges = (PERIODIC, PERIODIC, SPECULAR, SPECULAR)
+    case = inputs.random_case(200, 70, 9, edges=edges, solids=False, dirichlet=False)
+    assert (case.mask == FLUID).all()
+    h, u, v, _ = oracle_elab(("dense", edges), case, 0.9, 200)
+    sim = sim_of(case, precision, 0.9)
+    sim.step(200)
+    gh, gu, gv = sim.get_state()
+    th, tu = TOL[precision]
+    assert np.abs(gh - h).max() <= th * np.abs(h).max()
+    scale = np.hypot(u, v).max()
+    if precision == "f64":
+        scale = max(scale, case.g * np.abs(h).max() / case.e)
+    assert np.abs(gu - u).max() <= tu * scale and np.abs(gv - v).max() <= tu * scale
+    sim.close()
