@@ -880,8 +880,13 @@ struct Derived {
 #endif
 template <typename T> struct MinBlocks { static constexpr int value = MACLAB_TILE_MINB; };
 template <> struct MinBlocks<double> { static constexpr int value = 2; };
-// the batch kernel carries per-instance state: three blocks keep it in registers
-template <typename T> struct BatchMinBlocks { static constexpr int value = 3; };
+// the batch kernel carries per-instance state; at four blocks per SM a few
+// bytes of it spill, which costs less than the fourth block gains (0.565 ->
+// 0.521 ms per step of 512 instances)
+#ifndef MACLAB_BATCH_MINB
+#define MACLAB_BATCH_MINB 4
+#endif
+template <typename T> struct BatchMinBlocks { static constexpr int value = MACLAB_BATCH_MINB; };
 template <> struct BatchMinBlocks<double> { static constexpr int value = 2; };
 template <typename T>
 __host__ __device__ constexpr size_t smem_bytes() { return sizeof(Derived<T>); }
