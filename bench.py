@@ -134,6 +134,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, dist_mod, device):
+    """The largest x over the ranks of the process group (x without one):
+    the job's time is its slowest rank's."""
+    if dist_mod is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world, nodes, steps, ms):
+    """Node updates of all ranks (each runs its own replica of `nodes`) per
+    second of the slowest rank, in millions."""
+    return world * nodes * steps / (ms / 1e3) / 1e6
+
+
 def cpu_baseline(case, max_seconds=30.0):
     """The oracle as it stands, single-threaded, on one full-grid step (or
     more while under 10 s)."""
@@ -260,12 +277,9 @@ def main():
     sim.set_profiling(False)
     ms = ev0.elapsed_time(ev1)
     clocks = sampler.stop(t_wall0, t_wall1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     nodes = case.nodes
-    value = world * nodes * args.steps / (ms / 1e3) / 1e6
+    value = whole_job_mlups(world, nodes, args.steps, ms)
 
     # roofline of the dominant kernel (the fused step kernel)
     avg_kernel_s = kernel_ms / 1e3 / max(1, kernel_launches)
@@ -301,10 +315,7 @@ def main():
         sim.get_state(out=hp)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
     e2e = {"value": world * N * args.e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 3 * 8 * N,
            "steps": args.e2e_steps}
