@@ -448,6 +448,31 @@ def main():
                               "p50_steps": float(np.percentile(st[conv], 50)) if conv.any() else None,
                               "p99_steps": float(np.percentile(st[conv], 99)) if conv.any() else None}}
         bt.close()
+        # the batched form against the plain method on the same GPU: every
+        # 16th instance run to steady once as one batch and once one handle
+        # at a time; the same arithmetic stops each instance at the same step
+        sample = ens[::16]
+        bt = Batch(sample, precision=args.precision)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sb, _, _ = bt.run_to_steady(tol=1e-8, max_steps=args.batch_max_steps, check_every=1000)
+        torch.cuda.synchronize()
+        wall_b = time.perf_counter() - t0
+        bt.close()
+        wall_p, same = 0.0, 0
+        for i, c in enumerate(sample):
+            one = Simulation.from_case(c, precision=args.precision)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ok, n1, _ = one.run_to_steady(tol=1e-8, max_steps=args.batch_max_steps, check_every=1000)
+            torch.cuda.synchronize()
+            wall_p += time.perf_counter() - t0
+            same += int((n1 if ok else -1) == int(sb[i]))
+            one.close()
+        batched["batch_vs_plain"] = {
+            "sample": "every 16th instance (%d of %d)" % (len(sample), len(ens)),
+            "converged": int((sb >= 0).sum()), "same_stopping_step": same,
+            "wall_batch_s": wall_b, "wall_plain_one_by_one_s": wall_p, "speedup": wall_p / wall_b}
 
     # learned warm start: wall time to residual 1e-8 from rest vs from the
     # network's proposal on unseen seeded 256 x 256 dish lakes (both FP32

@@ -372,6 +372,19 @@ int maclab_batch_step(maclab_batch_t batch, int64_t n);
 /* Steps per CUDA-graph replay in maclab_batch_step (even, 0 = off). */
 int maclab_batch_set_graph_steps(maclab_batch_t batch, int steps);
 
+/* Persistent steps (no counterpart in the paper; a launch strategy): with
+ * mode 1, maclab_batch_step runs its steps in cooperative launches of one
+ * resident block per slot of the GPU (at most 4096 steps per launch), each
+ * block updating a fixed share of the packed tile list every step and all
+ * blocks meeting at a grid barrier between steps; mode 0 (the default)
+ * launches every step separately, replayed from a CUDA graph, which
+ * measured faster at every batch size tried (one 256 x 256 lake up to 512
+ * instances).  Results are bitwise the same either way.  A grid-barrier
+ * wait is bounded: if one times out, the next maclab_batch_residual or
+ * maclab_batch_get_state returns MACLAB_E_CUDA.  Without cooperative
+ * launch support mode 1 launches per step too.  Other modes: MACLAB_E_ARG. */
+int maclab_batch_set_persistent(maclab_batch_t batch, int mode);
+
 /* Residual of the last step per instance: out[4*i .. 4*i+3] as
  * maclab_residual for instance i.  Synchronises. */
 int maclab_batch_residual(maclab_batch_t batch, double* out);

@@ -394,6 +394,12 @@ class Batch:
     def set_graph_steps(self, steps: int) -> None:
         self._check(self._lib.maclab_batch_set_graph_steps(self._h, int(steps)))
 
+    def set_persistent(self, mode: int) -> None:
+        """1: steps in persistent cooperative launches (grid barrier between
+        steps), 0: one launch per step, replayed from a CUDA graph (the
+        default)."""
+        self._check(self._lib.maclab_batch_set_persistent(self._h, int(mode)))
+
     def residual(self) -> np.ndarray:
         """[count, 4]: residual, mass, max|u|, non-finite count per instance."""
         out = np.zeros(4 * self.count)

@@ -1493,6 +1493,11 @@ struct maclab_batch_s {
     int graph_steps = 64;
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // persistent steps (one cooperative launch for many steps)
+    int persist_mode = 0;           // 0 one launch per step, 1 persistent
+    int persist_grid = 0;           // resident blocks of the persistent kernel (0: not available)
+    GridBarrier* barrier = nullptr;
+    int* persist_err = nullptr;     // set when a grid-barrier wait timed out
     std::string err;
 };
 
@@ -1571,6 +1576,70 @@ void fill_insts(maclab_batch_t b, const std::vector<Prepared>& P, std::vector<Ba
             in.bv.qy[k] = P[i].bc.qy[k].mean;
         }
     }
+}
+
+// Resident blocks of the persistent batch kernel (0 when the device has no
+// cooperative launch).
+template <typename T>
+cudaError_t persistent_setup(maclab_batch_t b)
+{
+    int dev = 0, coop = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step_batch_persistent_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tile::smem_bytes<T>());
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_batch_persistent_kernel<T>, tile::THREADS,
+                                                          tile::smem_bytes<T>());
+    b->persist_grid = (e == cudaSuccess && coop) ? per_sm * sms : 0;
+    return e;
+}
+
+// Whether maclab_batch_step takes the persistent kernel (on request only).
+bool use_persistent(const maclab_batch_s* b) { return b->persist_grid > 0 && b->persist_mode == 1; }
+
+// n steps in cooperative launches of at most 4096 steps each.
+template <typename T>
+int batch_persistent(maclab_batch_t b, int64_t n)
+{
+    const BatchInst<T>* insts = (const BatchInst<T>*)b->insts;
+    const int grid = std::min(b->total_tiles, b->persist_grid);
+    while (n > 0) {
+        int k = (int)std::min<int64_t>(n, 4096);
+        int par = b->cur;
+        const int* dstart = b->dir_fused ? b->dir_start : nullptr;
+        int nsep = b->dir_fused ? 0 : b->n_dir;
+        unsigned int gen0 = 0;
+        void* args[] = {(void*)&insts, (void*)&b->tile_inst, (void*)&b->total_tiles, (void*)&b->active,
+                        (void*)&par, (void*)&k, (void*)&dstart, (void*)&b->dirs, (void*)&b->general,
+                        (void*)&b->n_general, (void*)&b->dir_owner, (void*)&nsep, (void*)&b->barrier,
+                        (void*)&gen0, (void*)&b->persist_err};
+        cudaError_t e = cudaMemsetAsync(b->barrier, 0, sizeof(GridBarrier), b->stream);
+        if (e == cudaSuccess)
+            e = cudaLaunchCooperativeKernel((const void*)step_batch_persistent_kernel<T>, dim3(grid),
+                                            dim3(tile::THREADS), args, tile::smem_bytes<T>(), b->stream);
+        if (e != cudaSuccess)
+            return bfail(b, MACLAB_E_CUDA, std::string("persistent batch launch: ") + cudaGetErrorString(e));
+        b->cur ^= (k & 1);
+        b->n += k;
+        b->have_prev = true;
+        n -= k;
+    }
+    return MACLAB_OK;
+}
+
+// MACLAB_E_CUDA once a grid-barrier wait of the persistent kernel has timed out.
+int check_persist_err(maclab_batch_t b)
+{
+    if (!b->persist_err) return MACLAB_OK;
+    int flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, b->persist_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, MACLAB_E_CUDA, std::string("persistent error flag: ") + cudaGetErrorString(e));
+    if (flag) return bfail(b, MACLAB_E_CUDA, "a grid-barrier wait of the persistent batch kernel timed out");
+    return MACLAB_OK;
 }
 
 template <typename T>
@@ -1758,7 +1827,9 @@ int maclab_batch_create(int count, const maclab_grid* grids, const maclab_params
          (b->tile_inst = (int*)bdev_alloc(b, tile_inst.size() * sizeof(int))) &&
          (b->active = (uint8_t*)bdev_alloc(b, count)) &&
          (b->partial = (double*)bdev_alloc(b, (size_t)b->total_tiles * RED_NVAL * 8)) &&
-         (b->red_out = (double*)bdev_alloc(b, (size_t)count * RED_NVAL * 8));
+         (b->red_out = (double*)bdev_alloc(b, (size_t)count * RED_NVAL * 8)) &&
+         (b->barrier = (GridBarrier*)bdev_alloc(b, sizeof(GridBarrier))) &&
+         (b->persist_err = (int*)bdev_alloc(b, sizeof(int)));
     if (ok && b->n_general) ok = (b->general = (int2*)bdev_alloc(b, general.size() * sizeof(int2))) != nullptr;
     if (ok && b->n_dir)
         ok = (b->dirs = (DirNode*)bdev_alloc(b, dirs.size() * sizeof(DirNode))) &&
@@ -1813,6 +1884,7 @@ int maclab_batch_create(int count, const maclab_grid* grids, const maclab_params
         if (ce == cudaSuccess) ce = cudaMemsetAsync(b->u[k], 0, NP * b->esize, b->stream);
         if (ce == cudaSuccess) ce = cudaMemsetAsync(b->v[k], 0, NP * b->esize, b->stream);
     }
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(b->persist_err, 0, sizeof(int), b->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(b->stream);
     if (ce == cudaSuccess)
         ce = b->prec == MACLAB_F32
@@ -1820,6 +1892,7 @@ int maclab_batch_create(int count, const maclab_grid* grids, const maclab_params
                                    (int)tile::smem_bytes<float>())
             : cudaFuncSetAttribute(step_batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)tile::smem_bytes<double>());
+    if (ce == cudaSuccess) ce = b->prec == MACLAB_F32 ? persistent_setup<float>(b) : persistent_setup<double>(b);
     if (ce != cudaSuccess) {
         bfail(nullptr, MACLAB_E_CUDA, std::string("batch upload: ") + cudaGetErrorString(ce));
         brelease(b);
@@ -1846,6 +1919,7 @@ int maclab_batch_step(maclab_batch_t b, int64_t n)
 {
     if (!b) return bfail(nullptr, MACLAB_E_ARG, "NULL batch");
     if (n < 0) return bfail(b, MACLAB_E_ARG, "n must be >= 0");
+    if (use_persistent(b)) return b->prec == MACLAB_F32 ? batch_persistent<float>(b, n) : batch_persistent<double>(b, n);
     while (b->graph_steps > 0 && n >= b->graph_steps) {
         if (!b->graph[b->cur]) {
             int rc = batch_capture(b);
@@ -1876,10 +1950,20 @@ int maclab_batch_set_graph_steps(maclab_batch_t b, int steps)
     return MACLAB_OK;
 }
 
+int maclab_batch_set_persistent(maclab_batch_t b, int mode)
+{
+    if (!b) return bfail(nullptr, MACLAB_E_ARG, "NULL batch");
+    if (mode < 0 || mode > 1) return bfail(b, MACLAB_E_ARG, "mode must be 0 (one launch per step) or 1 (persistent)");
+    b->persist_mode = mode;
+    return MACLAB_OK;
+}
+
 int maclab_batch_residual(maclab_batch_t b, double* out)
 {
     if (!b || !out) return bfail(b, MACLAB_E_ARG, "NULL argument");
     if (!b->have_prev) return bfail(b, MACLAB_E_STATE, "no step taken since create / set_state");
+    const int prc = check_persist_err(b);
+    if (prc != MACLAB_OK) return prc;
     return b->prec == MACLAB_F32 ? batch_residual_t<float>(b, out) : batch_residual_t<double>(b, out);
 }
 
@@ -1943,6 +2027,8 @@ int maclab_batch_run_to_steady(maclab_batch_t b, double tol, int64_t max_steps, 
 int maclab_batch_get_state(maclab_batch_t b, int i, double* h, double* u, double* v)
 {
     if (!b || i < 0 || i >= b->count) return bfail(b, MACLAB_E_ARG, "bad instance");
+    const int prc = check_persist_err(b);
+    if (prc != MACLAB_OK) return prc;
     const size_t N = (size_t)b->nx[i] * b->ny[i];
     const int c = b->cur;
     const size_t o = b->off[i];

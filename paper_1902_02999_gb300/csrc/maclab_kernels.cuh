@@ -1592,6 +1592,113 @@ __global__ void batch_dirichlet_kernel(const BatchInst<T>* __restrict__ insts, c
 }
 
 // ---------------------------------------------------------------------------
+// Persistent batched steps.  One cooperative launch of G blocks (all
+// resident at once, which the cooperative launch guarantees or refuses)
+// runs `nsteps` steps of the batch: in each step block b updates the tiles
+// b, b + G, ... of the packed list and a grid-stride share of the
+// bounce-back-link nodes (both read only the old state), then every block
+// meets at a grid barrier; Dirichlet nodes that could not be fused into
+// their tiles follow, with a second barrier.  The work of a step is that of
+// step_batch_kernel, batch_general_kernel and batch_dirichlet_kernel, so the
+// results are the same bitwise.
+//
+// Grid barrier: a counter and a generation word in device memory.  Thread 0
+// of each block publishes its block's writes (__threadfence), counts itself
+// in; the last to arrive resets the counter and advances the generation, the
+// others poll it.  The launch's first generation comes from the host, which
+// counts the barriers it has launched.  Every poll is bounded: after
+// BARRIER_POLLS rounds the block sets *err and reports failure, and the
+// kernel's blocks leave instead of stepping on.
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+};
+constexpr unsigned int BARRIER_POLLS = 1u << 22;
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// true when every block has arrived; `gen` is this block's count of the
+// barriers passed so far (it advances by one)
+__device__ __forceinline__ bool grid_barrier(GridBarrier* gb, unsigned int nblocks, unsigned int& gen, int* err)
+{
+    __shared__ int gb_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        const unsigned int g = gen;
+        if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
+            atomicExch(&gb->count, 0u);
+            __threadfence();
+            atomicExch(&gb->gen, g + 1);
+        } else {
+            unsigned int k = 0;
+            while (ld_acquire_gpu(&gb->gen) == g) {
+                if (++k >= BARRIER_POLLS) {
+                    atomicOr(err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        gb_ok = ok;
+    }
+    __syncthreads();
+    gen += 1;
+    return gb_ok != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(tile::THREADS, tile::BatchMinBlocks<T>::value)
+step_batch_persistent_kernel(const BatchInst<T>* __restrict__ insts, const int* __restrict__ tile_inst, int ntiles,
+                             const uint8_t* __restrict__ active, int parity, int nsteps,
+                             const int* __restrict__ dir_start, const DirNode* __restrict__ dirs,
+                             const int2* __restrict__ general, int n_general, const int* __restrict__ dir_owner,
+                             int n_dir_sep, GridBarrier* gb, unsigned int gen, int* err)
+{
+    extern __shared__ __align__(16) unsigned char smem_persist[];
+    tile::Derived<T>& sm = *reinterpret_cast<tile::Derived<T>*>(smem_persist);
+    const unsigned int G = gridDim.x;
+    const int gthreads = (int)(G * blockDim.x), gtid = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    for (int s = 0; s < nsteps; ++s, parity ^= 1) {
+        for (int t = blockIdx.x; t < ntiles; t += G) {
+            const int i = tile_inst[t];
+            if (!active[i]) continue;  // whole block
+            const BatchInst<T>& in = insts[i];
+            const Fields<T> f = in.f[parity];
+            const int tl = t - in.tile0;
+            const int x0 = (tl % in.tiles_x) * tile::TX, y0 = (tl / in.tiles_x) * tile::TY;
+            tile_update<T, F_WIND | F_FRICTION | F_CORIOLIS>(f, x0, y0, t, dir_start, dirs, in.D64, in.bv, sm);
+            __syncthreads();  // the gather's reads end before the next tile's derivation writes
+        }
+        for (int k = gtid; k < n_general; k += gthreads) {
+            const int2 e = general[k];
+            if (!active[e.x]) continue;
+            const Fields<T>& f = insts[e.x].f[parity];
+            general_node(f, e.y % f.nx, e.y / f.nx);
+        }
+        if (!grid_barrier(gb, G, gen, err)) return;
+        if (n_dir_sep > 0) {
+            for (int k = gtid; k < n_dir_sep; k += gthreads) {
+                const int i = dir_owner[k];
+                if (!active[i]) continue;
+                const BatchInst<T>& in = insts[i];
+                const Fields<T>& f = in.f[parity];
+                dirichlet_node(f.eta1, f.u1, f.v1, f.D, in.D64, dirs[k], in.bv);
+            }
+            if (!grid_barrier(gb, G, gen, err)) return;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Residual / mass / stability reduction in double precision.
 constexpr int RED_THREADS = 256;
 constexpr int RED_NVAL = 5;  // sum dq^2, sum q^2, sum eta, max |u|^2, non-finite count

@@ -80,3 +80,37 @@ def test_batch_rejects_time_dependent_boundaries():
     from paper_1902_02999_gb300 import Batch, MaclabError
     with pytest.raises(MaclabError):
         Batch([inputs.tidal_strip(60, 1)], precision="f32")
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_persistent_steps_equal_per_step_launches(precision):
+    """One cooperative launch for many steps (grid barrier between steps)
+    against one launch per step: bitwise the same after odd and even step
+    counts, with bounce-back links, Dirichlet nodes outside their inward
+    node's tile (east column of a 129-wide channel) and more tiles than
+    resident blocks (a 1024 x 640 channel alone has 640 tiles)."""
+    from paper_1902_02999_gb300 import Batch
+    cases = mixed_cases()[:4] + [inputs.bump_channel(129, 40, seed=6), inputs.bump_channel(1024, 640, seed=3)]
+    a = Batch(cases, precision=precision)
+    a.set_persistent(0)
+    b = Batch(cases, precision=precision)
+    b.set_persistent(1)
+    for n in (1, 2, 37, 120):
+        a.step(n)
+        b.step(n)
+        for i in range(len(cases)):
+            for x, y in zip(a.get_state(i), b.get_state(i)):
+                assert np.array_equal(x, y), (n, i, cases[i].name)
+    assert np.array_equal(a.residual(), b.residual())
+    b.set_active([1, 0, 1, 1, 0, 1])
+    a.set_active([1, 0, 1, 1, 0, 1])
+    a.step(9)
+    b.step(9)
+    for i in range(len(cases)):
+        for x, y in zip(a.get_state(i), b.get_state(i)):
+            assert np.array_equal(x, y), ("inactive", i)
+    for mode in (2, -1):
+        with pytest.raises(Exception):
+            b.set_persistent(mode)
+    a.close()
+    b.close()
