@@ -257,7 +257,10 @@ def main():
     stream = torch.cuda.current_stream()
     info = sim.info
     n_general = info["n_fluid"] - info["n_fast"] - info["n_dirichlet"]
-    launches_per_step = 1 + (n_general > 0) + (info["n_dirichlet"] > 0 and not info["dirichlet_fused"])
+    # the tile kernel updates the nodes with a bounce-back link itself; the
+    # other step kernels leave them to a second launch
+    launches_per_step = 1 + (n_general > 0 and info["step_kernel"] != 0) + \
+        (info["n_dirichlet"] > 0 and not info["dirichlet_fused"])
 
     sampler = ClockSampler(local)
     sim.step(max(args.warmup, 3))

@@ -80,6 +80,7 @@ struct maclab_s {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // per starting buffer parity
     bool dir_fused = false;    // Dirichlet nodes handled inside the tile kernel
     int* dir_tile_start = nullptr;  // per-tile ranges of the Dirichlet list
+    int* gen_tile_start = nullptr;  // per-tile ranges of the bounce-back-link list
     int64_t n_fluid = 0, n_fast = 0;
     double sumD = 0;           // sum of D64 over non-solid nodes
     size_t device_bytes = 0;
@@ -270,18 +271,22 @@ int launch_step(maclab_t s)
             }
         }
         if (s->kernel == MACLAB_KERNEL_TILE) {
+            // the tile kernel also updates each tile's nodes with a bounce-back link
+            TileDirichlet tg = td;
+            tg.gstart = s->gen_tile_start;
+            tg.glist = s->general;
             const size_t smem = tile::smem_bytes<T>();
             const dim3 grid(tx, std::min(ty, 65535), (ty + 65534) / 65535);
             switch (s->fmode) {  // compile-time variants for the force terms present
 #define MACLAB_FM(m) \
-    case m: step_tile_kernel<T, m><<<grid, tile::THREADS, smem, s->stream>>>(f, tx, ty, td); break;
+    case m: step_tile_kernel<T, m><<<grid, tile::THREADS, smem, s->stream>>>(f, tx, ty, tg); break;
                 MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
 #undef MACLAB_FM
             }
-        }
-        if (s->n_general > 0)
+        } else if (s->n_general > 0) {
             step_general_kernel<T><<<(s->n_general + 127) / 128, 128, 0, s->stream>>>(f, s->general,
                                                                                       s->n_general);
+        }
     } else {
         const int warps = s->ncb * s->nrb;
         int blocks = (warps + WARPS - 1) / WARPS;
@@ -329,7 +334,8 @@ void other_tiles_step(maclab_t s, void* ie, void* iu, void* iv, void* oe, void* 
     const Fields<float> f = fields_io<float>(s, ie, iu, iv, oe, ou, ov);
     const DirValues bv = dir_values(s, to_step);
     const int tx = (s->grid.nx + tile::TX - 1) / tile::TX;
-    const TileDirichlet td{s->dir_fused ? s->dir_tile_start : nullptr, s->dir, s->D64, bv};
+    const TileDirichlet td{s->dir_fused ? s->dir_tile_start : nullptr, s->dir, s->D64, bv, s->gen_tile_start,
+                           s->general};
     if (s->n_other > 0) {
         const size_t smem = tile::smem_bytes<float>();
         switch (s->fmode) {
@@ -339,8 +345,8 @@ void other_tiles_step(maclab_t s, void* ie, void* iu, void* iv, void* oe, void* 
 #undef MACLAB_FM
         }
     }
-    if (s->n_general > 0)
-        step_general_kernel<float><<<(s->n_general + 127) / 128, 128, 0, s->stream>>>(f, s->general, s->n_general);
+    // the tile-list kernel updates the nodes with a bounce-back link of its
+    // tiles (clean tiles have none)
     if (s->n_dir > 0 && !s->dir_fused)
         dirichlet_kernel<float><<<(s->n_dir + 127) / 128, 128, 0, s->stream>>>(
             (float*)oe, (float*)ou, (float*)ov, (const float*)s->D, s->D64, s->dir, s->n_dir, bv);
@@ -562,7 +568,8 @@ struct Prepared {
     int fmode = 0;
     bool steady_bc = true;
     std::vector<uint8_t> type;      // [ny][pitch], kind | GENERAL_BIT
-    std::vector<int> general;       // j * nx + i of nodes with a bounce-back link
+    std::vector<int> general;       // j * nx + i of nodes with a bounce-back link, in tile order
+    std::vector<int> gen_start;     // per-tile ranges of general
     std::vector<DirNode> dirs;      // in tile order, storage indices
     std::vector<int> dir_start;     // per-tile ranges of dirs
     bool dir_fused = false;
@@ -683,6 +690,14 @@ int prepare(const maclab_grid* grid, const maclab_params* params, const maclab_b
     }
     for (size_t k = 1; k < P.dir_start.size(); ++k) P.dir_start[k] += P.dir_start[k - 1];
     P.dir_fused = fused && !P.dirs.empty();
+    // nodes with a bounce-back link in tile order, with per-tile ranges: the
+    // tile kernel updates a tile's own ones after its gather
+    auto tile_of_node = [&](int g) { return (g / nx / tile::TY) * P.tiles_x + (g % nx) / tile::TX; };
+    std::stable_sort(P.general.begin(), P.general.end(),
+                     [&](int a, int c) { return tile_of_node(a) < tile_of_node(c); });
+    P.gen_start.assign((size_t)P.tiles_x * P.tiles_y + 1, 0);
+    for (int g : P.general) P.gen_start[tile_of_node(g) + 1]++;
+    for (size_t k = 1; k < P.gen_start.size(); ++k) P.gen_start[k] += P.gen_start[k - 1];
     return MACLAB_OK;
 }
 
@@ -765,7 +780,9 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
          (s->partial = (double*)dev_alloc(s, (size_t)s->red_blocks * RED_NVAL * 8)) &&
          (s->red_out = (double*)dev_alloc(s, RED_NVAL * 8));
     if (ok && s->prec == MACLAB_F32) ok = (s->tma_err = (int*)dev_alloc(s, sizeof(int))) != nullptr;
-    if (ok && !general.empty()) ok = (s->general = (int*)dev_alloc(s, general.size() * sizeof(int))) != nullptr;
+    if (ok && !general.empty())
+        ok = (s->general = (int*)dev_alloc(s, general.size() * sizeof(int))) &&
+             (s->gen_tile_start = (int*)dev_alloc(s, P.gen_start.size() * sizeof(int)));
     if (ok && !dirs.empty()) ok = (s->dir = (DirNode*)dev_alloc(s, dirs.size() * sizeof(DirNode))) != nullptr;
     if (ok && s->dir_fused)
         ok = (s->dir_tile_start = (int*)dev_alloc(s, dir_start.size() * sizeof(int))) != nullptr;
@@ -795,7 +812,10 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
     std::vector<uint8_t> tpad(type);
     tpad.resize(NP + 64, 0);
     put(s->type, tpad.data(), NP + 64);
-    if (!general.empty()) put(s->general, general.data(), general.size() * sizeof(int));
+    if (!general.empty()) {
+        put(s->general, general.data(), general.size() * sizeof(int));
+        put(s->gen_tile_start, P.gen_start.data(), P.gen_start.size() * sizeof(int));
+    }
     if (!dirs.empty()) put(s->dir, dirs.data(), dirs.size() * sizeof(DirNode));
     if (s->dir_fused) put(s->dir_tile_start, dir_start.data(), dir_start.size() * sizeof(int));
     if (s->tma_err && ce == cudaSuccess) ce = cudaMemsetAsync(s->tma_err, 0, sizeof(int), s->stream);
@@ -1477,8 +1497,10 @@ struct maclab_batch_s {
     void* insts = nullptr;          // BatchInst<T>[count]
     int* tile_inst = nullptr;
     uint8_t* active = nullptr;
-    int2* general = nullptr;
+    int2* general = nullptr;        // (instance, j * nx + i) of nodes with a bounce-back link
     int n_general = 0;
+    int* gen_nodes = nullptr;       // the same nodes (j * nx + i) in batch-tile order
+    int* gen_tile_start = nullptr;  // per batch tile ranges of gen_nodes
     DirNode* dirs = nullptr;
     int* dir_owner = nullptr;
     int* dir_start = nullptr;       // per batch tile, when fused
@@ -1647,11 +1669,10 @@ int batch_launch(maclab_batch_t b, cudaStream_t st)
 {
     const int par = b->cur;
     const BatchInst<T>* insts = (const BatchInst<T>*)b->insts;
+    // the tiles also update their own nodes with a bounce-back link
     step_batch_kernel<T><<<b->total_tiles, tile::THREADS, tile::smem_bytes<T>(), st>>>(
-        insts, b->tile_inst, b->active, par, b->dir_fused ? b->dir_start : nullptr, b->dirs);
-    if (b->n_general > 0)
-        batch_general_kernel<T><<<(b->n_general + 127) / 128, 128, 0, st>>>(insts, b->general, b->n_general,
-                                                                             b->active, par);
+        insts, b->tile_inst, b->active, par, b->dir_fused ? b->dir_start : nullptr, b->dirs, b->gen_tile_start,
+        b->gen_nodes);
     if (b->n_dir > 0 && !b->dir_fused)
         batch_dirichlet_kernel<T><<<(b->n_dir + 127) / 128, 128, 0, st>>>(insts, b->dir_owner, b->dirs,
                                                                            b->n_dir, b->active, par);
@@ -1785,6 +1806,7 @@ int maclab_batch_create(int count, const maclab_grid* grids, const maclab_params
     std::vector<int2> general;
     std::vector<DirNode> dirs;
     std::vector<int> dir_owner, dir_start(1, 0);
+    std::vector<int> gen_nodes, gen_start(1, 0);   // bounce-back-link nodes per batch tile
     bool fused = true;
     for (int i = 0; i < count; ++i) {
         const Prepared& p = P[i];
@@ -1807,6 +1829,8 @@ int maclab_batch_create(int count, const maclab_grid* grids, const maclab_params
                 dir_owner.push_back(i);
             }
             dir_start.push_back((int)dirs.size());
+            for (int k = p.gen_start[t]; k < p.gen_start[t + 1]; ++k) gen_nodes.push_back(p.general[k]);
+            gen_start.push_back((int)gen_nodes.size());
         }
         b->total_tiles += p.tiles_x * p.tiles_y;
         for (int g : p.general) general.push_back(make_int2(i, g));
@@ -1830,7 +1854,10 @@ int maclab_batch_create(int count, const maclab_grid* grids, const maclab_params
          (b->red_out = (double*)bdev_alloc(b, (size_t)count * RED_NVAL * 8)) &&
          (b->barrier = (GridBarrier*)bdev_alloc(b, sizeof(GridBarrier))) &&
          (b->persist_err = (int*)bdev_alloc(b, sizeof(int)));
-    if (ok && b->n_general) ok = (b->general = (int2*)bdev_alloc(b, general.size() * sizeof(int2))) != nullptr;
+    if (ok && b->n_general)
+        ok = (b->general = (int2*)bdev_alloc(b, general.size() * sizeof(int2))) &&
+             (b->gen_nodes = (int*)bdev_alloc(b, gen_nodes.size() * sizeof(int))) &&
+             (b->gen_tile_start = (int*)bdev_alloc(b, gen_start.size() * sizeof(int)));
     if (ok && b->n_dir)
         ok = (b->dirs = (DirNode*)bdev_alloc(b, dirs.size() * sizeof(DirNode))) &&
              (b->dir_owner = (int*)bdev_alloc(b, dir_owner.size() * sizeof(int)));
@@ -1862,7 +1889,11 @@ int maclab_batch_create(int count, const maclab_grid* grids, const maclab_params
     }
     put(b->type, type.data(), NP + 64);
     put(b->tile_inst, tile_inst.data(), tile_inst.size() * sizeof(int));
-    if (b->n_general) put(b->general, general.data(), general.size() * sizeof(int2));
+    if (b->n_general) {
+        put(b->general, general.data(), general.size() * sizeof(int2));
+        put(b->gen_nodes, gen_nodes.data(), gen_nodes.size() * sizeof(int));
+        put(b->gen_tile_start, gen_start.data(), gen_start.size() * sizeof(int));
+    }
     if (b->n_dir) {
         put(b->dirs, dirs.data(), dirs.size() * sizeof(DirNode));
         put(b->dir_owner, dir_owner.data(), dir_owner.size() * sizeof(int));

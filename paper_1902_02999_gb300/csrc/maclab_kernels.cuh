@@ -899,6 +899,10 @@ struct TileDirichlet {
     const DirNode* list;
     const double* D64;
     DirValues bv;
+    // nodes with a bounce-back link of tile t: glist[gstart[t] .. gstart[t + 1])
+    // (j * nx + i), or nullptr when a separate launch updates them
+    const int* gstart;
+    const int* glist;
 };
 
 template <typename T>
@@ -1234,11 +1238,15 @@ __device__ __forceinline__ void tile_phase_bc_f32(const Fields<float>& f, int x0
 }
 
 // Update of one tile whose top-left updated node is (x0, y0); `tile` indexes
-// the per-tile Dirichlet ranges.
+// the per-tile Dirichlet ranges and, when gstart is given, the per-tile
+// ranges of glist: the tile's nodes with a bounce-back link, updated here by
+// the per-link form (they read only the old state and no other node of the
+// step reads their new values before the next step, so no barrier is needed).
 template <typename T, int FM>
 __device__ __forceinline__ void tile_update(const Fields<T>& f, int x0, int y0, int tile, const int* dir_start,
                                             const DirNode* dir_list, const double* D64, const DirValues& bv,
-                                            tile::Derived<T>& sm)
+                                            tile::Derived<T>& sm, const int* gstart = nullptr,
+                                            const int* glist = nullptr)
 {
     uint32_t own_types[2];
     const bool inside = tile_inside(f, x0, y0);
@@ -1253,6 +1261,13 @@ __device__ __forceinline__ void tile_update(const Fields<T>& f, int x0, int y0, 
         __syncthreads();
         tile_phase_bc<T>(f, x0, y0, inside, tile, dir_start, dir_list, D64, bv, sm, own, own_types);
     }
+    if (gstart) {
+        const int e = gstart[tile + 1];
+        for (int k = gstart[tile] + (int)threadIdx.x; k < e; k += tile::THREADS) {
+            const int node = glist[k];
+            general_node<T>(f, node % f.nx, node / f.nx);
+        }
+    }
 }
 
 template <typename T, int FM>
@@ -1265,7 +1280,7 @@ step_tile_kernel(const __grid_constant__ Fields<T> f, int tiles_x, int tiles_y, 
     const int ty = blockIdx.z * gridDim.y + blockIdx.y;
     if (ty >= tiles_y) return;  // whole block
     tile_update<T, FM>(f, blockIdx.x * tile::TX, ty * tile::TY, ty * tiles_x + blockIdx.x, td.start, td.list, td.D64,
-                       td.bv, sm);
+                       td.bv, sm, td.gstart, td.glist);
 }
 
 // Single step over a list of tiles (the tiles a two-step launch leaves out).
@@ -1278,7 +1293,7 @@ step_tile_list_kernel(const __grid_constant__ Fields<T> f, int tiles_x, const __
     tile::Derived<T>& sm = *reinterpret_cast<tile::Derived<T>*>(smem_list);
     const int t = list[blockIdx.x];
     const int x0 = (t % tiles_x) * tile::TX, y0 = (t / tiles_x) * tile::TY;
-    tile_update<T, FM>(f, x0, y0, t, td.start, td.list, td.D64, td.bv, sm);
+    tile_update<T, FM>(f, x0, y0, t, td.start, td.list, td.D64, td.bv, sm, td.gstart, td.glist);
 }
 
 // ---------------------------------------------------------------------------
@@ -1546,7 +1561,7 @@ template <typename T>
 __global__ void __launch_bounds__(tile::THREADS, tile::BatchMinBlocks<T>::value)
 step_batch_kernel(const BatchInst<T>* __restrict__ insts, const int* __restrict__ tile_inst,
                   const uint8_t* __restrict__ active, int parity, const int* __restrict__ dir_start,
-                  const DirNode* __restrict__ dirs)
+                  const DirNode* __restrict__ dirs, const int* __restrict__ gstart, const int* __restrict__ glist)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     tile::Derived<T>& sm = *reinterpret_cast<tile::Derived<T>*>(smem_raw);
@@ -1558,7 +1573,8 @@ step_batch_kernel(const BatchInst<T>* __restrict__ insts, const int* __restrict_
     const int x0 = (t % in.tiles_x) * tile::TX, y0 = (t / in.tiles_x) * tile::TY;
     // all force terms: absent ones have zero coefficients and contribute
     // exact zeros, so every instance gets the same values as its own kernel
-    tile_update<T, F_WIND | F_FRICTION | F_CORIOLIS>(f, x0, y0, blockIdx.x, dir_start, dirs, in.D64, in.bv, sm);
+    tile_update<T, F_WIND | F_FRICTION | F_CORIOLIS>(f, x0, y0, blockIdx.x, dir_start, dirs, in.D64, in.bv, sm,
+                                                     gstart, glist);
 }
 
 // Nodes with a bounce-back link across a batch: (instance, node) pairs.
