@@ -1080,15 +1080,31 @@ __device__ __forceinline__ void node_update(const DR& sm, int lr, int lc, const 
     const T Sx = O::sub(OL, OR);
     const T Sy = O::sub(O::add(O::add(mL_o2, mR_o4), mC_o3), O::add(O::add(pL_o8, pR_o6), pC_o7));
     // lambda-weighted stencils of eta (.x) and D (.y): sum, x-moment, y-moment
-    const T MLe = O::fma(q, O::add(mL.x, pL.x), cL.x);
-    const T MRe = O::fma(q, O::add(mR.x, pR.x), cR.x);
-    const T MLd = O::fma(q, O::add(mL.y, pL.y), cL.y);
-    const T MRd = O::fma(q, O::add(mR.y, pR.y), cR.y);
-    const T Se = O::add(O::add(MLe, MRe), O::add(mC.x, pC.x));
-    const T Sd = O::add(O::add(MLd, MRd), O::add(mC.y, pC.y));
-    const T Xe = O::sub(MLe, MRe), Xd = O::sub(MLd, MRd);
-    const T Ye = O::fma(q, O::sub(O::add(mL.x, mR.x), O::add(pL.x, pR.x)), O::sub(mC.x, pC.x));
-    const T Yd = O::fma(q, O::sub(O::add(mL.y, mR.y), O::add(pL.y, pR.y)), O::sub(mC.y, pC.y));
+    T Se, Sd, Xe, Xd, Ye, Yd;
+#ifndef MACLAB_SCALAR_STENCIL
+    if constexpr (std::is_same<T, float>::value) {
+        // eta and D take the same operations: the two lanes of one paired
+        // instruction (each lane rounded as the scalar operation)
+        using P = Op2;
+        const float2 q2 = splat(q);
+        const float2 ML = P::fma(q2, P::add(mL, pL), cL), MR = P::fma(q2, P::add(mR, pR), cR);
+        const float2 S = P::add(P::add(ML, MR), P::add(mC, pC));
+        const float2 X = P::sub(ML, MR);
+        const float2 Y = P::fma(q2, P::sub(P::add(mL, mR), P::add(pL, pR)), P::sub(mC, pC));
+        Se = S.x, Sd = S.y, Xe = X.x, Xd = X.y, Ye = Y.x, Yd = Y.y;
+    } else
+#endif
+    {
+        const T MLe = O::fma(q, O::add(mL.x, pL.x), cL.x);
+        const T MRe = O::fma(q, O::add(mR.x, pR.x), cR.x);
+        const T MLd = O::fma(q, O::add(mL.y, pL.y), cL.y);
+        const T MRd = O::fma(q, O::add(mR.y, pR.y), cR.y);
+        Se = O::add(O::add(MLe, MRe), O::add(mC.x, pC.x));
+        Sd = O::add(O::add(MLd, MRd), O::add(mC.y, pC.y));
+        Xe = O::sub(MLe, MRe), Xd = O::sub(MLd, MRd);
+        Ye = O::fma(q, O::sub(O::add(mL.x, mR.x), O::add(pL.x, pR.x)), O::sub(mC.x, pC.x));
+        Yd = O::fma(q, O::sub(O::add(mL.y, mR.y), O::add(pL.y, pR.y)), O::sub(mC.y, pC.y));
+    }
     const T A = O::mul(K.G6, D), B = O::mul(K.G6, eta);
     // ownh already holds the receiver-only bed part 5 G6 eta_x D_x
     const T eta1 = O::add(O::add(ownh, Sh), O::fma(A, Se, O::mul(-B, Sd)));
