@@ -252,8 +252,13 @@ def main():
     sim = Simulation.from_case(case, precision=args.precision)
     if args.tile_rows:
         sim.set_tile_rows(args.tile_rows)
+    tuned = None
     if args.kernel != "default":
         sim.set_step_kernel(args.kernel)
+    else:
+        # the library's autotuner picks the launch shape and the temporal
+        # block depth on this grid (state unchanged)
+        tuned = sim.autotune(40)
     stream = torch.cuda.current_stream()
     info = sim.info
     n_general = info["n_fluid"] - info["n_fast"] - info["n_dirichlet"]
@@ -520,7 +525,8 @@ def main():
                            "l2": "inputs larger than L2 (state %.0f MB), no flush" %
                                  (nodes * BYTES_PER_NODE[args.precision] / 1e6),
                            "parallelism": "replicas" if world > 1 else "single-gpu",
-                           "step_kernel": KERNEL_LABEL[info["step_kernel"]]},
+                           "step_kernel": KERNEL_LABEL[info["step_kernel"]],
+                           "autotune_choice": tuned, "temporal_block": info["temporal_block"]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "steady_state": steady, "f64": f64, "batched": batched, "warm_start": warm,
                 "temporal_block": tblock, "distribution_form": dform,

@@ -320,10 +320,13 @@ int maclab_get_profile(maclab_t sim, double* step_kernel_ms, int64_t* launches);
 /* Time the step-kernel launch shapes on this handle's own grid and keep
  * the fastest: *choice = 0 for the 64 x 16 tile kernel, k = 1..4 for the
  * warp-strip kernel with 8, 16, 32 or 64 rows per strip, 5 for the
- * TMA-staged tile kernel (FP32 handles only).  Each shape runs
- * 2 + trial_steps steps; the state, step count and time are restored
- * afterwards (results are bitwise identical for every shape).  Allocates
- * and frees a copy of the state.  Synchronises. */
+ * TMA-staged tile kernel, 6 for the tile kernel with two steps per launch
+ * on clean tiles (maclab_set_temporal_block(sim, 2)); 5 and 6 are tried on
+ * FP32 MacLABSWE handles only, and the temporal block depth is set to the
+ * winner's (1 unless 6 wins).  Each shape runs 2 + trial_steps steps; the
+ * state, step count and time are restored afterwards (results are bitwise
+ * identical for every shape).  Allocates and frees a copy of the state.
+ * Synchronises. */
 int maclab_autotune(maclab_t sim, int trial_steps, int* choice);
 
 /* Facts about the handle. */

@@ -256,7 +256,8 @@ class Simulation:
     def autotune(self, trial_steps: int = 20) -> int:
         """Pick the fastest step-kernel launch shape for this grid (0 = tile
         kernel, 1..4 = strip kernel with 8/16/32/64 rows, 5 = TMA-staged tile
-        kernel); state unchanged."""
+        kernel, 6 = tile kernel with two steps per launch on clean tiles);
+        state unchanged."""
         c = ctypes.c_int()
         self._check(self._lib.maclab_autotune(self._h, int(trial_steps), ctypes.byref(c)))
         info = _abi.Info()

@@ -999,9 +999,11 @@ int maclab_autotune(maclab_t s, int trial_steps, int* choice)
     const int ty0 = s->ty;
     const int prof0 = s->profiling;
     // candidates: 0 = tile kernel; k = 1..4 strip kernel with 4 << k rows;
-    // 5 = TMA-staged tile kernel
+    // 5 = TMA-staged tile kernel; 6 = tile kernel with two steps per launch
+    // on clean tiles (FP32 MacLABSWE steps only)
     const int rows[5] = {0, 8, 16, 32, 64};
-    const int ncand = s->tma_ok ? 6 : 5;
+    const bool try_pairs = s->prec == MACLAB_F32 && !s->elab && !s->newlevel;
+    const int ncand = try_pairs ? 7 : (s->tma_ok ? 6 : 5);
     double best = 1e300;
     int best_k = 0;
     cudaEvent_t e0, e1;
@@ -1009,8 +1011,17 @@ int maclab_autotune(maclab_t s, int trial_steps, int* choice)
     cudaEventCreate(&e1);
     s->profiling = true;  // one launch per step (no graph replay) while timing
     int rc = MACLAB_OK;
+    s->tblock = 1;
     for (int k = 0; k < ncand && rc == MACLAB_OK; ++k) {
-        s->kernel = k == 0 ? MACLAB_KERNEL_TILE : k == 5 ? MACLAB_KERNEL_TMA : MACLAB_KERNEL_STRIP;
+        if (k == 5 && !s->tma_ok) continue;
+        if (k == 6) {
+            if ((rc = maclab_set_temporal_block(s, 2)) != MACLAB_OK) break;
+            if (s->n_clean == 0) {
+                s->tblock = 1;
+                continue;
+            }
+        }
+        s->kernel = (k == 0 || k == 6) ? MACLAB_KERNEL_TILE : k == 5 ? MACLAB_KERNEL_TMA : MACLAB_KERNEL_STRIP;
         if (k >= 1 && k <= 4) {
             s->ty = std::min(rows[k], s->grid.ny);
             s->nrb = (s->grid.ny + s->ty - 1) / s->ty;
@@ -1031,7 +1042,9 @@ int maclab_autotune(maclab_t s, int trial_steps, int* choice)
     s->profiling = prof0;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    s->kernel = best_k == 0 ? MACLAB_KERNEL_TILE : best_k == 5 ? MACLAB_KERNEL_TMA : MACLAB_KERNEL_STRIP;
+    s->kernel = (best_k == 0 || best_k == 6) ? MACLAB_KERNEL_TILE : best_k == 5 ? MACLAB_KERNEL_TMA
+                                                                                 : MACLAB_KERNEL_STRIP;
+    s->tblock = best_k == 6 ? 2 : 1;
     if (best_k >= 1 && best_k <= 4) {
         s->ty = std::min(rows[best_k], s->grid.ny);
     } else {

@@ -125,7 +125,8 @@ def test_autotune_keeps_state_and_results(precision):
     a.step(7)
     before = a.get_state()
     choice = a.autotune(4)
-    assert 0 <= choice <= (5 if precision == "f32" else 4) and a.time()[1] == 7
+    assert 0 <= choice <= (6 if precision == "f32" else 4) and a.time()[1] == 7
+    assert a.info["temporal_block"] == (2 if choice == 6 else 1)
     for x, y in zip(a.get_state(), before):
         assert np.array_equal(x, y)
     a.step(30)
