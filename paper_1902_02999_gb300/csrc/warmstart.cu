@@ -697,6 +697,7 @@ struct WgradArgs {
     const bf16* dY;   // [B][R][R][Cout]
     const bf16* X;    // [B][R][R][Cin]
     float* dW;        // [9][Cout][Cin]
+    float* part;      // [splits][9][Cout][Cin]: each split's sums, added in order afterwards
     int B, R, Cin, Cout, dil, relu_in, splits;
 };
 constexpr int WG_K = 32;  // pixels per stage
@@ -807,15 +808,35 @@ __global__ void __launch_bounds__(THREADS) ws_wgrad_kernel(const WgradArgs a)
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
             const int m = m0 + wm * 16 + g + 8 * hh;
-            float* d = a.dW + ((size_t)tap * Cout + m) * Cin + n;
-            atomicAdd(d, acc[j][2 * hh]);
-            atomicAdd(d + 1, acc[j][2 * hh + 1]);
+            float* d = a.part + (((size_t)split * 9 + tap) * Cout + m) * Cin + n;
+            *reinterpret_cast<float2*>(d) = make_float2(acc[j][2 * hh], acc[j][2 * hh + 1]);
         }
     }
 }
 
-// db[c] += sum_p dY[p][c]
-__global__ void __launch_bounds__(THREADS) ws_bias_grad_kernel(const bf16* dY, int P, int C, float* db)
+// out[i] = sum over s < S of part[s n + i], added in the order of s, so that
+// split sums combine the same way in every run
+__global__ void ws_sum_parts_kernel(const float* __restrict__ part, int S, size_t n, float* __restrict__ out)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float t = 0.f;
+        for (int s = 0; s < S; ++s) t += part[(size_t)s * n + i];
+        out[i] = t;
+    }
+}
+
+// out[c] = sum over b < nb of part[b k + c], c < k, in the order of b
+__global__ void ws_sum_doubles_kernel(const double* __restrict__ part, int nb, int k, double* __restrict__ out)
+{
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        double t = 0.0;
+        for (int b = 0; b < nb; ++b) t += part[(size_t)b * k + c];
+        out[c] = t;
+    }
+}
+
+// out_part[blockIdx.y][c] = the block's share of sum_p dY[p][c]
+__global__ void __launch_bounds__(THREADS) ws_bias_grad_kernel(const bf16* dY, int P, int C, float* out_part)
 {
     __shared__ float part[THREADS];
     const int c = blockIdx.x * 32 + (threadIdx.x & 31);
@@ -829,14 +850,14 @@ __global__ void __launch_bounds__(THREADS) ws_bias_grad_kernel(const bf16* dY, i
     if (threadIdx.x < 32 && c < C) {
         float t = 0.f;
         for (int k = 0; k < lanes; ++k) t += part[k * 32 + threadIdx.x];
-        atomicAdd(db + c, t);
+        out_part[(size_t)blockIdx.y * C + c] = t;
     }
 }
 
-// loss = sum_p w_p sum_{c < oc} (Y - T)^2 (block partials in double);
-// dY = 2 w (Y - T) for c < oc, 0 otherwise
+// loss = sum_p w_p sum_{c < oc} (Y - T)^2: block partials in double into
+// loss_part[blockIdx.x]; dY = 2 w (Y - T) for c < oc, 0 otherwise
 __global__ void __launch_bounds__(THREADS) ws_loss_kernel(const float* Y, const float* T, const float* W, int P,
-                                                          int oc, bf16* dY, double* loss)
+                                                          int oc, bf16* dY, double* loss_part)
 {
     __shared__ double part[THREADS];
     double s = 0.0;
@@ -856,7 +877,7 @@ __global__ void __launch_bounds__(THREADS) ws_loss_kernel(const float* Y, const 
         if (threadIdx.x < k) part[threadIdx.x] += part[threadIdx.x + k];
         __syncthreads();
     }
-    if (threadIdx.x == 0) atomicAdd(loss, part[0]);
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = part[0];
 }
 
 // float -> bf16
@@ -970,10 +991,10 @@ __global__ void ws_decode_kernel(int n, int R, const float* Y, const float* D, c
     v[k] = still ? 0.0 : out[2] * s3;
 }
 
-// sum over non-solid nodes of (h - D) and their count, block partials
-// added into acc[0..1]
+// sum over non-solid nodes of (h - D) and their count: block partials into
+// part[2 blockIdx.x], part[2 blockIdx.x + 1]
 __global__ void __launch_bounds__(THREADS) ws_eta_sum_kernel(int nn, const double* h, const float* D,
-                                                             const uint8_t* mask, double* acc)
+                                                             const uint8_t* mask, double* part)
 {
     __shared__ double ps[THREADS], pc[THREADS];
     double s = 0.0, c = 0.0;
@@ -993,8 +1014,8 @@ __global__ void __launch_bounds__(THREADS) ws_eta_sum_kernel(int nn, const doubl
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        atomicAdd(acc, ps[0]);
-        atomicAdd(acc + 1, pc[0]);
+        part[2 * blockIdx.x] = ps[0];
+        part[2 * blockIdx.x + 1] = pc[0];
     }
 }
 
@@ -1042,6 +1063,9 @@ struct maclab_ws_s {
     float* Yf = nullptr;        // [B][R][R][16]
     double* loss = nullptr;
     double* acc = nullptr;      // decode's (sum of eta, count)
+    float* part = nullptr;      // split and block partial sums of the gradients
+    double* dpart = nullptr;    // block partials of the loss and of decode's sums
+    size_t part_floats = 0;
     int* tc_err = nullptr;      // set when a tensor-core wait timed out
     std::vector<void*> bufs;
     std::string err;
@@ -1137,10 +1161,29 @@ void launch_wgrad(maclab_ws_t w, const WgradArgs& a0)
     const int tiles = (a.Cout / MT) * (a.Cin / NT);
     // about two blocks per SM over all (tile, tap, split) blocks
     a.splits = std::max(1, std::min(chunks, 304 / std::max(1, tiles * 9) + 1));
+    a.part = w->part;
     dim3 grid(tiles, 9, a.splits);
     if (MT == 64 && NT == 64) ws_wgrad_kernel<64, 64><<<grid, THREADS, 0, w->stream>>>(a);
     else if (MT == 64) ws_wgrad_kernel<64, 16><<<grid, THREADS, 0, w->stream>>>(a);
     else ws_wgrad_kernel<16, 64><<<grid, THREADS, 0, w->stream>>>(a);
+    const size_t n = (size_t)9 * a.Cout * a.Cin;
+    ws_sum_parts_kernel<<<grid_for(n), 256, 0, w->stream>>>(w->part, a.splits, n, a.dW);
+}
+
+// Floats of the partial-sum buffer: the weight gradient's splits of every
+// layer (at most 304 / (tiles * 9) + 1 of them) and the bias gradient's 64
+// block rows.
+size_t part_floats_for(const maclab_ws_s* w)
+{
+    size_t n = 0;
+    for (const auto& L : w->layers) {
+        const int MT = L.cout % 64 == 0 ? 64 : 16, NT = L.cin % 64 == 0 ? 64 : 16;
+        const int tiles = (L.cout / MT) * (L.cin / NT);
+        const size_t S = (size_t)(304 / std::max(1, tiles * 9) + 1);
+        n = std::max(n, S * 9 * L.cout * L.cin);
+        n = std::max(n, (size_t)64 * L.cout);
+    }
+    return n;
 }
 
 void pack_all(maclab_ws_t w)
@@ -1202,7 +1245,8 @@ void backward(maclab_ws_t w, int batch)
         g.relu_in = L.relu_in;
         launch_wgrad(w, g);
         dim3 bg((L.cout + 31) / 32, 64);
-        ws_bias_grad_kernel<<<bg, THREADS, 0, w->stream>>>(gout, P, L.cout, w->grad + L.b_off);
+        ws_bias_grad_kernel<<<bg, THREADS, 0, w->stream>>>(gout, P, L.cout, w->part);
+        ws_sum_parts_kernel<<<grid_for(L.cout), 256, 0, w->stream>>>(w->part, 64, L.cout, w->grad + L.b_off);
         if (l == 0) break;
         // gradient w.r.t. this layer's input H_{l-1}:
         //   head:  relu'(H) * conv^T(gout)
@@ -1237,8 +1281,9 @@ int loss_and_grad(maclab_ws_t w, int batch, int oc, const float* x, const float*
     const size_t P = (size_t)batch * R * R;
     ws_to_bf16_kernel<<<grid_for(P * IO), 256, 0, w->stream>>>(x, w->X, P * IO);
     forward(w, batch);
-    cudaMemsetAsync(w->loss, 0, sizeof(double), w->stream);
-    ws_loss_kernel<<<grid_for(P * IO, 1024), THREADS, 0, w->stream>>>(w->Yf, t, wt, (int)P, oc, w->dY, w->loss);
+    const int nb = grid_for(P * IO, 1024);
+    ws_loss_kernel<<<nb, THREADS, 0, w->stream>>>(w->Yf, t, wt, (int)P, oc, w->dY, w->dpart);
+    ws_sum_doubles_kernel<<<1, 32, 0, w->stream>>>(w->dpart, nb, 1, w->loss);
     backward(w, batch);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("warm-start launch: ") + cudaGetErrorString(e));
@@ -1304,6 +1349,8 @@ int maclab_ws_create(const maclab_ws_config* cfg, void* stream, maclab_ws_t* out
               walloc(w, &w->m2, w->nparam) && walloc(w, &w->X, P * IO) && walloc(w, &w->dY, P * IO) &&
               walloc(w, &w->Yf, P * IO) && walloc(w, &w->loss, 1) && walloc(w, &w->acc, 2) && walloc(w, &w->tc_err, 1) && walloc(w, &w->G[0], P * C) &&
               walloc(w, &w->G[1], P * C);
+    w->part_floats = part_floats_for(w);
+    ok = ok && walloc(w, &w->part, w->part_floats) && walloc(w, &w->dpart, 2 * 1024);
     w->H.assign(w->layers.size() - 1, nullptr);
     for (size_t l = 0; ok && l < w->H.size(); ++l) ok = walloc(w, &w->H[l], P * C);
     for (auto& L : w->layers) {
@@ -1464,8 +1511,9 @@ int maclab_ws_decode(maclab_ws_t w, int n, const float* y, const float* D, const
     ws_decode_kernel<<<(n * n + 255) / 256, 256, 0, w->stream>>>(n, R, y, D, mask, scale[1], scale[2], scale[3], h,
                                                                  u, v);
     if (std::isfinite(mass_eta)) {
-        cudaMemsetAsync(w->acc, 0, 2 * sizeof(double), w->stream);
-        ws_eta_sum_kernel<<<grid_for((size_t)n * n, 1024), THREADS, 0, w->stream>>>(n * n, h, D, mask, w->acc);
+        const int nb = grid_for((size_t)n * n, 1024);
+        ws_eta_sum_kernel<<<nb, THREADS, 0, w->stream>>>(n * n, h, D, mask, w->dpart);
+        ws_sum_doubles_kernel<<<1, 32, 0, w->stream>>>(w->dpart, nb, 2, w->acc);
         ws_eta_shift_kernel<<<(n * n + 255) / 256, 256, 0, w->stream>>>(n * n, h, mask, w->acc, mass_eta);
     }
     const cudaError_t e = cudaGetLastError();

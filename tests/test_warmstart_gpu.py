@@ -170,3 +170,25 @@ def test_warm_start_reaches_the_plain_accuracy_in_fewer_steps():
     assert np.median(res["matched_steps"]) < np.median(res["plain_steps"]), res
     assert (res["proposal_error"].max(axis=0) < 1.0).all()
     net.close()
+
+
+def test_training_is_deterministic():
+    """Split-K and block partial sums are added in a fixed order, so two
+    networks trained from the same seed on the same data end bitwise equal,
+    and a gradient evaluated twice is the same."""
+    C, dil = 128, (1, 2)
+    rng = np.random.default_rng(11)
+    X = torch.tensor(rng.standard_normal((4, 64, 64, IO)), dtype=torch.float32, device="cuda")
+    T = torch.tensor(rng.standard_normal((4, 64, 64, IO)), dtype=torch.float32, device="cuda")
+    w = torch.full((4, 64, 64), 1.0 / (4 * 64 * 64), device="cuda")
+    nets = [make(C, dil, 4, seed=5) for _ in range(2)]
+    losses = []
+    for net in nets:
+        losses.append([net.train_step(X, T, w, 1e-3) for _ in range(4)])
+    assert losses[0] == losses[1]
+    assert np.array_equal(nets[0].get_params(), nets[1].get_params())
+    g1 = nets[0].gradients(X, T, w)
+    g2 = nets[0].gradients(X, T, w)
+    assert g1[0] == g2[0] and np.array_equal(g1[1], g2[1])
+    for net in nets:
+        net.close()
