@@ -374,6 +374,46 @@ def summary(res):
             "proposal_error_median": np.median(res["proposal_error"], axis=0).tolist()}
 
 
+def time_kernels(batch: int = 16, reps: int = 50, paths=(0, 2)) -> dict:
+    """Forward and training-step times of the default network on random
+    inputs, per convolution path (0: tcgen05 fed by TMA, 1: tcgen05 fed by
+    cp.async, 2: mma.sync), with CUDA events on the current stream.  The
+    FLOP rates count 2 per multiply-add of the convolutions (a training
+    step: forward, input gradient and weight gradient, three times the
+    forward)."""
+    import torch
+    out = {}
+    for path in paths:
+        net = WarmStartNet(max_batch=batch, tensor_path=path)
+        g = torch.Generator(device="cuda").manual_seed(0)
+        R = net.res
+        X = torch.randn(batch, R, R, IO, device="cuda", generator=g)
+        T = torch.randn(batch, R, R, IO, device="cuda", generator=g)
+        Wt = torch.full((batch, R, R), 1.0 / (batch * R * R), device="cuda")
+        for _ in range(5):
+            net.train_step(X, T, Wt, 1e-4, want_loss=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            net.train_step(X, T, Wt, 1e-4, want_loss=False)
+        e1.record()
+        torch.cuda.synchronize()
+        train_ms = e0.elapsed_time(e1) / reps
+        e0.record()
+        for _ in range(reps):
+            net.forward(X)
+        e1.record()
+        torch.cuda.synchronize()
+        fwd_ms = e0.elapsed_time(e1) / reps
+        C, L = net.channels, len(net.dilations)
+        flop = 2.0 * batch * R * R * 9 * (IO * C + L * C * C + C * IO)
+        out["path%d" % path] = {"forward_ms": fwd_ms, "train_step_ms": train_ms,
+                                "forward_tflops": flop / fwd_ms / 1e9, "train_tflops": 3 * flop / train_ms / 1e9}
+        net.close()
+    return out
+
+
 def main():
     import torch
     import inputs
@@ -384,8 +424,13 @@ def main():
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--target-tol", type=float, default=1e-7)
+    ap.add_argument("--time-kernels", action="store_true",
+                    help="only time the network's forward pass and training step per convolution path")
     args = ap.parse_args()
     torch.cuda.set_device(0)
+    if args.time_kernels:
+        print(json.dumps({"batch": args.batch, **time_kernels(args.batch)}))
+        return
     net = WarmStartNet(max_batch=args.batch)
     t0 = time.perf_counter()
     train_cases = [inputs.dish_lake(256, seed=1000 + k) for k in range(args.train)]
