@@ -251,8 +251,9 @@ int launch_step(maclab_t s)
         if (s->n_all > 0)
             step_general_kernel<T, true><<<(s->n_all + 127) / 128, 128, 0, s->stream>>>(f, s->all_list, s->n_all);
     } else if (s->kernel != MACLAB_KERNEL_STRIP) {
-        // fast nodes and (when fused) Dirichlet nodes in one launch; nodes with a
-        // bounce-back link in a second launch when there are any
+        // fast nodes, (when fused) Dirichlet nodes and, with the tile kernel,
+        // nodes with a bounce-back link in one launch; the TMA-staged kernel
+        // leaves the latter to a second launch
         const int tx = (s->grid.nx + tile::TX - 1) / tile::TX, ty = (s->grid.ny + tile::TY - 1) / tile::TY;
         const TileDirichlet td{s->dir_fused ? s->dir_tile_start : nullptr, s->dir, s->D64, bv};
         if constexpr (std::is_same<T, float>::value) {
