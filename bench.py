@@ -214,7 +214,8 @@ def main():
     ap.add_argument("--tile-rows", type=int, default=0)
     ap.add_argument("--kernel", default="default", choices=["default", "tile", "strip", "tma"],
                     help="step kernel of the main leg (default: the library's choice)")
-    ap.add_argument("--no-extra", action="store_true", help="skip the steady-state and FP64 legs")
+    ap.add_argument("--no-extra", action="store_true", help="skip the extra legs (steady state, FP64, batch, warm start, temporal blocking, "
+                         "distribution form); they run only with a single rank")
     ap.add_argument("--steady-max-steps", type=int, default=2_000_000)
     ap.add_argument("--f64-steps", type=int, default=300)
     ap.add_argument("--batch-count", type=int, default=512)
@@ -286,6 +287,9 @@ def main():
     ms = ev0.elapsed_time(ev1)
     clocks = sampler.stop(t_wall0, t_wall1)
     ms = max_over_ranks(ms, dist, "cuda")
+    # the extra legs describe one GPU: they run in the single-rank line only
+    # (under torchrun every rank would hold its GPU for minutes)
+    extra = not args.no_extra and world == 1
     nodes = case.nodes
     value = whole_job_mlups(world, nodes, args.steps, ms)
 
@@ -332,7 +336,7 @@ def main():
     # steps per launch (bitwise the same states); 29 B per node update are
     # still counted per step, so a fraction above 1 is possible in principle
     tblock = None
-    if not args.no_extra and args.precision == "f32":
+    if extra and args.precision == "f32":
         sim.set_temporal_block(2)
         sim.step(max(args.warmup, 3))
         torch.cuda.synchronize()
@@ -353,7 +357,7 @@ def main():
     # on the same grid made periodic along x and all fluid (the form has no
     # Dirichlet rule): bytes and time per node update
     dform = None
-    if not args.no_extra and args.precision == "f32":
+    if extra and args.precision == "f32":
         import numpy as np
         pc = inputs.bump_channel(args.nx, args.ny, seed=0)
         pc.mask = np.full_like(pc.mask, inputs.FLUID)
@@ -382,7 +386,7 @@ def main():
     # the other half of the metric: wall time to a residual of 1e-8 for the
     # seeded 256 x 256 dish lake (plain method, FP32 storage)
     steady = None
-    if not args.no_extra:
+    if extra:
         lake = inputs.dish_lake(256, seed=0)
         ls = Simulation.from_case(lake, precision="f32")
         torch.cuda.synchronize()
@@ -397,7 +401,7 @@ def main():
 
     # the FP64 variant of the channel step (timed, not the headline)
     f64 = None
-    if not args.no_extra and args.precision == "f32":
+    if extra and args.precision == "f32":
         s64 = Simulation.from_case(case, precision="f64")
         choice64 = s64.autotune(10)
         s64.step(20)
@@ -425,7 +429,7 @@ def main():
 
     # the batched ensemble: 512 uneven lakes and channels advanced together
     batched = None
-    if not args.no_extra and args.batch_count > 0:
+    if extra and args.batch_count > 0:
         from paper_1902_02999_gb300 import Batch
         ens = inputs.ensemble(args.batch_count, seed=0)
         bt = Batch(ens, precision=args.precision)
@@ -491,7 +495,7 @@ def main():
     # batches of the plain iteration on this GPU); the network trains here,
     # on steady states of the same solver
     warm = None
-    if not args.no_extra and args.ws_train > 0 and rank == 0:
+    if extra and args.ws_train > 0 and rank == 0:
         from paper_1902_02999_gb300 import warmstart as ws
         net = ws.WarmStartNet(max_batch=16)
         t0 = time.perf_counter()
