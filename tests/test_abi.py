@@ -91,3 +91,20 @@ def test_warm_start_config_layout_and_argument_checks(tmp_path):
 def test_build_targets_sm103a_only():
     assert buildmod.ARCH == "-gencode=arch=compute_103a,code=sm_103a"
     assert os.path.exists(buildmod.build())
+
+
+def test_null_handles_are_argument_errors():
+    """Every entry point that takes a handle answers a NULL one with
+    MACLAB_E_ARG (no GPU involved)."""
+    lib = _abi.load()
+    c = ctypes.c_int()
+    assert lib.maclab_autotune(None, 4, ctypes.byref(c)) == -1
+    assert lib.maclab_set_temporal_block(None, 2) == -1
+    assert lib.maclab_set_relaxation(None, 0.8) == -1
+    assert lib.maclab_set_hbar_level(None, 1) == -1
+    assert lib.maclab_set_graph_steps(None, 64) == -1
+    assert lib.maclab_batch_step(None, 1) == -1
+    assert lib.maclab_batch_set_graph_steps(None, 64) == -1
+    assert lib.maclab_batch_set_persistent(None, 1) == -1
+    assert b"NULL" in lib.maclab_batch_last_error(None)
+    lib.maclab_batch_destroy(None)
