@@ -43,8 +43,10 @@ F64_NOMINAL_TFLOPS = 1.25                  # GB300 dense FP64, nominal (no measu
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_JSON = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
 # step-kernel codes of the library (maclab_step_kernel)
-KERNEL_SYMBOL = {0: "step_tile_kernel<%s>", 1: "step_fast_kernel<%s>", 2: "step_tile_tma_kernel (%s)"}
-KERNEL_LABEL = {0: "tile 64x16", 1: "warp strip", 2: "TMA-staged tile 64x16, persistent"}
+KERNEL_SYMBOL = {0: "step_tile_kernel<%s>", 1: "step_fast_kernel<%s>", 2: "step_tile_tma_kernel (%s)",
+                 3: "step_march_kernel<%s>"}
+KERNEL_LABEL = {0: "tile 64x16", 1: "warp strip", 2: "TMA-staged tile 64x16, persistent",
+                3: "row march, 64-column strip blocks"}
 
 
 def kernel_source_hash() -> str:
@@ -212,7 +214,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tile-rows", type=int, default=0)
-    ap.add_argument("--kernel", default="default", choices=["default", "tile", "strip", "tma"],
+    ap.add_argument("--kernel", default="default", choices=["default", "tile", "strip", "tma", "march"],
                     help="step kernel of the main leg (default: the library's choice)")
     ap.add_argument("--no-extra", action="store_true", help="skip the extra legs (steady state, FP64, batch, warm start, temporal blocking, "
                          "distribution form); they run only with a single rank")
@@ -263,9 +265,9 @@ def main():
     stream = torch.cuda.current_stream()
     info = sim.info
     n_general = info["n_fluid"] - info["n_fast"] - info["n_dirichlet"]
-    # the tile kernel updates the nodes with a bounce-back link itself; the
-    # other step kernels leave them to a second launch
-    launches_per_step = 1 + (n_general > 0 and info["step_kernel"] != 0) + \
+    # the tile and row-march kernels update the nodes with a bounce-back link
+    # themselves; the other step kernels leave them to a second launch
+    launches_per_step = 1 + (n_general > 0 and info["step_kernel"] not in (0, 3)) + \
         (info["n_dirichlet"] > 0 and not info["dirichlet_fused"])
 
     sampler = ClockSampler(local)
@@ -424,7 +426,7 @@ def main():
                "achieved_gbs": BYTES_PER_NODE["f64"] * nodes / (k64 / max(1, n64) / 1e3) / 1e9,
                "bytes_per_node": BYTES_PER_NODE["f64"],
                "step_kernel": ("tile 64x16" if choice64 == 0 else "TMA-staged tile 64x16" if choice64 == 5
-                               else "warp strip, %d rows" % (4 << choice64))}
+                               else "row march" if choice64 == 7 else "warp strip, %d rows" % (4 << choice64))}
         s64.close()
 
     # the batched ensemble: 512 uneven lakes and channels advanced together

@@ -78,13 +78,16 @@ typedef enum {
 
 enum { MACLAB_W = 0, MACLAB_E = 1, MACLAB_S = 2, MACLAB_N = 3 };
 
-/* Step kernels.  All three compute the same step and give bitwise
+/* Step kernels.  All four compute the same step and give bitwise
  * identical results; they differ in how a block reads the old state. */
 typedef enum {
     MACLAB_KERNEL_TILE = 0,  /* 64 x 16 node tiles, one block per tile         */
     MACLAB_KERNEL_STRIP = 1, /* one warp per strip of rows                     */
-    MACLAB_KERNEL_TMA = 2    /* FP32 only: persistent blocks; interior tiles
+    MACLAB_KERNEL_TMA = 2,   /* FP32 only: persistent blocks; interior tiles
                                 staged in shared memory by tensor copies     */
+    MACLAB_KERNEL_MARCH = 3  /* one warp per 64-column strip block walking
+                                down its rows, neighbours by warp shuffles,
+                                three rows of loads in flight (the default)  */
 } maclab_step_kernel;
 
 typedef struct {
@@ -321,9 +324,9 @@ int maclab_get_profile(maclab_t sim, double* step_kernel_ms, int64_t* launches);
  * the fastest: *choice = 0 for the 64 x 16 tile kernel, k = 1..4 for the
  * warp-strip kernel with 8, 16, 32 or 64 rows per strip, 5 for the
  * TMA-staged tile kernel, 6 for the tile kernel with two steps per launch
- * on clean tiles (maclab_set_temporal_block(sim, 2)); 5 and 6 are tried on
- * FP32 MacLABSWE handles only, and the temporal block depth is set to the
- * winner's (1 unless 6 wins).  Each shape runs 2 + trial_steps steps; the
+ * on clean tiles (maclab_set_temporal_block(sim, 2)), 7 for the row-march
+ * kernel; 5 and 6 are tried on FP32 MacLABSWE handles only, and the
+ * temporal block depth is set to the winner's (1 unless 6 wins).  Each shape runs 2 + trial_steps steps; the
  * state, step count and time are restored afterwards (results are bitwise
  * identical for every shape).  Allocates and frees a copy of the state.
  * Synchronises. */

@@ -225,10 +225,10 @@ class Simulation:
         self.info["tile_rows"] = min(int(rows), self.ny)
         self.info["grid_blocks"] = int(blocks)
 
-    KERNELS = {"tile": 0, "strip": 1, "tma": 2}
+    KERNELS = {"tile": 0, "strip": 1, "tma": 2, "march": 3}
 
     def set_step_kernel(self, kernel) -> None:
-        """Step kernel: "tile", "strip" or "tma" (FP32 only), or its code."""
+        """Step kernel: "tile", "strip", "tma" (FP32 only) or "march", or its code."""
         code = self.KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
         self._check(self._lib.maclab_set_step_kernel(self._h, code))
         self.info["step_kernel"] = code

@@ -8,6 +8,7 @@
 // memory, classifies nodes, and sequences the launches.
 #include "maclab.h"
 #include "maclab_kernels.cuh"
+#include "maclab_march.cuh"
 #include "maclab_elab.cuh"
 
 #include <cuda.h>
@@ -69,7 +70,9 @@ struct maclab_s {
     int ncb = 0, nrb = 0, ty = 0;
     int fmode = 0;             // force terms present: F_WIND | F_FRICTION | F_CORIOLIS
     int grid_blocks = 0;       // cap on step-kernel blocks (0 = one warp per strip)
-    int kernel = MACLAB_KERNEL_TILE;  // step kernel: tile, warp strip or TMA-staged tile
+    int kernel = MACLAB_KERNEL_TILE;  // step kernel: tile, warp strip, TMA-staged tile or row march
+    march::Geom mgeom{};       // row-march launch: strips, strip blocks, rows and per-block lists
+    bool march_dir_fused = false;  // Dirichlet nodes handled inside the row-march kernel
     bool tma_ok = false;       // tensor maps encoded (FP32, 16-byte aligned buffers)
     TmaMaps tma_maps[2];       // per buffer parity of the state being read
     int tma_grid = 0;          // persistent blocks of the TMA-staged kernel
@@ -116,6 +119,13 @@ int fail(maclab_t s, int code, const std::string& msg)
 int cuda_fail(maclab_t s, cudaError_t e, const char* what)
 {
     return fail(s, MACLAB_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Dirichlet nodes are applied inside the step kernel of this launch shape
+bool dirichlet_in_kernel(const maclab_s* s)
+{
+    if (s->kernel == MACLAB_KERNEL_MARCH) return s->march_dir_fused;
+    return s->kernel != MACLAB_KERNEL_STRIP && s->dir_fused;
 }
 
 void* dev_alloc(maclab_t s, size_t bytes)
@@ -250,6 +260,21 @@ int launch_step(maclab_t s)
     } else if (s->newlevel) {
         if (s->n_all > 0)
             step_general_kernel<T, true><<<(s->n_all + 127) / 128, 128, 0, s->stream>>>(f, s->all_list, s->n_all);
+    } else if (s->kernel == MACLAB_KERNEL_MARCH) {
+        // fast nodes, the nodes with a bounce-back link and (when fused) the
+        // Dirichlet nodes of every strip block in one launch
+        march::Geom g = s->mgeom;
+        g.bv = bv;
+        if (!s->march_dir_fused) g.dstart = nullptr;
+        const int blocks = (g.strips * g.nrb + march::WARPS - 1) / march::WARPS;
+        switch (s->fmode) {
+#define MACLAB_FM(m) \
+    case m:                                                                                        \
+        step_march_kernel<T, m><<<blocks, march::THREADS, march::smem_bytes<T>(), s->stream>>>(f, g); \
+        break;
+            MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
+#undef MACLAB_FM
+        }
     } else if (s->kernel != MACLAB_KERNEL_STRIP) {
         // fast nodes, (when fused) Dirichlet nodes and, with the tile kernel,
         // nodes with a bounce-back link in one launch; the TMA-staged kernel
@@ -303,7 +328,7 @@ int launch_step(maclab_t s)
                                                                                       s->n_general);
     }
     if (s->profiling) cudaEventRecord(ev1, s->stream);
-    if (s->n_dir > 0 && !s->elab && (s->newlevel || !(s->kernel != MACLAB_KERNEL_STRIP && s->dir_fused)))
+    if (s->n_dir > 0 && !s->elab && (s->newlevel || !dirichlet_in_kernel(s)))
         dirichlet_kernel<T><<<(s->n_dir + 127) / 128, 128, 0, s->stream>>>(
             (T*)s->eta[b], (T*)s->u[b], (T*)s->v[b], (const T*)s->D, s->D64, s->dir, s->n_dir, bv);
     cudaError_t e = cudaGetLastError();
@@ -702,6 +727,98 @@ int prepare(const maclab_grid* grid, const maclab_params* params, const maclab_b
     return MACLAB_OK;
 }
 
+// Launch geometry and per-strip-block lists of the row-march kernel.  The
+// strip blocks are sized so that all of them are resident at once (one
+// wave): strips = nx / 62 + 1 across, rows per block chosen so that
+// strips x blocks fills the resident warps of the device.
+template <typename T>
+int march_blocks_per_sm(int fmode, int* nb)
+{
+    cudaError_t e = cudaErrorInvalidValue;
+    const int smem = (int)march::smem_bytes<T>();
+    switch (fmode) {
+#define MACLAB_FM(m)                                                                                           \
+    case m:                                                                                                    \
+        e = cudaFuncSetAttribute(step_march_kernel<T, m>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+        if (e == cudaSuccess)                                                                                  \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, step_march_kernel<T, m>, march::THREADS, smem); \
+        break;
+        MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
+#undef MACLAB_FM
+    }
+    return e == cudaSuccess ? MACLAB_OK : MACLAB_E_CUDA;
+}
+
+int setup_march(maclab_t s, const Prepared& P, int sms)
+{
+    const int nx = P.nx, ny = P.ny, pitch = P.pitch;
+    int nb = 0;
+    const int rc = s->prec == MACLAB_F32 ? march_blocks_per_sm<float>(s->fmode, &nb)
+                                         : march_blocks_per_sm<double>(s->fmode, &nb);
+    if (rc != MACLAB_OK) {
+        cudaGetLastError();
+        return fail(nullptr, MACLAB_E_CUDA, "occupancy of the row-march kernel");
+    }
+    const int resident = std::max(1, nb) * march::WARPS * sms * march::WAVES;
+    march::Geom& g = s->mgeom;
+    g.strips = march::strips(nx);
+    const int want = std::max(1, resident / g.strips);
+    g.rows = std::min(ny, std::max(march::MIN_ROWS, (ny + want - 1) / want));
+    g.nrb = (ny + g.rows - 1) / g.rows;
+    const int items = g.strips * g.nrb;
+    auto item_of = [&](int i, int j) { return (j / g.rows) * g.strips + march::strip_of(i); };
+    // nodes with a bounce-back link, by strip block
+    std::vector<int> gl(P.general);
+    std::stable_sort(gl.begin(), gl.end(),
+                     [&](int a, int c) { return item_of(a % nx, a / nx) < item_of(c % nx, c / nx); });
+    std::vector<int> gs((size_t)items + 1, 0);
+    for (int n : gl) gs[item_of(n % nx, n / nx) + 1]++;
+    for (size_t k = 1; k < gs.size(); ++k) gs[k] += gs[k - 1];
+    // Dirichlet nodes, by strip block; fused when each inward node is written
+    // by the same strip block's row pass
+    std::vector<DirNode> dl(P.dirs);
+    auto item_of_idx = [&](int idx) { return item_of(idx % pitch, idx / pitch); };
+    std::stable_sort(dl.begin(), dl.end(),
+                     [&](const DirNode& a, const DirNode& c) { return item_of_idx(a.x) < item_of_idx(c.x); });
+    std::vector<int> ds((size_t)items + 1, 0);
+    bool fused = !dl.empty();
+    for (const DirNode& d : dl) {
+        fused = fused && item_of_idx(d.x) == item_of_idx(d.n1) && !(P.type[d.n1] & GENERAL_BIT);
+        ds[item_of_idx(d.x) + 1]++;
+    }
+    for (size_t k = 1; k < ds.size(); ++k) ds[k] += ds[k - 1];
+    s->march_dir_fused = fused;
+    int *dgs = nullptr, *dgl = nullptr, *dds = nullptr;
+    DirNode* ddl = nullptr;
+    bool ok = true;
+    if (!gl.empty())
+        ok = (dgs = (int*)dev_alloc(s, gs.size() * sizeof(int))) && (dgl = (int*)dev_alloc(s, gl.size() * sizeof(int)));
+    if (ok && fused)
+        ok = (dds = (int*)dev_alloc(s, ds.size() * sizeof(int))) &&
+             (ddl = (DirNode*)dev_alloc(s, dl.size() * sizeof(DirNode)));
+    if (!ok) return fail(nullptr, MACLAB_E_NOMEM, "device allocation failed");
+    cudaError_t ce = cudaSuccess;
+    auto put = [&](void* dst, const void* src, size_t bytes) {
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream);
+    };
+    if (dgs) {
+        put(dgs, gs.data(), gs.size() * sizeof(int));
+        put(dgl, gl.data(), gl.size() * sizeof(int));
+    }
+    if (dds) {
+        put(dds, ds.data(), ds.size() * sizeof(int));
+        put(ddl, dl.data(), dl.size() * sizeof(DirNode));
+    }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+    if (ce != cudaSuccess) return cuda_fail(nullptr, ce, "upload");
+    g.gstart = dgs;
+    g.glist = dgl;
+    g.dstart = dds;
+    g.dlist = ddl;
+    g.D64 = s->D64;
+    return MACLAB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -744,6 +861,8 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
     s->bc = P.bc;
     s->prec = params->precision;
     s->esize = s->prec == MACLAB_F32 ? 4 : 8;
+    // FP32: the row-march kernel (fastest measured on GB300); FP64: tiles
+    s->kernel = s->prec == MACLAB_F32 ? MACLAB_KERNEL_MARCH : MACLAB_KERNEL_TILE;
     s->e = P.e;
     s->dt = P.dt;
     s->stream = (cudaStream_t)stream;
@@ -894,6 +1013,14 @@ int maclab_create(const maclab_grid* grid, const maclab_params* params, const ma
     }
     s->ty = choose_tile_rows(ny, s->ncb, sms);
     s->nrb = (ny + s->ty - 1) / s->ty;
+    {
+        const int mrc = setup_march(s, P, sms);
+        if (mrc != MACLAB_OK) {
+            release_all(s);
+            delete s;
+            return mrc;
+        }
+    }
     *out = s;
     return MACLAB_OK;
 }
@@ -980,6 +1107,21 @@ int maclab_step(maclab_t s, int64_t n)
     return advance(s, n);
 }
 
+}  // extern "C"
+
+namespace {
+// step kernel of an autotune candidate
+int kernel_of_choice(int k)
+{
+    if (k == 0 || k == 6) return MACLAB_KERNEL_TILE;
+    if (k == 5) return MACLAB_KERNEL_TMA;
+    if (k == 7) return MACLAB_KERNEL_MARCH;
+    return MACLAB_KERNEL_STRIP;
+}
+}  // namespace
+
+extern "C" {
+
 int maclab_autotune(maclab_t s, int trial_steps, int* choice)
 {
     if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
@@ -1001,10 +1143,10 @@ int maclab_autotune(maclab_t s, int trial_steps, int* choice)
     const int prof0 = s->profiling;
     // candidates: 0 = tile kernel; k = 1..4 strip kernel with 4 << k rows;
     // 5 = TMA-staged tile kernel; 6 = tile kernel with two steps per launch
-    // on clean tiles (FP32 MacLABSWE steps only)
+    // on clean tiles (FP32 MacLABSWE steps only); 7 = row-march kernel
     const int rows[5] = {0, 8, 16, 32, 64};
     const bool try_pairs = s->prec == MACLAB_F32 && !s->elab && !s->newlevel;
-    const int ncand = try_pairs ? 7 : (s->tma_ok ? 6 : 5);
+    const int ncand = 8;
     double best = 1e300;
     int best_k = 0;
     cudaEvent_t e0, e1;
@@ -1015,6 +1157,8 @@ int maclab_autotune(maclab_t s, int trial_steps, int* choice)
     s->tblock = 1;
     for (int k = 0; k < ncand && rc == MACLAB_OK; ++k) {
         if (k == 5 && !s->tma_ok) continue;
+        if (k == 6 && !try_pairs) continue;
+        if (k == 7) s->tblock = 1;
         if (k == 6) {
             if ((rc = maclab_set_temporal_block(s, 2)) != MACLAB_OK) break;
             if (s->n_clean == 0) {
@@ -1022,7 +1166,7 @@ int maclab_autotune(maclab_t s, int trial_steps, int* choice)
                 continue;
             }
         }
-        s->kernel = (k == 0 || k == 6) ? MACLAB_KERNEL_TILE : k == 5 ? MACLAB_KERNEL_TMA : MACLAB_KERNEL_STRIP;
+        s->kernel = kernel_of_choice(k);
         if (k >= 1 && k <= 4) {
             s->ty = std::min(rows[k], s->grid.ny);
             s->nrb = (s->grid.ny + s->ty - 1) / s->ty;
@@ -1043,8 +1187,7 @@ int maclab_autotune(maclab_t s, int trial_steps, int* choice)
     s->profiling = prof0;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    s->kernel = (best_k == 0 || best_k == 6) ? MACLAB_KERNEL_TILE : best_k == 5 ? MACLAB_KERNEL_TMA
-                                                                                 : MACLAB_KERNEL_STRIP;
+    s->kernel = kernel_of_choice(best_k);
     s->tblock = best_k == 6 ? 2 : 1;
     if (best_k >= 1 && best_k <= 4) {
         s->ty = std::min(rows[best_k], s->grid.ny);
@@ -1263,7 +1406,8 @@ int maclab_set_launch(maclab_t s, int rows, int blocks)
 int maclab_set_step_kernel(maclab_t s, int kernel)
 {
     if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
-    if (kernel != MACLAB_KERNEL_TILE && kernel != MACLAB_KERNEL_STRIP && kernel != MACLAB_KERNEL_TMA)
+    if (kernel != MACLAB_KERNEL_TILE && kernel != MACLAB_KERNEL_STRIP && kernel != MACLAB_KERNEL_TMA &&
+        kernel != MACLAB_KERNEL_MARCH)
         return fail(s, MACLAB_E_ARG, "unknown step kernel");
     if (kernel == MACLAB_KERNEL_TMA && !s->tma_ok)
         return fail(s, MACLAB_E_ARG, "the TMA-staged kernel needs an FP32 handle with 16-byte aligned buffers");
@@ -1451,7 +1595,7 @@ int maclab_get_info(maclab_t s, maclab_info* info)
     info->device_bytes = s->device_bytes;
     info->tile_rows = s->ty;
     info->step_kernel = s->kernel;
-    info->dirichlet_fused = (s->kernel != MACLAB_KERNEL_STRIP && s->dir_fused) ? 1 : 0;
+    info->dirichlet_fused = dirichlet_in_kernel(s) ? 1 : 0;
     info->temporal_block = s->tblock;
     info->clean_tiles = s->n_clean;
     info->tau = s->tau;

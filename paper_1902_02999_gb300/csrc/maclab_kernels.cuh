@@ -1056,29 +1056,20 @@ __device__ __forceinline__ void tile_phase_a(const Fields<T>& f, int x0, int y0,
     }
 }
 
-// New eta, u, v of the node at tile row lr, column lc from the derived values
-// of its eight neighbours in shared memory (Eqs. Mac.lb.6 / Mac.lb.7 in the
-// perturbation form); eta, D, ownh, hFx, hFy are the node's own source
-// quantities.  Every kernel that gathers from shared memory calls this one
-// function, so their results agree bitwise.
-template <typename T, typename DR>
-__device__ __forceinline__ void node_update(const DR& sm, int lr, int lc, const Coef<T>& K, T eta, T D, T ownh,
-                                            T hFx, T hFy, bool noslip, T& oe, T& ou, T& ov)
+// New eta, u, v of a node from its streamed sums (Sh, Sx, Sy: the first
+// terms of Eqs. Mac.lb.6 / Mac.lb.7 over the eight incoming outgoing values)
+// and the (eta, D) of its eight neighbours (m: row above, c: same row,
+// p: row below; L / C / R: column left / same / right), in the perturbation
+// form; eta, D, ownh, hFx, hFy are the node's own source quantities.  Every
+// kernel that updates fast-path nodes ends in this one function, so their
+// results agree bitwise.
+template <typename T, typename V2 = typename Vec2<T>::type>
+__device__ __forceinline__ void update_tail(const Coef<T>& K, T Sh, T Sx, T Sy, V2 mL, V2 mC, V2 mR, V2 cL, V2 cR,
+                                            V2 pL, V2 pC, V2 pR, T eta, T D, T ownh, T hFx, T hFy, bool noslip,
+                                            T& oe, T& ou, T& ov)
 {
     using O = Op<T>;
-    using V2 = typename Vec2<T>::type;
     const T q = T(0.25);
-    const T cL_o1 = sm.o(0, lr, lc - 1), mL_o2 = sm.o(1, lr - 1, lc - 1), pL_o8 = sm.o(7, lr + 1, lc - 1);
-    const T cR_o5 = sm.o(4, lr, lc + 1), mR_o4 = sm.o(3, lr - 1, lc + 1), pR_o6 = sm.o(5, lr + 1, lc + 1);
-    const T mC_o3 = sm.o(2, lr - 1, lc), pC_o7 = sm.o(6, lr + 1, lc);
-    const V2 mL = sm.ed(lr - 1, lc - 1), mC = sm.ed(lr - 1, lc), mR = sm.ed(lr - 1, lc + 1);
-    const V2 cL = sm.ed(lr, lc - 1), cR = sm.ed(lr, lc + 1);
-    const V2 pL = sm.ed(lr + 1, lc - 1), pC = sm.ed(lr + 1, lc), pR = sm.ed(lr + 1, lc + 1);
-    const T OL = O::add(O::add(cL_o1, mL_o2), pL_o8);
-    const T OR = O::add(O::add(cR_o5, mR_o4), pR_o6);
-    const T Sh = O::add(O::add(OL, OR), O::add(mC_o3, pC_o7));
-    const T Sx = O::sub(OL, OR);
-    const T Sy = O::sub(O::add(O::add(mL_o2, mR_o4), mC_o3), O::add(O::add(pL_o8, pR_o6), pC_o7));
     // lambda-weighted stencils of eta (.x) and D (.y): sum, x-moment, y-moment
     T Se, Sd, Xe, Xd, Ye, Yd;
 #ifndef MACLAB_SCALAR_STENCIL
@@ -1114,6 +1105,43 @@ __device__ __forceinline__ void node_update(const DR& sm, int lr, int lc, const 
     oe = eta1;
     ou = noslip ? T(0) : O::mul(hu1, inv);
     ov = noslip ? T(0) : O::mul(hv1, inv);
+}
+
+// Streamed sums of the first terms of Eqs. Mac.lb.6 / Mac.lb.7 from the
+// eight incoming values, grouped as (left column), (right column), centre:
+// a1 = cL_o1 + mL_o2 and a2 = cR_o5 + mR_o4 and sym = mL_o2 + mR_o4 + mC_o3
+// take only the node's own row and the row above, so a kernel that walks
+// down the rows can form them before the row below exists.
+template <typename T>
+__device__ __forceinline__ void streamed_sums(T a1, T a2, T sym, T mC_o3, T pL_o8, T pR_o6, T pC_o7, T& Sh, T& Sx,
+                                              T& Sy)
+{
+    using O = Op<T>;
+    const T OL = O::add(a1, pL_o8);
+    const T OR = O::add(a2, pR_o6);
+    Sh = O::add(O::add(OL, OR), O::add(mC_o3, pC_o7));
+    Sx = O::sub(OL, OR);
+    Sy = O::sub(sym, O::add(O::add(pL_o8, pR_o6), pC_o7));
+}
+
+// New eta, u, v of the node at tile row lr, column lc from the derived values
+// of its eight neighbours in shared memory (Eqs. Mac.lb.6 / Mac.lb.7 in the
+// perturbation form); eta, D, ownh, hFx, hFy are the node's own source
+// quantities.
+template <typename T, typename DR>
+__device__ __forceinline__ void node_update(const DR& sm, int lr, int lc, const Coef<T>& K, T eta, T D, T ownh,
+                                            T hFx, T hFy, bool noslip, T& oe, T& ou, T& ov)
+{
+    using O = Op<T>;
+    const T cL_o1 = sm.o(0, lr, lc - 1), mL_o2 = sm.o(1, lr - 1, lc - 1), pL_o8 = sm.o(7, lr + 1, lc - 1);
+    const T cR_o5 = sm.o(4, lr, lc + 1), mR_o4 = sm.o(3, lr - 1, lc + 1), pR_o6 = sm.o(5, lr + 1, lc + 1);
+    const T mC_o3 = sm.o(2, lr - 1, lc), pC_o7 = sm.o(6, lr + 1, lc);
+    T Sh, Sx, Sy;
+    streamed_sums<T>(O::add(cL_o1, mL_o2), O::add(cR_o5, mR_o4), O::add(O::add(mL_o2, mR_o4), mC_o3), mC_o3, pL_o8,
+                     pR_o6, pC_o7, Sh, Sx, Sy);
+    update_tail<T>(K, Sh, Sx, Sy, sm.ed(lr - 1, lc - 1), sm.ed(lr - 1, lc), sm.ed(lr - 1, lc + 1), sm.ed(lr, lc - 1),
+                   sm.ed(lr, lc + 1), sm.ed(lr + 1, lc - 1), sm.ed(lr + 1, lc), sm.ed(lr + 1, lc + 1), eta, D, ownh,
+                   hFx, hFy, noslip, oe, ou, ov);
 }
 
 // Phases B and C of a tile whose phase A is complete and visible; `tile`
