@@ -266,7 +266,7 @@ int launch_step(maclab_t s)
         march::Geom g = s->mgeom;
         g.bv = bv;
         if (!s->march_dir_fused) g.dstart = nullptr;
-        const int blocks = (g.strips * g.nrb + march::WARPS - 1) / march::WARPS;
+        const int blocks = (g.nitems + march::WARPS - 1) / march::WARPS;
         switch (s->fmode) {
 #define MACLAB_FM(m) \
     case m:                                                                                        \
@@ -759,14 +759,73 @@ int setup_march(maclab_t s, const Prepared& P, int sms)
         cudaGetLastError();
         return fail(nullptr, MACLAB_E_CUDA, "occupancy of the row-march kernel");
     }
-    const int resident = std::max(1, nb) * march::WARPS * sms * march::WAVES;
+    const int R = std::max(1, nb) * march::WARPS * sms;  // resident warps: one wave
     march::Geom& g = s->mgeom;
-    g.strips = march::strips(nx);
-    const int want = std::max(1, resident / g.strips);
-    g.rows = std::min(ny, std::max(march::MIN_ROWS, (ny + want - 1) / want));
-    g.nrb = (ny + g.rows - 1) / g.rows;
-    const int items = g.strips * g.nrb;
-    auto item_of = [&](int i, int j) { return (j / g.rows) * g.strips + march::strip_of(i); };
+    const int S = march::strips(nx);
+    g.strips = S;
+    // strip blocks (strip, j0, j1) in launch order; blocks are dispatched in
+    // index order as warp slots free up
+    std::vector<int> it;
+    auto add = [&](int st, int j0, int j1) {
+        it.push_back(st);
+        it.push_back(j0);
+        it.push_back(j1);
+        it.push_back(0);
+    };
+    const double phi = MACLAB_MARCH_GUIDED_PHI;
+    if (phi > 0) {
+        // guided: tall blocks first (one wave), then shorter ones
+        const int H1 = std::min(ny, std::max(march::MIN_ROWS, (int)(phi * S * (double)ny / R)));
+        const int H2 = std::max(march::MIN_ROWS, H1 / MACLAB_MARCH_GUIDED_DIV);
+        std::vector<int> nbig(S);
+        int maxbig = 0;
+        for (int st = 0; st < S; ++st) {
+            nbig[st] = std::min(ny / H1, R / S + (st < R % S ? 1 : 0));
+            maxbig = std::max(maxbig, nbig[st]);
+        }
+        for (int k = 0; k < maxbig; ++k)
+            for (int st = 0; st < S; ++st)
+                if (k < nbig[st]) add(st, k * H1, (k + 1) * H1);
+        std::vector<std::vector<int>> smallb(S);
+        size_t maxsmall = 0;
+        for (int st = 0; st < S; ++st) {
+            const int j0 = nbig[st] * H1, rem = ny - j0;
+            if (rem <= 0) continue;
+            const int n = (rem + H2 - 1) / H2;
+            for (int k = 0; k <= n; ++k) smallb[st].push_back(j0 + (int)((int64_t)k * rem / n));
+            maxsmall = std::max(maxsmall, smallb[st].size() - 1);
+        }
+        for (size_t k = 0; k < maxsmall; ++k)
+            for (int st = 0; st < S; ++st)
+                if (k + 1 < smallb[st].size()) add(st, smallb[st][k], smallb[st][k + 1]);
+    } else {
+        // uniform: WAVES strip blocks per resident warp
+        const int want = std::max(1, R * march::WAVES / S);
+        const int rows = std::min(ny, std::max(march::MIN_ROWS, (ny + want - 1) / want));
+        for (int j0 = 0; j0 < ny; j0 += rows)
+            for (int st = 0; st < S; ++st) add(st, j0, std::min(ny, j0 + rows));
+    }
+    const int items = (int)(it.size() / 4);
+    g.nitems = items;
+    // strip block of each node: per strip, the block index of each row
+    std::vector<int> item_of_row((size_t)S * ny, -1);
+    for (int t = 0; t < items; ++t)
+        for (int j = it[4 * t + 1]; j < it[4 * t + 2]; ++j) item_of_row[(size_t)it[4 * t] * ny + j] = t;
+    // plain interior blocks: every row they read and write lies inside the
+    // grid (32-bit offsets), and every node they write is a fluid or
+    // Dirichlet node without a bounce-back link (no node type is needed)
+    const bool idx32 = (int64_t)pitch * ny < ((int64_t)1 << 31);
+    for (int t = 0; t < items; ++t) {
+        const int st = it[4 * t], j0 = it[4 * t + 1], j1 = it[4 * t + 2], x0 = march::first_col(st);
+        bool plain = idx32 && x0 >= 0 && x0 + 64 <= nx && j0 >= 1 && j1 + 1 <= ny;
+        for (int j = j0; j < j1 && plain; ++j)
+            for (int i = x0 + 1; i <= x0 + march::OUT && plain; ++i) {
+                const uint8_t ty = P.type[(size_t)j * pitch + i];
+                plain = ty == MACLAB_FLUID || ty == MACLAB_DIR_H || ty == MACLAB_DIR_Q || ty == MACLAB_DIR_HU;
+            }
+        it[4 * t + 3] = plain ? 1 : 0;
+    }
+    auto item_of = [&](int i, int j) { return item_of_row[(size_t)march::strip_of(i) * ny + j]; };
     // nodes with a bounce-back link, by strip block
     std::vector<int> gl(P.general);
     std::stable_sort(gl.begin(), gl.end(),
@@ -788,10 +847,10 @@ int setup_march(maclab_t s, const Prepared& P, int sms)
     }
     for (size_t k = 1; k < ds.size(); ++k) ds[k] += ds[k - 1];
     s->march_dir_fused = fused;
-    int *dgs = nullptr, *dgl = nullptr, *dds = nullptr;
+    int *dgs = nullptr, *dgl = nullptr, *dds = nullptr, *dit = nullptr;
     DirNode* ddl = nullptr;
-    bool ok = true;
-    if (!gl.empty())
+    bool ok = (dit = (int*)dev_alloc(s, it.size() * sizeof(int))) != nullptr;  // 256-byte aligned (int4 reads)
+    if (ok && !gl.empty())
         ok = (dgs = (int*)dev_alloc(s, gs.size() * sizeof(int))) && (dgl = (int*)dev_alloc(s, gl.size() * sizeof(int)));
     if (ok && fused)
         ok = (dds = (int*)dev_alloc(s, ds.size() * sizeof(int))) &&
@@ -801,6 +860,7 @@ int setup_march(maclab_t s, const Prepared& P, int sms)
     auto put = [&](void* dst, const void* src, size_t bytes) {
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream);
     };
+    put(dit, it.data(), it.size() * sizeof(int));
     if (dgs) {
         put(dgs, gs.data(), gs.size() * sizeof(int));
         put(dgl, gl.data(), gl.size() * sizeof(int));
@@ -811,6 +871,7 @@ int setup_march(maclab_t s, const Prepared& P, int sms)
     }
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
     if (ce != cudaSuccess) return cuda_fail(nullptr, ce, "upload");
+    g.items = dit;
     g.gstart = dgs;
     g.glist = dgl;
     g.dstart = dds;

@@ -45,7 +45,15 @@ constexpr int MIN_ROWS = 8;          // rows per strip block, at least
 #ifndef MACLAB_MARCH_WAVES
 #define MACLAB_MARCH_WAVES 6
 #endif
-constexpr int WAVES = MACLAB_MARCH_WAVES;  // strip blocks per resident warp slot
+constexpr int WAVES = MACLAB_MARCH_WAVES;  // uniform split: strip blocks per resident warp slot
+// guided split (GUIDED_PHI > 0): one wave of tall strip blocks covering the
+// fraction GUIDED_PHI of the rows, then blocks GUIDED_DIV times shorter
+#ifndef MACLAB_MARCH_GUIDED_PHI
+#define MACLAB_MARCH_GUIDED_PHI 0.6
+#endif
+#ifndef MACLAB_MARCH_GUIDED_DIV
+#define MACLAB_MARCH_GUIDED_DIV 3
+#endif
 
 // Strip s derives columns 62 s - 2 .. 62 s + 61 and writes 62 s - 1 .. 62 s + 60.
 __host__ __device__ constexpr int strips(int nx) { return nx / OUT + 1; }
@@ -54,6 +62,10 @@ __host__ __device__ constexpr int first_col(int s) { return OUT * s - 2; }
 __host__ __device__ constexpr int strip_of(int x) { return (x + 1) / OUT; }
 
 constexpr int AHEAD = 2;  // rows of loads in flight per warp
+#ifndef MACLAB_MARCH_CARRY
+#define MACLAB_MARCH_CARRY 2
+#endif
+constexpr int CARRY = MACLAB_MARCH_CARRY;  // 1: o3 in registers; 2: also the lane's own (eta, D)
 
 #ifndef MACLAB_MARCH_MINB_F32
 #define MACLAB_MARCH_MINB_F32 5
@@ -64,8 +76,9 @@ template <> struct MinBlocks<double> { static constexpr int value = 2; };
 // Geometry and per-strip-block companion lists of one launch.
 struct Geom {
     int strips;        // strips across the grid
-    int nrb;           // strip blocks down the grid
-    int rows;          // rows per strip block (the last may be shorter)
+    int nitems;        // strip blocks
+    const int* items;  // strip block t: strip items[4t], rows items[4t + 1] .. items[4t + 2] - 1,
+                       // items[4t + 3] = 1 for a plain interior block (the fast path)
     const int* gstart; // nodes with a bounce-back link of item t: glist[gstart[t] .. gstart[t + 1]), or nullptr
     const int* glist;  // (j * nx + i)
     const int* dstart; // Dirichlet nodes of item t: dlist[dstart[t] .. dstart[t + 1]), or nullptr (not fused)
@@ -169,8 +182,10 @@ __device__ __forceinline__ void cp_async_z(uint32_t dst, const void* src, bool v
 }
 
 // Issue the copies of the lane's pair of row y into raw slot `slot` (one
-// commit group).  EDGE = false: the whole strip block reads inside the grid
-// with 32-bit offsets.  EDGE = true: a row outside the grid is resolved
+// commit group).  EDGE = false: a plain interior strip block (it reads
+// inside the grid with 32-bit offsets, and the nodes it writes are fluid or
+// Dirichlet nodes without a bounce-back link, so no node type is needed).
+// EDGE = true: any strip block; a row outside the grid is resolved
 // through the S / N edge kinds (the same for the whole warp), the lane's
 // columns through its fixed sources; sources behind a wall read zero.
 template <typename T, bool EDGE>
@@ -191,7 +206,8 @@ __device__ __forceinline__ void fetch_row(const Fields<T>& f, int y, int x, cons
 #pragma unroll
         for (int q = 0; q < 4; ++q) cp_async_z<2 * sizeof(T)>(dst + q * FS, fld[q] + off, true);
         // the type bytes of x, x + 1 lie in the aligned word at off & ~3
-        cp_async_z<4>(tdst, f.type + (off & ~(size_t)3), true);
+        // (plain interior blocks do not need them)
+        if (EDGE) cp_async_z<4>(tdst, f.type + (off & ~(size_t)3), true);
     } else {
         const bool ok0 = rr >= 0 && lc.c0 >= 0, ok1 = rr >= 0 && lc.c1 >= 0;
         const size_t row = rr >= 0 ? (size_t)rr * f.pitch : 0;
@@ -217,7 +233,7 @@ __device__ __forceinline__ void read_row(const Fields<T>& f, int y, int x, const
     p.v = sm.raw[slot][2][lane];
     p.d = sm.raw[slot][3][lane];
     if (!EDGE) {
-        p.types = (sm.rtype[slot][lane][0] >> (8 * (x & 3))) & 0xffffu;
+        p.types = 0;  // plain interior block: fluid or Dirichlet nodes only, no mirrors
         return;
     }
     uint8_t fy = 0;
@@ -310,7 +326,8 @@ __device__ __forceinline__ void gather_pair(const Coef<float>& K, float2 A1, flo
 template <typename T, int FM, bool EDGE>
 __device__ __forceinline__ void march_row(const Fields<T>& f, int r, int x, const LaneCols2& lc, int last,
                                           unsigned colmask, int lane, WarpSmem<T>& sm, int sp, int sc, int sm_,
-                                          Own<T>& own, bool done)
+                                          Own<T>& own, bool done, typename Vec2<T>::type (&o3r)[3],
+                                          typename Vec2<T>::type (&edr)[3][2])
 {
     using V2 = typename Vec2<T>::type;
     Pair<T> p;
@@ -328,7 +345,7 @@ __device__ __forceinline__ void march_row(const Fields<T>& f, int r, int x, cons
             sm.o[sp][q][0][1 + lane] = ov4[q].x;
             sm.o[sp][q][1][1 + lane] = ov4[q].y;
         }
-        sm.o3[sp][lane] = d.o3;
+        if (CARRY == 0) sm.o3[sp][lane] = d.o3;
         sm.ed[sp][0][1 + lane] = V2{d.eta.x, d.D.x};
         sm.ed[sp][1][1 + lane] = V2{d.eta.y, d.D.y};
     }
@@ -336,21 +353,23 @@ __device__ __forceinline__ void march_row(const Fields<T>& f, int r, int x, cons
     __syncwarp();  // derived slot sp is visible to the warp
     if (done) {
         // output row r - 1: its own row in slot sc, the row above in sm_, the row below r
-        const V2 m[4] = {sm.ed[sm_][1][lane], sm.ed[sm_][0][1 + lane], sm.ed[sm_][1][1 + lane],
-                         sm.ed[sm_][0][2 + lane]};
-        const V2 c[4] = {sm.ed[sc][1][lane], sm.ed[sc][0][1 + lane], sm.ed[sc][1][1 + lane], sm.ed[sc][0][2 + lane]};
+        const V2 m[4] = {sm.ed[sm_][1][lane], CARRY >= 2 ? edr[sm_][0] : sm.ed[sm_][0][1 + lane],
+                         CARRY >= 2 ? edr[sm_][1] : sm.ed[sm_][1][1 + lane], sm.ed[sm_][0][2 + lane]};
+        const V2 c[4] = {sm.ed[sc][1][lane], CARRY >= 2 ? edr[sc][0] : sm.ed[sc][0][1 + lane],
+                         CARRY >= 2 ? edr[sc][1] : sm.ed[sc][1][1 + lane], sm.ed[sc][0][2 + lane]};
         const V2 pe[4] = {sm.ed[sp][1][lane], V2{d.eta.x, d.D.x}, V2{d.eta.y, d.D.y}, sm.ed[sp][0][2 + lane]};
         // o2 at x - 1, x; o4 at x + 1, x + 2; o3 at x, x + 1 (row above); o1 at x - 1, x; o5 at x + 1, x + 2
         // (column x - 1 is odd column j = lane - 1, x + 2 even column j = lane + 1)
         const V2 M2 = V2{sm.o[sm_][1][1][lane], sm.o[sm_][1][0][1 + lane]};
         const V2 M4 = V2{sm.o[sm_][2][1][1 + lane], sm.o[sm_][2][0][2 + lane]};
-        const V2 M3 = sm.o3[sm_][lane];
+        const V2 M3 = CARRY >= 1 ? o3r[sm_] : sm.o3[sm_][lane];
         const V2 A1 = V2{sm.o[sc][0][1][lane], sm.o[sc][0][0][1 + lane]};
         const V2 C5 = V2{sm.o[sc][3][1][1 + lane], sm.o[sc][3][0][2 + lane]};
-        // written: node kinds 1 .. 7 without the bounce-back bit (type byte in 1 .. 7)
+        // written: node kinds 1 .. 7 without the bounce-back bit (type byte in
+        // 1 .. 7); a plain interior block has only such nodes and no no-slip ones
         const uint32_t k0 = own.types & 0xffu, k1 = (own.types >> 8) & 0xffu;
-        const unsigned ok = colmask & ((k0 - 1u < 7u ? 1u : 0u) | (k1 - 1u < 7u ? 2u : 0u));
-        const bool ns0 = (k0 & KIND_MASK) == K_NOSLIP, ns1 = (k1 & KIND_MASK) == K_NOSLIP;
+        const unsigned ok = EDGE ? colmask & ((k0 - 1u < 7u ? 1u : 0u) | (k1 - 1u < 7u ? 2u : 0u)) : colmask;
+        const bool ns0 = EDGE && (k0 & KIND_MASK) == K_NOSLIP, ns1 = EDGE && (k1 & KIND_MASK) == K_NOSLIP;
         V2 oe, ou, ov;
         if constexpr (std::is_same<T, float>::value) {
             gather_pair(f.c, A1, M2, C5, M4, M3, V2{Lo8, d.o8.x}, V2{d.o6.y, Ro6}, d.o7, m, c, pe, own.ownh,
@@ -386,6 +405,11 @@ __device__ __forceinline__ void march_row(const Fields<T>& f, int r, int x, cons
     own.hFx = d.hFx;
     own.hFy = d.hFy;
     own.types = p.types;
+    if (CARRY >= 1) o3r[sp] = d.o3;
+    if (CARRY >= 2) {
+        edr[sp][0] = V2{d.eta.x, d.D.x};
+        edr[sp][1] = V2{d.eta.y, d.D.y};
+    }
 }
 
 // Rows j0 .. j1 - 1 of strip s (derived rows j0 - 1 .. j1).
@@ -409,15 +433,16 @@ __device__ __forceinline__ void march_strip(const Fields<T>& f, int s, int j0, i
         else asm volatile("cp.async.commit_group;\n" ::);
     }
     Own<T> own;
+    typename Vec2<T>::type o3r[3], edr[3][2];  // carried in registers (CARRY)
     // rows rotate through slots: row r in raw and derived slot (r - j0 + 1) % 3
-    march_row<T, FM, EDGE>(f, j0 - 1, x, lc, last, colmask, lane, sm, 0, 2, 1, own, false);
-    march_row<T, FM, EDGE>(f, j0, x, lc, last, colmask, lane, sm, 1, 0, 2, own, false);
+    march_row<T, FM, EDGE>(f, j0 - 1, x, lc, last, colmask, lane, sm, 0, 2, 1, own, false, o3r, edr);
+    march_row<T, FM, EDGE>(f, j0, x, lc, last, colmask, lane, sm, 1, 0, 2, own, false, o3r, edr);
     for (int r = j0 + 1;; r += 3) {
-        march_row<T, FM, EDGE>(f, r, x, lc, last, colmask, lane, sm, 2, 1, 0, own, true);
+        march_row<T, FM, EDGE>(f, r, x, lc, last, colmask, lane, sm, 2, 1, 0, own, true, o3r, edr);
         if (r >= last) break;
-        march_row<T, FM, EDGE>(f, r + 1, x, lc, last, colmask, lane, sm, 0, 2, 1, own, true);
+        march_row<T, FM, EDGE>(f, r + 1, x, lc, last, colmask, lane, sm, 0, 2, 1, own, true, o3r, edr);
         if (r + 1 >= last) break;
-        march_row<T, FM, EDGE>(f, r + 2, x, lc, last, colmask, lane, sm, 1, 0, 2, own, true);
+        march_row<T, FM, EDGE>(f, r + 2, x, lc, last, colmask, lane, sm, 1, 0, 2, own, true, o3r, edr);
         if (r + 2 >= last) break;
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
@@ -434,12 +459,10 @@ step_march_kernel(const __grid_constant__ Fields<T> f, const __grid_constant__ m
     const int lane = threadIdx.x & 31, wib = (int)(threadIdx.x >> 5);
     march::WarpSmem<T>& sm = reinterpret_cast<march::WarpSmem<T>*>(march_smem)[wib];
     const int item = (int)blockIdx.x * march::WARPS + wib;
-    if (item >= g.strips * g.nrb) return;  // whole warp
-    const int s = item % g.strips, rb = item / g.strips;
-    const int j0 = rb * g.rows, j1 = min(f.ny, j0 + g.rows);
-    const int x0 = march::first_col(s);
-    const bool inside = f.idx32 && x0 >= 0 && x0 + 64 <= f.nx && j0 >= 1 && j1 + 1 <= f.ny;
-    if (inside) march::march_strip<T, FM, false>(f, s, j0, j1, lane, sm);
+    if (item >= g.nitems) return;  // whole warp
+    const int4 t = reinterpret_cast<const int4*>(g.items)[item];
+    const int s = t.x, j0 = t.y, j1 = t.z;
+    if (t.w) march::march_strip<T, FM, false>(f, s, j0, j1, lane, sm);
     else march::march_strip<T, FM, true>(f, s, j0, j1, lane, sm);
     if (g.gstart) {
         const int e = g.gstart[item + 1];
