@@ -86,8 +86,9 @@ typedef enum {
     MACLAB_KERNEL_TMA = 2,   /* FP32 only: persistent blocks; interior tiles
                                 staged in shared memory by tensor copies     */
     MACLAB_KERNEL_MARCH = 3  /* one warp per 64-column strip block walking
-                                down its rows, neighbours by warp shuffles,
-                                three rows of loads in flight (the default)  */
+                                down its rows through a shared-memory row
+                                ring, rows staged two ahead by cp.async
+                                (the FP32 default)                           */
 } maclab_step_kernel;
 
 typedef struct {

@@ -819,7 +819,7 @@ int setup_march(maclab_t s, const Prepared& P, int sms)
         const int st = it[4 * t], j0 = it[4 * t + 1], j1 = it[4 * t + 2], x0 = march::first_col(st);
         bool plain = idx32 && x0 >= 0 && x0 + 64 <= nx && j0 >= 1 && j1 + 1 <= ny;
         for (int j = j0; j < j1 && plain; ++j)
-            for (int i = x0 + 1; i <= x0 + march::OUT && plain; ++i) {
+            for (int i = x0 + 1 + march::HALF; i <= x0 + 62 - march::HALF && plain; ++i) {
                 const uint8_t ty = P.type[(size_t)j * pitch + i];
                 plain = ty == MACLAB_FLUID || ty == MACLAB_DIR_H || ty == MACLAB_DIR_Q || ty == MACLAB_DIR_HU;
             }

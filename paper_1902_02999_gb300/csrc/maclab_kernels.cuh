@@ -256,14 +256,27 @@ __device__ __forceinline__ void flip_lane(uint8_t fl, float& u, float& v, float&
     if (fl && (fl & 3) != 3) Om = -Om;
 }
 
+// The FP32 coefficients as lane pairs (both lanes equal), the operand form
+// of the paired instructions; a kernel can take them ready-made in its
+// parameters (one 8-byte constant load each) or form them from Coef.
+struct Coef2 {
+    float2 e, G6, nG6, K6, k3, k2, k1, KF, hdt, nCb, wfx, wfy, Om, nz;
+};
+__host__ __device__ inline Coef2 coef2_of(const Coef<float>& c)
+{
+    const auto sp = [](float a) { return make_float2(a, a); };
+    return Coef2{sp(c.e), sp(c.G6), sp(-c.G6), sp(c.K6), sp(c.k3), sp(c.k2), sp(c.k1), sp(c.KF), sp(c.hdt),
+                 sp(-c.Cb), sp(c.wfx), sp(c.wfy), sp(c.Om), sp(c.nz)};
+}
+
 template <int FM>
-__device__ __forceinline__ void derive2(const Coef<float>& c, const Raw<float>& r0, const Raw<float>& r1, Src2& s)
+__device__ __forceinline__ void derive2(const Coef2& c, const Raw<float>& r0, const Raw<float>& r1, Src2& s)
 {
     using P = Op2;
     using O = Op<float>;
-    const float2 z = splat(c.nz);
+    const float2 z = c.nz;
     float2 u = make_float2(r0.u, r1.u), v = make_float2(r0.v, r1.v);
-    float2 wfx = splat(c.wfx), wfy = splat(c.wfy), Om = splat(c.Om);
+    float2 wfx = c.wfx, wfy = c.wfy, Om = c.Om;
     if (r0.flip | r1.flip) {  // specular ghosts: normal components reversed, rotation sense too
         flip_lane(r0.flip, u.x, v.x, wfx.x, wfy.x, Om.x);
         flip_lane(r1.flip, u.y, v.y, wfx.y, wfy.y, Om.y);
@@ -271,8 +284,8 @@ __device__ __forceinline__ void derive2(const Coef<float>& c, const Raw<float>& 
     const float2 eta = make_float2(r0.eta, r1.eta), D = make_float2(r0.D, r1.D);
     const float2 h = P::add(D, eta);
     const float2 uu = P::fma(u, u, P::mul(v, v, z));
-    const float2 ge = P::mul(splat(c.G6), eta, z);
-    const float2 ku = P::mul(splat(c.K6), uu, z);
+    const float2 ge = P::mul(c.G6, eta, z);
+    const float2 ku = P::mul(c.K6, uu, z);
     const float2 ap = P::mul(h, P::sub(ge, ku), z);
     // eta - h (5 ge + 4 ku)
     s.ownh = P::fma(h, P::fma(splat(-5.f), ge, P::mul(splat(-4.f), ku, z)), eta);
@@ -284,24 +297,24 @@ __device__ __forceinline__ void derive2(const Coef<float>& c, const Raw<float>& 
         Fy = P::fma(nomh, u, Fy);
     }
     if (FM & F_FRICTION) {
-        const float2 ncbs = P::mul(splat(-c.Cb), make_float2(O::sqrt(uu.x), O::sqrt(uu.y)), z);
+        const float2 ncbs = P::mul(c.nCb, make_float2(O::sqrt(uu.x), O::sqrt(uu.y)), z);
         Fx = P::fma(ncbs, u, Fx);
         Fy = P::fma(ncbs, v, Fy);
     }
     const float2 hu = P::mul(h, u, z), hv = P::mul(h, v, z);
-    float2 qx = P::mul(hu, splat(c.k3), z), qy = P::mul(hv, splat(c.k3), z);
+    float2 qx = P::mul(hu, c.k3, z), qy = P::mul(hv, c.k3, z);
     if (FM) {
-        s.hFx = P::mul(splat(c.hdt), Fx, z);
-        s.hFy = P::mul(splat(c.hdt), Fy, z);
-        qx = P::fma(splat(c.KF), Fx, qx);
-        qy = P::fma(splat(c.KF), Fy, qy);
+        s.hFx = P::mul(c.hdt, Fx, z);
+        s.hFy = P::mul(c.hdt, Fy, z);
+        qx = P::fma(c.KF, Fx, qx);
+        qy = P::fma(c.KF, Fy, qy);
     } else {
         s.hFx = splat(0.f);
         s.hFy = splat(0.f);
     }
-    const float2 sxx = P::mul(P::mul(hu, u, z), splat(c.k2), z);
-    const float2 syy = P::mul(P::mul(hv, v, z), splat(c.k2), z);
-    const float2 sxy = P::mul(P::mul(hu, v, z), splat(c.k1), z);
+    const float2 sxx = P::mul(P::mul(hu, u, z), c.k2, z);
+    const float2 syy = P::mul(P::mul(hv, v, z), c.k2, z);
+    const float2 sxy = P::mul(P::mul(hu, v, z), c.k1, z);
     const float2 ax = P::add(ap, sxx), ay = P::add(ap, syy);
     s.o1 = P::add(ax, qx);
     s.o5 = P::sub(ax, qx);
@@ -1248,12 +1261,12 @@ __device__ __forceinline__ void tile_phase_a_f32(const Fields<float>& f, int x0,
     }
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-        derive2<FM>(f.c, raw[r][0], raw[r][1], own[r]);
+        derive2<FM>(coef2_of(f.c), raw[r][0], raw[r][1], own[r]);
         store_pair2(sm, 1 + 2 * tyy + r, 2 + 2 * tx, own[r]);
     }
     if (has_halo) {
         Src2 hs;
-        derive2<FM>(f.c, hraw[0], hraw[1], hs);
+        derive2<FM>(coef2_of(f.c), hraw[0], hraw[1], hs);
         store_pair2(sm, hpr, 2 * hpc, hs);
     }
 }
@@ -1414,7 +1427,7 @@ step_tile2_kernel(const __grid_constant__ Fields<float> f, float* __restrict__ o
         const float2 d2 = *reinterpret_cast<const float2*>(f.D + base);
         const uint32_t types = *reinterpret_cast<const uint16_t*>(f.type + base);
         Src2 s;
-        derive2<FM>(K, Raw<float>{e2.x, u2.x, v2.x, d2.x, 0}, Raw<float>{e2.y, u2.y, v2.y, d2.y, 0}, s);
+        derive2<FM>(coef2_of(K), Raw<float>{e2.x, u2.x, v2.x, d2.x, 0}, Raw<float>{e2.y, u2.y, v2.y, d2.y, 0}, s);
         store_window_pair(sm, r, j, s, types);
     }
     __syncthreads();
@@ -1456,7 +1469,7 @@ step_tile2_kernel(const __grid_constant__ Fields<float> f, float* __restrict__ o
         if (p >= MID) break;
         const int r = 1 + p / PC, j = p % PC;
         Src2 s;
-        derive2<FM>(K, Raw<float>{he[k].x, hu[k].x, hv[k].x, hd[k].x, 0},
+        derive2<FM>(coef2_of(K), Raw<float>{he[k].x, hu[k].x, hv[k].x, hd[k].x, 0},
                     Raw<float>{he[k].y, hu[k].y, hv[k].y, hd[k].y, 0}, s);
         store_window_pair(sm, r, j, s, ht[k]);
     }

@@ -2,30 +2,34 @@
 // arXiv:1902.02999, Section 3, Eqs. Mac.lb.6 / Mac.lb.7 in the perturbation
 // form of maclab_kernels.cuh) for sm_103a.
 //
-// A warp owns a strip of 64 grid columns and a block of rows and walks down
-// the rows.  Lane k derives the node pair at columns X0 + 2k, X0 + 2k + 1 of
-// each row (the source quantities of Section 3: the eight outgoing
-// equilibrium differences with the source halves of the bed and force
-// terms, as in derive2), exchanges the edge column of the pair with its two
-// neighbouring lanes by warp shuffles, and keeps in registers only what the
-// next two rows need:
-//   * of each row, the (eta, D) of the four columns X0 + 2k - 1 .. X0 + 2k + 2
-//     (the lane's pair and one neighbour either side);
-//   * of each row r, the partial sums of output row r that need only rows
-//     r - 1 and r (a1 = cL_o1 + mL_o2, a2 = cR_o5 + mR_o4,
-//     sym = mL_o2 + mR_o4 + mC_o3), and the values that row r + 1 takes from
-//     row r (o2, o3, o4 of the right columns).
-// When row r has been derived, output row r - 1 is complete: the row below
-// supplies o6, o7, o8 and its (eta, D), and update_tail finishes the node
-// exactly as the tile kernel does, so both kernels give bitwise-equal
-// states.  Columns X0 + 1 .. X0 + 62 are written (62 per strip; lane 0's
-// first and lane 31's second column lack a neighbour), rows j0 .. j1 - 1;
-// rows j0 - 1 and j1 are derived only.
+// A warp owns a strip of 64 grid columns and a block of rows (a "strip
+// block") and walks down the rows.  Lane k derives the node pair at columns
+// X0 + 2k, X0 + 2k + 1 of each row: the source quantities of Section 3 (the
+// eight outgoing equilibrium differences with the source halves of the bed
+// and force terms, derive2), written to a three-row ring in the warp's
+// shared memory (o1, o2, o4, o5 and (eta, D) split by column parity, so
+// that a warp reading one column per lane has no bank conflicts).  When
+// row r is derived, output row r - 1 is complete: each lane updates its two
+// nodes (x, x + 1) from the ring (rows r - 2, r - 1), its own registers
+// (row r, o3 and its own (eta, D) of the two rows above) and two warp
+// shuffles (o8, o6 of row r from the neighbouring lanes).  The update runs
+// the streamed sums and the final arithmetic of the tile kernel with one
+// node per lane of the paired FP32 instructions; every lane takes the same
+// operations in the same order, so the states are bitwise those of the tile
+// kernel.  A strip writes columns X0 + 2 .. X0 + 61 (OUT = 60: lanes 0 and
+// 31 only supply the neighbours) and rows j0 .. j1 - 1; rows j0 - 1 and j1
+// are derived only.
 //
-// The loads of row r + 3 are issued when row r is derived (three rows in
-// flight per warp, 17 bytes per node), so no row waits for memory after the
-// first.  The row loop is unrolled three times with the roles of three sets
-// of row registers rotating, so no row state is copied between registers.
+// Raw rows are staged two rows ahead by cp.async into lane-private slots of
+// the warp's shared memory, so no row waits for memory after the first two
+// and no prefetch occupies registers; raw and derived rows share the ring
+// period 3, and the row loop is unrolled three times with compile-time
+// slots.  Strip blocks whose rows and columns lie inside the grid and whose
+// written nodes are all fluid or Dirichlet nodes without a bounce-back link
+// ("plain" interior blocks, flagged by the host) take a path with no node
+// types at all; the others resolve rows and columns through the edge rules.
+// The host orders the strip blocks tall first and short last (blocks start
+// in index order as warp slots free up), so the last wave is short.
 //
 // After its rows, a warp updates the nodes of its strip block that have a
 // bounce-back link (general_node, old state only) and then, when every
@@ -40,7 +44,11 @@ namespace march {
 
 constexpr int WARPS = 4;             // warps (strip blocks) per block
 constexpr int THREADS = 32 * WARPS;
-constexpr int OUT = 62;              // columns written per strip
+#ifndef MACLAB_MARCH_OUT
+#define MACLAB_MARCH_OUT 60
+#endif
+constexpr int OUT = MACLAB_MARCH_OUT;  // columns written per strip: 62 or 60
+constexpr int HALF = (62 - OUT) / 2;   // derived columns beyond the one-column halo, per side
 constexpr int MIN_ROWS = 8;          // rows per strip block, at least
 #ifndef MACLAB_MARCH_WAVES
 #define MACLAB_MARCH_WAVES 6
@@ -55,11 +63,13 @@ constexpr int WAVES = MACLAB_MARCH_WAVES;  // uniform split: strip blocks per re
 #define MACLAB_MARCH_GUIDED_DIV 3
 #endif
 
-// Strip s derives columns 62 s - 2 .. 62 s + 61 and writes 62 s - 1 .. 62 s + 60.
-__host__ __device__ constexpr int strips(int nx) { return nx / OUT + 1; }
+// Strip s derives the 64 columns from X0 = OUT s - 2 and writes local
+// columns 1 + HALF .. 62 - HALF: with OUT = 62 global columns 62 s - 1 ..
+// 62 s + 60, with OUT = 60 columns 60 s .. 60 s + 59.
 __host__ __device__ constexpr int first_col(int s) { return OUT * s - 2; }
 // strip of the node at column x (the strip that writes it)
-__host__ __device__ constexpr int strip_of(int x) { return (x + 1) / OUT; }
+__host__ __device__ constexpr int strip_of(int x) { return (x + 1 - HALF) / OUT; }
+__host__ __device__ constexpr int strips(int nx) { return strip_of(nx - 1) + 1; }
 
 constexpr int AHEAD = 2;  // rows of loads in flight per warp
 #ifndef MACLAB_MARCH_CARRY
@@ -100,8 +110,16 @@ struct SrcP {  // source quantities of the pair (x: column 0, y: column 1)
     V2 eta, D, o1, o2, o3, o4, o5, o6, o7, o8, ownh, hFx, hFy;
 };
 
+// FP32 coefficients as lane pairs (FP64 does not use them)
+template <typename T>
+__device__ __forceinline__ Coef2 pairs_of(const Coef<T>& c)
+{
+    if constexpr (std::is_same<T, float>::value) return coef2_of(c);
+    else return Coef2{};
+}
+
 template <typename T, int FM>
-__device__ __forceinline__ void derive_pair(const Coef<T>& c, const Pair<T>& p, SrcP<T>& s)
+__device__ __forceinline__ void derive_pair(const Coef<T>& c, const Coef2& c2, const Pair<T>& p, SrcP<T>& s)
 {
     const Raw<T> r0{p.e.x, p.u.x, p.v.x, p.d.x, (uint8_t)((p.types >> 16) & 3)};
     const Raw<T> r1{p.e.y, p.u.y, p.v.y, p.d.y, (uint8_t)((p.types >> 18) & 3)};
@@ -111,7 +129,7 @@ __device__ __forceinline__ void derive_pair(const Coef<T>& c, const Pair<T>& p, 
     if constexpr (false) {
 #endif
         Src2 q;
-        derive2<FM>(c, r0, r1, q);
+        derive2<FM>(c2, r0, r1, q);
         s.eta = q.eta; s.D = q.D; s.o1 = q.o1; s.o2 = q.o2; s.o3 = q.o3; s.o4 = q.o4; s.o5 = q.o5;
         s.o6 = q.o6; s.o7 = q.o7; s.o8 = q.o8; s.ownh = q.ownh; s.hFx = q.hFx; s.hFy = q.hFy;
     } else {
@@ -275,13 +293,13 @@ struct Own {
 // A1 = cL_o1, M2 = mL_o2, C5 = cR_o5, M4 = mR_o4, M3 = mC_o3, P8 = pL_o8,
 // P6 = pR_o6, P7 = pC_o7; m, c, p hold (eta, D) at columns x - 1 .. x + 2
 // of the rows above, own and below.
-__device__ __forceinline__ void gather_pair(const Coef<float>& K, float2 A1, float2 M2, float2 C5, float2 M4,
+__device__ __forceinline__ void gather_pair(const Coef2& K, float2 A1, float2 M2, float2 C5, float2 M4,
                                             float2 M3, float2 P8, float2 P6, float2 P7, const float2 (&m)[4],
                                             const float2 (&c)[4], const float2 (&p)[4], float2 ownh, float2 hFx,
                                             float2 hFy, bool ns0, bool ns1, float2& oe, float2& ou, float2& ov)
 {
     using P = Op2;
-    const float2 z = splat(K.nz), q2 = splat(0.25f);
+    const float2 z = K.nz, q2 = splat(0.25f);
     float2 S[2], X[2], Y[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
@@ -304,9 +322,9 @@ __device__ __forceinline__ void gather_pair(const Coef<float>& K, float2 A1, flo
     const float2 Sx = P::sub(OL, OR);
     const float2 Sy = P::sub(sym, P::add(P::add(P8, P6), P7));
     // update: -B = round(-G6 eta), the negated rounded product
-    const float2 A = P::mul(splat(K.G6), D, z), nB = P::mul(splat(-K.G6), E, z);
+    const float2 A = P::mul(K.G6, D, z), nB = P::mul(K.nG6, E, z);
     oe = P::add(P::add(ownh, Sh), P::fma(A, SE, P::mul(nB, SD, z)));
-    const float2 e2 = splat(K.e);
+    const float2 e2 = K.e;
     const float2 hu = P::fma(e2, P::add(Sx, P::fma(A, XE, P::mul(nB, XD, z))), hFx);
     const float2 hv = P::fma(e2, P::add(Sy, P::fma(A, YE, P::mul(nB, YD, z))), hFy);
     const float2 h = P::add(D, oe);
@@ -325,7 +343,8 @@ __device__ __forceinline__ void gather_pair(const Coef<float>& K, float2 A1, flo
 // raw slot sc (freed by row r - 1).
 template <typename T, int FM, bool EDGE>
 __device__ __forceinline__ void march_row(const Fields<T>& f, int r, int x, const LaneCols2& lc, int last,
-                                          unsigned colmask, int lane, WarpSmem<T>& sm, int sp, int sc, int sm_,
+                                          unsigned colmask, int lane, WarpSmem<T>& sm, const Coef2& c2, int sp,
+                                          int sc, int sm_,
                                           Own<T>& own, bool done, typename Vec2<T>::type (&o3r)[3],
                                           typename Vec2<T>::type (&edr)[3][2])
 {
@@ -336,7 +355,7 @@ __device__ __forceinline__ void march_row(const Fields<T>& f, int r, int x, cons
     asm volatile("cp.async.wait_group %0;\n" ::"n"(AHEAD));
     read_row<T, EDGE>(f, r, x, lc, sm, sp, lane, p);
     SrcP<T> d;
-    derive_pair<T, FM>(f.c, p, d);
+    derive_pair<T, FM>(f.c, c2, p, d);
     __syncwarp();  // every lane has read derived slot sp (row r - 3) for the last time
     {
         const V2 ov4[4] = {d.o1, d.o2, d.o4, d.o5};
@@ -372,7 +391,7 @@ __device__ __forceinline__ void march_row(const Fields<T>& f, int r, int x, cons
         const bool ns0 = EDGE && (k0 & KIND_MASK) == K_NOSLIP, ns1 = EDGE && (k1 & KIND_MASK) == K_NOSLIP;
         V2 oe, ou, ov;
         if constexpr (std::is_same<T, float>::value) {
-            gather_pair(f.c, A1, M2, C5, M4, M3, V2{Lo8, d.o8.x}, V2{d.o6.y, Ro6}, d.o7, m, c, pe, own.ownh,
+            gather_pair(c2, A1, M2, C5, M4, M3, V2{Lo8, d.o8.x}, V2{d.o6.y, Ro6}, d.o7, m, c, pe, own.ownh,
                         own.hFx, own.hFy, ns0, ns1, oe, ou, ov);
         } else {
             using O = Op<T>;
@@ -387,7 +406,14 @@ __device__ __forceinline__ void march_row(const Fields<T>& f, int r, int x, cons
                            own.ownh.y, own.hFx.y, own.hFy.y, ns1, oe.y, ou.y, ov.y);
         }
         const size_t idx = EDGE ? (size_t)(r - 1) * f.pitch + x : (size_t)(unsigned)((r - 1) * f.pitch + x);
-        if (ok == 3u) {
+        if (!EDGE && OUT == 60) {
+            // plain interior block, lanes 0 and 31 pure halo: both columns or none
+            if (ok) {
+                *reinterpret_cast<V2*>(f.eta1 + idx) = oe;
+                *reinterpret_cast<V2*>(f.u1 + idx) = ou;
+                *reinterpret_cast<V2*>(f.v1 + idx) = ov;
+            }
+        } else if (ok == 3u) {
             *reinterpret_cast<V2*>(f.eta1 + idx) = oe;
             *reinterpret_cast<V2*>(f.u1 + idx) = ou;
             *reinterpret_cast<V2*>(f.v1 + idx) = ov;
@@ -414,11 +440,13 @@ __device__ __forceinline__ void march_row(const Fields<T>& f, int r, int x, cons
 
 // Rows j0 .. j1 - 1 of strip s (derived rows j0 - 1 .. j1).
 template <typename T, int FM, bool EDGE>
-__device__ __forceinline__ void march_strip(const Fields<T>& f, int s, int j0, int j1, int lane, WarpSmem<T>& sm)
+__device__ __forceinline__ void march_strip(const Fields<T>& f, const Coef2& c2, int s, int j0, int j1, int lane,
+                                            WarpSmem<T>& sm)
 {
     const int x = first_col(s) + 2 * lane;
     // the lane's columns that the strip writes and that lie in the grid
-    unsigned colmask = lane == 0 ? 2u : lane == 31 ? 1u : 3u;
+    unsigned colmask = (2 * lane >= 1 + HALF && 2 * lane <= 62 - HALF ? 1u : 0u) |
+                       (2 * lane + 1 >= 1 + HALF && 2 * lane + 1 <= 62 - HALF ? 2u : 0u);
     LaneCols2 lc{x, x + 1, 0u, true};
     if (EDGE) {
         lc = lane_cols(f, x);
@@ -435,14 +463,14 @@ __device__ __forceinline__ void march_strip(const Fields<T>& f, int s, int j0, i
     Own<T> own;
     typename Vec2<T>::type o3r[3], edr[3][2];  // carried in registers (CARRY)
     // rows rotate through slots: row r in raw and derived slot (r - j0 + 1) % 3
-    march_row<T, FM, EDGE>(f, j0 - 1, x, lc, last, colmask, lane, sm, 0, 2, 1, own, false, o3r, edr);
-    march_row<T, FM, EDGE>(f, j0, x, lc, last, colmask, lane, sm, 1, 0, 2, own, false, o3r, edr);
+    march_row<T, FM, EDGE>(f, j0 - 1, x, lc, last, colmask, lane, sm, c2, 0, 2, 1, own, false, o3r, edr);
+    march_row<T, FM, EDGE>(f, j0, x, lc, last, colmask, lane, sm, c2, 1, 0, 2, own, false, o3r, edr);
     for (int r = j0 + 1;; r += 3) {
-        march_row<T, FM, EDGE>(f, r, x, lc, last, colmask, lane, sm, 2, 1, 0, own, true, o3r, edr);
+        march_row<T, FM, EDGE>(f, r, x, lc, last, colmask, lane, sm, c2, 2, 1, 0, own, true, o3r, edr);
         if (r >= last) break;
-        march_row<T, FM, EDGE>(f, r + 1, x, lc, last, colmask, lane, sm, 0, 2, 1, own, true, o3r, edr);
+        march_row<T, FM, EDGE>(f, r + 1, x, lc, last, colmask, lane, sm, c2, 0, 2, 1, own, true, o3r, edr);
         if (r + 1 >= last) break;
-        march_row<T, FM, EDGE>(f, r + 2, x, lc, last, colmask, lane, sm, 1, 0, 2, own, true, o3r, edr);
+        march_row<T, FM, EDGE>(f, r + 2, x, lc, last, colmask, lane, sm, c2, 1, 0, 2, own, true, o3r, edr);
         if (r + 2 >= last) break;
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
@@ -462,8 +490,8 @@ step_march_kernel(const __grid_constant__ Fields<T> f, const __grid_constant__ m
     if (item >= g.nitems) return;  // whole warp
     const int4 t = reinterpret_cast<const int4*>(g.items)[item];
     const int s = t.x, j0 = t.y, j1 = t.z;
-    if (t.w) march::march_strip<T, FM, false>(f, s, j0, j1, lane, sm);
-    else march::march_strip<T, FM, true>(f, s, j0, j1, lane, sm);
+    if (t.w) march::march_strip<T, FM, false>(f, march::pairs_of(f.c), s, j0, j1, lane, sm);
+    else march::march_strip<T, FM, true>(f, march::pairs_of(f.c), s, j0, j1, lane, sm);
     if (g.gstart) {
         const int e = g.gstart[item + 1];
         for (int k = g.gstart[item] + lane; k < e; k += 32) {
