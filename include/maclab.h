@@ -240,7 +240,11 @@ int maclab_residual(maclab_t sim, double out[4]);
  * Returns MACLAB_OK, MACLAB_E_ARG, MACLAB_E_CUDA, or MACLAB_E_UNSTABLE with
  * out filled when a value is non-finite.  The first call on a device looks
  * up the scratch array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All
+ * device current; make that first call before any stream capture.  The
+ * address is kept with the context it was taken in and looked up again
+ * when another context is current (after cudaDeviceReset the device's
+ * context and the library's module are new); that later lookup, too, must
+ * not fall inside a stream capture.  All
  * calls share the one scratch array and it keeps the last call's contents
  * (every value the reduction reads is written first by the same call), so
  * calls that overlap on the GPU -- on different streams or host threads --
@@ -387,10 +391,23 @@ int maclab_batch_set_graph_steps(maclab_batch_t batch, int steps);
  * launches every step separately, replayed from a CUDA graph, which
  * measured faster at every batch size tried (one 256 x 256 lake up to 512
  * instances).  Results are bitwise the same either way.  A grid-barrier
- * wait is bounded: if one times out, the next maclab_batch_residual or
- * maclab_batch_get_state returns MACLAB_E_CUDA.  Without cooperative
- * launch support mode 1 launches per step too.  Other modes: MACLAB_E_ARG. */
+ * wait is bounded: if one times out, the blocks leave the launch at
+ * different steps, the next maclab_batch_residual or maclab_batch_get_state
+ * returns MACLAB_E_CUDA, and from then on maclab_batch_step, _residual and
+ * _get_state return MACLAB_E_STATE until every instance has been reloaded
+ * with maclab_batch_set_state (the device state then matches no step
+ * count).  Without cooperative launch support mode 1 launches per step
+ * too.  Other modes: MACLAB_E_ARG. */
 int maclab_batch_set_persistent(maclab_batch_t batch, int mode);
+
+/* Failure-detection test hook for the persistent grid barrier (no
+ * counterpart in the paper): the barrier waits for extra arrivals beyond
+ * the launched grid, and each wait gives up after `polls` polls (default
+ * 4194304, about a second).  With extra >= 1 no barrier can complete, so
+ * every wait runs out: the way to exercise the bounded wait without
+ * faulting or hanging the GPU.  extra = 0 restores normal operation.
+ * MACLAB_E_ARG for extra < 0 or polls == 0. */
+int maclab_batch_set_barrier_test(maclab_batch_t batch, int extra, unsigned int polls);
 
 /* Residual of the last step per instance: out[4*i .. 4*i+3] as
  * maclab_residual for instance i.  Synchronises. */

@@ -401,6 +401,11 @@ class Batch:
         default)."""
         self._check(self._lib.maclab_batch_set_persistent(self._h, int(mode)))
 
+    def set_barrier_test(self, extra: int, polls: int) -> None:
+        """Failure-detection test hook of the persistent grid barrier: expect
+        `extra` arrivals beyond the grid and give up after `polls` polls."""
+        self._check(self._lib.maclab_batch_set_barrier_test(self._h, int(extra), int(polls)))
+
     def residual(self) -> np.ndarray:
         """[count, 4]: residual, mass, max|u|, non-finite count per instance."""
         out = np.zeros(4 * self.count)

@@ -91,6 +91,7 @@ PROTOTYPES = [
     ("maclab_batch_step", c_int, [c_void_p, c_int64]),
     ("maclab_batch_set_graph_steps", c_int, [c_void_p, c_int]),
     ("maclab_batch_set_persistent", c_int, [c_void_p, c_int]),
+    ("maclab_batch_set_barrier_test", c_int, [c_void_p, c_int, ctypes.c_uint]),
     ("maclab_batch_residual", c_int, [c_void_p, P(c_double)]),
     ("maclab_batch_set_active", c_int, [c_void_p, P(ctypes.c_uint8)]),
     ("maclab_batch_run_to_steady", c_int, [c_void_p, c_double, c_int64, c_int, P(c_int64),

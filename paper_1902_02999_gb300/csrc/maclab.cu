@@ -1339,10 +1339,32 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_MAX_BLOCKS * RED_NVAL + RED_NVAL];
 std::mutex g_noalloc_mutex;
 double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+CUcontext g_noalloc_ctx[NOALLOC_MAX_DEVICES] = {};
+
+// The context current on this thread (nullptr when none is, or when the
+// driver entry point is missing).
+CUcontext current_context()
+{
+    static PFN_cuCtxGetCurrent_v4000 get = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get = (PFN_cuCtxGetCurrent_v4000)fn;
+        cudaGetLastError();
+    });
+    CUcontext c = nullptr;
+    if (get && get(&c) != CUDA_SUCCESS) c = nullptr;
+    return c;
+}
 
 // Device address of the scratch array on the current device.  The array's
 // name in host code is only a host-side stand-in, so the address must come
-// from cudaGetSymbolAddress, once per device, with that device current.
+// from cudaGetSymbolAddress, with that device current: once per device, and
+// again whenever the current context is not the one the address was taken
+// in (after cudaDeviceReset the library's module is loaded anew).
 int noalloc_scratch(double** out)
 {
     int dev = 0;
@@ -1350,11 +1372,13 @@ int noalloc_scratch(double** out)
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(nullptr, MACLAB_E_ARG, "device index out of range");
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    const CUcontext ctx = current_context();
+    if (!g_noalloc_ptr[dev] || !ctx || ctx != g_noalloc_ctx[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return cuda_fail(nullptr, e, "cudaGetSymbolAddress(scratch)");
         g_noalloc_ptr[dev] = (double*)p;
+        g_noalloc_ctx[dev] = current_context();  // the lookup made the device's context current
     }
     *out = g_noalloc_ptr[dev];
     return MACLAB_OK;
@@ -1739,6 +1763,10 @@ struct maclab_batch_s {
     int persist_grid = 0;           // resident blocks of the persistent kernel (0: not available)
     GridBarrier* barrier = nullptr;
     int* persist_err = nullptr;     // set when a grid-barrier wait timed out
+    unsigned int bar_extra = 0;     // test hook: arrivals the grid barrier expects beyond the grid
+    unsigned int bar_polls = BARRIER_POLLS;  // polls before a grid-barrier wait gives up
+    bool broken = false;            // a persistent step stopped early: the state must be reloaded
+    std::vector<uint8_t> reloaded;  // instances set since the batch broke
     std::string err;
 };
 
@@ -1847,6 +1875,7 @@ int batch_persistent(maclab_batch_t b, int64_t n)
 {
     const BatchInst<T>* insts = (const BatchInst<T>*)b->insts;
     const int grid = std::min(b->total_tiles, b->persist_grid);
+    const unsigned int nbar = (unsigned int)grid + b->bar_extra;
     while (n > 0) {
         int k = (int)std::min<int64_t>(n, 4096);
         int par = b->cur;
@@ -1856,7 +1885,7 @@ int batch_persistent(maclab_batch_t b, int64_t n)
         void* args[] = {(void*)&insts, (void*)&b->tile_inst, (void*)&b->total_tiles, (void*)&b->active,
                         (void*)&par, (void*)&k, (void*)&dstart, (void*)&b->dirs, (void*)&b->general,
                         (void*)&b->n_general, (void*)&b->dir_owner, (void*)&nsep, (void*)&b->barrier,
-                        (void*)&gen0, (void*)&b->persist_err};
+                        (void*)&gen0, (void*)&b->persist_err, (void*)&nbar, (void*)&b->bar_polls};
         cudaError_t e = cudaMemsetAsync(b->barrier, 0, sizeof(GridBarrier), b->stream);
         if (e == cudaSuccess)
             e = cudaLaunchCooperativeKernel((const void*)step_batch_persistent_kernel<T>, dim3(grid),
@@ -1874,13 +1903,27 @@ int batch_persistent(maclab_batch_t b, int64_t n)
 // MACLAB_E_CUDA once a grid-barrier wait of the persistent kernel has timed out.
 int check_persist_err(maclab_batch_t b)
 {
-    if (!b->persist_err) return MACLAB_OK;
+    if (!b->persist_err || b->broken) return MACLAB_OK;  // a known failure is reported by batch_usable
     int flag = 0;
     cudaError_t e = cudaMemcpyAsync(&flag, b->persist_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(b, MACLAB_E_CUDA, std::string("persistent error flag: ") + cudaGetErrorString(e));
-    if (flag) return bfail(b, MACLAB_E_CUDA, "a grid-barrier wait of the persistent batch kernel timed out");
+    if (flag) {
+        // the blocks left at different steps: the device state matches no
+        // step count, so the batch refuses further use until every
+        // instance is reloaded
+        b->broken = true;
+        b->reloaded.assign(b->count, 0);
+        return bfail(b, MACLAB_E_CUDA, "a grid-barrier wait of the persistent batch kernel timed out");
+    }
     return MACLAB_OK;
+}
+
+int batch_usable(maclab_batch_t b)
+{
+    if (!b->broken) return MACLAB_OK;
+    return bfail(b, MACLAB_E_STATE,
+                 "a persistent step stopped early; reload every instance (maclab_batch_set_state) to continue");
 }
 
 template <typename T>
@@ -2168,6 +2211,7 @@ int maclab_batch_create(int count, const maclab_grid* grids, const maclab_params
 int maclab_batch_step(maclab_batch_t b, int64_t n)
 {
     if (!b) return bfail(nullptr, MACLAB_E_ARG, "NULL batch");
+    if (int rc = batch_usable(b)) return rc;
     if (n < 0) return bfail(b, MACLAB_E_ARG, "n must be >= 0");
     if (use_persistent(b)) return b->prec == MACLAB_F32 ? batch_persistent<float>(b, n) : batch_persistent<double>(b, n);
     while (b->graph_steps > 0 && n >= b->graph_steps) {
@@ -2214,6 +2258,7 @@ int maclab_batch_residual(maclab_batch_t b, double* out)
     if (!b->have_prev) return bfail(b, MACLAB_E_STATE, "no step taken since create / set_state");
     const int prc = check_persist_err(b);
     if (prc != MACLAB_OK) return prc;
+    if (int rc = batch_usable(b)) return rc;
     return b->prec == MACLAB_F32 ? batch_residual_t<float>(b, out) : batch_residual_t<double>(b, out);
 }
 
@@ -2279,6 +2324,7 @@ int maclab_batch_get_state(maclab_batch_t b, int i, double* h, double* u, double
     if (!b || i < 0 || i >= b->count) return bfail(b, MACLAB_E_ARG, "bad instance");
     const int prc = check_persist_err(b);
     if (prc != MACLAB_OK) return prc;
+    if (int rc = batch_usable(b)) return rc;
     const size_t N = (size_t)b->nx[i] * b->ny[i];
     const int c = b->cur;
     const size_t o = b->off[i];
@@ -2341,7 +2387,28 @@ int maclab_batch_set_state(maclab_batch_t b, int i, const double* h, const doubl
     if (rc == MACLAB_OK && (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
         return bfail(b, MACLAB_E_CUDA, std::string("batch set_state: ") + cudaGetErrorString(e));
     b->have_prev = false;
+    if (rc == MACLAB_OK && b->broken) {
+        // usable again once every instance holds a state set by the caller
+        b->reloaded[i] = 1;
+        bool all = true;
+        for (uint8_t r : b->reloaded) all = all && r;
+        if (all) {
+            if ((e = cudaMemsetAsync(b->persist_err, 0, sizeof(int), b->stream)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
+                return bfail(b, MACLAB_E_CUDA, std::string("batch set_state: ") + cudaGetErrorString(e));
+            b->broken = false;
+        }
+    }
     return rc;
+}
+
+int maclab_batch_set_barrier_test(maclab_batch_t b, int extra, unsigned int polls)
+{
+    if (!b) return bfail(nullptr, MACLAB_E_ARG, "NULL batch");
+    if (extra < 0 || polls < 1) return bfail(b, MACLAB_E_ARG, "extra must be >= 0 and polls >= 1");
+    b->bar_extra = (unsigned int)extra;
+    b->bar_polls = polls;
+    return MACLAB_OK;
 }
 
 int maclab_batch_info(maclab_batch_t b, int* count, int64_t* nodes, int64_t* tiles, int64_t* steps)

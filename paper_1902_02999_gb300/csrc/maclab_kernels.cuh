@@ -1697,7 +1697,8 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p)
 
 // true when every block has arrived; `gen` is this block's count of the
 // barriers passed so far (it advances by one)
-__device__ __forceinline__ bool grid_barrier(GridBarrier* gb, unsigned int nblocks, unsigned int& gen, int* err)
+__device__ __forceinline__ bool grid_barrier(GridBarrier* gb, unsigned int nblocks, unsigned int& gen, int* err,
+                                             unsigned int polls)
 {
     __shared__ int gb_ok;
     __syncthreads();
@@ -1712,7 +1713,7 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier* gb, unsigned int nbloc
         } else {
             unsigned int k = 0;
             while (ld_acquire_gpu(&gb->gen) == g) {
-                if (++k >= BARRIER_POLLS) {
+                if (++k >= polls) {
                     atomicOr(err, 1);
                     ok = 0;
                     break;
@@ -1734,7 +1735,8 @@ step_batch_persistent_kernel(const BatchInst<T>* __restrict__ insts, const int* 
                              const uint8_t* __restrict__ active, int parity, int nsteps,
                              const int* __restrict__ dir_start, const DirNode* __restrict__ dirs,
                              const int2* __restrict__ general, int n_general, const int* __restrict__ dir_owner,
-                             int n_dir_sep, GridBarrier* gb, unsigned int gen, int* err)
+                             int n_dir_sep, GridBarrier* gb, unsigned int gen, int* err, unsigned int nbar,
+                             unsigned int polls)
 {
     extern __shared__ __align__(16) unsigned char smem_persist[];
     tile::Derived<T>& sm = *reinterpret_cast<tile::Derived<T>*>(smem_persist);
@@ -1757,7 +1759,7 @@ step_batch_persistent_kernel(const BatchInst<T>* __restrict__ insts, const int* 
             const Fields<T>& f = insts[e.x].f[parity];
             general_node(f, e.y % f.nx, e.y / f.nx);
         }
-        if (!grid_barrier(gb, G, gen, err)) return;
+        if (!grid_barrier(gb, nbar, gen, err, polls)) return;
         if (n_dir_sep > 0) {
             for (int k = gtid; k < n_dir_sep; k += gthreads) {
                 const int i = dir_owner[k];
@@ -1766,7 +1768,7 @@ step_batch_persistent_kernel(const BatchInst<T>* __restrict__ insts, const int* 
                 const Fields<T>& f = in.f[parity];
                 dirichlet_node(f.eta1, f.u1, f.v1, f.D, in.D64, dirs[k], in.bv);
             }
-            if (!grid_barrier(gb, G, gen, err)) return;
+            if (!grid_barrier(gb, nbar, gen, err, polls)) return;
         }
     }
 }

@@ -25,11 +25,20 @@ def pitched(view, pitch, dtype):
     return out
 
 
+# one reduction block (131 x 70); many blocks (2048 x 1500); exactly the
+# node limit, the most blocks the scratch holds (8192 x 2048, the benchmark
+# channel)
+GRIDS = {"one_block": lambda: inputs.random_case(131, 70, 3),
+         "many_blocks": lambda: inputs.bump_channel(2048, 1500, seed=1),
+         "at_limit": lambda: inputs.bump_channel(8192, 2048, seed=0)}
+
+
+@pytest.mark.parametrize("grid", sorted(GRIDS))
 @pytest.mark.parametrize("precision", ["f32", "f64"])
-def test_noalloc_residual_matches_handle_residual(precision):
+def test_noalloc_residual_matches_handle_residual(precision, grid):
     from paper_1902_02999_gb300 import Simulation, _abi
     lib = _abi.load()
-    case = inputs.random_case(131, 70, 3)
+    case = GRIDS[grid]()
     sim = Simulation.from_case(case, precision=precision)
     nx, ny, pitch = case.nx, case.ny, sim.info["pitch"]
     dt = torch.float32 if precision == "f32" else torch.float64
