@@ -253,13 +253,16 @@ def bump_channel(nx: int = 8192, ny: int = 2048, seed: int = 0) -> Case:
 
 def random_case(nx: int, ny: int, seed: int, edges=(BOUNCEBACK, BOUNCEBACK, SPECULAR, SPECULAR),
                 solids: bool = True, dirichlet: bool = True, forcing: bool = True,
-                amp: float = 0.15) -> Case:
+                amp: float = 0.15, dirichlet_sn: bool = False) -> Case:
     """Small random problem for parity tests: smooth random bed, random
     solid blocks (with no-slip borders), Dirichlet columns on non-periodic
     W/E edges (DIR_H west, DIR_Q east, DIR_HU on the first and last rows of
     the west column when ny > 6), random smooth initial state, random wind,
-    friction and Coriolis.  Speeds stay well inside the stability condition
-    of Section 3 (R_le = U dx / nu < 1)."""
+    friction and Coriolis.  With dirichlet_sn, Dirichlet rows on
+    non-periodic S/N edges too (DIR_Q south, DIR_H north, columns 2 ..
+    nx - 3, so that no corner's inward node is a Dirichlet node).  Speeds
+    stay well inside the stability condition of Section 3
+    (R_le = U dx / nu < 1)."""
     rng = Rng(seed)
     dx = 1.0
     nu = rng.scalar(3.0, 4.5)            # e = 6 nu / dx in [18, 27] m/s
@@ -304,6 +307,12 @@ def random_case(nx: int, ny: int, seed: int, edges=(BOUNCEBACK, BOUNCEBACK, SPEC
         bc[W, 2] = (0.0, 0.01, 2 * math.pi / 50.0, 1.0)
         bc[E, 1] = (0.08, 0.0, 0.0, 0.0)
         bc[E, 2] = (0.005, 0.0, 0.0, 0.0)
+    if dirichlet_sn and edges[S] != PERIODIC and ny >= 8 and nx >= 8:
+        mask[0, 2:nx - 2] = DIR_Q
+        mask[-1, 2:nx - 2] = DIR_H
+        bc[S, 1] = (0.1, 0.01, 2 * math.pi / 45.0, 0.2)
+        bc[S, 2] = (0.0, 0.005, 2 * math.pi / 35.0, 0.0)
+        bc[N, 0] = (href + 0.005, 0.005, 2 * math.pi / 60.0, 0.7)
     h0 = (href - zb) + smooth_field(0.05)
     u0 = 0.1 + smooth_field(amp)
     v0 = smooth_field(amp)
