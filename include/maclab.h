@@ -213,6 +213,23 @@ int maclab_set_state(maclab_t sim, const double* h, const double* u, const doubl
  * MACLAB_E_UNSTABLE (with out filled) if out[3] > 0.  Synchronises. */
 int maclab_residual(maclab_t sim, double out[4]);
 
+/* Mark the current state (a device copy, allocated on the first call: three
+ * arrays of the state size) for maclab_residual_since_mark.  Asynchronous
+ * on the handle's stream.  maclab_set_state drops the mark. */
+int maclab_mark(maclab_t sim);
+
+/* The steady-state residual over the m >= 1 steps since the mark (the
+ * stopping test "until a solution is reached" of procedure step (e), read
+ * as a change per step over an interval):
+ *   out[0] = ||q - q_mark||_2 / (m ||q||_2),  q = (h, hu, hv) over
+ *            non-solid nodes, reduced in double precision;
+ *   out[1..3] as maclab_residual.
+ * A state that only alternates by rounding (an FP32 limit cycle) has zero
+ * change over an even interval; a steady decay gives the mean change per
+ * step.  MACLAB_E_STATE without a mark or a step since it;
+ * MACLAB_E_UNSTABLE as maclab_residual.  Synchronises. */
+int maclab_residual_since_mark(maclab_t sim, double out[4]);
+
 /* Residual of maclab_residual, computed without allocating anything.
  *
  * No counterpart in the paper: this exists for callers that cannot call
@@ -254,10 +271,11 @@ int maclab_residual_noalloc(int precision, int nx, int ny, int pitch, const void
                             const void* u_cur, const void* v_cur, const void* D,
                             const uint8_t* type, double sum_D, void* stream, double out[4]);
 
-/* Step until the residual of a step is <= tol, checking every check_every
- * steps, for at most max_steps steps.  Reports the steps taken and the last
- * residual.  Returns MACLAB_OK when converged, MACLAB_E_STATE when
- * max_steps ran out, MACLAB_E_UNSTABLE on a non-finite state. */
+/* Step until the steady-state residual over a check interval is <= tol:
+ * mark, take check_every steps, compare (maclab_residual_since_mark), for at
+ * most max_steps steps.  Reports the steps taken and the last residual.
+ * Returns MACLAB_OK when converged, MACLAB_E_STATE when max_steps ran out,
+ * MACLAB_E_UNSTABLE on a non-finite state. */
 int maclab_run_to_steady(maclab_t sim, double tol, int64_t max_steps, int check_every,
                          int64_t* steps_done, double* r_final);
 
@@ -413,11 +431,18 @@ int maclab_batch_set_barrier_test(maclab_batch_t batch, int extra, unsigned int 
  * maclab_residual for instance i.  Synchronises. */
 int maclab_batch_residual(maclab_batch_t batch, double* out);
 
+/* maclab_mark and maclab_residual_since_mark for every instance of the
+ * batch at once (out [4 * count]); the mark copies the whole packed state
+ * (allocated on the first call) and maclab_batch_set_state drops it. */
+int maclab_batch_mark(maclab_batch_t batch);
+int maclab_batch_residual_since_mark(maclab_batch_t batch, double* out);
+
 /* Instances with flags[i] == 0 stop advancing (their state stays as it is);
  * flags [count]. */
 int maclab_batch_set_active(maclab_batch_t batch, const uint8_t* flags);
 
-/* Step the batch until every active instance has a step residual <= tol,
+/* Step the batch until every active instance has a steady-state residual
+ * over the check interval (maclab_batch_residual_since_mark) <= tol,
  * checking every check_every steps and switching converged instances off.
  * steps[i] (may be NULL) receives the batch step count at which instance i
  * converged (-1 if it did not), r_final[i] its last residual, seconds[i]

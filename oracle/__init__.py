@@ -75,7 +75,7 @@ def _load():
             lib.oracle_force.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double, d]
             lib.oracle_step.argtypes = [pp, d, u8, d, d, d, d, d, d, ctypes.c_double]
             lib.oracle_run.argtypes = [pp, d, u8, d, d, d, ctypes.c_int64, ctypes.c_int64]
-            lib.oracle_residual.argtypes = [pp, u8, d, d, d, d, d, d, d]
+            lib.oracle_residual.argtypes = [pp, u8, d, d, d, d, d, d, ctypes.c_int, d]
             lib.oracle_step_push.argtypes = [pp, d, d, d, d, d, d, d]
             lib.oracle_step_newlevel.argtypes = [pp, d, u8, d, d, d, d, d, d, ctypes.c_double]
             lib.oracle_elab_step.argtypes = [pp, d, u8, ctypes.c_double, d, d]
@@ -154,15 +154,17 @@ def run(case, nsteps: int, state=None, n0: int = 0):
     return h, u, v
 
 
-def residual(case, s0, s1):
-    """(r, mass, max|u|) of state s1 against the previous state s0."""
+def residual(case, s0, s1, interval: int = 1):
+    """(r, mass, max|u|) of state s1 against state s0 taken ``interval``
+    steps earlier: r = ||q1 - q0|| / (interval ||q1||) with q = (h, hu, hv)
+    over non-solid nodes (the steady-state residual, reading R7)."""
     lib = _load()
     a = [_arr(x, case) for x in (*s0, *s1)]
     out = np.zeros(3)
     mask = np.ascontiguousarray(case.mask, dtype=np.uint8)
     lib.oracle_residual(ctypes.byref(_problem(case)),
                         mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
-                        *[_dp(x) for x in a], _dp(out))
+                        *[_dp(x) for x in a], int(interval), _dp(out))
     return float(out[0]), float(out[1]), float(out[2])
 
 

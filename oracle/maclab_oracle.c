@@ -295,7 +295,7 @@ int oracle_run(const oracle_problem* p, const double* zb, const uint8_t* type,
  *   out[1] = sum h1,   out[2] = max |u1|. */
 void oracle_residual(const oracle_problem* p, const uint8_t* type,
                      const double* h0, const double* u0, const double* v0,
-                     const double* h1, const double* u1, const double* v1, double out[3])
+                     const double* h1, const double* u1, const double* v1, int interval, double out[3])
 {
     size_t N = (size_t)p->nx * p->ny, x;
     double num = 0.0, den = 0.0, mass = 0.0, umax = 0.0;
@@ -311,7 +311,9 @@ void oracle_residual(const oracle_problem* p, const uint8_t* type,
         sp = sqrt(u1[x] * u1[x] + v1[x] * v1[x]);
         if (sp > umax) umax = sp;
     }
-    out[0] = den > 0.0 ? sqrt(num) / sqrt(den) : 0.0;
+    /* R7: the change over an interval of `interval` steps (state 0 is the
+     * state `interval` steps before state 1), per step */
+    out[0] = den > 0.0 ? sqrt(num) / sqrt(den) / (double)interval : 0.0;
     out[1] = mass;
     out[2] = umax;
 }

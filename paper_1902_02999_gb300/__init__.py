@@ -206,8 +206,20 @@ class Simulation:
         self._check(self._lib.maclab_residual(self._h, _dptr(out)))
         return float(out[0]), float(out[1]), float(out[2])
 
+    def mark(self) -> None:
+        """Keep a copy of the current state for residual_since_mark."""
+        self._check(self._lib.maclab_mark(self._h))
+
+    def residual_since_mark(self):
+        """(r, mass, max|u|): r = ||q - q_mark|| / (m ||q||) over the m steps
+        since the mark, q = (h, hu, hv)."""
+        out = np.zeros(4)
+        self._check(self._lib.maclab_residual_since_mark(self._h, _dptr(out)))
+        return float(out[0]), float(out[1]), float(out[2])
+
     def run_to_steady(self, tol: float = 1e-8, max_steps: int = 10 ** 7, check_every: int = 100):
-        """Returns (converged, steps_done, last_residual)."""
+        """Steps until the residual over each check interval is <= tol.
+        Returns (converged, steps_done, last_residual)."""
         done, r = ctypes.c_int64(), ctypes.c_double()
         rc = self._lib.maclab_run_to_steady(self._h, float(tol), int(max_steps), int(check_every),
                                            ctypes.byref(done), ctypes.byref(r))
@@ -405,6 +417,17 @@ class Batch:
         """Failure-detection test hook of the persistent grid barrier: expect
         `extra` arrivals beyond the grid and give up after `polls` polls."""
         self._check(self._lib.maclab_batch_set_barrier_test(self._h, int(extra), int(polls)))
+
+    def mark(self) -> None:
+        """Keep a copy of every instance's state for residual_since_mark."""
+        self._check(self._lib.maclab_batch_mark(self._h))
+
+    def residual_since_mark(self) -> np.ndarray:
+        """[count, 4]: residual over the steps since the mark (per step),
+        mass, max|u|, non-finite count per instance."""
+        out = np.zeros(4 * self.count)
+        self._check(self._lib.maclab_batch_residual_since_mark(self._h, _dptr(out)))
+        return out.reshape(self.count, 4)
 
     def residual(self) -> np.ndarray:
         """[count, 4]: residual, mass, max|u|, non-finite count per instance."""

@@ -68,6 +68,8 @@ PROTOTYPES = [
     ("maclab_get_state", c_int, [c_void_p, P(c_double), P(c_double), P(c_double)]),
     ("maclab_set_state", c_int, [c_void_p, P(c_double), P(c_double), P(c_double)]),
     ("maclab_residual", c_int, [c_void_p, P(c_double)]),
+    ("maclab_mark", c_int, [c_void_p]),
+    ("maclab_residual_since_mark", c_int, [c_void_p, P(c_double)]),
     ("maclab_residual_noalloc", c_int, [c_int, c_int, c_int, c_int] + [c_void_p] * 7 +
      [P(ctypes.c_uint8), c_double, c_void_p, P(c_double)]),
     ("maclab_run_to_steady", c_int, [c_void_p, c_double, c_int64, c_int, P(c_int64),
@@ -93,6 +95,8 @@ PROTOTYPES = [
     ("maclab_batch_set_persistent", c_int, [c_void_p, c_int]),
     ("maclab_batch_set_barrier_test", c_int, [c_void_p, c_int, ctypes.c_uint]),
     ("maclab_batch_residual", c_int, [c_void_p, P(c_double)]),
+    ("maclab_batch_mark", c_int, [c_void_p]),
+    ("maclab_batch_residual_since_mark", c_int, [c_void_p, P(c_double)]),
     ("maclab_batch_set_active", c_int, [c_void_p, P(ctypes.c_uint8)]),
     ("maclab_batch_run_to_steady", c_int, [c_void_p, c_double, c_int64, c_int, P(c_int64),
                                            P(c_double), P(c_double)]),

@@ -102,6 +102,8 @@ struct maclab_s {
     int n_all = 0;
     bool elab = false;
     void* gdist[2] = {nullptr, nullptr};  // 9 planes of [ny][pitch] per buffer
+    void* snap[3] = {nullptr, nullptr, nullptr};  // marked state (eta, u, v), allocated on first mark
+    int64_t mark_n = -1;       // step count of the marked state (-1: none)
     std::vector<cudaEvent_t> events;  // pairs around step-kernel launches
     size_t events_used = 0;
     std::string err;
@@ -438,12 +440,17 @@ int advance(maclab_t s, int64_t n)
     return MACLAB_OK;
 }
 
+// The residual reduction of the current state against the previous step's
+// state, or (since_mark) against the marked state.
 template <typename T>
-int launch_residual(maclab_t s)
+int launch_residual(maclab_t s, bool since_mark = false)
 {
     const int a = s->cur, b = 1 - s->cur;
+    const void* pe = since_mark ? s->snap[0] : s->eta[b];
+    const void* pu = since_mark ? s->snap[1] : s->u[b];
+    const void* pv = since_mark ? s->snap[2] : s->v[b];
     residual_partial_kernel<T><<<s->red_blocks, RED_THREADS, 0, s->stream>>>(
-        (const T*)s->eta[b], (const T*)s->u[b], (const T*)s->v[b], (const T*)s->eta[a],
+        (const T*)pe, (const T*)pu, (const T*)pv, (const T*)s->eta[a],
         (const T*)s->u[a], (const T*)s->v[a], (const T*)s->D, s->type, s->grid.nx, s->grid.ny,
         s->pitch, s->partial);
     residual_final_kernel<<<1, 32 * RED_NVAL, 0, s->stream>>>(s->partial, s->red_blocks, s->red_out);
@@ -549,6 +556,7 @@ int upload_state(maclab_t s, const double* h, const double* u, const double* v)
     // the host arrays must stay valid until the copies have read them
     if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return cuda_fail(s, e, "state upload");
     s->have_prev = false;
+    s->mark_n = -1;  // the marked state belongs to the replaced history
     return MACLAB_OK;
 }
 
@@ -1304,24 +1312,61 @@ int maclab_set_state(maclab_t s, const double* h, const double* u, const double*
     return elab_restart(s);
 }
 
-int maclab_residual(maclab_t s, double out[4])
+}  // extern "C"
+
+namespace {
+// out[0] = ||q - q_prev|| / (interval ||q||) and the mass, speed and
+// non-finite count, for the previous step's state or the marked one
+int residual_common(maclab_t s, double out[4], bool since_mark)
 {
-    if (!s || !out) return fail(s, MACLAB_E_ARG, "NULL argument");
-    if (!s->have_prev) return fail(s, MACLAB_E_STATE, "no step taken since create / set_state");
     int rc = check_tma_err(s);
     if (rc != MACLAB_OK) return rc;
-    rc = s->prec == MACLAB_F32 ? launch_residual<float>(s) : launch_residual<double>(s);
+    rc = s->prec == MACLAB_F32 ? launch_residual<float>(s, since_mark) : launch_residual<double>(s, since_mark);
     if (rc != MACLAB_OK) return rc;
     double r[RED_NVAL];
     cudaError_t e = cudaMemcpyAsync(r, s->red_out, sizeof(r), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e, "residual");
-    out[0] = r[1] > 0 ? std::sqrt(r[0]) / std::sqrt(r[1]) : 0.0;
+    const double interval = since_mark ? (double)(s->n - s->mark_n) : 1.0;
+    out[0] = r[1] > 0 ? std::sqrt(r[0]) / std::sqrt(r[1]) / interval : 0.0;
     out[1] = s->sumD + r[2];
     out[2] = std::sqrt(r[3]);
     out[3] = r[4];
     if (r[4] > 0 || !std::isfinite(out[0])) return fail(s, MACLAB_E_UNSTABLE, "non-finite values in the state");
     return MACLAB_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int maclab_residual(maclab_t s, double out[4])
+{
+    if (!s || !out) return fail(s, MACLAB_E_ARG, "NULL argument");
+    if (!s->have_prev) return fail(s, MACLAB_E_STATE, "no step taken since create / set_state");
+    return residual_common(s, out, false);
+}
+
+int maclab_mark(maclab_t s)
+{
+    if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
+    const size_t bytes = (size_t)s->pitch * s->grid.ny * s->esize;
+    for (int k = 0; k < 3; ++k)
+        if (!s->snap[k] && !(s->snap[k] = dev_alloc(s, bytes))) return fail(s, MACLAB_E_NOMEM, "mark: device memory");
+    const void* src[3] = {s->eta[s->cur], s->u[s->cur], s->v[s->cur]};
+    for (int k = 0; k < 3; ++k) {
+        cudaError_t e = cudaMemcpyAsync(s->snap[k], src[k], bytes, cudaMemcpyDeviceToDevice, s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "mark");
+    }
+    s->mark_n = s->n;
+    return MACLAB_OK;
+}
+
+int maclab_residual_since_mark(maclab_t s, double out[4])
+{
+    if (!s || !out) return fail(s, MACLAB_E_ARG, "NULL argument");
+    if (s->mark_n < 0 || s->n <= s->mark_n)
+        return fail(s, MACLAB_E_STATE, "no marked state, or no step since the mark");
+    return residual_common(s, out, true);
 }
 
 }  // extern "C"
@@ -1449,10 +1494,11 @@ int maclab_run_to_steady(maclab_t s, double tol, int64_t max_steps, int check_ev
     int rc = MACLAB_E_STATE;
     while (done < max_steps) {
         const int64_t k = std::min<int64_t>(check_every, max_steps - done);
+        if ((rc = maclab_mark(s)) != MACLAB_OK) break;
         if ((rc = maclab_step(s, k)) != MACLAB_OK) break;
         done += k;
         double out[4];
-        rc = maclab_residual(s, out);
+        rc = maclab_residual_since_mark(s, out);
         r = out[0];
         if (rc != MACLAB_OK) break;
         if (r <= tol) break;
@@ -1767,6 +1813,8 @@ struct maclab_batch_s {
     unsigned int bar_polls = BARRIER_POLLS;  // polls before a grid-barrier wait gives up
     bool broken = false;            // a persistent step stopped early: the state must be reloaded
     std::vector<uint8_t> reloaded;  // instances set since the batch broke
+    void* snap[3] = {nullptr, nullptr, nullptr};  // marked state, packed like eta / u / v
+    int64_t mark_n = -1;            // step count of the marked state (-1: none)
     std::string err;
 };
 
@@ -1983,13 +2031,16 @@ int batch_capture(maclab_batch_t b)
 }
 
 template <typename T>
-int batch_residual_t(maclab_batch_t b, double* out)
+int batch_residual_t(maclab_batch_t b, double* out, bool since_mark = false)
 {
     // the state before the last step sits in buffer 1 - cur: parity 1 - cur
     const int par = 1 - b->cur;
     const BatchInst<T>* insts = (const BatchInst<T>*)b->insts;
-    batch_residual_tile_kernel<T><<<b->total_tiles, RED_THREADS, 0, b->stream>>>(insts, b->tile_inst, par,
-                                                                                 b->partial);
+    const int c = b->cur;
+    const T* se = since_mark ? (const T*)b->snap[0] : nullptr;
+    batch_residual_tile_kernel<T><<<b->total_tiles, RED_THREADS, 0, b->stream>>>(
+        insts, b->tile_inst, par, b->partial, se, (const T*)b->snap[1], (const T*)b->snap[2],
+        (const T*)b->eta[c], (const T*)b->u[c], (const T*)b->v[c]);
     batch_residual_final_kernel<T><<<(b->count + 7) / 8, 256, 0, b->stream>>>(insts, b->count, b->partial,
                                                                              b->red_out);
     cudaError_t e = cudaGetLastError();
@@ -1999,9 +2050,10 @@ int batch_residual_t(maclab_batch_t b, double* out)
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(b, MACLAB_E_CUDA, std::string("batch residual: ") + cudaGetErrorString(e));
     int rc = MACLAB_OK;
+    const double interval = since_mark ? (double)(b->n - b->mark_n) : 1.0;
     for (int i = 0; i < b->count; ++i) {
         const double* q = &r[(size_t)i * RED_NVAL];
-        out[4 * i + 0] = q[1] > 0 ? std::sqrt(q[0]) / std::sqrt(q[1]) : 0.0;
+        out[4 * i + 0] = q[1] > 0 ? std::sqrt(q[0]) / std::sqrt(q[1]) / interval : 0.0;
         out[4 * i + 1] = b->sumD[i] + q[2];
         out[4 * i + 2] = std::sqrt(q[3]);
         out[4 * i + 3] = q[4];
@@ -2262,6 +2314,32 @@ int maclab_batch_residual(maclab_batch_t b, double* out)
     return b->prec == MACLAB_F32 ? batch_residual_t<float>(b, out) : batch_residual_t<double>(b, out);
 }
 
+int maclab_batch_mark(maclab_batch_t b)
+{
+    if (!b) return bfail(nullptr, MACLAB_E_ARG, "NULL batch");
+    if (int rc = batch_usable(b)) return rc;
+    const size_t bytes = b->total_np * b->esize;
+    for (int k = 0; k < 3; ++k)
+        if (!b->snap[k] && !(b->snap[k] = bdev_alloc(b, bytes))) return bfail(b, MACLAB_E_NOMEM, "mark: device memory");
+    const void* src[3] = {b->eta[b->cur], b->u[b->cur], b->v[b->cur]};
+    for (int k = 0; k < 3; ++k) {
+        cudaError_t e = cudaMemcpyAsync(b->snap[k], src[k], bytes, cudaMemcpyDeviceToDevice, b->stream);
+        if (e != cudaSuccess) return bfail(b, MACLAB_E_CUDA, std::string("mark: ") + cudaGetErrorString(e));
+    }
+    b->mark_n = b->n;
+    return MACLAB_OK;
+}
+
+int maclab_batch_residual_since_mark(maclab_batch_t b, double* out)
+{
+    if (!b || !out) return bfail(b, MACLAB_E_ARG, "NULL argument");
+    if (b->mark_n < 0 || b->n <= b->mark_n) return bfail(b, MACLAB_E_STATE, "no marked state, or no step since it");
+    const int prc = check_persist_err(b);
+    if (prc != MACLAB_OK) return prc;
+    if (int rc = batch_usable(b)) return rc;
+    return b->prec == MACLAB_F32 ? batch_residual_t<float>(b, out, true) : batch_residual_t<double>(b, out, true);
+}
+
 int maclab_batch_set_active(maclab_batch_t b, const uint8_t* flags)
 {
     if (!b || !flags) return bfail(b, MACLAB_E_ARG, "NULL argument");
@@ -2294,9 +2372,10 @@ int maclab_batch_run_to_steady(maclab_batch_t b, double tol, int64_t max_steps, 
     for (uint8_t a : act) remaining += a ? 1 : 0;
     while (remaining > 0 && total < max_steps) {
         const int64_t k = std::min<int64_t>(check_every, max_steps - total);
+        if ((rc = maclab_batch_mark(b)) != MACLAB_OK) break;
         if ((rc = maclab_batch_step(b, k)) != MACLAB_OK) break;
         total += k;
-        rc = maclab_batch_residual(b, r.data());
+        rc = maclab_batch_residual_since_mark(b, r.data());
         if (rc != MACLAB_OK) break;
         const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         bool changed = false;
@@ -2387,6 +2466,7 @@ int maclab_batch_set_state(maclab_batch_t b, int i, const double* h, const doubl
     if (rc == MACLAB_OK && (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
         return bfail(b, MACLAB_E_CUDA, std::string("batch set_state: ") + cudaGetErrorString(e));
     b->have_prev = false;
+    b->mark_n = -1;  // the mark belongs to the replaced history
     if (rc == MACLAB_OK && b->broken) {
         // usable again once every instance holds a state set by the caller
         b->reloaded[i] = 1;

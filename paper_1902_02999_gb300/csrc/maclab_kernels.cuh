@@ -1855,11 +1855,17 @@ __global__ void residual_final_kernel(const double* __restrict__ partial, int nb
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS)
 batch_residual_tile_kernel(const BatchInst<T>* __restrict__ insts, const int* __restrict__ tile_inst,
-                           int parity, double* __restrict__ partial)
+                           int parity, double* __restrict__ partial, const T* se, const T* su, const T* sv,
+                           const T* ce, const T* cu, const T* cv)
 {
     const int i = tile_inst[blockIdx.x];
     const BatchInst<T>& in = insts[i];
     const Fields<T>& f = in.f[parity];  // eta = previous state, eta1 = current state
+    // with a marked state (se != nullptr): the previous state is the mark,
+    // laid out like the current buffer (ce, cu, cv: its bases)
+    const T* pe = se ? se + (f.eta1 - ce) : f.eta;
+    const T* pu = se ? su + (f.u1 - cu) : f.u;
+    const T* pv = se ? sv + (f.v1 - cv) : f.v;
     const int t = blockIdx.x - in.tile0;
     const int x0 = (t % in.tiles_x) * tile::TX, y0 = (t / in.tiles_x) * tile::TY;
     double s[RED_NVAL] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -1869,9 +1875,9 @@ batch_residual_tile_kernel(const BatchInst<T>* __restrict__ insts, const int* __
         const size_t p = (size_t)y * f.pitch + x;
         if ((f.type[p] & KIND_MASK) == K_SOLID) continue;
         const double d = (double)f.D[p];
-        const double a0 = (double)f.eta[p], a1 = (double)f.eta1[p];
+        const double a0 = (double)pe[p], a1 = (double)f.eta1[p];
         const double h0 = d + a0, h1 = d + a1;
-        const double qx0 = h0 * (double)f.u[p], qy0 = h0 * (double)f.v[p];
+        const double qx0 = h0 * (double)pu[p], qy0 = h0 * (double)pv[p];
         const double qx1 = h1 * (double)f.u1[p], qy1 = h1 * (double)f.v1[p];
         const double dh = a1 - a0, dqx = qx1 - qx0, dqy = qy1 - qy0;
         s[0] += dh * dh + dqx * dqx + dqy * dqy;

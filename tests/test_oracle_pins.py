@@ -294,3 +294,34 @@ def test_solid_nodes_untouched_and_residual():
     assert abs(r - np.linalg.norm(dq) / np.linalg.norm(q)) < 1e-14
     assert abs(mass - s2[0][fl].sum()) < 1e-12
     assert abs(umax - np.hypot(s2[1], s2[2])[fl].max()) < 1e-15
+
+
+def test_interval_residual():
+    """R7 over an interval of m steps, r_m = ||q^n - q^(n-m)|| / (m ||q^n||):
+    its definition restated; per step (a constant change per step gives the
+    same value for every m); zero for a state that alternates with period
+    two and m = 2 (a rounding flicker is not a change of the solution)."""
+    c = inputs.random_case(20, 16, 41)
+    fl = c.mask != SOLID
+    s0 = oracle.run(c, 3)
+    s7 = oracle.run(c, 7, s0, n0=3)
+    r, mass, umax = oracle.residual(c, s0, s7, interval=7)
+    q = lambda s: np.concatenate([s[0][fl], (s[0] * s[1])[fl], (s[0] * s[2])[fl]])
+    assert abs(r - np.linalg.norm(q(s7) - q(s0)) / (7 * np.linalg.norm(q(s7)))) < 1e-14
+    assert abs(mass - s7[0][fl].sum()) < 1e-12
+    # a constant change per step in (h, hu, hv)
+    rng = np.random.default_rng(3)
+    h0 = 1.0 + 0.1 * rng.random(c.mask.shape)
+    hu0, hv0 = 0.1 * rng.random(c.mask.shape), 0.1 * rng.random(c.mask.shape)
+    dh, dhu, dhv = (1e-6 * rng.standard_normal(c.mask.shape) for _ in range(3))
+
+    def at(n):
+        h = h0 + n * dh
+        return h, (hu0 + n * dhu) / h, (hv0 + n * dhv) / h
+    r1 = oracle.residual(c, at(99), at(100))[0]
+    for m in (2, 5, 40):
+        assert abs(oracle.residual(c, at(100 - m), at(100), interval=m)[0] - r1) <= 1e-9 * r1
+    # period-two flicker
+    a, b = at(0), at(1)
+    assert oracle.residual(c, a, b)[0] > 0
+    assert oracle.residual(c, a, a, interval=2)[0] == 0.0

@@ -400,3 +400,30 @@ def test_channel_slice_1000_steps(precision):
     sim = sim_of(case, precision)
     sim.step(1000)
     compare(case, sim.get_state(), want, precision, "channel-512x128")
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_interval_residual_matches_oracle(precision):
+    """maclab_residual_since_mark over 37 steps (and the batch's) against
+    the oracle's interval residual on the same two states."""
+    from paper_1902_02999_gb300 import Batch
+    case = inputs.random_case(90, 50, 81)
+    sim = sim_of(case, precision)
+    sim.step(30)
+    s30 = sim.get_state()
+    sim.mark()
+    sim.step(37)
+    r, m, umax = sim.residual_since_mark()
+    r_o, m_o, u_o = oracle.residual(case, s30, sim.get_state(), interval=37)
+    tol = 1e-9 if precision == "f64" else 1e-5
+    assert abs(r - r_o) <= tol * r_o and abs(m - m_o) <= 1e-12 * m_o
+    steady = case.copy()
+    steady.bc[:, :, 1] = 0.0
+    b = Batch([steady], precision=precision)
+    b.step(30)
+    b30 = b.get_state(0)
+    b.mark()
+    b.step(37)
+    rb = b.residual_since_mark()[0, 0]
+    rb_o = oracle.residual(steady, b30, b.get_state(0), interval=37)[0]
+    assert abs(rb - rb_o) <= tol * rb_o
