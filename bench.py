@@ -50,9 +50,13 @@ KERNEL_LABEL = {0: "tile 64x16", 1: "warp strip", 2: "TMA-staged tile 64x16, per
 
 
 def kernel_source_hash() -> str:
-    """Hash of the device code the ncu counters describe."""
-    with open(os.path.join(ROOT, "paper_1902_02999_gb300", "csrc", "maclab_kernels.cuh"), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()
+    """Hash of the device code the ncu counters describe (the step kernels'
+    headers, in this order)."""
+    h = hashlib.sha256()
+    for name in ("maclab_kernels.cuh", "maclab_march.cuh"):
+        with open(os.path.join(ROOT, "paper_1902_02999_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def hbm_peak():
@@ -153,50 +157,77 @@ def whole_job_mlups(world, nodes, steps, ms):
     return world * nodes * steps / (ms / 1e3) / 1e6
 
 
-def cpu_baseline(case, max_seconds=30.0):
-    """The oracle as it stands, single-threaded, on one full-grid step (or
-    more while under 10 s)."""
+def host_cores() -> int:
+    """Threads the OpenMP oracle uses: OMP_NUM_THREADS, else every core."""
+    try:
+        return int(os.environ["OMP_NUM_THREADS"])
+    except (KeyError, ValueError):
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as fh:
+            info = fh.read()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model", "CPU part"):
+        for line in info.splitlines():
+            if line.startswith(key):
+                return line.split(":", 1)[1].strip() + ("" if key == "model name" else " (%s)" % key)
+    return "unknown"
+
+
+def cpu_baseline(case, max_seconds=20.0):
+    """The oracle as it stands, built with OpenMP (the rows of a step over
+    every host core, the arithmetic per node unchanged), timed on full-grid
+    steps of the workload for about 10-20 s."""
     import oracle
-    oracle.build()
-    state = (case.h0, case.u0, case.v0)
+    oracle.build_omp()
+    state = oracle.run_threads(case, 1)                 # warm: the build, page faults
     t0 = time.perf_counter()
-    steps = 0
-    while True:
-        state = oracle.run(case, 1, state, n0=steps)
-        steps += 1
-        el = time.perf_counter() - t0
-        if el >= 10.0 or el * (steps + 1) / steps > max_seconds:
-            break
-    return {"value": case.nodes * steps / el / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "%d full-grid step(s) of the %dx%d workload, %.1f s" % (steps, case.nx,
-                                                                               case.ny, el)}
+    state = oracle.run_threads(case, 1, state, n0=1)
+    one = time.perf_counter() - t0
+    steps = max(1, min(50, int(max_seconds / max(one, 1e-3)) - 1))
+    t0 = time.perf_counter()
+    oracle.run_threads(case, steps, state, n0=2)
+    el = time.perf_counter() - t0
+    return {"value": case.nodes * steps / el / 1e6, "unit": "MLUPS", "cores": host_cores(), "kind": "oracle",
+            "cpu": cpu_model(),
+            "sample": "%d full-grid steps of the %dx%d workload (OpenMP over rows), %.1f s" % (
+                steps, case.nx, case.ny, el)}
 
 
 def run_reference(args, workload):
-    """The oracle on the host cores, on bounded samples of the workload."""
+    """The oracle (OpenMP over rows, every host core) on samples of the
+    workload: each step one oracle step of the full 8192 x 2048 channel, or
+    of a horizontal slice of it when K + W full steps would not end within
+    about 150 s."""
     import inputs
     import oracle
-    oracle.build()
-    rate_guess = 2.0e6                       # oracle node updates per second (one core)
-    nodes = int(150.0 * rate_guess / max(1, args.steps + args.warmup))
-    ny = max(8, min(256, nodes // 512))
-    case = inputs.bump_channel(512, ny, seed=0)
-    state = (case.h0, case.u0, case.v0)
-    for k in range(args.warmup):
-        state = oracle.run(case, 1, state, n0=k)
+    oracle.build_omp()
+    probe = inputs.bump_channel(args.nx, 64, seed=0)
+    oracle.run_threads(probe, 1)
     t0 = time.perf_counter()
-    for k in range(args.steps):
-        state = oracle.run(case, 1, state, n0=args.warmup + k)
+    oracle.run_threads(probe, 2)
+    rate = probe.nodes * 2 / (time.perf_counter() - t0)   # node updates per second
+    ny = int(150.0 * rate / max(1, args.steps + args.warmup) / args.nx)
+    ny = max(8, min(args.ny, ny))
+    case = inputs.bump_channel(args.nx, ny, seed=0) if ny < args.ny else inputs.bump_channel(args.nx, args.ny, seed=0)
+    state = oracle.run_threads(case, args.warmup) if args.warmup else None
+    t0 = time.perf_counter()
+    oracle.run_threads(case, args.steps, state, n0=args.warmup)
     el = time.perf_counter() - t0
     value = case.nodes * args.steps / el / 1e6
-    sample = "each step: one oracle step of a 512x%d slice of the workload generator" % ny
+    sample = ("each step: one oracle step of the full %dx%d workload" % (case.nx, case.ny) if ny >= args.ny else
+              "each step: one oracle step of a %dx%d slice of the workload generator" % (case.nx, ny))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": el * 1e3 / max(1, args.steps), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload, "sample_nodes": case.nodes},
-            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "config": {"workload": workload, "sample_nodes": case.nodes, "same_config": ny >= args.ny},
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": host_cores(), "kind": "oracle",
+                             "cpu": cpu_model(), "sample": sample},
             "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -222,7 +253,7 @@ def main():
     ap.add_argument("--f64-steps", type=int, default=300)
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=200)
-    ap.add_argument("--batch-max-steps", type=int, default=50_000)
+    ap.add_argument("--batch-max-steps", type=int, default=200_000)
     ap.add_argument("--ws-train", type=int, default=2048, help="lakes the warm-start network trains on (0: skip)")
     ap.add_argument("--ws-epochs", type=int, default=20)
     ap.add_argument("--ws-test", type=int, default=16, help="unseen lakes timed from rest and from the proposal")
@@ -401,6 +432,76 @@ def main():
                   "mlups": lake.nodes * nsteps / wall / 1e6, "simulated_s": nsteps * lake.dt}
         ls.close()
 
+    # Section 4.1 as the 400 x 3 FP64 strip over two tidal periods, against
+    # the asymptotic solution (horizontal surface at the tide level of
+    # Eq. veri-Ini-Bc.3r, h u = 0 at x = 1500 m): level error (paper: below
+    # 0.005 %) and velocity error at four sample times
+    tidal = None
+    if extra:
+        import numpy as np
+        tc = inputs.tidal_strip(400, 3)
+        ts = Simulation.from_case(tc, precision="f64")
+        xs = np.arange(tc.nx) * tc.dx
+        om = 4 * math.pi / 86400.0
+        samples, n0 = [], 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for T in (10800.0, 32400.0, 54000.0, 75600.0, 86400.0):
+            n = int(round(T / tc.dt))
+            ts.step(n - n0)
+            n0 = n
+            h, u, _ = ts.get_state()
+            t = n * tc.dt
+            eta = 20.0 - 4.0 * math.sin(om * t + math.pi / 2)
+            ua = (xs - inputs.TIDAL_LENGTH) * 4.0 * om * math.cos(om * t + math.pi / 2) / (eta - tc.zb[0])
+            samples.append({"t_s": T, "level_rel_err": float(np.abs(h + tc.zb - eta).max() / eta),
+                            "u_max_abs_err_mps": float(np.abs(u - ua).max())})
+        torch.cuda.synchronize()
+        twall = time.perf_counter() - t0
+        tidal = {"workload": "tidal_strip_400x3_f64 (Section 4.1), two tidal periods (86,400 s)",
+                 "steps": n0, "dt_s": tc.dt, "wall_s": twall, "steps_per_s": n0 / twall,
+                 "paper_level_bound": 5e-5, "paper_times_s": [10800.0, 32400.0], "samples": samples,
+                 "note": "velocity: the scheme carries a start-up seiche the asymptotic solution lacks"}
+        ts.close()
+
+    # the FP32 path's error against the FP64 oracle, per result: (a) the
+    # benchmark's channel family after 1000 steps (a 1024 x 256 channel:
+    # the full grid would take the host hours), (b) the seeded 256 x 256
+    # dish lake's steady state at residual 1e-8 against the oracle's own
+    # steady state (oracle built with OpenMP, on the host cores)
+    f32_error = None
+    if extra and args.precision == "f32" and rank == 0:
+        import numpy as np
+        import oracle
+
+        def errs(case, got, want):
+            live = case.mask != inputs.SOLID
+            sp = max(np.hypot(want[1], want[2])[live].max(), 1e-30)
+            return {"h": float(np.abs(got[0] - want[0])[live].max() / np.abs(want[0][live]).max()),
+                    "u": float(np.abs(got[1] - want[1])[live].max() / sp),
+                    "v": float(np.abs(got[2] - want[2])[live].max() / sp)}
+        cs = inputs.bump_channel(1024, 256, seed=0)
+        g = Simulation.from_case(cs, precision="f32")
+        g.step(1000)
+        f32_error = {"norm": "max-norm over non-solid nodes; h by max|h|, u and v by the largest oracle speed",
+                     "channel_1024x256_1000_steps": errs(cs, g.get_state(), oracle.run_threads(cs, 1000))}
+        g.close()
+        lake = inputs.dish_lake(256, seed=0)
+        g = Simulation.from_case(lake, precision="f32")
+        ok32, n32, r32 = g.run_to_steady(tol=1e-8, max_steps=1_000_000, check_every=1000)
+        s32 = g.get_state()
+        g.close()
+        t0 = time.perf_counter()
+        st, n, r_o = None, 0, float("inf")
+        while r_o > 1e-8 and time.perf_counter() - t0 < 180.0 and n < 1_000_000:
+            prev = st if st is not None else (lake.h0, lake.u0, lake.v0)
+            st = oracle.run_threads(lake, 1000, st, n0=n)
+            n += 1000
+            r_o = oracle.residual(lake, prev, st, interval=1000)[0]
+        f32_error["dish_lake_256_steady_1e-8"] = dict(
+            errs(lake, s32, st), fp32_steps=n32, fp32_residual=r32, oracle_steps=n, oracle_residual=r_o,
+            oracle_converged=bool(r_o <= 1e-8), oracle_wall_s=time.perf_counter() - t0)
+
     # the FP64 variant of the channel step (timed, not the headline)
     f64 = None
     if extra and args.precision == "f32":
@@ -545,7 +646,7 @@ def main():
                            "step_kernel": KERNEL_LABEL[info["step_kernel"]],
                            "autotune_choice": tuned, "temporal_block": info["temporal_block"]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "steady_state": steady, "f64": f64, "batched": batched, "warm_start": warm,
+                "steady_state": steady, "tidal": tidal, "f32_error": f32_error, "f64": f64, "batched": batched, "warm_start": warm,
                 "temporal_block": tblock, "distribution_form": dform,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clocks}
         print(json.dumps(line), flush=True)

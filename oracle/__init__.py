@@ -61,6 +61,38 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
+_lib_omp = None
+
+
+def build_omp(force: bool = False) -> str:
+    """The same source built with -fopenmp (rows of a step split over the
+    host cores, the arithmetic per node unchanged): used only to time the
+    oracle as the CPU baseline; the tests use the serial build."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC):
+        tmp = _LIB_OMP + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-fopenmp",
+                               "-std=c99", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
+def run_threads(case, nsteps: int, state=None, n0: int = 0):
+    """oracle.run on the OpenMP build (all host cores unless OMP_NUM_THREADS
+    says otherwise): for timing the CPU baseline."""
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            lib = ctypes.CDLL(build_omp())
+            P = ctypes.POINTER
+            lib.oracle_run.argtypes = [P(_Problem), P(ctypes.c_double), P(ctypes.c_uint8), P(ctypes.c_double),
+                                       P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int64, ctypes.c_int64]
+            lib.oracle_run.restype = ctypes.c_int
+            _lib_omp = lib
+    return _run_with(_lib_omp, case, nsteps, state, n0)
+
+
 def _load():
     global _lib
     with _lock:
@@ -140,7 +172,10 @@ def step(case, h, u, v, t_next: float):
 def run(case, nsteps: int, state=None, n0: int = 0):
     """Advance ``nsteps`` steps from ``state`` (default: the case's initial
     state) starting at step index n0.  Returns (h, u, v)."""
-    lib = _load()
+    return _run_with(_load(), case, nsteps, state, n0)
+
+
+def _run_with(lib, case, nsteps, state, n0):
     if state is None:
         state = (case.h0, case.u0, case.v0)
     h, u, v = (_arr(a, case) for a in state)
