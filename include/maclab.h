@@ -355,6 +355,13 @@ int maclab_get_profile(maclab_t sim, double* step_kernel_ms, int64_t* launches);
  * Synchronises. */
 int maclab_autotune(maclab_t sim, int trial_steps, int* choice);
 
+/* Measured FP64 rate of the current device (no counterpart in the paper;
+ * the denominator of the FP64 step's arithmetic roofline): eight
+ * independent fused multiply-add chains per thread on eight 256-thread
+ * blocks per SM, best of five timed launches (CUDA events), two flops per
+ * multiply-add.  Synchronises the device's default stream. */
+int maclab_measure_fp64(double* tflops);
+
 /* Facts about the handle. */
 int maclab_get_info(maclab_t sim, maclab_info* info);
 

@@ -28,7 +28,7 @@ SOLID, FLUID, NOSLIP, DIR_H, DIR_Q, DIR_HU = 0, 1, 2, 3, 4, 5
 BOUNCEBACK, SPECULAR, PERIODIC = 0, 1, 2
 F32, F64 = 0, 1
 
-__all__ = ["Simulation", "Batch", "MaclabError", "build_library", "lib"]
+__all__ = ["Simulation", "Batch", "MaclabError", "build_library", "lib", "measure_fp64"]
 
 
 class MaclabError(RuntimeError):
@@ -45,6 +45,16 @@ def build_library(force: bool = False) -> str:
 def lib() -> ctypes.CDLL:
     """The loaded C library (built on first use)."""
     return _abi.load()
+
+
+def measure_fp64() -> float:
+    """Measured FP64 fused multiply-add rate of the current device, TFLOP/s."""
+    out = ctypes.c_double()
+    L = lib()
+    rc = L.maclab_measure_fp64(ctypes.byref(out))
+    if rc != 0:
+        raise MaclabError(rc, L.maclab_last_error(None).decode())
+    return out.value
 
 
 def _dptr(a: np.ndarray):

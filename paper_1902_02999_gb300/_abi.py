@@ -85,6 +85,7 @@ PROTOTYPES = [
     ("maclab_set_profiling", c_int, [c_void_p, c_int]),
     ("maclab_get_profile", c_int, [c_void_p, P(c_double), P(c_int64)]),
     ("maclab_get_info", c_int, [c_void_p, P(Info)]),
+    ("maclab_measure_fp64", c_int, [P(c_double)]),
     ("maclab_device_state", c_int, [c_void_p, P(c_void_p), P(c_void_p), P(c_void_p)]),
     ("maclab_last_error", ctypes.c_char_p, [c_void_p]),
     ("maclab_batch_create", c_int, [c_int, P(Grid), P(Params), P(BC), P(P(c_double)),

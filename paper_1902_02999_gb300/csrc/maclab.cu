@@ -1690,6 +1690,59 @@ int maclab_set_profiling(maclab_t s, int on)
     return MACLAB_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// Eight independent FMA chains per thread (x <- a x + b, |a| < 1, so the
+// values stay normal and bounded): the FP64 pipe's throughput, not its
+// latency, sets the pace.
+__global__ void fp64_rate_kernel(double* sink, int iters, double a, double b)
+{
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = __fma_rn(x[k], a, b);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += x[k];
+    if (t == -1.0) sink[blockIdx.x] = t;  // never true: keeps the chains live
+}
+}  // namespace
+
+extern "C" {
+
+int maclab_measure_fp64(double* tflops)
+{
+    if (!tflops) return fail(nullptr, MACLAB_E_ARG, "NULL argument");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "device query");
+    const int threads = 256, blocks = 8 * sms, iters = 4096;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, 0);
+        fp64_rate_kernel<<<blocks, threads>>>(nullptr, iters, 0.9999999, 1e-7);
+        cudaEventRecord(e1, 0);
+        e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) best = std::min(best, ms);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "FP64 rate kernel");
+    const double flops = 2.0 * 8.0 * iters * (double)threads * blocks;  // an FMA is two flops
+    *tflops = flops / (best * 1e-3) / 1e12;
+    return MACLAB_OK;
+}
+
 int maclab_get_profile(maclab_t s, double* ms, int64_t* launches)
 {
     if (!s) return fail(nullptr, MACLAB_E_ARG, "NULL handle");
