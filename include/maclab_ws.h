@@ -86,6 +86,27 @@ int maclab_ws_gradients(maclab_ws_t ws, int batch, int out_ch, const float* x_de
 int maclab_ws_train_step(maclab_ws_t ws, int batch, int out_ch, const float* x_dev, const float* t_dev,
                          const float* w_dev, float lr, double* loss);
 
+/* Checks of single layers.  With keep on, the backward pass of
+ * maclab_ws_gradients / maclab_ws_train_step leaves the loss gradient with
+ * respect to every H_l in a buffer of its own (L + 1 more activation-sized
+ * bf16 buffers, allocated on the first call with on = 1 and kept until
+ * destroy) instead of overwriting two.  MACLAB_E_NOMEM if they do not fit. */
+int maclab_ws_keep_gradients(maclab_ws_t ws, int on);
+
+/* Float copy into out_dev of a tensor the handle stores, as of the last
+ * call, for the first `batch` samples of that call:
+ *   what 0: H_{index+1} (index 0..L) [batch][R][R][C], bf16 as stored,
+ *           after a forward, gradients or train step;
+ *   what 1: d loss / d H_{index+1} (index 0..L) [batch][R][R][C], bf16 as
+ *           stored, after a gradients or train step taken with keep on;
+ *   what 2: d loss / d Y [batch][R][R][16], bf16 as stored, after a
+ *           gradients or train step (index 0);
+ *   what 3: Y [batch][R][R][16], float (index 0).
+ * n must equal the element count.  MACLAB_E_ARG when the tensor is not
+ * there (no such call since the last forward pass, or batch too large).
+ * Runs on the handle's stream; does not synchronise. */
+int maclab_ws_inspect(maclab_ws_t ws, int what, int index, int batch, float* out_dev, int64_t n);
+
 /* Problem inputs of one fine n x n grid -> coarse network input and, when
  * eta/u/v are given, coarse targets.  n = R * MACLAB_WS_CELL.
  *   D_dev     [n][n] still-water depth h_ref - z_b (m)

@@ -119,6 +119,8 @@ PROTOTYPES = [
                                     P(c_double)]),
     ("maclab_ws_train_step", c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_float,
                                      P(c_double)]),
+    ("maclab_ws_keep_gradients", c_int, [c_void_p, c_int]),
+    ("maclab_ws_inspect", c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_int64]),
     ("maclab_ws_encode", c_int, [c_void_p, c_int, c_void_p, c_void_p, c_double, c_double, c_double, c_double,
                                  c_void_p,
                                  c_void_p, c_void_p, c_int, P(c_double), c_void_p, c_void_p, c_void_p]),

@@ -880,6 +880,13 @@ __global__ void __launch_bounds__(THREADS) ws_loss_kernel(const float* Y, const 
     if (threadIdx.x == 0) loss_part[blockIdx.x] = part[0];
 }
 
+// bf16 -> float
+__global__ void ws_from_bf16_kernel(const bf16* x, float* y, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = __bfloat162float(x[i]);
+}
+
 // float -> bf16
 __global__ void ws_to_bf16_kernel(const float* x, bf16* y, size_t n)
 {
@@ -1059,6 +1066,11 @@ struct maclab_ws_s {
     bf16* X = nullptr;          // [B][R][R][16]
     std::vector<bf16*> H;       // H_1 .. H_{L+1}, [B][R][R][C]
     bf16* G[2] = {nullptr, nullptr};  // gradient ping-pong [B][R][R][C]
+    std::vector<bf16*> GK;      // kept gradients w.r.t. H_1 .. H_{L+1} (maclab_ws_keep_gradients)
+    bool keep = false;
+    int fwd_batch = 0;          // batch of the last forward pass (0: none yet)
+    int grad_batch = 0;         // batch of the last backward pass while keep is on
+    int loss_batch = 0;         // batch of the last loss (dY) after the last forward pass
     bf16* dY = nullptr;         // [B][R][R][16]
     float* Yf = nullptr;        // [B][R][R][16]
     double* loss = nullptr;
@@ -1219,6 +1231,8 @@ void forward(maclab_ws_t w, int batch)
         launch_conv(w, a, batch);
         if (l < nl - 1) in = w->H[l];
     }
+    w->fwd_batch = batch;
+    w->loss_batch = w->grad_batch = 0;
 }
 
 // gradients of the loss into w->grad (zeroed first); dY from the loss kernel
@@ -1261,11 +1275,12 @@ void backward(maclab_ws_t w, int batch)
         a.relu_in = 0;
         a.gate = w->H[l - 1];
         a.res = l < nl - 1 ? gout : nullptr;
-        a.Y = w->G[ping];
+        a.Y = w->keep ? w->GK[l - 1] : w->G[ping];
         launch_conv(w, a, batch);
-        gout = w->G[ping];
+        gout = a.Y;
         ping ^= 1;
     }
+    w->grad_batch = w->keep ? batch : 0;
 }
 
 int check_batch(maclab_ws_t w, int batch)
@@ -1284,6 +1299,7 @@ int loss_and_grad(maclab_ws_t w, int batch, int oc, const float* x, const float*
     const int nb = grid_for(P * IO, 1024);
     ws_loss_kernel<<<nb, THREADS, 0, w->stream>>>(w->Yf, t, wt, (int)P, oc, w->dY, w->dpart);
     ws_sum_doubles_kernel<<<1, 32, 0, w->stream>>>(w->dpart, nb, 1, w->loss);
+    w->loss_batch = batch;
     backward(w, batch);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("warm-start launch: ") + cudaGetErrorString(e));
@@ -1480,6 +1496,55 @@ int maclab_ws_train_step(maclab_ws_t w, int batch, int oc, const float* x, const
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("train_step: ") + cudaGetErrorString(e));
     return read_loss(w, loss);
+}
+
+int maclab_ws_keep_gradients(maclab_ws_t w, int on)
+{
+    if (!w) return wfail(nullptr, MACLAB_E_ARG, "NULL warm-start handle");
+    if (on && w->GK.empty()) {
+        const size_t P = (size_t)w->cfg.max_batch * w->cfg.res * w->cfg.res;
+        std::vector<bf16*> k(w->H.size(), nullptr);
+        for (auto& p : k)
+            if (!walloc(w, &p, P * w->cfg.channels)) return wfail(w, MACLAB_E_NOMEM, "keep_gradients: out of memory");
+        w->GK = k;
+    }
+    w->keep = on != 0;
+    w->grad_batch = 0;
+    return MACLAB_OK;
+}
+
+int maclab_ws_inspect(maclab_ws_t w, int what, int index, int batch, float* out, int64_t n)
+{
+    if (!w || !out) return wfail(w, MACLAB_E_ARG, "NULL argument");
+    const int L1 = (int)w->H.size();
+    const size_t pix = (size_t)batch * w->cfg.res * w->cfg.res;
+    const bf16* src = nullptr;
+    const float* srcf = nullptr;
+    size_t ch = w->cfg.channels;
+    if (what == 0 || what == 1) {
+        if (index < 0 || index >= L1) return wfail(w, MACLAB_E_ARG, "inspect: index must be 0..blocks");
+        if (what == 0 && (batch < 1 || batch > w->fwd_batch))
+            return wfail(w, MACLAB_E_ARG, "inspect: batch exceeds the last forward pass");
+        if (what == 1 && (batch < 1 || batch > w->grad_batch))
+            return wfail(w, MACLAB_E_ARG, "inspect: no kept gradients of that batch");
+        src = what == 0 ? w->H[index] : w->GK[index];
+    } else if (what == 2 || what == 3) {
+        if (index != 0) return wfail(w, MACLAB_E_ARG, "inspect: index must be 0");
+        if (batch < 1 || batch > (what == 2 ? w->loss_batch : w->fwd_batch))
+            return wfail(w, MACLAB_E_ARG, "inspect: batch exceeds the last pass");
+        ch = IO;
+        if (what == 2) src = w->dY;
+        else srcf = w->Yf;
+    } else {
+        return wfail(w, MACLAB_E_ARG, "inspect: what must be 0..3");
+    }
+    if (n != (int64_t)(pix * ch)) return wfail(w, MACLAB_E_ARG, "inspect: n must be batch * res * res * channels");
+    cudaError_t e = cudaSuccess;
+    if (src) ws_from_bf16_kernel<<<grid_for(pix * ch), 256, 0, w->stream>>>(src, out, pix * ch);
+    else e = cudaMemcpyAsync(out, srcf, pix * ch * 4, cudaMemcpyDeviceToDevice, w->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("inspect: ") + cudaGetErrorString(e));
+    return MACLAB_OK;
 }
 
 int maclab_ws_encode(maclab_ws_t w, int n, const float* D, const uint8_t* mask, double wind_u, double wind_v,
