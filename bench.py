@@ -41,6 +41,7 @@ HBM_NOMINAL_GBS = 7900.0                   # GB300 HBM3e, nominal
 F64_FLOPS_PER_NODE = 120
 F64_NOMINAL_TFLOPS = 1.25                  # GB300 dense FP64, nominal (the bench also measures it)
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
 PROFILE_JSON = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
 # step-kernel codes of the library (maclab_step_kernel)
 KERNEL_SYMBOL = {0: "step_tile_kernel<%s>", 1: "step_fast_kernel<%s>", 2: "step_tile_tma_kernel (%s)",
@@ -70,6 +71,18 @@ def hbm_peak():
     except (OSError, ValueError):
         pass
     return FALLBACK_HBM_GBS, "fallback"
+
+
+def bf16_peak():
+    """Dense bf16 tensor rate (TFLOP/s) of this GPU timed alone (burst)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        if "bf16_tflops" in d:
+            return float(d["bf16_tflops"]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_BF16_TFLOPS, "fallback"
 
 
 def traffic_per_launch(precision, workload, kernel):
@@ -638,6 +651,14 @@ def main():
                 "error_reference": "fp64 plain iteration to residual 1e-11"}
         warm.update(ws.summary(res))
         net.close()
+        kt = ws.time_kernels(batch=16, reps=20, paths=(0,))["path0"]
+        pk, pk_src = bf16_peak()
+        warm["network_kernels"] = {
+            "batch": 16, "forward_ms": kt["forward_ms"], "train_step_ms": kt["train_step_ms"],
+            "forward_tflops": kt["forward_tflops"], "train_tflops": kt["train_tflops"],
+            "peak_tflops": pk, "peak_source": pk_src, "forward_frac": kt["forward_tflops"] / pk,
+            "train_frac": kt["train_tflops"] / pk,
+            "flops": "2 per multiply-add of the convolutions; a training step counts three times the forward"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,

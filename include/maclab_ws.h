@@ -52,11 +52,14 @@ typedef struct {
     int dilation[64];  /* d_l >= 1 of block l (entries past L unused) */
     int max_batch;     /* largest batch the activation buffers hold */
     uint64_t seed;     /* weight initialisation (SplitMix64 stream) */
-    int tensor_path;   /* the 128 -> 128 convolutions (residual blocks) on
-                          0: tcgen05, operands staged by TMA (default),
-                          1: tcgen05, operands staged by cp.async,
-                          2: mma.sync; the other convolutions always run on
-                          mma.sync.  Other values are rejected. */
+    int tensor_path;   /* 0 (default): every convolution and weight
+                          gradient on tcgen05, operands staged by TMA
+                          (channel counts 16 or multiples of 64 in, 16 or
+                          multiples of 128 out; other shapes on mma.sync);
+                          1: the 128 -> 128 convolutions on tcgen05 with
+                          operands staged by cp.async, the rest on mma.sync;
+                          2: everything on mma.sync.  Other values are
+                          rejected. */
 } maclab_ws_config;
 
 /* Create a network with freshly initialised weights (He-scaled normal

@@ -4,22 +4,22 @@
 //
 // Every convolution is an implicit GEMM on the tensor cores with bfloat16
 // operands and float accumulators:
-//   by default (tensor_path = 0) the 128 -> 128 channel convolutions of the
-//     residual blocks (forward and input gradient, most of the work) run on
-//     tcgen05.mma with operands brought in by TMA tensor copies into
-//     128-byte swizzled shared memory, the 128 x 128 accumulator in tensor
-//     memory, one thread issuing, completion through mbarriers
-//     (ws_conv_tma_kernel);
-//   tensor_path = 1 stages the same operands with cp.async in the canonical
-//     no-swizzle K-major layout instead (ws_conv_tc_kernel, slower: its
-//     per-thread copies set its pace);
-//   the other convolutions (16-channel input and output layers), the weight
-//     gradient, and every convolution under tensor_path = 2, run on mma.sync
-//     m16n8k16 with ldmatrix fragment loads (ws_conv_kernel, ws_wgrad_kernel);
+//   by default (tensor_path = 0) every convolution (forward and input
+//     gradient, the 16-channel input and output layers included) and every
+//     weight gradient runs on tcgen05.mma with operands brought in by TMA
+//     tensor copies into swizzled shared memory, accumulators in tensor
+//     memory, copies, MMAs and the epilogue in warps of their own
+//     (ws_conv5_kernel, ws_wgrad5_kernel in ws_tc5.cuh);
+//   tensor_path = 1 runs the 128 -> 128 convolutions on tcgen05 with
+//     operands staged by cp.async in the canonical no-swizzle K-major layout
+//     (ws_conv_tc_kernel, slower: its per-thread copies set its pace), the
+//     rest on mma.sync;
+//   tensor_path = 2 runs everything on mma.sync m16n8k16 with ldmatrix
+//     fragment loads (ws_conv_kernel, ws_wgrad_kernel);
 //   forward / input gradient: M = pixels, N = output channels,
 //     K = 9 taps x input channels;
-//   weight gradient: M = output channels, N = input channels, K = pixels
-//     (split over blocks, float atomics into the gradient).
+//   weight gradient: M and N the two channel sides, K = pixels (split over
+//     blocks, the splits' sums added in order afterwards).
 #include "maclab.h"
 #include "maclab_ws.h"
 
@@ -456,238 +456,12 @@ __global__ void __launch_bounds__(TC_THREADS) ws_conv_tc_kernel(const ConvArgs a
 }
 
 // ---------------------------------------------------------------------------
-// tcgen05 with TMA-fed operands (tensor_path = 0, the default).  Per stage (one tap, 64
-// input channels) one thread issues two tensor copies into 128-byte
-// swizzled shared memory: the 128 pixels of the block shifted by the tap
-// (a 4D box over [batch][y][x][c]; pixels outside the image arrive as
-// zeros) and the 128 x 64 weight slice (a 2D box).  A "full" mbarrier per
-// buffer counts the bytes, an "empty" one receives the tcgen05.commit of
-// the stage's MMAs; copies run two stages ahead of the MMAs in four buffers.
-//   operand layout: rows of 128 bytes (64 bf16), 16-byte chunk j of row r at
-//   chunk j ^ (r % 8) (the 128-byte swizzle of the tensor copy), 8-row
-//   groups 1024 bytes apart: descriptor stride byte offset 1024, swizzle
-//   mode 128B, and each K = 16 step advances the start address by 32 bytes.
+// Tensor maps of the TMA-fed tcgen05 kernels (ws_tc5.cuh): A and B operand
+// of a convolution, or output gradient and input of a weight gradient.
 struct TmaOperands {
-    CUtensorMap A;   // activations [batch][R][R][Cin], box {64, bx, by, 1}
-    CUtensorMap B;   // weights [9 Cout][Cin], box {64, 128}
+    CUtensorMap A;
+    CUtensorMap B;
 };
-#ifndef MACLAB_TT_STAGES
-#define MACLAB_TT_STAGES 3
-#endif
-#ifndef MACLAB_TT_AHEAD
-#define MACLAB_TT_AHEAD 2
-#endif
-constexpr int TT_STAGES = MACLAB_TT_STAGES, TT_AHEAD = MACLAB_TT_AHEAD, TT_THREADS = 128;
-constexpr uint32_t TT_OPER = 128 * 64 * 2;                    // 16 KB per operand and stage
-constexpr size_t TT_SMEM = TT_STAGES * 2 * TT_OPER + 1024;
-
-__device__ __forceinline__ uint64_t tt_desc(uint32_t saddr)
-{
-    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)1 << 16;            // leading byte offset (unused by swizzled K-major operands)
-    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset: next group of 8 rows
-    d |= (uint64_t)1 << 46;            // descriptor version of this tensor-core generation
-    d |= (uint64_t)2 << 61;            // 128-byte swizzle
-    return d;
-}
-__device__ __forceinline__ void tt_expect(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__global__ void __launch_bounds__(TT_THREADS) ws_conv_tma_kernel(const __grid_constant__ TmaOperands maps,
-                                                                  const ConvArgs a, int* err)
-{
-    extern __shared__ __align__(16) unsigned char ttm_raw[];
-    __shared__ __align__(8) uint64_t full[TT_STAGES], empty[TT_STAGES];
-    __shared__ uint32_t tmem_slot;
-    __shared__ int abort_flag;
-    const uint32_t raw = smem_addr(ttm_raw);
-    const uint32_t base = (raw + 1023u) & ~1023u;
-    unsigned char* tsm = ttm_raw + (base - raw);
-    const int R = a.R, Cin = a.Cin, Cout = a.Cout, dil = a.dil;
-    const int P = R * R, tiles = P / TC_M;
-    const int b = blockIdx.x / tiles, p0 = (blockIdx.x % tiles) * TC_M;
-    const int y0 = p0 / R, x0 = p0 % R;
-    const int n0 = blockIdx.y * TC_N;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&tmem_slot)),
-                     "r"(TC_N)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
-    }
-    if (tid == 0) {
-        for (int k = 0; k < TT_STAGES; ++k) {
-            tc_mbar_init(smem_addr(&full[k]));
-            tc_mbar_init(smem_addr(&empty[k]));
-        }
-        abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const uint32_t tmem = tmem_slot;
-    const int kch = Cin / 64;
-    const int KT = 9 * kch;
-    uint32_t pf[TT_STAGES], pe[TT_STAGES];
-#pragma unroll
-    for (int k = 0; k < TT_STAGES; ++k) pf[k] = pe[k] = 0;
-
-    auto issue = [&](int kk) {  // thread 0: the two tensor copies of stage kk
-        const int buf = kk % TT_STAGES;
-        const int tap = kk / kch, ci0 = (kk % kch) * 64;
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        const uint32_t sa = smem_addr(tsm + buf * 2 * TT_OPER), sb = sa + TT_OPER;
-        const uint32_t bar = smem_addr(&full[buf]);
-        tt_expect(bar, 2 * TT_OPER);
-        asm volatile(
-            "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-            "[%6];\n" ::"r"(sa),
-            "l"(reinterpret_cast<uint64_t>(&maps.A)), "r"(ci0), "r"(x0 + dx * dil), "r"(y0 + dy * dil), "r"(b),
-            "r"(bar)
-            : "memory");
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::
-                "r"(sb),
-            "l"(reinterpret_cast<uint64_t>(&maps.B)), "r"(ci0), "r"(tap * Cout + n0), "r"(bar)
-            : "memory");
-    };
-
-    bool ok = true;
-    if (tid == 0)
-        for (int s = 0; s < TT_AHEAD && s < KT; ++s) issue(s);
-    for (int kk = 0; kk < KT; ++kk) {
-        if (tid == 0 && kk + TT_AHEAD < KT) {
-            const int nb = (kk + TT_AHEAD) % TT_STAGES;
-            if (kk + TT_AHEAD >= TT_STAGES) {  // that buffer's last MMAs must be done
-                if (!tc_mbar_wait(smem_addr(&empty[nb]), pe[nb])) atomicOr(&abort_flag, 1);
-                pe[nb] ^= 1u;
-            }
-            issue(kk + TT_AHEAD);
-        }
-        const int buf = kk % TT_STAGES;
-        if (!tc_mbar_wait(smem_addr(&full[buf]), pf[buf])) atomicOr(&abort_flag, 1);
-        pf[buf] ^= 1u;
-        unsigned char* A = tsm + buf * 2 * TT_OPER;
-        if (a.relu_in) {
-            for (int i = tid; i < (int)(TT_OPER / 16); i += TT_THREADS) {
-                uint4* q = reinterpret_cast<uint4*>(A + i * 16);
-                uint4 v = *q;
-                v.x = relu2(v.x);
-                v.y = relu2(v.y);
-                v.z = relu2(v.z);
-                v.w = relu2(v.w);
-                *q = v;
-            }
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        }
-        __syncthreads();
-        if (abort_flag) {
-            ok = false;
-            break;
-        }
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t sa = smem_addr(A), sb = sa + TT_OPER;
-#pragma unroll
-            for (int k16 = 0; k16 < 4; ++k16) {
-                const uint64_t ad = tt_desc(sa + k16 * 32), bd = tt_desc(sb + k16 * 32);
-                const uint32_t acc = (kk > 0 || k16 > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(TC_IDESC), "r"(acc)
-                    : "memory");
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                             smem_addr(&empty[buf]))
-                         : "memory");
-        }
-    }
-    if (tid == 0) {
-        if (ok && KT > 0) {
-            // the commit of the last stage covers every MMA issued before it;
-            // the earlier commits of its buffer were waited for by the producer
-            const int lb = (KT - 1) % TT_STAGES;
-            if (!tc_mbar_wait(smem_addr(&empty[lb]), pe[lb])) atomicOr(&abort_flag, 1);
-        } else if (!ok) {
-            // gave up: let copies and MMAs in flight finish (bounded) before
-            // shared and tensor memory are released
-            for (int k = 0; k < TT_STAGES; ++k) {
-                tc_mbar_wait(smem_addr(&full[k]), pf[k]);
-                tc_mbar_wait(smem_addr(&empty[k]), pe[k]);
-            }
-        }
-    }
-    __syncthreads();
-    ok = ok && !abort_flag;
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (ok) {
-        const int m = warp * 32 + lane;
-        const size_t orow = ((size_t)b * P + p0 + m) * Cout + n0;
-#pragma unroll 1
-        for (int c0 = 0; c0 < TC_N; c0 += 16) {
-            uint32_t r[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-                "%14, %15}, [%16];\n"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15])
-                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            // a thread owns 16 consecutive channels of its pixel: 32-byte
-            // (bf16) and 64-byte (float) runs, moved as 16-byte vectors
-            const size_t o = orow + c0;
-            float v[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]) + (a.bias ? a.bias[n0 + c0 + j] : 0.f);
-            if (a.gate) {
-                uint4 g2[2];
-                g2[0] = *reinterpret_cast<const uint4*>(a.gate + o);
-                g2[1] = *reinterpret_cast<const uint4*>(a.gate + o + 8);
-                const __nv_bfloat162* gt = reinterpret_cast<const __nv_bfloat162*>(g2);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    if (!(__bfloat162float(gt[j].x) > 0.f)) v[2 * j] = 0.f;
-                    if (!(__bfloat162float(gt[j].y) > 0.f)) v[2 * j + 1] = 0.f;
-                }
-            }
-            if (a.res) {
-                uint4 r2[2];
-                r2[0] = *reinterpret_cast<const uint4*>(a.res + o);
-                r2[1] = *reinterpret_cast<const uint4*>(a.res + o + 8);
-                const __nv_bfloat162* rr = reinterpret_cast<const __nv_bfloat162*>(r2);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    v[2 * j] += __bfloat162float(rr[j].x);
-                    v[2 * j + 1] += __bfloat162float(rr[j].y);
-                }
-            }
-            if (a.Y) {
-                uint4 w2[2];
-                __nv_bfloat162* wb = reinterpret_cast<__nv_bfloat162*>(w2);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) wb[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                *reinterpret_cast<uint4*>(a.Y + o) = w2[0];
-                *reinterpret_cast<uint4*>(a.Y + o + 8) = w2[1];
-            }
-            if (a.Yf) {
-#pragma unroll
-                for (int j = 0; j < 16; j += 4)
-                    *reinterpret_cast<float4*>(a.Yf + o + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-            }
-        }
-    } else if (tid == 0) {
-        atomicOr(err, 1);
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_N) : "memory");
-}
 
 // ---------------------------------------------------------------------------
 // Weight gradient: dW[tap][co][ci] += sum_p dY[p][co] * act(X)[p + off(tap)][ci]
@@ -814,43 +588,87 @@ __global__ void __launch_bounds__(THREADS) ws_wgrad_kernel(const WgradArgs a)
     }
 }
 
+#include "ws_tc5.cuh"
+
 // out[i] = sum over s < S of part[s n + i], added in the order of s, so that
-// split sums combine the same way in every run
+// split sums combine the same way in every run; eight loads are issued
+// before their additions
 __global__ void ws_sum_parts_kernel(const float* __restrict__ part, int S, size_t n, float* __restrict__ out)
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         float t = 0.f;
-        for (int s = 0; s < S; ++s) t += part[(size_t)s * n + i];
+        int s = 0;
+        for (; s + 8 <= S; s += 8) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = part[(size_t)(s + j) * n + i];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) t += v[j];
+        }
+        for (; s < S; ++s) t += part[(size_t)s * n + i];
         out[i] = t;
     }
 }
 
 // out[c] = sum over b < nb of part[b k + c], c < k, in the order of b
-__global__ void ws_sum_doubles_kernel(const double* __restrict__ part, int nb, int k, double* __restrict__ out)
+// out[c] = sum over b < nb of part[b k + c], c < k: one block per c, the
+// threads' strided sums then a tree in shared memory, the same order in
+// every run
+__global__ void __launch_bounds__(THREADS) ws_sum_doubles_kernel(const double* __restrict__ part, int nb, int k,
+                                                                 double* __restrict__ out)
 {
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-        double t = 0.0;
-        for (int b = 0; b < nb; ++b) t += part[(size_t)b * k + c];
-        out[c] = t;
+    __shared__ double red[THREADS];
+    const int c = blockIdx.x;
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nb; b += THREADS) t += part[(size_t)b * k + c];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int h = THREADS / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) out[c] = red[0];
 }
 
-// out_part[blockIdx.y][c] = the block's share of sum_p dY[p][c]
-__global__ void __launch_bounds__(THREADS) ws_bias_grad_kernel(const bf16* dY, int P, int C, float* out_part)
+// out_part[blockIdx.x][c] = sum of dY[p][c] over the block's share of the
+// P pixels: thread (lane l, group g) adds 8 channels (one 16-byte vector)
+// of every (THREADS / (C / 8))-th pixel, then the lanes' sums are added in
+// lane order; C a multiple of 8, at most 8 THREADS
+constexpr int BG_BLOCKS = 256;
+__global__ void __launch_bounds__(THREADS) ws_bias_grad_kernel(const bf16* __restrict__ dY, int P, int C,
+                                                               float* __restrict__ out_part)
 {
-    __shared__ float part[THREADS];
-    const int c = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int lanes = THREADS / 32;
-    float s = 0.f;
-    if (c < C)
-        for (int p = blockIdx.y * lanes + (threadIdx.x >> 5); p < P; p += gridDim.y * lanes)
-            s += __bfloat162float(dY[(size_t)p * C + c]);
-    part[threadIdx.x] = s;
+    __shared__ float red[THREADS * 8];
+    const int G = C / 8, L = THREADS / G;
+    const int g = threadIdx.x % G, l = threadIdx.x / G;
+    const int p0 = (int)((long long)blockIdx.x * P / gridDim.x), p1 = (int)((long long)(blockIdx.x + 1) * P / gridDim.x);
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    auto add = [&](const uint4& q) {
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            acc[2 * j] += __bfloat162float(h[j].x);
+            acc[2 * j + 1] += __bfloat162float(h[j].y);
+        }
+    };
+    if (l < L) {
+        int p = p0 + l;
+        for (; p + 3 * L < p1; p += 4 * L) {  // four loads in flight, added in pixel order
+            uint4 q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) q[u] = *reinterpret_cast<const uint4*>(dY + (size_t)(p + u * L) * C + g * 8);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) add(q[u]);
+        }
+        for (; p < p1; p += L) add(*reinterpret_cast<const uint4*>(dY + (size_t)p * C + g * 8));
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) red[threadIdx.x * 8 + j] = acc[j];
     __syncthreads();
-    if (threadIdx.x < 32 && c < C) {
+    for (int c = threadIdx.x; c < C; c += THREADS) {
         float t = 0.f;
-        for (int k = 0; k < lanes; ++k) t += part[k * 32 + threadIdx.x];
-        out_part[(size_t)blockIdx.y * C + c] = t;
+        for (int k = 0; k < L; ++k) t += red[k * G * 8 + c];
+        out_part[(size_t)blockIdx.x * C + c] = t;
     }
 }
 
@@ -895,33 +713,52 @@ __global__ void ws_to_bf16_kernel(const float* x, bf16* y, size_t n)
 }
 
 // Adam on the flat parameter vector; lr_t carries the bias corrections
-__global__ void ws_adam_kernel(float* p, const float* g, float* m, float* v, size_t n, float lr_t, float b1,
-                               float b2, float eps)
+// Layers of the parameter vector for ws_update_kernel: where each layer's
+// weights start, and its channel counts (at most 64 blocks + lift + head).
+constexpr int WS_MAX_LAYERS = 66;
+struct LayerTable {
+    int n;
+    long long w_off[WS_MAX_LAYERS];
+    int cin[WS_MAX_LAYERS], cout[WS_MAX_LAYERS];
+};
+
+// One pass over the parameter vector: with adam, one Adam step (lr_t
+// carries the bias corrections); then every weight is packed in bfloat16
+// twice, Wf[tap][co][ci] for the forward convolution and Wb[8 - tap][ci][co]
+// (taps mirrored, channels swapped) for the input gradient, both at the
+// weight's own offset in the parameter vector (biases leave gaps).
+__global__ void ws_update_kernel(float* p, const float* g, float* m, float* v, size_t n, int adam, float lr_t,
+                                 float b1, float b2, float eps, const __grid_constant__ LayerTable tab, bf16* Wf,
+                                 bf16* Wb)
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        const float mi = b1 * m[i] + (1.f - b1) * gi;
-        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        p[i] -= lr_t * mi / (sqrtf(vi) + eps);
+        float pi = p[i];
+        if (adam) {
+            const float gi = g[i];
+            const float mi = b1 * m[i] + (1.f - b1) * gi;
+            const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+            m[i] = mi;
+            v[i] = vi;
+            pi -= lr_t * mi / (sqrtf(vi) + eps);
+            p[i] = pi;
+        }
+        int lo = 0, hi = tab.n - 1;  // the last layer starting at or before i
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tab.w_off[mid] <= (long long)i) lo = mid;
+            else hi = mid - 1;
+        }
+        const long long k = (long long)i - tab.w_off[lo];
+        const int Cin = tab.cin[lo], Cout = tab.cout[lo];
+        if (k < 9LL * Cin * Cout) {
+            const int ci = (int)(k % Cin), co = (int)((k / Cin) % Cout), t = (int)(k / ((long long)Cin * Cout));
+            const bf16 w = __float2bfloat16_rn(pi);
+            Wf[i] = w;
+            Wb[tab.w_off[lo] + ((long long)(8 - t) * Cin + ci) * Cout + co] = w;
+        }
     }
 }
 
-// bf16 copies of one layer's weights: forward layout [9][co][ci] and the
-// input-gradient layout Wb[t][ci][co] = W[8 - t][co][ci]
-__global__ void ws_pack_kernel(const float* W, int Cout, int Cin, bf16* Wf, bf16* Wb)
-{
-    const size_t n = (size_t)9 * Cout * Cin;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int ci = (int)(i % Cin);
-        const int co = (int)((i / Cin) % Cout);
-        const int t = (int)(i / ((size_t)Cin * Cout));
-        const bf16 w = __float2bfloat16_rn(W[i]);
-        Wf[i] = w;
-        Wb[((size_t)(8 - t) * Cin + ci) * Cout + co] = w;
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Fine grid <-> coarse grid
@@ -1057,6 +894,9 @@ struct maclab_ws_s {
         bf16* Wb = nullptr;     // [9][cin][cout], flipped
     };
     std::vector<Layer> layers;  // lift, blocks, head
+    LayerTable table{};         // the layers for ws_update_kernel
+    bf16* Wf_all = nullptr;     // packed weights, each layer's at its parameter offset
+    bf16* Wb_all = nullptr;
     int64_t nparam = 0;
     float* param = nullptr;     // master weights
     float* grad = nullptr;
@@ -1121,39 +961,108 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return encode;
 }
 
-// tensor maps of one convolution for ws_conv_tma_kernel; false if the
-// driver entry point is missing or an encode fails
-bool tma_operands(const ConvArgs& a, int batch, TmaOperands& m)
+// 4-d map of an NHWC bf16 tensor [batch][R][R][C] with a box of bc
+// channels x bx x by pixels; rows of bc channels, swizzled to their width
+// (128 bytes for 64 channels, 32 bytes for 16)
+bool act_map(CUtensorMap* m, const bf16* p, int C, int R, int batch, int bc, int bx, int by)
 {
     const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
     if (!encode) return false;
-    const int bx = a.R < 128 ? a.R : 128, by = 128 / bx;
-    const cuuint64_t adims[4] = {(cuuint64_t)a.Cin, (cuuint64_t)a.R, (cuuint64_t)a.R, (cuuint64_t)batch};
-    const cuuint64_t astr[3] = {(cuuint64_t)a.Cin * 2, (cuuint64_t)a.R * a.Cin * 2, (cuuint64_t)a.R * a.R * a.Cin * 2};
-    const cuuint32_t abox[4] = {64, (cuuint32_t)bx, (cuuint32_t)by, 1};
+    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)R, (cuuint64_t)R, (cuuint64_t)batch};
+    const cuuint64_t str[3] = {(cuuint64_t)C * 2, (cuuint64_t)R * C * 2, (cuuint64_t)R * R * C * 2};
+    const cuuint32_t box[4] = {(cuuint32_t)bc, (cuuint32_t)bx, (cuuint32_t)by, 1};
     const cuuint32_t one[4] = {1, 1, 1, 1};
-    if (encode(&m.A, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)a.X, adims, astr, abox, one,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return false;
-    const cuuint64_t bdims[2] = {(cuuint64_t)a.Cin, (cuuint64_t)9 * a.Cout};
-    const cuuint64_t bstr[1] = {(cuuint64_t)a.Cin * 2};
-    const cuuint32_t bbox[2] = {64, 128};
-    return encode(&m.B, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)a.Wk, bdims, bstr, bbox, one,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+    return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)p, dims, str, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  bc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 2-d map of the packed weights [9 Cout][Cin], box of bc channels x bn rows
+bool weight_map(CUtensorMap* m, const bf16* Wk, int Cin, int Cout, int bc, int bn)
+{
+    const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)Cin, (cuuint64_t)9 * Cout};
+    const cuuint64_t str[1] = {(cuuint64_t)Cin * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)bc, (cuuint32_t)bn};
+    const cuuint32_t one[2] = {1, 1};
+    return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)Wk, dims, str, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  bc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the tcgen05 kernels' configurations: operand buffers (three stages: two
+// convolution blocks share an SM) and the weight gradient's blocks
+constexpr int T5_ST = 3, T5_WST = 3;
+constexpr int T5_WBLOCKS = 150;  // weight-gradient blocks: one per SM, 64 KB stages
+template <int KC, int N, int ST>
+constexpr size_t t5_conv_smem()
+{
+    return (size_t)ST * (128 * KC * 2 * (64 / KC) + (64 / KC) * N * KC * 2) + 1024;
+}
+template <bool MG, int N, int ST>
+constexpr size_t t5_wgrad_smem()
+{
+    return (size_t)ST * ((MG ? 16384 : N * 128) + 3 * (MG ? N * 128 : 16384)) + 1024;
+}
+
+// set the dynamic shared-memory limit of every tcgen05 kernel instance
+cudaError_t t5_set_limits()
+{
+    cudaError_t e = cudaFuncSetAttribute(ws_conv5_kernel<64, 128, T5_ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)t5_conv_smem<64, 128, T5_ST>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ws_conv5_kernel<16, 128, T5_ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)t5_conv_smem<16, 128, T5_ST>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ws_conv5_kernel<64, 16, T5_ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)t5_conv_smem<64, 16, T5_ST>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ws_wgrad5_kernel<true, 128, T5_WST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)t5_wgrad_smem<true, 128, T5_WST>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ws_wgrad5_kernel<true, 16, T5_WST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)t5_wgrad_smem<true, 16, T5_WST>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(ws_wgrad5_kernel<false, 16, T5_WST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)t5_wgrad_smem<false, 16, T5_WST>());
+    return e;
+}
+
+// tensor_path 0: the convolution on ws_conv5_kernel; false if its shape or
+// tensor maps are not supported (the caller falls back to mma.sync)
+bool launch_conv5(maclab_ws_t w, const ConvArgs& a, int batch)
+{
+    const int R = a.R;
+    const bool shape = (a.Cin % 64 == 0 || a.Cin == 16) && (a.Cout % 128 == 0 || a.Cout == 16) && R % 64 == 0 &&
+                       (R < 128 ? 128 % R == 0 : R % 128 == 0);
+    if (!shape) return false;
+    const int KC = a.Cin == 16 ? 16 : 64, N = a.Cout == 16 ? 16 : 128;
+    const int bx = R < 128 ? R : 128, by = 128 / bx;
+    TmaOperands maps;
+    if (!act_map(&maps.A, a.X, a.Cin, R, batch, KC, bx, by) || !weight_map(&maps.B, a.Wk, a.Cin, a.Cout, KC, N))
+        return false;
+    dim3 grid(batch * (R * R / 128), a.Cout / N);
+    if (KC == 64 && N == 128) {
+        ws_conv5_kernel<64, 128, T5_ST>
+            <<<grid, T5_THREADS, t5_conv_smem<64, 128, T5_ST>(), w->stream>>>(maps, a, w->tc_err);
+    } else if (KC == 16 && N == 128) {
+        ws_conv5_kernel<16, 128, T5_ST>
+            <<<grid, T5_THREADS, t5_conv_smem<16, 128, T5_ST>(), w->stream>>>(maps, a, w->tc_err);
+    } else if (KC == 64 && N == 16) {
+        ws_conv5_kernel<64, 16, T5_ST>
+            <<<grid, T5_THREADS, t5_conv_smem<64, 16, T5_ST>(), w->stream>>>(maps, a, w->tc_err);
+    } else {
+        return false;  // 16 -> 16 channels: no such layer
+    }
+    return true;
 }
 
 void launch_conv(maclab_ws_t w, const ConvArgs& a, int batch)
 {
     const int segs = a.R / CONV_M;
-    const bool tc_shape = a.Cin % 64 == 0 && a.Cout % TC_N == 0 && (a.R * a.R) % TC_M == 0 &&
-                          (a.R < 128 ? 128 % a.R == 0 : a.R % 128 == 0);
-    TmaOperands maps;
-    if (w->cfg.tensor_path == 0 && tc_shape && tma_operands(a, batch, maps)) {
-        dim3 grid(batch * (a.R * a.R / TC_M), a.Cout / TC_N);
-        ws_conv_tma_kernel<<<grid, TT_THREADS, TT_SMEM, w->stream>>>(maps, a, w->tc_err);
-    } else if (w->cfg.tensor_path == 1 && a.Cin % TC_KS == 0 && a.Cout % TC_N == 0 && (a.R * a.R) % TC_M == 0) {
+    if (w->cfg.tensor_path == 0 && launch_conv5(w, a, batch)) return;
+    if (w->cfg.tensor_path == 1 && a.Cin % TC_KS == 0 && a.Cout % TC_N == 0 && (a.R * a.R) % TC_M == 0) {
         dim3 grid(batch * (a.R * a.R / TC_M), a.Cout / TC_N);
         ws_conv_tc_kernel<<<grid, TC_THREADS, TC_SMEM, w->stream>>>(a, w->tc_err);
     } else if (a.Cout % 128 == 0) {
@@ -1165,8 +1074,41 @@ void launch_conv(maclab_ws_t w, const ConvArgs& a, int batch)
     }
 }
 
+// tensor_path 0: the weight gradient on ws_wgrad5_kernel; false if its
+// shape or tensor maps are not supported
+bool launch_wgrad5(maclab_ws_t w, const WgradArgs& a0)
+{
+    WgradArgs a = a0;
+    const bool mg = a.Cout % 128 == 0 && (a.Cin % 128 == 0 || a.Cin == 16);
+    const bool head = !mg && a.Cin % 128 == 0 && a.Cout == 16;
+    if (!(mg || head) || a.R % 64) return false;
+    const int N = mg ? (a.Cin == 16 ? 16 : 128) : 16;
+    const int gbox = (mg || N == 128) ? 64 : 16, xbox = (!mg || N == 128) ? 64 : 16;
+    TmaOperands maps;
+    if (!act_map(&maps.A, a.dY, a.Cout, a.R, a.B, gbox, 64, 1) || !act_map(&maps.B, a.X, a.Cin, a.R, a.B, xbox, 64, 1))
+        return false;
+    const int tiles = (mg ? a.Cout / 128 * (a.Cin / N) : a.Cin / 128 * (a.Cout / N));
+    const int segs = a.B * a.R * (a.R / 64);
+    a.splits = std::max(1, std::min(segs, T5_WBLOCKS / (3 * tiles)));
+    a.part = w->part;
+    dim3 grid(3, a.splits, tiles);
+    if (mg && N == 128)
+        ws_wgrad5_kernel<true, 128, T5_WST>
+            <<<grid, T5_THREADS, t5_wgrad_smem<true, 128, T5_WST>(), w->stream>>>(maps, a, w->tc_err);
+    else if (mg)
+        ws_wgrad5_kernel<true, 16, T5_WST>
+            <<<grid, T5_THREADS, t5_wgrad_smem<true, 16, T5_WST>(), w->stream>>>(maps, a, w->tc_err);
+    else
+        ws_wgrad5_kernel<false, 16, T5_WST>
+            <<<grid, T5_THREADS, t5_wgrad_smem<false, 16, T5_WST>(), w->stream>>>(maps, a, w->tc_err);
+    const size_t n = (size_t)9 * a.Cout * a.Cin;
+    ws_sum_parts_kernel<<<grid_for(n), 256, 0, w->stream>>>(w->part, a.splits, n, a.dW);
+    return true;
+}
+
 void launch_wgrad(maclab_ws_t w, const WgradArgs& a0)
 {
+    if (w->cfg.tensor_path == 0 && launch_wgrad5(w, a0)) return;
     WgradArgs a = a0;
     const int chunks = a.B * a.R * a.R / WG_K;
     const int MT = a.Cout % 64 == 0 ? 64 : 16, NT = a.Cin % 64 == 0 ? 64 : 16;
@@ -1183,8 +1125,8 @@ void launch_wgrad(maclab_ws_t w, const WgradArgs& a0)
 }
 
 // Floats of the partial-sum buffer: the weight gradient's splits of every
-// layer (at most 304 / (tiles * 9) + 1 of them) and the bias gradient's 64
-// block rows.
+// layer (at most 304 / (tiles * 9) + 1 of them on mma.sync, T5_WBLOCKS / 3
+// on tcgen05) and the bias gradient's block rows.
 size_t part_floats_for(const maclab_ws_s* w)
 {
     size_t n = 0;
@@ -1192,17 +1134,18 @@ size_t part_floats_for(const maclab_ws_s* w)
         const int MT = L.cout % 64 == 0 ? 64 : 16, NT = L.cin % 64 == 0 ? 64 : 16;
         const int tiles = (L.cout / MT) * (L.cin / NT);
         const size_t S = (size_t)(304 / std::max(1, tiles * 9) + 1);
-        n = std::max(n, S * 9 * L.cout * L.cin);
-        n = std::max(n, (size_t)64 * L.cout);
+        n = std::max(n, std::max(S, (size_t)(T5_WBLOCKS / 3)) * 9 * L.cout * L.cin);
+        n = std::max(n, (size_t)BG_BLOCKS * L.cout);
     }
     return n;
 }
 
-void pack_all(maclab_ws_t w)
+// pack the weights (and with lr_t > 0 first take one Adam step)
+void update(maclab_ws_t w, int adam, float lr_t)
 {
-    for (auto& L : w->layers)
-        ws_pack_kernel<<<grid_for((size_t)9 * L.cout * L.cin), 256, 0, w->stream>>>(w->param + L.w_off, L.cout, L.cin,
-                                                                                 L.Wf, L.Wb);
+    ws_update_kernel<<<grid_for((size_t)w->nparam), 256, 0, w->stream>>>(
+        w->param, w->grad, w->m1, w->m2, (size_t)w->nparam, adam, lr_t, 0.9f, 0.999f, 1e-8f, w->table, w->Wf_all,
+        w->Wb_all);
 }
 
 // forward of `batch` samples from w->X; head output to w->Yf
@@ -1258,9 +1201,8 @@ void backward(maclab_ws_t w, int batch)
         g.dil = L.dil;
         g.relu_in = L.relu_in;
         launch_wgrad(w, g);
-        dim3 bg((L.cout + 31) / 32, 64);
-        ws_bias_grad_kernel<<<bg, THREADS, 0, w->stream>>>(gout, P, L.cout, w->part);
-        ws_sum_parts_kernel<<<grid_for(L.cout), 256, 0, w->stream>>>(w->part, 64, L.cout, w->grad + L.b_off);
+        ws_bias_grad_kernel<<<BG_BLOCKS, THREADS, 0, w->stream>>>(gout, P, L.cout, w->part);
+        ws_sum_parts_kernel<<<grid_for(L.cout), 256, 0, w->stream>>>(w->part, BG_BLOCKS, L.cout, w->grad + L.b_off);
         if (l == 0) break;
         // gradient w.r.t. this layer's input H_{l-1}:
         //   head:  relu'(H) * conv^T(gout)
@@ -1298,7 +1240,7 @@ int loss_and_grad(maclab_ws_t w, int batch, int oc, const float* x, const float*
     forward(w, batch);
     const int nb = grid_for(P * IO, 1024);
     ws_loss_kernel<<<nb, THREADS, 0, w->stream>>>(w->Yf, t, wt, (int)P, oc, w->dY, w->dpart);
-    ws_sum_doubles_kernel<<<1, 32, 0, w->stream>>>(w->dpart, nb, 1, w->loss);
+    ws_sum_doubles_kernel<<<1, THREADS, 0, w->stream>>>(w->dpart, nb, 1, w->loss);
     w->loss_batch = batch;
     backward(w, batch);
     const cudaError_t e = cudaGetLastError();
@@ -1369,9 +1311,15 @@ int maclab_ws_create(const maclab_ws_config* cfg, void* stream, maclab_ws_t* out
     ok = ok && walloc(w, &w->part, w->part_floats) && walloc(w, &w->dpart, 2 * 1024);
     w->H.assign(w->layers.size() - 1, nullptr);
     for (size_t l = 0; ok && l < w->H.size(); ++l) ok = walloc(w, &w->H[l], P * C);
-    for (auto& L : w->layers) {
-        if (!ok) break;
-        ok = walloc(w, &L.Wf, (size_t)9 * L.cin * L.cout) && walloc(w, &L.Wb, (size_t)9 * L.cin * L.cout);
+    ok = ok && walloc(w, &w->Wf_all, w->nparam) && walloc(w, &w->Wb_all, w->nparam);
+    w->table.n = (int)w->layers.size();
+    for (int l = 0; ok && l < w->table.n; ++l) {
+        auto& L = w->layers[l];
+        L.Wf = w->Wf_all + L.w_off;
+        L.Wb = w->Wb_all + L.w_off;
+        w->table.w_off[l] = L.w_off;
+        w->table.cin[l] = L.cin;
+        w->table.cout[l] = L.cout;
     }
     if (!ok) {
         maclab_ws_destroy(w);
@@ -1397,10 +1345,9 @@ int maclab_ws_create(const maclab_ws_config* cfg, void* stream, maclab_ws_t* out
     if (e == cudaSuccess) e = cudaMemsetAsync(w->tc_err, 0, sizeof(int), w->stream);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(ws_conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ws_conv_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT_SMEM);
+    if (e == cudaSuccess) e = t5_set_limits();
     if (e == cudaSuccess) {
-        pack_all(w);
+        update(w, 0, 0.f);
         e = cudaStreamSynchronize(w->stream);
     }
     if (e != cudaSuccess) {
@@ -1442,7 +1389,7 @@ int maclab_ws_set_params(maclab_ws_t w, const float* host, int64_t n)
     if (e == cudaSuccess) e = cudaMemsetAsync(w->m1, 0, (size_t)n * 4, w->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(w->m2, 0, (size_t)n * 4, w->stream);
     if (e == cudaSuccess) {
-        pack_all(w);
+        update(w, 0, 0.f);
         e = cudaStreamSynchronize(w->stream);
     }
     if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("set_params: ") + cudaGetErrorString(e));
@@ -1489,10 +1436,7 @@ int maclab_ws_train_step(maclab_ws_t w, int batch, int oc, const float* x, const
     w->step += 1;
     const double b1 = 0.9, b2 = 0.999;
     const double lr_t = lr * std::sqrt(1.0 - std::pow(b2, (double)w->step)) / (1.0 - std::pow(b1, (double)w->step));
-    ws_adam_kernel<<<grid_for((size_t)w->nparam), 256, 0, w->stream>>>(w->param, w->grad, w->m1, w->m2,
-                                                                      (size_t)w->nparam, (float)lr_t, (float)b1,
-                                                                      (float)b2, 1e-8f);
-    pack_all(w);
+    update(w, 1, (float)lr_t);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return wfail(w, MACLAB_E_CUDA, std::string("train_step: ") + cudaGetErrorString(e));
     return read_loss(w, loss);
@@ -1578,7 +1522,7 @@ int maclab_ws_decode(maclab_ws_t w, int n, const float* y, const float* D, const
     if (std::isfinite(mass_eta)) {
         const int nb = grid_for((size_t)n * n, 1024);
         ws_eta_sum_kernel<<<nb, THREADS, 0, w->stream>>>(n * n, h, D, mask, w->dpart);
-        ws_sum_doubles_kernel<<<1, 32, 0, w->stream>>>(w->dpart, nb, 2, w->acc);
+        ws_sum_doubles_kernel<<<2, THREADS, 0, w->stream>>>(w->dpart, nb, 2, w->acc);
         ws_eta_shift_kernel<<<(n * n + 255) / 256, 256, 0, w->stream>>>(n * n, h, mask, w->acc, mass_eta);
     }
     const cudaError_t e = cudaGetLastError();

@@ -65,20 +65,28 @@ def conv_chain(cin):
 
 
 def wgrad_chain(cin, cout, pixels):
-    """Float additions on the longest path of one weight-gradient entry: the
-    32-pixel chunks one split takes (two 16-product accumulations each),
-    then the splits' partial sums in order."""
+    """Float additions on the longest path of one weight-gradient entry, the
+    longer of the two kernels' (then 16 inside a 16-product accumulation):
+    mma.sync, the 32-pixel chunks one split takes, two accumulations each,
+    then the splits' sums in order; tcgen05, the 64-pixel segments of one of
+    at most 50 splits, four accumulations each, then the splits' sums."""
     chunks = pixels // 32
     mt = 64 if cout % 64 == 0 else 16
     nt = 64 if cin % 64 == 0 else 16
     splits = max(1, min(chunks, 304 // max(1, (cout // mt) * (cin // nt) * 9) + 1))
-    return 2 * (-(-chunks // splits)) + 16 + splits
+    mma_sync = 2 * (-(-chunks // splits)) + splits
+    segs = pixels // 64
+    s5 = max(1, min(segs, 50))
+    tc5 = 4 * (-(-segs // s5)) + s5
+    return max(mma_sync, tc5) + 16
 
 
-def bias_chain(pixels):
-    """Float additions of one bias-gradient entry: a thread's share of the
-    pixels (64 x 8 threads), the block's 8 warps, the 64 block sums."""
-    return -(-pixels // 512) + 8 + 64
+def bias_chain(pixels, channels):
+    """Float additions of one bias-gradient entry: a thread's share of one
+    of 256 blocks' pixels (256 / (channels / 8) threads share a channel),
+    the block's threads in order, the 256 block sums."""
+    lanes = 256 // (channels // 8)
+    return -(-(-(-pixels // 256)) // lanes) + lanes + 256
 
 
 def abs_input_grad(G, W, d):
@@ -197,7 +205,7 @@ def test_full_shape_every_layer_elementwise(path):
         w0, b0 = offs[k]
         check("weight grad layer %d" % k, g[w0:b0].astype(np.float64), dW.ravel(), SdW.ravel(),
               wgrad_chain(ci, co, P), False, report)
-        check("bias grad layer %d" % k, g[b0:b0 + co].astype(np.float64), db, Sdb, bias_chain(P), False, report)
+        check("bias grad layer %d" % k, g[b0:b0 + co].astype(np.float64), db, Sdb, bias_chain(P, co), False, report)
         if k == 0:
             continue
         want = dA * (H[k - 1] > 0)
