@@ -993,7 +993,15 @@ bool weight_map(CUtensorMap* m, const bf16* Wk, int Cin, int Cout, int bc, int b
 
 // the tcgen05 kernels' configurations: operand buffers (three stages: two
 // convolution blocks share an SM) and the weight gradient's blocks
+#ifndef MACLAB_T5_CS
+#define MACLAB_T5_CS 1
+#endif
 constexpr int T5_ST = 3, T5_WST = 3;
+// blocks of a cluster sharing each weight stage of the 128 -> 128
+// convolution by multicast (each fetches 1 / T5_CS of it); 1 by default:
+// clusters of 2 and 4 measured slower (forward 0.574 and 0.584 against
+// 0.536 ms), the blocks of a cluster waiting for each other's releases
+constexpr int T5_CS = MACLAB_T5_CS;
 constexpr int T5_WBLOCKS = 150;  // weight-gradient blocks: one per SM, 64 KB stages
 template <int KC, int N, int ST>
 constexpr size_t t5_conv_smem()
@@ -1009,13 +1017,14 @@ constexpr size_t t5_wgrad_smem()
 // set the dynamic shared-memory limit of every tcgen05 kernel instance
 cudaError_t t5_set_limits()
 {
-    cudaError_t e = cudaFuncSetAttribute(ws_conv5_kernel<64, 128, T5_ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(ws_conv5_kernel<64, 128, T5_ST, T5_CS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)t5_conv_smem<64, 128, T5_ST>());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ws_conv5_kernel<16, 128, T5_ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(ws_conv5_kernel<16, 128, T5_ST, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)t5_conv_smem<16, 128, T5_ST>());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(ws_conv5_kernel<64, 16, T5_ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(ws_conv5_kernel<64, 16, T5_ST, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)t5_conv_smem<64, 16, T5_ST>());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(ws_wgrad5_kernel<true, 128, T5_WST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1039,18 +1048,34 @@ bool launch_conv5(maclab_ws_t w, const ConvArgs& a, int batch)
     if (!shape) return false;
     const int KC = a.Cin == 16 ? 16 : 64, N = a.Cout == 16 ? 16 : 128;
     const int bx = R < 128 ? R : 128, by = 128 / bx;
+    const int cs = KC == 64 && N == 128 ? T5_CS : 1;  // the weight box: N / cs rows
     TmaOperands maps;
-    if (!act_map(&maps.A, a.X, a.Cin, R, batch, KC, bx, by) || !weight_map(&maps.B, a.Wk, a.Cin, a.Cout, KC, N))
+    if (!act_map(&maps.A, a.X, a.Cin, R, batch, KC, bx, by) || !weight_map(&maps.B, a.Wk, a.Cin, a.Cout, KC, N / cs))
         return false;
     dim3 grid(batch * (R * R / 128), a.Cout / N);
-    if (KC == 64 && N == 128) {
-        ws_conv5_kernel<64, 128, T5_ST>
+    if (KC == 64 && N == 128 && T5_CS == 1) {
+        ws_conv5_kernel<64, 128, T5_ST, 1>
             <<<grid, T5_THREADS, t5_conv_smem<64, 128, T5_ST>(), w->stream>>>(maps, a, w->tc_err);
+    } else if (KC == 64 && N == 128) {
+        if (grid.x % T5_CS) return false;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = grid;
+        cfg.blockDim = dim3(T5_THREADS);
+        cfg.dynamicSmemBytes = t5_conv_smem<64, 128, T5_ST>();
+        cfg.stream = w->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = T5_CS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, ws_conv5_kernel<64, 128, T5_ST, T5_CS>, maps, a, w->tc_err);
     } else if (KC == 16 && N == 128) {
-        ws_conv5_kernel<16, 128, T5_ST>
+        ws_conv5_kernel<16, 128, T5_ST, 1>
             <<<grid, T5_THREADS, t5_conv_smem<16, 128, T5_ST>(), w->stream>>>(maps, a, w->tc_err);
     } else if (KC == 64 && N == 16) {
-        ws_conv5_kernel<64, 16, T5_ST>
+        ws_conv5_kernel<64, 16, T5_ST, 1>
             <<<grid, T5_THREADS, t5_conv_smem<64, 16, T5_ST>(), w->stream>>>(maps, a, w->tc_err);
     } else {
         return false;  // 16 -> 16 channels: no such layer

@@ -86,6 +86,27 @@ __device__ __forceinline__ void t5_load2(uint32_t dst, const CUtensorMap* map, i
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
         : "memory");
 }
+// the same copy delivered to the same offset, and signalled on the same
+// barrier, in every block of the cluster named in mask
+__device__ __forceinline__ void t5_load2_mc(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar,
+                                            uint16_t mask)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
+        "%3}], [%4], %5;\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar), "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ uint32_t t5_cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void t5_cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
 __device__ __forceinline__ void t5_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
 {
     asm volatile(
@@ -97,6 +118,15 @@ __device__ __forceinline__ void t5_mma(uint32_t tmem, uint64_t ad, uint64_t bd, 
 __device__ __forceinline__ void t5_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                 : "memory");
+}
+// arrives, once the MMAs complete, on the barrier at this offset in every
+// block of the cluster named in mask
+__device__ __forceinline__ void t5_commit_mc(uint32_t bar, uint16_t mask)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n" ::
+                     "r"(bar),
+                 "h"(mask)
                  : "memory");
 }
 // relu of `bytes` bytes of bf16 pairs, by nt threads (t = 0 .. nt-1)
@@ -130,7 +160,7 @@ template <int ST>
 struct T5Bars {
     uint64_t full[ST], ready[ST], empty[ST], done;
 };
-template <int ST>
+template <int ST, int CS = 1>
 __device__ __forceinline__ uint32_t t5_start(T5Bars<ST>& bars, uint32_t* tmem_slot, uint32_t cols, int* flags)
 {
     const int tid = threadIdx.x;
@@ -144,20 +174,23 @@ __device__ __forceinline__ uint32_t t5_start(T5Bars<ST>& bars, uint32_t* tmem_sl
         for (int k = 0; k < ST; ++k) {
             t5_bar_init(smem_addr(&bars.full[k]), 1);
             t5_bar_init(smem_addr(&bars.ready[k]), 4);
-            t5_bar_init(smem_addr(&bars.empty[k]), 1);
+            t5_bar_init(smem_addr(&bars.empty[k]), CS);  // every block of the cluster releases it
         }
         t5_bar_init(smem_addr(&bars.done), 1);
         flags[0] = flags[1] = flags[2] = 0;  // abort, stages issued, stages seen landed
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
+    if (CS > 1)
+        t5_cluster_sync();  // no block copies into a peer's buffers before its barriers exist
+    else
+        __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     return *tmem_slot;
 }
 // Block end: after a time-out, the copies still in flight land (bounded)
 // before shared and tensor memory are released.
-template <int ST>
+template <int ST, int CS = 1>
 __device__ __forceinline__ void t5_finish(T5Bars<ST>& bars, uint32_t tmem, uint32_t cols, int* flags, int* err)
 {
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -166,7 +199,13 @@ __device__ __forceinline__ void t5_finish(T5Bars<ST>& bars, uint32_t tmem, uint3
         for (int s = flags[2]; s < flags[1]; ++s) tc_mbar_wait(smem_addr(&bars.full[s % ST]), (uint32_t)(s / ST) & 1u);
         atomicOr(err, 1);
     }
-    __syncthreads();
+    // with a cluster: no block leaves while a peer's copies or MMA
+    // completions may still signal its barriers (every peer has waited for
+    // its own MMAs by now)
+    if (CS > 1)
+        t5_cluster_sync();
+    else
+        __syncthreads();
     if (threadIdx.x < 32)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(cols) : "memory");
 }
@@ -184,10 +223,11 @@ __device__ __forceinline__ void t5_finish(T5Bars<ST>& bars, uint32_t tmem, uint3
 // is waited for at the end.
 //   stage layout: A chunks [64 / KC] of 128 x KC bf16, then B chunks
 //   [64 / KC] of N x KC bf16, every chunk on a 1024-byte boundary.
-template <int KC, int N, int ST>
+template <int KC, int N, int ST, int CS>
 __global__ void __launch_bounds__(T5_THREADS, 2) ws_conv5_kernel(const __grid_constant__ TmaOperands maps,
                                                                const ConvArgs a, int* err)
 {
+    constexpr uint16_t MASK = (uint16_t)((1u << CS) - 1u);
     constexpr int CPS = 64 / KC;
     constexpr uint32_t ACH = 128 * KC * 2, BCH = N * KC * 2;
     constexpr uint32_t ABYTES = CPS * ACH, SBYTES = ABYTES + CPS * BCH;
@@ -208,7 +248,8 @@ __global__ void __launch_bounds__(T5_THREADS, 2) ws_conv5_kernel(const __grid_co
     const int n0 = blockIdx.y * N;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int kch = Cin / KC, KT = 9 * kch, NS = (KT + CPS - 1) / CPS;
-    const uint32_t tmem = t5_start<ST>(bars, &tmem_slot, COLS, flags);
+    const uint32_t tmem = t5_start<ST, CS>(bars, &tmem_slot, COLS, flags);
+    const int rank = CS > 1 ? (int)t5_cluster_rank() : 0;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -221,12 +262,19 @@ __global__ void __launch_bounds__(T5_THREADS, 2) ws_conv5_kernel(const __grid_co
                 }
                 const int c0 = s * CPS, nc = min(CPS, KT - c0);
                 const uint32_t sA = base + buf * SBYTES, sB = sA + ABYTES, bar = smem_addr(&bars.full[buf]);
+                // the block's own A; B whole, of which this block fetches
+                // rows [rank N / CS, (rank + 1) N / CS) for every block of
+                // the cluster (the clusters' blocks share n0)
                 t5_expect(bar, (uint32_t)nc * (ACH + BCH));
                 for (int c = 0; c < nc; ++c) {
                     const int kk = c0 + c, tap = kk / kch, ci0 = (kk % kch) * KC;
                     const int dy = tap / 3 - 1, dx = tap % 3 - 1;
                     t5_load4(sA + c * ACH, &maps.A, ci0, p0 % R + dx * dil, p0 / R + dy * dil, b, bar);
-                    t5_load2(sB + c * BCH, &maps.B, ci0, tap * Cout + n0, bar);
+                    if (CS > 1)
+                        t5_load2_mc(sB + c * BCH + rank * (BCH / CS), &maps.B, ci0, tap * Cout + n0 + rank * (N / CS),
+                                    bar, MASK);
+                    else
+                        t5_load2(sB + c * BCH, &maps.B, ci0, tap * Cout + n0, bar);
                 }
             }
             flags[1] = s;
@@ -253,7 +301,12 @@ __global__ void __launch_bounds__(T5_THREADS, 2) ws_conv5_kernel(const __grid_co
                         t5_mma(tmem, ad, bd, IDESC, (s | c | k16) != 0 ? 1u : 0u);
                     }
                 }
-                t5_commit(smem_addr(&bars.empty[buf]));
+                // the buffer is free once every block of the cluster is done
+                // with it (its B arrived in all of them together)
+                if (CS > 1)
+                    t5_commit_mc(smem_addr(&bars.empty[buf]), MASK);
+                else
+                    t5_commit(smem_addr(&bars.empty[buf]));
             }
             if (!a.relu_in) flags[2] = s;
             // arrives once every MMA issued above has completed
@@ -341,7 +394,7 @@ __global__ void __launch_bounds__(T5_THREADS, 2) ws_conv5_kernel(const __grid_co
             }
         }
     }
-    t5_finish<ST>(bars, tmem, COLS, flags, err);
+    t5_finish<ST, CS>(bars, tmem, COLS, flags, err);
 }
 
 // ---------------------------------------------------------------------------
