@@ -157,6 +157,10 @@ typedef struct {
     double tau;              /* relaxation time: 1 = MacLABSWE, otherwise the
                                 distribution form (maclab_set_relaxation)      */
     int hbar_level;          /* 0: hbar at the old level, 1: at the new level */
+    int64_t two_step_blocks; /* row-march strip blocks that take both steps of a
+                                pair in one pass (0 until
+                                maclab_set_temporal_block(sim, 2) classifies
+                                them; only with the row-march step kernel) */
 } maclab_info;
 
 /* Create a simulation (procedure steps (a)-(b) of Section 3).
@@ -321,15 +325,22 @@ int maclab_set_relaxation(maclab_t sim, double tau);
  * call with level 1 lists the nodes (synchronises). */
 int maclab_set_hbar_level(maclab_t sim, int level);
 
-/* Temporal blocking (FP32): with k = 2, maclab_step advances "clean"
- * 64 x 16 tiles two steps per launch (a tile is clean when the tile and two
- * nodes of halo on every side lie inside the grid and hold only fluid and
- * no-slip nodes without bounce-back links).  The other tiles, bounce-back
- * links and Dirichlet nodes take two single steps through a scratch state.
- * The results are bitwise identical to k = 1.  The last step of every
+/* Temporal blocking (FP32): with k = 2, maclab_step advances the grid two
+ * steps at a time.  With the row-march step kernel (and Dirichlet nodes, if
+ * any, handled inside it), a strip block whose rows j0 - 2 .. j1 + 1 and 64
+ * columns lie inside the grid and hold only fluid nodes takes both steps in
+ * one pass; the other strip blocks take two single steps through a scratch
+ * state, the first also writing a one-node fringe around each block.  With
+ * the other step kernels, "clean" 64 x 16 tiles take both steps in one
+ * launch (a tile is clean when the tile and two nodes of halo on every side
+ * lie inside the grid and hold only fluid and no-slip nodes without
+ * bounce-back links), and the other tiles, bounce-back links and Dirichlet
+ * nodes take two single steps through the scratch state.  The results are
+ * bitwise identical to k = 1.  The last step of every
  * maclab_step call (and of every captured graph) is a single step, so the
  * residual always compares consecutive steps.  The first call with k = 2
- * classifies the tiles and allocates the scratch state (synchronises).
+ * classifies the tiles and strip blocks and allocates the scratch state
+ * (synchronises).
  * MACLAB_E_ARG for k outside 1..2 or k = 2 on an FP64 handle. */
 int maclab_set_temporal_block(maclab_t sim, int k);
 
@@ -348,8 +359,9 @@ int maclab_get_profile(maclab_t sim, double* step_kernel_ms, int64_t* launches);
  * warp-strip kernel with 8, 16, 32 or 64 rows per strip, 5 for the
  * TMA-staged tile kernel, 6 for the tile kernel with two steps per launch
  * on clean tiles (maclab_set_temporal_block(sim, 2)), 7 for the row-march
- * kernel; 5 and 6 are tried on FP32 MacLABSWE handles only, and the
- * temporal block depth is set to the winner's (1 unless 6 wins).  Each shape runs 2 + trial_steps steps; the
+ * kernel, 8 for the row-march kernel with two steps per pass on plain strip
+ * blocks; 5, 6 and 8 are tried on FP32 MacLABSWE handles only, and the
+ * temporal block depth is set to the winner's (1 unless 6 or 8 wins).  Each shape runs 2 + trial_steps steps; the
  * state, step count and time are restored afterwards (results are bitwise
  * identical for every shape).  Allocates and frees a copy of the state.
  * Synchronises. */

@@ -46,7 +46,7 @@ class Info(ctypes.Structure):
                 ("n_dirichlet", c_int64), ("n_fluid", c_int64), ("n_fast", c_int64),
                 ("device_bytes", c_size_t), ("tile_rows", c_int), ("step_kernel", c_int),
                 ("dirichlet_fused", c_int), ("temporal_block", c_int), ("clean_tiles", c_int64),
-                ("tau", c_double), ("hbar_level", c_int)]
+                ("tau", c_double), ("hbar_level", c_int), ("two_step_blocks", c_int64)]
 
 
 class WSConfig(ctypes.Structure):

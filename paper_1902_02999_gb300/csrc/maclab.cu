@@ -95,6 +95,13 @@ struct maclab_s {
     int* clean_list = nullptr; // tiles that take two steps per launch
     int* other_list = nullptr; // the rest
     void* mid[3] = {nullptr, nullptr, nullptr};  // scratch state (eta, u, v) at the middle step
+    // temporal blocking with the row march: strip blocks taking both steps
+    // in one pass (step_march2_kernel), and the others (two single steps
+    // through mid, the first with a one-node fringe)
+    bool march2_ready = false;
+    int n_m2 = 0, n_m2_other = 0;
+    int* m2_sel = nullptr;
+    int* m2_other = nullptr;
     int graph_end[2] = {0, 1}; // buffer parity after a replay of graph[parity]
     double tau = 1.0;          // relaxation time; != 1: distribution form
     bool newlevel = false;     // hbar at the new time level (per-link kernel for every node)
@@ -380,9 +387,50 @@ void other_tiles_step(maclab_t s, void* ie, void* iu, void* iv, void* oe, void* 
             (float*)oe, (float*)ou, (float*)ov, (const float*)s->D, s->D64, s->dir, s->n_dir, bv);
 }
 
+// Two steps with the row march: eligible strip blocks in one pass each
+// (step_march2_kernel, state a to state b), the others in two single steps
+// through s->mid, the first writing each strip block with its one-node
+// fringe so that the second finds every neighbour at the middle state.
+void launch_pair_march(maclab_t s, int a, int b)
+{
+    const size_t smem1 = march::smem_bytes<float>(), smem2 = march::smem2_bytes();
+    if (s->n_m2 > 0) {
+        const Fields<float> f = fields_io<float>(s, s->eta[a], s->u[a], s->v[a], s->eta[b], s->u[b], s->v[b]);
+        const int blocks = (s->n_m2 + march::WARPS - 1) / march::WARPS;
+        switch (s->fmode) {
+#define MACLAB_FM(m)                                                                                              \
+    case m:                                                                                                       \
+        step_march2_kernel<m><<<blocks, march::THREADS, smem2, s->stream>>>(f, s->mgeom.items, s->m2_sel, s->n_m2); \
+        break;
+            MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
+#undef MACLAB_FM
+        }
+    }
+    if (s->n_m2_other > 0) {
+        const int blocks = (s->n_m2_other + march::WARPS - 1) / march::WARPS;
+        march::Geom g1 = s->mgeom, g2 = s->mgeom;
+        g1.bv = dir_values(s, s->n + 1);
+        g2.bv = dir_values(s, s->n + 2);
+        const Fields<float> f1 = fields_io<float>(s, s->eta[a], s->u[a], s->v[a], s->mid[0], s->mid[1], s->mid[2]);
+        const Fields<float> f2 = fields_io<float>(s, s->mid[0], s->mid[1], s->mid[2], s->eta[b], s->u[b], s->v[b]);
+        switch (s->fmode) {
+#define MACLAB_FM(m)                                                                                      \
+    case m:                                                                                               \
+        step_march_list_kernel<m, true><<<blocks, march::THREADS, smem1, s->stream>>>(f1, g1, s->m2_other,  \
+                                                                                   s->n_m2_other);      \
+        step_march_list_kernel<m, false><<<blocks, march::THREADS, smem1, s->stream>>>(f2, g2, s->m2_other, \
+                                                                                    s->n_m2_other);     \
+        break;
+            MACLAB_FM(0) MACLAB_FM(1) MACLAB_FM(2) MACLAB_FM(3) MACLAB_FM(4) MACLAB_FM(5) MACLAB_FM(6) MACLAB_FM(7)
+#undef MACLAB_FM
+        }
+    }
+}
+
 // Two steps: clean tiles in one launch (step_tile2_kernel), the other tiles
 // in two single steps through the scratch state s->mid (which also receives
-// the clean tiles' outer rings at the middle step).
+// the clean tiles' outer rings at the middle step).  With the row march and
+// its strip blocks classified, launch_pair_march instead.
 int launch_pair(maclab_t s)
 {
     const int a = s->cur, b = 1 - s->cur;
@@ -399,7 +447,9 @@ int launch_pair(maclab_t s)
         s->prof_steps += 2;
         cudaEventRecord(ev0, s->stream);
     }
-    if (s->n_clean > 0) {
+    if (s->kernel == MACLAB_KERNEL_MARCH && s->march2_ready) {
+        launch_pair_march(s, a, b);
+    } else if (s->n_clean > 0) {
         const Fields<float> f = fields_io<float>(s, s->eta[a], s->u[a], s->v[a], s->mid[0], s->mid[1], s->mid[2]);
         const int tx = (s->grid.nx + tile::TX - 1) / tile::TX;
         const size_t smem = sizeof(tile2::Smem);
@@ -413,8 +463,10 @@ int launch_pair(maclab_t s)
 #undef MACLAB_FM
         }
     }
-    other_tiles_step(s, s->eta[a], s->u[a], s->v[a], s->mid[0], s->mid[1], s->mid[2], s->n + 1);
-    other_tiles_step(s, s->mid[0], s->mid[1], s->mid[2], s->eta[b], s->u[b], s->v[b], s->n + 2);
+    if (!(s->kernel == MACLAB_KERNEL_MARCH && s->march2_ready)) {
+        other_tiles_step(s, s->eta[a], s->u[a], s->v[a], s->mid[0], s->mid[1], s->mid[2], s->n + 1);
+        other_tiles_step(s, s->mid[0], s->mid[1], s->mid[2], s->eta[b], s->u[b], s->v[b], s->n + 2);
+    }
     if (s->profiling) cudaEventRecord(ev1, s->stream);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(s, e, "two-step launch");
@@ -1184,7 +1236,7 @@ int kernel_of_choice(int k)
 {
     if (k == 0 || k == 6) return MACLAB_KERNEL_TILE;
     if (k == 5) return MACLAB_KERNEL_TMA;
-    if (k == 7) return MACLAB_KERNEL_MARCH;
+    if (k == 7 || k == 8) return MACLAB_KERNEL_MARCH;
     return MACLAB_KERNEL_STRIP;
 }
 }  // namespace
@@ -1212,10 +1264,12 @@ int maclab_autotune(maclab_t s, int trial_steps, int* choice)
     const int prof0 = s->profiling;
     // candidates: 0 = tile kernel; k = 1..4 strip kernel with 4 << k rows;
     // 5 = TMA-staged tile kernel; 6 = tile kernel with two steps per launch
-    // on clean tiles (FP32 MacLABSWE steps only); 7 = row-march kernel
+    // on clean tiles (FP32 MacLABSWE steps only); 7 = row-march kernel;
+    // 8 = row-march kernel with two steps per pass on plain strip blocks
+    // (FP32 MacLABSWE steps only)
     const int rows[5] = {0, 8, 16, 32, 64};
     const bool try_pairs = s->prec == MACLAB_F32 && !s->elab && !s->newlevel;
-    const int ncand = 8;
+    const int ncand = 9;
     double best = 1e300;
     int best_k = 0;
     cudaEvent_t e0, e1;
@@ -1226,8 +1280,15 @@ int maclab_autotune(maclab_t s, int trial_steps, int* choice)
     s->tblock = 1;
     for (int k = 0; k < ncand && rc == MACLAB_OK; ++k) {
         if (k == 5 && !s->tma_ok) continue;
-        if (k == 6 && !try_pairs) continue;
+        if ((k == 6 || k == 8) && !try_pairs) continue;
         if (k == 7) s->tblock = 1;
+        if (k == 8) {
+            if ((rc = maclab_set_temporal_block(s, 2)) != MACLAB_OK) break;
+            if (!s->march2_ready || s->n_m2 == 0) {
+                s->tblock = 1;
+                continue;
+            }
+        }
         if (k == 6) {
             if ((rc = maclab_set_temporal_block(s, 2)) != MACLAB_OK) break;
             if (s->n_clean == 0) {
@@ -1257,7 +1318,7 @@ int maclab_autotune(maclab_t s, int trial_steps, int* choice)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     s->kernel = kernel_of_choice(best_k);
-    s->tblock = best_k == 6 ? 2 : 1;
+    s->tblock = best_k == 6 || best_k == 8 ? 2 : 1;
     if (best_k >= 1 && best_k <= 4) {
         s->ty = std::min(rows[best_k], s->grid.ny);
     } else {
@@ -1676,6 +1737,63 @@ int maclab_set_temporal_block(maclab_t s, int k)
         s->n_other = (int)other.size();
         s->tiles_classified = true;
     }
+    if (k == 2 && !s->march2_ready && s->mgeom.items && (s->n_dir == 0 || s->march_dir_fused)) {
+        // row-march strip blocks: both steps in one pass when rows j0 - 2 ..
+        // j1 + 1 and the strip's 64 columns lie inside the grid and hold only
+        // fluid nodes (no edge rule, wall, link or Dirichlet node reaches
+        // two consecutive steps of the block)
+        const int nx = s->grid.nx, ny = s->grid.ny, pitch = s->pitch, nit = s->mgeom.nitems;
+        std::vector<uint8_t> type((size_t)pitch * ny);
+        std::vector<int> it((size_t)4 * nit);
+        cudaError_t e = cudaMemcpyAsync(type.data(), s->type, type.size(), cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(it.data(), s->mgeom.items, it.size() * sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "temporal block setup");
+        const bool idx32 = (int64_t)pitch * ny < ((int64_t)1 << 31);
+        std::vector<int> two, rest;
+        for (int t = 0; t < nit; ++t) {
+            const int x0 = march::first_col(it[4 * t]), j0 = it[4 * t + 1], j1 = it[4 * t + 2];
+            bool ok = idx32 && x0 >= 0 && x0 + 64 <= nx && j0 - 2 >= 0 && j1 + 2 <= ny;
+            for (int y = j0 - 2; ok && y <= j1 + 1; ++y)
+                for (int x = x0; ok && x < x0 + 64; ++x) ok = type[(size_t)y * pitch + x] == MACLAB_FLUID;
+            (ok ? two : rest).push_back(t);
+        }
+        const size_t NP = (size_t)pitch * ny;
+        for (int q = 0; q < 3; ++q)
+            if (!s->mid[q]) {
+                if (!(s->mid[q] = dev_alloc(s, NP * sizeof(float)))) return fail(s, MACLAB_E_NOMEM, "temporal block scratch");
+                if ((e = cudaMemsetAsync(s->mid[q], 0, NP * sizeof(float), s->stream)) != cudaSuccess)
+                    return cuda_fail(s, e, "temporal block setup");
+            }
+        if ((!two.empty() && !(s->m2_sel = (int*)dev_alloc(s, two.size() * sizeof(int)))) ||
+            (!rest.empty() && !(s->m2_other = (int*)dev_alloc(s, rest.size() * sizeof(int)))))
+            return fail(s, MACLAB_E_NOMEM, "temporal block lists");
+        if (!two.empty())
+            e = cudaMemcpyAsync(s->m2_sel, two.data(), two.size() * sizeof(int), cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess && !rest.empty())
+            e = cudaMemcpyAsync(s->m2_other, rest.data(), rest.size() * sizeof(int), cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_fail(s, e, "temporal block setup");
+        cudaError_t ae = cudaSuccess;
+#define MACLAB_ATTR(m)                                                                                         \
+    if (ae == cudaSuccess)                                                                                     \
+        ae = cudaFuncSetAttribute(step_march2_kernel<m>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                                  (int)march::smem2_bytes());                                                  \
+    if (ae == cudaSuccess)                                                                                     \
+        ae = cudaFuncSetAttribute(step_march_list_kernel<m, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  (int)march::smem_bytes<float>());                                            \
+    if (ae == cudaSuccess)                                                                                     \
+        ae = cudaFuncSetAttribute(step_march_list_kernel<m, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  (int)march::smem_bytes<float>());
+        MACLAB_ATTR(0) MACLAB_ATTR(1) MACLAB_ATTR(2) MACLAB_ATTR(3) MACLAB_ATTR(4) MACLAB_ATTR(5) MACLAB_ATTR(6)
+        MACLAB_ATTR(7)
+#undef MACLAB_ATTR
+        if (ae != cudaSuccess) return cuda_fail(s, ae, "cudaFuncSetAttribute");
+        s->n_m2 = (int)two.size();
+        s->n_m2_other = (int)rest.size();
+        s->march2_ready = true;
+    }
     s->tblock = k;
     drop_graphs(s);
     return MACLAB_OK;
@@ -1781,6 +1899,7 @@ int maclab_get_info(maclab_t s, maclab_info* info)
     info->step_kernel = s->kernel;
     info->dirichlet_fused = dirichlet_in_kernel(s) ? 1 : 0;
     info->temporal_block = s->tblock;
+    info->two_step_blocks = s->march2_ready ? s->n_m2 : 0;
     info->clean_tiles = s->n_clean;
     info->tau = s->tau;
     info->hbar_level = s->newlevel ? 1 : 0;

@@ -206,14 +206,13 @@ __device__ __forceinline__ void cp_async_z(uint32_t dst, const void* src, bool v
 // EDGE = true: any strip block; a row outside the grid is resolved
 // through the S / N edge kinds (the same for the whole warp), the lane's
 // columns through its fixed sources; sources behind a wall read zero.
-template <typename T, bool EDGE>
-__device__ __forceinline__ void fetch_row(const Fields<T>& f, int y, int x, const LaneCols2& lc, WarpSmem<T>& sm,
-                                          int slot, int lane)
+template <typename T, bool EDGE, typename SM = WarpSmem<T>>
+__device__ __forceinline__ void fetch_row(const Fields<T>& f, int y, int x, const LaneCols2& lc, SM& sm, int slot,
+                                          int lane)
 {
     const T* fld[4] = {f.eta, f.u, f.v, f.D};
     const uint32_t dst = smem_addr(&sm.raw[slot][0][lane]);
     constexpr uint32_t FS = 32 * sizeof(typename Vec2<T>::type);  // bytes between fields of a slot
-    const uint32_t tdst = smem_addr(&sm.rtype[slot][lane][0]);
     int rr = y;
     if (EDGE && (y < 0 || y >= f.ny)) {
         uint8_t fy = 0;
@@ -225,7 +224,7 @@ __device__ __forceinline__ void fetch_row(const Fields<T>& f, int y, int x, cons
         for (int q = 0; q < 4; ++q) cp_async_z<2 * sizeof(T)>(dst + q * FS, fld[q] + off, true);
         // the type bytes of x, x + 1 lie in the aligned word at off & ~3
         // (plain interior blocks do not need them)
-        if (EDGE) cp_async_z<4>(tdst, f.type + (off & ~(size_t)3), true);
+        if constexpr (EDGE) cp_async_z<4>(smem_addr(&sm.rtype[slot][lane][0]), f.type + (off & ~(size_t)3), true);
     } else {
         const bool ok0 = rr >= 0 && lc.c0 >= 0, ok1 = rr >= 0 && lc.c1 >= 0;
         const size_t row = rr >= 0 ? (size_t)rr * f.pitch : 0;
@@ -235,25 +234,28 @@ __device__ __forceinline__ void fetch_row(const Fields<T>& f, int y, int x, cons
             cp_async_z<sizeof(T)>(dst + q * FS, fld[q] + i0, ok0);
             cp_async_z<sizeof(T)>(dst + q * FS + sizeof(T), fld[q] + i1, ok1);
         }
-        cp_async_z<4>(tdst, f.type + (i0 & ~(size_t)3), ok0);
-        cp_async_z<4>(tdst + 4, f.type + (i1 & ~(size_t)3), ok1);
+        if constexpr (EDGE) {
+            const uint32_t tdst = smem_addr(&sm.rtype[slot][lane][0]);
+            cp_async_z<4>(tdst, f.type + (i0 & ~(size_t)3), ok0);
+            cp_async_z<4>(tdst + 4, f.type + (i1 & ~(size_t)3), ok1);
+        }
     }
     asm volatile("cp.async.commit_group;\n" ::);
 }
 
 // Read back the lane's staged pair of row y (its copies complete).
-template <typename T, bool EDGE>
-__device__ __forceinline__ void read_row(const Fields<T>& f, int y, int x, const LaneCols2& lc,
-                                         const WarpSmem<T>& sm, int slot, int lane, Pair<T>& p)
+template <typename T, bool EDGE, typename SM = WarpSmem<T>>
+__device__ __forceinline__ void read_row(const Fields<T>& f, int y, int x, const LaneCols2& lc, const SM& sm, int slot,
+                                         int lane, Pair<T>& p)
 {
     p.e = sm.raw[slot][0][lane];
     p.u = sm.raw[slot][1][lane];
     p.v = sm.raw[slot][2][lane];
     p.d = sm.raw[slot][3][lane];
-    if (!EDGE) {
+    if constexpr (!EDGE) {
         p.types = 0;  // plain interior block: fluid or Dirichlet nodes only, no mirrors
         return;
-    }
+    } else {
     uint8_t fy = 0;
     int rr = y;
     if (y < 0 || y >= f.ny) rr = resolve_index(y, f.ny, f.edge[2], f.edge[3], 2, fy);
@@ -269,6 +271,7 @@ __device__ __forceinline__ void read_row(const Fields<T>& f, int y, int x, const
         t |= (((sm.rtype[slot][lane][1] >> (8 * (lc.c1 & 3))) & 0xffu) << 8) | (lc.flips & (3u << 18)) |
              ((uint32_t)fy << 18);
     p.types = t;
+    }
 }
 
 template <typename T>
@@ -341,12 +344,17 @@ __device__ __forceinline__ void gather_pair(const Coef2& K, float2 A1, float2 M2
 // r - 1) and sp (row r, partly still in registers).  Raw and derived rows
 // share the period 3: row r's raw slot is sp, and row r + 2 is copied into
 // raw slot sc (freed by row r - 1).
-template <typename T, int FM, bool EDGE>
+// FR (a fringe pass, EDGE only): output rows fr0 and fr1 and the lane's
+// columns in fcol are a one-node fringe around the strip block; a fringe
+// node is written only if it is a fluid or no-slip node (its own strip
+// block writes a Dirichlet node).
+template <typename T, int FM, bool EDGE, bool FR = false>
 __device__ __forceinline__ void march_row(const Fields<T>& f, int r, int x, const LaneCols2& lc, int last,
                                           unsigned colmask, int lane, WarpSmem<T>& sm, const Coef2& c2, int sp,
                                           int sc, int sm_,
                                           Own<T>& own, bool done, typename Vec2<T>::type (&o3r)[3],
-                                          typename Vec2<T>::type (&edr)[3][2])
+                                          typename Vec2<T>::type (&edr)[3][2], int fr0 = 0, int fr1 = 0,
+                                          unsigned fcol = 0)
 {
     using V2 = typename Vec2<T>::type;
     Pair<T> p;
@@ -387,7 +395,13 @@ __device__ __forceinline__ void march_row(const Fields<T>& f, int r, int x, cons
         // written: node kinds 1 .. 7 without the bounce-back bit (type byte in
         // 1 .. 7); a plain interior block has only such nodes and no no-slip ones
         const uint32_t k0 = own.types & 0xffu, k1 = (own.types >> 8) & 0xffu;
-        const unsigned ok = EDGE ? colmask & ((k0 - 1u < 7u ? 1u : 0u) | (k1 - 1u < 7u ? 2u : 0u)) : colmask;
+        unsigned ok = EDGE ? colmask & ((k0 - 1u < 7u ? 1u : 0u) | (k1 - 1u < 7u ? 2u : 0u)) : colmask;
+        if (FR) {
+            const unsigned fr = (r - 1 == fr0 || r - 1 == fr1) ? 3u : fcol;
+            const unsigned dir = (k0 - (unsigned)K_DIR_H < 3u ? 1u : 0u) | (k1 - (unsigned)K_DIR_H < 3u ? 2u : 0u);
+            ok &= ~(fr & dir);
+            if (r - 1 < 0 || r - 1 >= f.ny) ok = 0;  // a fringe row beyond the grid edge
+        }
         const bool ns0 = EDGE && (k0 & KIND_MASK) == K_NOSLIP, ns1 = EDGE && (k1 & KIND_MASK) == K_NOSLIP;
         V2 oe, ou, ov;
         if constexpr (std::is_same<T, float>::value) {
@@ -438,15 +452,21 @@ __device__ __forceinline__ void march_row(const Fields<T>& f, int r, int x, cons
     }
 }
 
-// Rows j0 .. j1 - 1 of strip s (derived rows j0 - 1 .. j1).
-template <typename T, int FM, bool EDGE>
+// Rows j0 .. j1 - 1 of strip s (derived rows j0 - 1 .. j1).  FR: a
+// fringe pass, which also writes local columns 1 and 62 and whose rows
+// j0 and j1 - 1 are the fringe (see march_row).
+template <typename T, int FM, bool EDGE, bool FR = false>
 __device__ __forceinline__ void march_strip(const Fields<T>& f, const Coef2& c2, int s, int j0, int j1, int lane,
                                             WarpSmem<T>& sm)
 {
     const int x = first_col(s) + 2 * lane;
     // the lane's columns that the strip writes and that lie in the grid
-    unsigned colmask = (2 * lane >= 1 + HALF && 2 * lane <= 62 - HALF ? 1u : 0u) |
-                       (2 * lane + 1 >= 1 + HALF && 2 * lane + 1 <= 62 - HALF ? 2u : 0u);
+    constexpr int LO = FR ? 1 : 1 + HALF, HI = FR ? 62 : 62 - HALF;
+    unsigned colmask = (2 * lane >= LO && 2 * lane <= HI ? 1u : 0u) | (2 * lane + 1 >= LO && 2 * lane + 1 <= HI ? 2u : 0u);
+    // fringe columns: local 1 (lane 0, second column) and 62 (lane 31,
+    // first column), derived but not written by a 60-column strip
+    static_assert(!FR || HALF == 1, "a fringe pass needs 60-column strips");
+    const unsigned fcol = FR ? ((lane == 0 ? 2u : 0u) | (lane == 31 ? 1u : 0u)) : 0u;
     LaneCols2 lc{x, x + 1, 0u, true};
     if (EDGE) {
         lc = lane_cols(f, x);
@@ -463,14 +483,165 @@ __device__ __forceinline__ void march_strip(const Fields<T>& f, const Coef2& c2,
     Own<T> own;
     typename Vec2<T>::type o3r[3], edr[3][2];  // carried in registers (CARRY)
     // rows rotate through slots: row r in raw and derived slot (r - j0 + 1) % 3
-    march_row<T, FM, EDGE>(f, j0 - 1, x, lc, last, colmask, lane, sm, c2, 0, 2, 1, own, false, o3r, edr);
-    march_row<T, FM, EDGE>(f, j0, x, lc, last, colmask, lane, sm, c2, 1, 0, 2, own, false, o3r, edr);
+    march_row<T, FM, EDGE, FR>(f, j0 - 1, x, lc, last, colmask, lane, sm, c2, 0, 2, 1, own, false, o3r, edr, j0, j1 - 1, fcol);
+    march_row<T, FM, EDGE, FR>(f, j0, x, lc, last, colmask, lane, sm, c2, 1, 0, 2, own, false, o3r, edr, j0, j1 - 1, fcol);
     for (int r = j0 + 1;; r += 3) {
-        march_row<T, FM, EDGE>(f, r, x, lc, last, colmask, lane, sm, c2, 2, 1, 0, own, true, o3r, edr);
+        march_row<T, FM, EDGE, FR>(f, r, x, lc, last, colmask, lane, sm, c2, 2, 1, 0, own, true, o3r, edr, j0, j1 - 1, fcol);
         if (r >= last) break;
-        march_row<T, FM, EDGE>(f, r + 1, x, lc, last, colmask, lane, sm, c2, 0, 2, 1, own, true, o3r, edr);
+        march_row<T, FM, EDGE, FR>(f, r + 1, x, lc, last, colmask, lane, sm, c2, 0, 2, 1, own, true, o3r, edr, j0, j1 - 1, fcol);
         if (r + 1 >= last) break;
-        march_row<T, FM, EDGE>(f, r + 2, x, lc, last, colmask, lane, sm, c2, 1, 0, 2, own, true, o3r, edr);
+        march_row<T, FM, EDGE, FR>(f, r + 2, x, lc, last, colmask, lane, sm, c2, 1, 0, 2, own, true, o3r, edr, j0, j1 - 1, fcol);
+        if (r + 2 >= last) break;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+
+// ---------------------------------------------------------------------------
+// Two steps per pass (temporal blocking, FP32, plain strip blocks whose
+// rows j0 - 2 .. j1 + 1 and 64 columns lie inside the grid and hold only
+// fluid nodes).  Level 1 is the row march above: derive row r (state n),
+// update row r - 1 to state n + 1, but in registers only.  Level 2 derives
+// that row again from those registers into a second ring and, one row
+// behind, updates row r - 2 to state n + 2 and stores it.  Level 1 is valid
+// on local columns 1 .. 62 (it needs a derived column either side), level 2
+// on 2 .. 61, the 60 columns a strip writes.  Every node takes the
+// operations of two single steps in their order, so the result is bitwise
+// that of two single steps.
+struct Ring {
+    float o[3][4][2][34];  // o1, o2, o4, o5 by column parity
+    float2 ed[3][2][34];   // (eta, D) by column parity
+};
+struct WarpSmem2 {
+    float2 raw[RAW_SLOTS][4][32];  // raw staging (plain blocks: no type words)
+    Ring a;                        // level 1 (o3 and the lane's own (eta, D) in registers)
+    Ring b;                        // level 2
+};
+__host__ __device__ constexpr size_t smem2_bytes() { return WARPS * sizeof(WarpSmem2); }
+
+template <int FM>
+__device__ __forceinline__ void march2_row(const Fields<float>& f, int r, int x, int last, int lane, WarpSmem2& sm,
+                                           const Coef2& c2, int sp, int sc, int sm_, Own<float>& own1,
+                                           Own<float>& own2, bool lv1, bool lv2, float2 (&o3a)[3], float2 (&eda)[3][2],
+                                           float2 (&o3b)[3], float2 (&edb)[3][2])
+{
+    Ring& A = sm.a;
+    Ring& B = sm.b;
+    const LaneCols2 lc{x, x + 1, 0u, true};
+    Pair<float> p;
+    if (r + AHEAD <= last) fetch_row<float, false, WarpSmem2>(f, r + AHEAD, x, lc, sm, sc, lane);
+    else asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(AHEAD));
+    read_row<float, false, WarpSmem2>(f, r, x, lc, sm, sp, lane, p);
+    SrcP<float> d;
+    derive_pair<float, FM>(f.c, c2, p, d);
+    __syncwarp();  // every lane is done with level-1 slot sp (row r - 3) and level-2 slot sc (row r - 4)
+    {
+        const float2 ov4[4] = {d.o1, d.o2, d.o4, d.o5};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            A.o[sp][q][0][1 + lane] = ov4[q].x;
+            A.o[sp][q][1][1 + lane] = ov4[q].y;
+        }
+        A.ed[sp][0][1 + lane] = float2{d.eta.x, d.D.x};
+        A.ed[sp][1][1 + lane] = float2{d.eta.y, d.D.y};
+    }
+    const float Lo8 = shfl_up1(d.o8.y), Ro6 = shfl_dn1(d.o6.x);
+    __syncwarp();
+    if (lv1) {
+        // level 1: row r - 1 to state n + 1 (own row in slot sc, above sm_, below r)
+        const float2 m[4] = {A.ed[sm_][1][lane], eda[sm_][0], eda[sm_][1], A.ed[sm_][0][2 + lane]};
+        const float2 c[4] = {A.ed[sc][1][lane], eda[sc][0], eda[sc][1], A.ed[sc][0][2 + lane]};
+        const float2 pe[4] = {A.ed[sp][1][lane], float2{d.eta.x, d.D.x}, float2{d.eta.y, d.D.y}, A.ed[sp][0][2 + lane]};
+        const float2 M2 = float2{A.o[sm_][1][1][lane], A.o[sm_][1][0][1 + lane]};
+        const float2 M4 = float2{A.o[sm_][2][1][1 + lane], A.o[sm_][2][0][2 + lane]};
+        const float2 A1 = float2{A.o[sc][0][1][lane], A.o[sc][0][0][1 + lane]};
+        const float2 C5 = float2{A.o[sc][3][1][1 + lane], A.o[sc][3][0][2 + lane]};
+        float2 oe, ou, ov;
+        gather_pair(c2, A1, M2, C5, M4, o3a[sm_], float2{Lo8, d.o8.x}, float2{d.o6.y, Ro6}, d.o7, m, c, pe, own1.ownh,
+                    own1.hFx, own1.hFy, false, false, oe, ou, ov);
+        // level 2: derive row r - 1 of state n + 1 into slot sc
+        Pair<float> q;
+        q.e = oe;
+        q.u = ou;
+        q.v = ov;
+        q.d = float2{c[1].y, c[2].y};
+        q.types = 0;
+        SrcP<float> d2;
+        derive_pair<float, FM>(f.c, c2, q, d2);
+        {
+            const float2 ov4[4] = {d2.o1, d2.o2, d2.o4, d2.o5};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                B.o[sc][k][0][1 + lane] = ov4[k].x;
+                B.o[sc][k][1][1 + lane] = ov4[k].y;
+            }
+            B.ed[sc][0][1 + lane] = float2{d2.eta.x, d2.D.x};
+            B.ed[sc][1][1 + lane] = float2{d2.eta.y, d2.D.y};
+        }
+        const float Lo8b = shfl_up1(d2.o8.y), Ro6b = shfl_dn1(d2.o6.x);
+        __syncwarp();  // level-2 slot sc is visible to the warp
+        if (lv2) {
+            // level 2: row r - 2 to state n + 2 (own row in slot sm_, above sp, below r - 1)
+            const float2 mb[4] = {B.ed[sp][1][lane], edb[sp][0], edb[sp][1], B.ed[sp][0][2 + lane]};
+            const float2 cb[4] = {B.ed[sm_][1][lane], edb[sm_][0], edb[sm_][1], B.ed[sm_][0][2 + lane]};
+            const float2 pb[4] = {B.ed[sc][1][lane], float2{d2.eta.x, d2.D.x}, float2{d2.eta.y, d2.D.y},
+                                  B.ed[sc][0][2 + lane]};
+            const float2 M2b = float2{B.o[sp][1][1][lane], B.o[sp][1][0][1 + lane]};
+            const float2 M4b = float2{B.o[sp][2][1][1 + lane], B.o[sp][2][0][2 + lane]};
+            const float2 A1b = float2{B.o[sm_][0][1][lane], B.o[sm_][0][0][1 + lane]};
+            const float2 C5b = float2{B.o[sm_][3][1][1 + lane], B.o[sm_][3][0][2 + lane]};
+            float2 oe2, ou2, ov2;
+            gather_pair(c2, A1b, M2b, C5b, M4b, o3b[sp], float2{Lo8b, d2.o8.x}, float2{d2.o6.y, Ro6b}, d2.o7, mb, cb,
+                        pb, own2.ownh, own2.hFx, own2.hFy, false, false, oe2, ou2, ov2);
+            // lanes 0 and 31 only supply neighbours (60 written columns)
+            if (lane >= 1 && lane <= 30) {
+                const size_t idx = (size_t)(unsigned)((r - 2) * f.pitch + x);
+                *reinterpret_cast<float2*>(f.eta1 + idx) = oe2;
+                *reinterpret_cast<float2*>(f.u1 + idx) = ou2;
+                *reinterpret_cast<float2*>(f.v1 + idx) = ov2;
+            }
+        }
+        own2.ownh = d2.ownh;
+        own2.hFx = d2.hFx;
+        own2.hFy = d2.hFy;
+        o3b[sc] = d2.o3;
+        edb[sc][0] = float2{d2.eta.x, d2.D.x};
+        edb[sc][1] = float2{d2.eta.y, d2.D.y};
+    }
+    own1.ownh = d.ownh;
+    own1.hFx = d.hFx;
+    own1.hFy = d.hFy;
+    o3a[sp] = d.o3;
+    eda[sp][0] = float2{d.eta.x, d.D.x};
+    eda[sp][1] = float2{d.eta.y, d.D.y};
+}
+
+// Rows j0 .. j1 - 1 of strip s at state n + 2 (derived rows j0 - 2 .. j1 + 1
+// of state n, level-1 rows j0 - 1 .. j1).
+template <int FM>
+__device__ __forceinline__ void march_strip2(const Fields<float>& f, const Coef2& c2, int s, int j0, int j1, int lane,
+                                             WarpSmem2& sm)
+{
+    static_assert(HALF == 1, "two levels need 60-column strips");
+    const int x = first_col(s) + 2 * lane;
+    const LaneCols2 lc{x, x + 1, 0u, true};
+    const int last = j1 + 1;
+#pragma unroll
+    for (int q = 0; q < AHEAD; ++q) fetch_row<float, false, WarpSmem2>(f, j0 - 2 + q, x, lc, sm, q, lane);
+    Own<float> own1, own2;
+    float2 o3a[3], eda[3][2], o3b[3], edb[3][2];
+    // row r in slot (r - j0 + 2) % 3
+    march2_row<FM>(f, j0 - 2, x, last, lane, sm, c2, 0, 2, 1, own1, own2, false, false, o3a, eda, o3b, edb);
+    march2_row<FM>(f, j0 - 1, x, last, lane, sm, c2, 1, 0, 2, own1, own2, false, false, o3a, eda, o3b, edb);
+    march2_row<FM>(f, j0, x, last, lane, sm, c2, 2, 1, 0, own1, own2, true, false, o3a, eda, o3b, edb);
+    march2_row<FM>(f, j0 + 1, x, last, lane, sm, c2, 0, 2, 1, own1, own2, true, false, o3a, eda, o3b, edb);
+    for (int r = j0 + 2;; r += 3) {
+        march2_row<FM>(f, r, x, last, lane, sm, c2, 1, 0, 2, own1, own2, true, true, o3a, eda, o3b, edb);
+        if (r >= last) break;
+        march2_row<FM>(f, r + 1, x, last, lane, sm, c2, 2, 1, 0, own1, own2, true, true, o3a, eda, o3b, edb);
+        if (r + 1 >= last) break;
+        march2_row<FM>(f, r + 2, x, last, lane, sm, c2, 0, 2, 1, own1, own2, true, true, o3a, eda, o3b, edb);
         if (r + 2 >= last) break;
     }
     asm volatile("cp.async.wait_group 0;\n" ::);
@@ -505,6 +676,64 @@ step_march_kernel(const __grid_constant__ Fields<T> f, const __grid_constant__ m
             __syncwarp();  // the strip block's new values are visible to the warp
             for (int k = b + lane; k < e; k += 32)
                 dirichlet_node(f.eta1, f.u1, f.v1, f.D, g.D64, g.dlist[k], g.bv);
+        }
+    }
+}
+
+}  // namespace maclab
+
+namespace maclab {
+
+// Two steps of the strip blocks sel[0 .. n) (plain, see march_strip2) from
+// (eta, u, v) to (eta1, u1, v1).
+template <int FM>
+__global__ void __launch_bounds__(march::THREADS, 4)
+step_march2_kernel(const __grid_constant__ Fields<float> f, const int* __restrict__ items, const int* __restrict__ sel,
+                   int n)
+{
+    extern __shared__ __align__(16) unsigned char march_smem[];
+    const int lane = threadIdx.x & 31, wib = (int)(threadIdx.x >> 5);
+    march::WarpSmem2& sm = reinterpret_cast<march::WarpSmem2*>(march_smem)[wib];
+    const int k = (int)blockIdx.x * march::WARPS + wib;
+    if (k >= n) return;  // whole warp
+    const int4 t = reinterpret_cast<const int4*>(items)[sel[k]];
+    march::march_strip2<FM>(f, march::pairs_of(f.c), t.x, t.y, t.z, lane, sm);
+}
+
+// One step of the strip blocks sel[0 .. n), with their nodes with a
+// bounce-back link and (fused) Dirichlet nodes.  FR: the strip blocks also
+// write a one-node fringe (rows j0 - 1 and j1, local columns 1 and 62; its
+// Dirichlet nodes excepted), so that a second step of the same strip blocks
+// finds every neighbour it reads at the middle state.
+template <int FM, bool FR>
+__global__ void __launch_bounds__(march::THREADS, march::MinBlocks<float>::value)
+step_march_list_kernel(const __grid_constant__ Fields<float> f, const __grid_constant__ march::Geom g,
+                       const int* __restrict__ sel, int n)
+{
+    extern __shared__ __align__(16) unsigned char march_smem[];
+    const int lane = threadIdx.x & 31, wib = (int)(threadIdx.x >> 5);
+    march::WarpSmem<float>& sm = reinterpret_cast<march::WarpSmem<float>*>(march_smem)[wib];
+    const int k = (int)blockIdx.x * march::WARPS + wib;
+    if (k >= n) return;  // whole warp
+    const int item = sel[k];
+    const int4 t = reinterpret_cast<const int4*>(g.items)[item];
+    const int s = t.x, j0 = t.y, j1 = t.z;
+    if (FR) march::march_strip<float, FM, true, true>(f, march::pairs_of(f.c), s, j0 - 1, j1 + 1, lane, sm);
+    else if (t.w) march::march_strip<float, FM, false>(f, march::pairs_of(f.c), s, j0, j1, lane, sm);
+    else march::march_strip<float, FM, true>(f, march::pairs_of(f.c), s, j0, j1, lane, sm);
+    if (g.gstart) {
+        const int e = g.gstart[item + 1];
+        for (int q = g.gstart[item] + lane; q < e; q += 32) {
+            const int node = g.glist[q];
+            general_node<float>(f, node % f.nx, node / f.nx);
+        }
+    }
+    if (g.dstart) {
+        const int b = g.dstart[item], e = g.dstart[item + 1];
+        if (b < e) {
+            __syncwarp();  // the strip block's new values are visible to the warp
+            for (int q = b + lane; q < e; q += 32)
+                dirichlet_node(f.eta1, f.u1, f.v1, f.D, g.D64, g.dlist[q], g.bv);
         }
     }
 }
