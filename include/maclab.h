@@ -197,12 +197,16 @@ int maclab_set_graph_steps(maclab_t sim, int steps);
 
 /* Copy the current state to caller-owned host double arrays [ny*nx]
  * (any may be NULL).  h is reconstructed as (h_ref - z_b) + eta in double.
- * Synchronises the stream. */
+ * When all three arrays are page-locked host memory mapped into the
+ * device's address space (cudaHostAlloc, cudaHostRegister), the conversion
+ * kernel stores into them directly over the host link; otherwise it fills
+ * a device stage that is then copied.  Synchronises the stream. */
 int maclab_get_state(maclab_t sim, double* h, double* u, double* v);
 
 /* Replace the current state from host double arrays [ny*nx] (all three
- * required).  Does not change the time.  Asynchronous: the call returns
- * once the host arrays have been read. */
+ * required).  Does not change the time.  Page-locked, mapped arrays are
+ * read by the conversion kernel itself; others are copied to a device
+ * stage first.  The call returns once the host arrays have been read. */
 int maclab_set_state(maclab_t sim, const double* h, const double* u, const double* v);
 
 /* Residual and mass of the last step, reduced in double precision over

@@ -591,18 +591,41 @@ int elab_restart(maclab_t s)
     return MACLAB_OK;
 }
 
+// The device address of host memory the GPU can load and store directly
+// (page-locked and mapped into the unified address space: cudaHostAlloc,
+// cudaHostRegister), else null (pageable memory takes the staged copies).
+void* mapped_host(const void* p)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 template <typename T>
 int upload_state(maclab_t s, const double* h, const double* u, const double* v)
 {
     const size_t N = (size_t)s->grid.nx * s->grid.ny;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(s->stage, h, N * 8, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(s->stage + N, u, N * 8, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(s->stage + 2 * N, v, N * 8, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess)
-        return cuda_fail(s, e, "state upload");
+    // pinned, mapped host arrays: the conversion kernel loads them itself
+    // (over the host link, no staging copy); otherwise copy to the stage
+    const double* dh = (const double*)mapped_host(h);
+    const double* du = (const double*)mapped_host(u);
+    const double* dv = (const double*)mapped_host(v);
+    if (!dh || !du || !dv) {
+        if ((e = cudaMemcpyAsync(s->stage, h, N * 8, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(s->stage + N, u, N * 8, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(s->stage + 2 * N, v, N * 8, cudaMemcpyHostToDevice, s->stream)) != cudaSuccess)
+            return cuda_fail(s, e, "state upload");
+        dh = s->stage;
+        du = s->stage + N;
+        dv = s->stage + 2 * N;
+    }
     const int a = s->cur, b = 1 - s->cur;
     state_in_kernel<T><<<grid_blocks(N, 256, 4096), 256, 0, s->stream>>>(
-        s->stage, s->stage + N, s->stage + 2 * N, s->D64, s->type, (T*)s->eta[a], (T*)s->u[a],
+        dh, du, dv, s->D64, s->type, (T*)s->eta[a], (T*)s->u[a],
         (T*)s->v[a], (T*)s->eta[b], (T*)s->u[b], (T*)s->v[b], s->grid.nx, s->grid.ny, s->pitch);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(s, e, "state conversion");
     // the host arrays must stay valid until the copies have read them
@@ -617,13 +640,19 @@ int download_state(maclab_t s, double* h, double* u, double* v)
 {
     const size_t N = (size_t)s->grid.nx * s->grid.ny;
     const int a = s->cur;
+    // all three arrays pinned and mapped: the conversion kernel stores into
+    // them itself; otherwise into the stage, then copies
+    double* dh = h ? (double*)mapped_host(h) : nullptr;
+    double* du = u ? (double*)mapped_host(u) : nullptr;
+    double* dv = v ? (double*)mapped_host(v) : nullptr;
+    const bool direct = dh && du && dv;
     state_out_kernel<T><<<grid_blocks(N, 256, 4096), 256, 0, s->stream>>>(
-        (const T*)s->eta[a], (const T*)s->u[a], (const T*)s->v[a], s->D64, s->stage, s->stage + N,
-        s->stage + 2 * N, s->grid.nx, s->grid.ny, s->pitch);
+        (const T*)s->eta[a], (const T*)s->u[a], (const T*)s->v[a], s->D64, direct ? dh : s->stage,
+        direct ? du : s->stage + N, direct ? dv : s->stage + 2 * N, s->grid.nx, s->grid.ny, s->pitch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(s, e, "state conversion");
     double* dst[3] = {h, u, v};
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 3 && !direct; ++k)
         if (dst[k] && (e = cudaMemcpyAsync(dst[k], s->stage + k * N, N * 8, cudaMemcpyDeviceToHost,
                                            s->stream)) != cudaSuccess)
             return cuda_fail(s, e, "state download");
