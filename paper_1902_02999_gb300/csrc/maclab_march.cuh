@@ -60,7 +60,7 @@ constexpr int WAVES = MACLAB_MARCH_WAVES;  // uniform split: strip blocks per re
 #define MACLAB_MARCH_GUIDED_PHI 0.6
 #endif
 #ifndef MACLAB_MARCH_GUIDED_DIV
-#define MACLAB_MARCH_GUIDED_DIV 3
+#define MACLAB_MARCH_GUIDED_DIV 6
 #endif
 
 // Strip s derives the 64 columns from X0 = OUT s - 2 and writes local
