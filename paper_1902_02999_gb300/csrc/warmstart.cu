@@ -1070,7 +1070,10 @@ bool launch_conv5(maclab_ws_t w, const ConvArgs& a, int batch)
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        cudaLaunchKernelEx(&cfg, ws_conv5_kernel<64, 128, T5_ST, T5_CS>, maps, a, w->tc_err);
+        if (cudaLaunchKernelEx(&cfg, ws_conv5_kernel<64, 128, T5_ST, T5_CS>, maps, a, w->tc_err) != cudaSuccess) {
+            cudaGetLastError();
+            return false;  // the caller falls back to mma.sync
+        }
     } else if (KC == 16 && N == 128) {
         ws_conv5_kernel<16, 128, T5_ST, 1>
             <<<grid, T5_THREADS, t5_conv_smem<16, 128, T5_ST>(), w->stream>>>(maps, a, w->tc_err);
