@@ -67,3 +67,17 @@ def test_reference_arm_prints_on_rank_zero_only(rank):
         d = json.loads(lines[0])
         assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
         assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_step_kernel_traffic_record_matches_the_kernel_sources():
+    """The DRAM traffic the bench reports comes from an ncu record keyed by
+    the step kernels' source hash; a kernel edit without a new capture
+    would silently drop it (the bench then reports null), so the committed
+    record must belong to the committed sources."""
+    import json
+    import bench
+    with open(bench.PROFILE_JSON) as fh:
+        rec = json.load(fh)
+    assert rec["source_sha256"] == bench.kernel_source_hash()
+    assert bench.traffic_per_launch(rec["precision"], rec["workload"], rec["kernel"].split("<")[0]) == \
+        rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
